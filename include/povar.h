@@ -1,0 +1,191 @@
+/*
+ * povar.h -- C-ABI of libpovar, a GB300-native (sm_103a) implementation of
+ * the Power Variable Projection (PoVar) inner solve for initialization-free
+ * bundle adjustment (Weber, Hong, Cremers, ECCV 2024).
+ *
+ * The problem statement follows the paper's first stage: given only image
+ * measurements m_ij of landmark j in camera i (Sec. 3, observation set
+ * Omega), n_p projective 3x4 cameras and n_l landmarks (Eq. ba_first_stage),
+ * minimize the pOSE cost (Eq. pose) with weight eta by damped Variable
+ * Projection (Sec. 4.1) whose reduced camera system is inverted by the
+ * truncated power series of Sec. 4.2 (PoVar), optionally restricted to the
+ * tangent space of the unit-norm camera manifold (Sec. 4.3).
+ *
+ * Conventions shared by every call
+ *  - All arrays passed in or out are HOST arrays owned by the caller; the
+ *    library copies inputs and writes outputs into caller-allocated memory.
+ *    The problem handle owns all device memory until povar_destroy.
+ *  - Cameras are 3x4 matrices stored row-major, 12 doubles per camera
+ *    (rows p1, p2, p3). Landmarks are 3 doubles (X, Y, Z); the homogeneous
+ *    landmark is (X, Y, Z, 1).
+ *  - Measurements are normalized image coordinates (pixel - pp) / f,
+ *    2 doubles (u, v) per observation.
+ *  - Every call returns a povar_status; nothing aborts or throws across the
+ *    ABI. After an error, povar_last_error() describes it.
+ *  - A handle is used by one host thread at a time; handles are independent.
+ *  - Device work is issued on the CUDA stream given to povar_create (NULL =
+ *    the legacy default stream). Calls that return host data synchronize that
+ *    stream before returning.
+ */
+#ifndef POVAR_H
+#define POVAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct povar_problem povar_problem; /* opaque; owns device memory */
+
+typedef enum {
+  POVAR_OK = 0,
+  POVAR_EINVAL = 1,          /* invalid argument (sizes, indices, params) */
+  POVAR_ENOMEM = 2,          /* device or host allocation failed */
+  POVAR_ECUDA = 3,           /* a CUDA runtime call or kernel launch failed */
+  POVAR_ENUMERIC = 4,        /* non-finite cost or step on the device */
+  POVAR_ETIMEOUT = 5,        /* reserved: a bounded device wait gave up */
+  POVAR_ENOTCONVERGED = 6    /* damping diverged (step rejected repeatedly) */
+} povar_status;
+
+enum { POVAR_EUCLID = 0, POVAR_SPHERE = 1 };
+enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1 };
+
+/* Solver parameters (Sec. 5.2 of the paper gives eta = 0.1, lambda0 = 1e-4,
+ * series order 20 with threshold 0.01).
+ *  eta        pOSE weight in [0, 1] (Eq. pose).
+ *  lambda0    initial damping of the camera block (D_p = I); used by the
+ *             first step after povar_create / povar_set_cameras /
+ *             povar_init_random (later steps use the adapted damping).
+ *  series_eps series threshold: after term k >= 1 the series stops when
+ *             ||x_k||_2 <= series_eps * ||delta_k||_2; 0 runs exactly m terms.
+ *  lambda_l   reserved landmark damping; must be 0 (VarPro's V_0 is undamped,
+ *             Sec. 4.1).
+ *  m          number of series terms, >= 1 (delta = sum_{i<m} M^i U^-1 g; the
+ *             paper's "order 20" is m = 21).
+ *  manifold   POVAR_EUCLID (unconstrained cameras, Eq. ba_first_stage) or
+ *             POVAR_SPHERE (unit-norm cameras, tangent-space step and
+ *             retraction by normalization, Sec. 4.3).
+ *  precision  POVAR_FP64: every kernel in FP64.
+ *             POVAR_MIXED_FP32: series and linearization in FP32; landmark
+ *             elimination, 12x12 inverses, cost and gain ratio in FP64.
+ *  schedule   -1 = library default; 0 = point-gather / camera-scatter. */
+typedef struct {
+  double eta;
+  double lambda0;
+  double series_eps;
+  double lambda_l;
+  int32_t m;
+  int32_t manifold;
+  int32_t precision;
+  int32_t schedule;
+} povar_params;
+
+/* Report of one damped VarPro iteration. cost_before is F at the iterate the
+ * step started from, cost_after is F at the trial cameras (with landmarks
+ * re-solved in closed form), pred the predicted decrease
+ * 2 g^T d - d^T (S - lambda I) d, rho = (cost_before - cost_after) / pred.
+ * The step is accepted iff cost_after < cost_before. */
+typedef struct {
+  double cost_before;
+  double cost_after;
+  double pred;
+  double rho;
+  double lambda_used;
+  double lambda_next;
+  int32_t accepted;
+  int32_t terms_used;
+  int32_t iteration;
+  int32_t converged;
+  float ms;                  /* device time of the step (0 if not measured) */
+  float reserved[3];
+} povar_step_report;
+
+/* Create a problem from the observation set Omega (Sec. 3):
+ *  n_cams, n_points  number of cameras (n_p) and landmarks (n_l), >= 1.
+ *  n_obs             number of observations, >= 1.
+ *  cam_idx[n_obs]    camera index of each observation, 0 <= . < n_cams.
+ *  pt_idx[n_obs]     landmark index of each observation, 0 <= . < n_points.
+ *  meas[2*n_obs]     normalized measurement (u, v) of each observation.
+ *  cuda_stream       cudaStream_t to issue work on (NULL = default stream).
+ * Every landmark must be observed at least once (else POVAR_EINVAL); a
+ * camera without observations is allowed (its step is zero).
+ * Builds the camera-major and point-major observation orders on the device
+ * (stable integer sorts, bit-exact) and allocates all device state.
+ * Cameras start at zero: call povar_set_cameras or povar_init_random. */
+povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs,
+                          const int32_t* cam_idx, const int32_t* pt_idx,
+                          const double* meas, void* cuda_stream,
+                          povar_problem** out);
+
+/* Release all device and host memory of the handle (NULL is a no-op). */
+void povar_destroy(povar_problem* p);
+
+/* Text of the last error on this handle ("" if none). Owned by the handle. */
+const char* povar_last_error(const povar_problem* p);
+
+/* Set the cameras (n_cams x 12 row-major doubles) and re-solve every
+ * landmark in closed form (Eq. update_landmark) at pOSE weight eta. Resets
+ * the damping state: the next step starts from params->lambda0. */
+povar_status povar_set_cameras(povar_problem* p, const double* P, double eta);
+
+/* Random initialization of the paper's experiments (Sec. 5.2): every camera
+ * entry iid N(0, 1) from a counter-based Philox4x32-10 stream keyed by
+ * seed, normalized to unit Frobenius norm when manifold == POVAR_SPHERE;
+ * landmarks then follow in closed form. Resets the damping state. */
+povar_status povar_init_random(povar_problem* p, uint64_t seed, int32_t manifold,
+                               double eta);
+
+/* Copy the current cameras (n_cams x 12) / landmarks (n_points x 3) out. */
+povar_status povar_get_cameras(povar_problem* p, double* P_out);
+povar_status povar_get_points(povar_problem* p, double* X_out);
+
+/* pOSE cost F = ||r||^2 (Eq. ba_first_stage) at the current cameras with
+ * the landmarks at their closed-form optimum for this eta. */
+povar_status povar_cost(povar_problem* p, double eta, double* cost_out);
+
+/* One damped VarPro iteration (Sec. 4.1-4.3): linearize at (P, X*(P)),
+ * damped tangent-space camera blocks, PoVar series for the reduced camera
+ * system, predicted decrease, update + retraction, closed-form landmarks at
+ * the trial cameras, cost, gain ratio, accept/reject, damping update.
+ * report may be NULL. Synchronizes the stream. */
+povar_status povar_step(povar_problem* p, const povar_params* params,
+                        povar_step_report* report);
+
+/* Iterate povar_step until an accepted step has relative decrease below
+ * ftol, the cost reaches target_cost (if > 0), or max_iters steps ran.
+ * last (may be NULL) receives the report of the last step, iters_out (may
+ * be NULL) the number of steps taken. Steps are issued without a host
+ * round-trip in between; the stream is synchronized every few steps. */
+povar_status povar_solve(povar_problem* p, const povar_params* params,
+                         int32_t max_iters, double ftol, double target_cost,
+                         povar_step_report* last, int32_t* iters_out);
+
+/* ---- diagnostics (inspection of intermediate results for testing) ---- */
+
+/* Observation orders built by povar_create: perm_pt[n_obs] lists the
+ * observation ids sorted by (landmark, id), off_pt[n_points + 1] the segment
+ * starts; perm_cam / off_cam the same by (camera, id). Any pointer may be
+ * NULL. */
+povar_status povar_get_orders(povar_problem* p, uint32_t* perm_pt, uint32_t* off_pt,
+                              uint32_t* perm_cam, uint32_t* off_cam);
+
+/* Linearization of the last step (undamped U_i = J_p^T J_p as n_cams x 144
+ * row-major, and b_p = J_p^T r as n_cams x 12) and the step delta of the
+ * last step in the ambient camera space (n_cams x 12, tangent to the
+ * unit sphere in POVAR_SPHERE mode). Any pointer may be NULL. */
+povar_status povar_get_last_step(povar_problem* p, double* U_out, double* bp_out,
+                                 double* delta_out);
+
+/* Number of kernel launches this handle has issued so far. */
+int64_t povar_launch_count(const povar_problem* p);
+
+/* Library version string. */
+const char* povar_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POVAR_H */

@@ -1,0 +1,416 @@
+// C-ABI entry points of libpovar (declared in include/povar.h).
+//
+// The host side only validates arguments, owns the device allocations and
+// enqueues kernels; every step of the solve runs in the kernels of csr.cu,
+// landmark.cu, linearize.cu, series.cu and step.cu.
+#include "povar_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+struct povar_problem {
+  povar::Problem impl;
+};
+
+namespace povar {
+
+povar_status fail(Problem* p, povar_status s, const std::string& msg) {
+  if (p) p->err = msg;
+  return s;
+}
+
+povar_status check_launch(Problem* p, const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(p, POVAR_ECUDA, std::string("kernel launch (") + what + "): " +
+                                    cudaGetErrorString(e));
+  return POVAR_OK;
+}
+
+povar_status dev_alloc_bytes(Problem* p, void** ptr, size_t bytes, const char* what) {
+  void* q = nullptr;
+  const cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(p, POVAR_ENOMEM, std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
+  }
+  p->allocs.push_back(q);
+  *ptr = q;
+  return POVAR_OK;
+}
+
+namespace {
+
+povar_status sync_state(Problem* p) {
+  POVAR_CUDA(cudaMemcpyAsync(p->h_state, p->state, sizeof(DeviceState), cudaMemcpyDeviceToHost,
+                             p->stream));
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  return POVAR_OK;
+}
+
+povar_status check_params(Problem* p, const povar_params* q) {
+  if (!q) return fail(p, POVAR_EINVAL, "params is NULL");
+  if (!(q->eta >= 0.0 && q->eta <= 1.0)) return fail(p, POVAR_EINVAL, "eta must be in [0, 1]");
+  if (!(q->lambda0 > 0.0) || !std::isfinite(q->lambda0))
+    return fail(p, POVAR_EINVAL, "lambda0 must be positive");
+  if (q->m < 1 || q->m > 10000) return fail(p, POVAR_EINVAL, "m must be in [1, 10000]");
+  if (!(q->series_eps >= 0.0)) return fail(p, POVAR_EINVAL, "series_eps must be >= 0");
+  if (q->lambda_l != 0.0) return fail(p, POVAR_EINVAL, "lambda_l must be 0 (undamped V_0)");
+  if (q->manifold != POVAR_EUCLID && q->manifold != POVAR_SPHERE)
+    return fail(p, POVAR_EINVAL, "unknown manifold");
+  if (q->precision != POVAR_FP64 && q->precision != POVAR_MIXED_FP32)
+    return fail(p, POVAR_EINVAL, "unknown precision");
+  if (q->schedule < -1 || q->schedule > 0) return fail(p, POVAR_EINVAL, "unknown schedule");
+  return POVAR_OK;
+}
+
+// Landmarks + cost at the current cameras for eta (no damping reset).
+povar_status refresh_landmarks(Problem* p, double eta) {
+  povar_status s;
+  if ((s = launch_landmarks(p, 0, eta)) != POVAR_OK) return s;
+  if ((s = launch_cost_finish(p, 0)) != POVAR_OK) return s;
+  if ((s = launch_init_state(p, 0.0, 0, 0)) != POVAR_OK) return s;  // need_lin = 1
+  p->eta_cur = eta;
+  return POVAR_OK;
+}
+
+// Enqueue one damped VarPro iteration (no host synchronization).
+povar_status enqueue_step(Problem* p, const povar_params* q) {
+  povar_status s;
+  if (p->fresh) {
+    if ((s = launch_init_state(p, q->lambda0, 1, 0)) != POVAR_OK) return s;
+    p->fresh = false;
+  }
+  if (q->eta != p->eta_cur && (s = refresh_landmarks(p, q->eta)) != POVAR_OK) return s;
+  const int prec = q->precision;
+  if ((s = launch_linearize(p, prec, q->eta)) != POVAR_OK) return s;
+  if ((s = launch_camera_prepare(p, prec, q->manifold, q->eta)) != POVAR_OK) return s;
+  for (int k = 1; k < q->m; ++k)
+    if ((s = launch_series_term(p, prec, q->eta, k, q->series_eps)) != POVAR_OK) return s;
+  if ((s = launch_pred(p, prec, q->eta, q->manifold, q->m)) != POVAR_OK) return s;
+  if ((s = launch_update(p, prec, q->manifold)) != POVAR_OK) return s;
+  if ((s = launch_landmarks(p, 1, q->eta)) != POVAR_OK) return s;
+  if ((s = launch_cost_finish(p, 1)) != POVAR_OK) return s;
+  if ((s = launch_controller(p)) != POVAR_OK) return s;
+  p->last_precision = prec;
+  return POVAR_OK;
+}
+
+void fill_report(Problem* p, povar_step_report* r, float ms) {
+  *r = *p->h_report;
+  r->ms = ms;
+}
+
+}  // namespace
+}  // namespace povar
+
+using povar::Problem;
+
+extern "C" {
+
+const char* povar_version(void) { return "povar-gb300 0.1 (sm_103a)"; }
+
+const char* povar_last_error(const povar_problem* pp) {
+  return pp ? pp->impl.err.c_str() : "null handle";
+}
+
+int64_t povar_launch_count(const povar_problem* pp) { return pp ? pp->impl.launches : 0; }
+
+void povar_destroy(povar_problem* pp) {
+  if (!pp) return;
+  Problem* p = &pp->impl;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  for (void* q : p->allocs) cudaFree(q);
+  if (p->h_state) cudaFreeHost(p->h_state);
+  if (p->h_report) cudaFreeHost(p->h_report);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  delete pp;
+}
+
+povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const int32_t* cam_idx,
+                          const int32_t* pt_idx, const double* meas, void* cuda_stream,
+                          povar_problem** out) {
+  if (!out) return POVAR_EINVAL;
+  *out = nullptr;
+  if (n_cams < 1 || n_points < 1 || n_obs < 1 || n_obs >= (int64_t)1 << 31 || !cam_idx ||
+      !pt_idx || !meas)
+    return POVAR_EINVAL;
+  for (int64_t k = 0; k < n_obs; ++k) {
+    if (cam_idx[k] < 0 || cam_idx[k] >= n_cams || pt_idx[k] < 0 || pt_idx[k] >= n_points)
+      return POVAR_EINVAL;
+    if (!std::isfinite(meas[2 * k]) || !std::isfinite(meas[2 * k + 1])) return POVAR_EINVAL;
+  }
+  povar_problem* pp = new (std::nothrow) povar_problem();
+  if (!pp) return POVAR_ENOMEM;
+  Problem* p = &pp->impl;
+  p->nc = n_cams;
+  p->np = n_points;
+  p->nobs = n_obs;
+  p->stream = static_cast<cudaStream_t>(cuda_stream);
+  p->np_pad = (int32_t)(((int64_t)n_points + povar::BLOCK - 1) / povar::BLOCK * povar::BLOCK);
+  p->nslices = p->np_pad / povar::SLICE;
+  p->n_slot_blocks = p->np_pad / povar::BLOCK;
+  povar_status s = POVAR_OK;
+  const size_t nc = n_cams, npd = p->np_pad, no = n_obs;
+#define ALLOC(ptr, count)                                                    \
+  if ((s = povar::dev_alloc(p, &(ptr), (count), #ptr)) != POVAR_OK) {       \
+    povar_destroy(pp);                                                       \
+    return s;                                                                \
+  }
+  ALLOC(p->d_cam, no);
+  ALLOC(p->d_pt, no);
+  ALLOC(p->d_meas, 2 * no);
+  ALLOC(p->perm_pt, no);
+  ALLOC(p->perm_cam, no);
+  ALLOC(p->off_pt, (size_t)n_points + 1);
+  ALLOC(p->off_cam, nc + 1);
+  ALLOC(p->slot_pt, npd);
+  ALLOC(p->pt_slot, (size_t)n_points);
+  ALLOC(p->slot_len, npd);
+  ALLOC(p->sell_off, (size_t)p->nslices + 1);
+  ALLOC(p->cm_slot, no);
+  ALLOC(p->cm_m32, no);
+  ALLOC(p->cm_m64, no);
+  ALLOC(p->cam_nchunk, nc);
+  ALLOC(p->cam_chunk0, nc);
+  ALLOC(p->cam_ticket, nc);
+  ALLOC(p->done_ticket, 1);
+  ALLOC(p->P64[0], nc * 12);
+  ALLOC(p->P64[1], nc * 12);
+  ALLOC(p->Ltab, nc * 48);
+  ALLOC(p->camP32, nc * 12);
+  ALLOC(p->U64, nc * 144);
+  ALLOC(p->bp64, nc * 12);
+  ALLOC(p->G64, nc * 144);
+  ALLOC(p->G32, nc * 144);
+  ALLOC(p->Y32, nc * 12);
+  ALLOC(p->D32, nc * 12);
+  ALLOC(p->Y64, nc * 12);
+  ALLOC(p->D64, nc * 12);
+  ALLOC(p->camnorm, nc * 2);
+  for (int t = 0; t < 2; ++t) {
+    ALLOC(p->X64[t], npd * 3);
+    ALLOC(p->F64[t], npd * 6);
+    ALLOC(p->pdA[t], npd);
+    ALLOC(p->pdB[t], npd);
+    ALLOC(p->pdC[t], npd);
+  }
+  ALLOC(p->rec32, npd * 2);
+  ALLOC(p->rec64, npd * 4);
+  ALLOC(p->cost_part, (size_t)p->n_slot_blocks);
+  ALLOC(p->pred_part, (size_t)p->n_slot_blocks);
+  ALLOC(p->pinv_part, (size_t)p->n_slot_blocks);
+  ALLOC(p->state, 1);
+  ALLOC(p->d_report, 1);
+#define CK(call)                                                             \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      cudaGetLastError();                                                    \
+      povar_destroy(pp);                                                     \
+      return POVAR_ECUDA;                                                    \
+    }                                                                        \
+  } while (0)
+  CK(cudaMallocHost(&p->h_state, sizeof(povar::DeviceState)));
+  CK(cudaMallocHost(&p->h_report, sizeof(povar_step_report)));
+  CK(cudaEventCreate(&p->ev0));
+  CK(cudaEventCreate(&p->ev1));
+  CK(cudaMemcpyAsync(p->d_cam, cam_idx, no * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream));
+  CK(cudaMemcpyAsync(p->d_pt, pt_idx, no * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream));
+  CK(cudaMemcpyAsync(p->d_meas, meas, 2 * no * sizeof(double), cudaMemcpyHostToDevice,
+                     p->stream));
+  CK(cudaMemsetAsync(p->cam_ticket, 0, nc * sizeof(uint32_t), p->stream));
+  CK(cudaMemsetAsync(p->done_ticket, 0, sizeof(uint32_t), p->stream));
+  CK(cudaMemsetAsync(p->P64[0], 0, nc * 12 * sizeof(double), p->stream));
+  CK(cudaMemsetAsync(p->P64[1], 0, nc * 12 * sizeof(double), p->stream));
+  CK(cudaMemsetAsync(p->camnorm, 0, nc * 2 * sizeof(double), p->stream));
+  CK(cudaMemsetAsync(p->state, 0, sizeof(povar::DeviceState), p->stream));
+  CK(cudaMemsetAsync(p->d_report, 0, sizeof(povar_step_report), p->stream));
+  if ((s = povar::build_orders(p, cam_idx, pt_idx)) != POVAR_OK) {
+    povar_destroy(pp);
+    return s;
+  }
+  ALLOC(*reinterpret_cast<char**>(&p->part_lin), (size_t)std::max(p->nchunks, 1) * povar::LIN_ACC * sizeof(double));
+  ALLOC(*reinterpret_cast<char**>(&p->part_ser), (size_t)std::max(p->nchunks, 1) * 12 * sizeof(double));
+#undef ALLOC
+#undef CK
+  if ((s = povar::launch_init_state(p, 1e-4, 1, 1)) != POVAR_OK ||
+      (s = povar::sync_state(p)) != POVAR_OK) {
+    povar_destroy(pp);
+    return s;
+  }
+  *out = pp;
+  return POVAR_OK;
+}
+
+povar_status povar_set_cameras(povar_problem* pp, const double* P, double eta) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  if (!P) return povar::fail(p, POVAR_EINVAL, "P is NULL");
+  if (!(eta >= 0.0 && eta <= 1.0)) return povar::fail(p, POVAR_EINVAL, "eta must be in [0, 1]");
+  for (int64_t e = 0; e < (int64_t)p->nc * 12; ++e)
+    if (!std::isfinite(P[e])) return povar::fail(p, POVAR_EINVAL, "non-finite camera");
+  povar_status s;
+  if ((s = povar::launch_init_state(p, 1e-4, 1, 1)) != POVAR_OK) return s;
+  POVAR_CUDA(cudaMemcpyAsync(p->P64[0], P, (size_t)p->nc * 12 * sizeof(double),
+                             cudaMemcpyHostToDevice, p->stream));
+  if ((s = povar::refresh_landmarks(p, eta)) != POVAR_OK) return s;
+  p->fresh = true;
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  if (p->h_state->error) return povar::fail(p, (povar_status)p->h_state->error, "non-finite cost");
+  return POVAR_OK;
+}
+
+povar_status povar_init_random(povar_problem* pp, uint64_t seed, int32_t manifold, double eta) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  if (manifold != POVAR_EUCLID && manifold != POVAR_SPHERE)
+    return povar::fail(p, POVAR_EINVAL, "unknown manifold");
+  if (!(eta >= 0.0 && eta <= 1.0)) return povar::fail(p, POVAR_EINVAL, "eta must be in [0, 1]");
+  povar_status s;
+  if ((s = povar::launch_init_state(p, 1e-4, 1, 1)) != POVAR_OK) return s;
+  if ((s = povar::launch_random_cameras(p, seed, manifold == POVAR_SPHERE)) != POVAR_OK) return s;
+  if ((s = povar::refresh_landmarks(p, eta)) != POVAR_OK) return s;
+  p->fresh = true;
+  return povar::sync_state(p);
+}
+
+povar_status povar_get_cameras(povar_problem* pp, double* P_out) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  if (!P_out) return povar::fail(p, POVAR_EINVAL, "P_out is NULL");
+  povar_status s;
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  POVAR_CUDA(cudaMemcpyAsync(P_out, p->P64[p->h_state->cur], (size_t)p->nc * 12 * sizeof(double),
+                             cudaMemcpyDeviceToHost, p->stream));
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  return POVAR_OK;
+}
+
+povar_status povar_get_points(povar_problem* pp, double* X_out) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  if (!X_out) return povar::fail(p, POVAR_EINVAL, "X_out is NULL");
+  // the gather stages the landmarks in the series record buffer (free between steps)
+  double* d = reinterpret_cast<double*>(p->rec64);
+  povar_status s = povar::launch_gather_points(p, d);
+  if (s != POVAR_OK) return s;
+  POVAR_CUDA(cudaMemcpyAsync(X_out, d, (size_t)p->np * 3 * sizeof(double),
+                             cudaMemcpyDeviceToHost, p->stream));
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  return POVAR_OK;
+}
+
+povar_status povar_cost(povar_problem* pp, double eta, double* cost_out) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  if (!cost_out) return povar::fail(p, POVAR_EINVAL, "cost_out is NULL");
+  if (!(eta >= 0.0 && eta <= 1.0)) return povar::fail(p, POVAR_EINVAL, "eta must be in [0, 1]");
+  povar_status s;
+  if (eta != p->eta_cur && (s = povar::refresh_landmarks(p, eta)) != POVAR_OK) return s;
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  *cost_out = p->h_state->F;
+  return POVAR_OK;
+}
+
+povar_status povar_step(povar_problem* pp, const povar_params* params, povar_step_report* report) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  povar_status s;
+  if ((s = povar::check_params(p, params)) != POVAR_OK) return s;
+  if ((s = povar::launch_begin(p, 0.0, 0.0, 0)) != POVAR_OK) return s;
+  POVAR_CUDA(cudaEventRecord(p->ev0, p->stream));
+  if ((s = povar::enqueue_step(p, params)) != POVAR_OK) return s;
+  POVAR_CUDA(cudaEventRecord(p->ev1, p->stream));
+  POVAR_CUDA(cudaMemcpyAsync(p->h_report, p->d_report, sizeof(povar_step_report),
+                             cudaMemcpyDeviceToHost, p->stream));
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+  if (report) povar::fill_report(p, report, ms);
+  if (p->h_state->error)
+    return povar::fail(p, (povar_status)p->h_state->error, "device reported a numerical error");
+  return POVAR_OK;
+}
+
+povar_status povar_solve(povar_problem* pp, const povar_params* params, int32_t max_iters,
+                         double ftol, double target_cost, povar_step_report* last,
+                         int32_t* iters_out) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  povar_status s;
+  if ((s = povar::check_params(p, params)) != POVAR_OK) return s;
+  if (max_iters < 1) return povar::fail(p, POVAR_EINVAL, "max_iters must be >= 1");
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  const int it0 = p->h_state->iteration;
+  if ((s = povar::launch_begin(p, ftol, target_cost, max_iters)) != POVAR_OK) return s;
+  POVAR_CUDA(cudaEventRecord(p->ev0, p->stream));
+  const int check_every = 4;
+  for (int it = 0; it < max_iters; ++it) {
+    if ((s = povar::enqueue_step(p, params)) != POVAR_OK) return s;
+    if ((it + 1) % check_every == 0 && it + 1 < max_iters) {
+      if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+      if (p->h_state->converged) break;
+    }
+  }
+  POVAR_CUDA(cudaEventRecord(p->ev1, p->stream));
+  POVAR_CUDA(cudaMemcpyAsync(p->h_report, p->d_report, sizeof(povar_step_report),
+                             cudaMemcpyDeviceToHost, p->stream));
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+  if (last) povar::fill_report(p, last, ms);
+  if (iters_out) *iters_out = p->h_state->iteration - it0;
+  if (p->h_state->error)
+    return povar::fail(p, (povar_status)p->h_state->error, "device reported an error");
+  return POVAR_OK;
+}
+
+povar_status povar_get_orders(povar_problem* pp, uint32_t* perm_pt, uint32_t* off_pt,
+                              uint32_t* perm_cam, uint32_t* off_cam) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  const size_t no = p->nobs;
+  if (perm_pt)
+    POVAR_CUDA(cudaMemcpyAsync(perm_pt, p->perm_pt, no * 4, cudaMemcpyDeviceToHost, p->stream));
+  if (off_pt)
+    POVAR_CUDA(cudaMemcpyAsync(off_pt, p->off_pt, ((size_t)p->np + 1) * 4, cudaMemcpyDeviceToHost,
+                               p->stream));
+  if (perm_cam)
+    POVAR_CUDA(cudaMemcpyAsync(perm_cam, p->perm_cam, no * 4, cudaMemcpyDeviceToHost, p->stream));
+  if (off_cam)
+    POVAR_CUDA(cudaMemcpyAsync(off_cam, p->off_cam, ((size_t)p->nc + 1) * 4,
+                               cudaMemcpyDeviceToHost, p->stream));
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  return POVAR_OK;
+}
+
+povar_status povar_get_last_step(povar_problem* pp, double* U_out, double* bp_out,
+                                 double* delta_out) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  const size_t nc = p->nc;
+  if (U_out)
+    POVAR_CUDA(cudaMemcpyAsync(U_out, p->U64, nc * 144 * 8, cudaMemcpyDeviceToHost, p->stream));
+  if (bp_out)
+    POVAR_CUDA(cudaMemcpyAsync(bp_out, p->bp64, nc * 12 * 8, cudaMemcpyDeviceToHost, p->stream));
+  if (delta_out) {
+    if (p->last_precision == POVAR_FP64) {
+      POVAR_CUDA(cudaMemcpyAsync(delta_out, p->D64, nc * 12 * 8, cudaMemcpyDeviceToHost,
+                                 p->stream));
+    } else {
+      std::vector<float> tmp(nc * 12);
+      POVAR_CUDA(cudaMemcpyAsync(tmp.data(), p->D32, nc * 12 * 4, cudaMemcpyDeviceToHost,
+                                 p->stream));
+      POVAR_CUDA(cudaStreamSynchronize(p->stream));
+      for (size_t e = 0; e < nc * 12; ++e) delta_out[e] = tmp[e];
+    }
+  }
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  return POVAR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,432 @@
+// a1: observation orders (built once per problem).
+//
+// The point-major and camera-major orders are stable sorts of the
+// observation ids by landmark and by camera (ties keep the input order), so
+// they equal a CPU stable sort bit for bit. The sort is an LSD radix sort
+// with 8-bit digits; each pass ranks the keys of a 2048-key tile with warp
+// match/ballot and a per-digit running count, which keeps it stable.
+#include "povar_internal.cuh"
+
+#include <algorithm>
+
+namespace povar {
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+__global__ void k_iota(uint32_t* v, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (uint32_t)i;
+}
+
+__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                             uint32_t* __restrict__ hist, int ntiles) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    const int64_t i = base + (int64_t)k * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter of one tile: chunk c of the tile is items [c*256, c*256+256)
+// in input order; warp w owns 32 consecutive items of the chunk.
+__global__ void k_radix_scatter(const uint32_t* __restrict__ kin,
+                                const uint32_t* __restrict__ vin,
+                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                int64_t n, int shift, const uint32_t* __restrict__ offs,
+                                int ntiles) {
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wcnt[RS_WARPS][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  run[threadIdx.x] = 0;
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int c = 0; c < RS_ITEMS; ++c) {
+#pragma unroll
+    for (int q = 0; q < RS_WARPS; ++q) wcnt[q][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = base + (int64_t)c * RS_THREADS + threadIdx.x;
+    const bool valid = i < n;
+    uint32_t key = 0, val = 0;
+    unsigned d = 256u + (unsigned)lane;  // unique sentinel for invalid lanes
+    if (valid) {
+      key = kin[i];
+      val = vin[i];
+      d = (key >> shift) & 255u;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned rank = __popc(peers & lt_mask);
+    const int leader = __ffs(peers) - 1;
+    if (valid && lane == leader) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t acc = run[threadIdx.x];
+#pragma unroll
+      for (int q = 0; q < RS_WARPS; ++q) {
+        const uint32_t t = wcnt[q][threadIdx.x];
+        wcnt[q][threadIdx.x] = acc;
+        acc += t;
+      }
+      run[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = offs[(size_t)d * ntiles + blockIdx.x] + wcnt[w][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of 2048 elements per block (256 threads x 8 consecutive).
+__global__ void k_scan_block(uint32_t* __restrict__ data, int64_t n,
+                             uint32_t* __restrict__ block_sums) {
+  __shared__ uint32_t warp_tot[RS_WARPS];
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)threadIdx.x * RS_ITEMS;
+  uint32_t v[RS_ITEMS];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    v[k] = (base + k < n) ? data[base + k] : 0u;
+    s += v[k];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  uint32_t wbase = 0, tot = 0;
+#pragma unroll
+  for (int q = 0; q < RS_WARPS; ++q) {
+    if (q < w) wbase += warp_tot[q];
+    tot += warp_tot[q];
+  }
+  uint32_t run = wbase + incl - s;
+#pragma unroll
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    if (base + k < n) data[base + k] = run;
+    run += v[k];
+  }
+  if (block_sums != nullptr && threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ data, int64_t n,
+                           const uint32_t* __restrict__ block_off) {
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)threadIdx.x * RS_ITEMS;
+  const uint32_t a = block_off[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < RS_ITEMS; ++k)
+    if (base + k < n) data[base + k] += a;
+}
+
+// off[k] = first position whose sorted key is >= k, for k in [0, nkeys].
+__global__ void k_offsets(const uint32_t* __restrict__ skeys, int64_t n, int64_t nkeys,
+                          uint32_t* __restrict__ off) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t k = skeys[i];
+  const int64_t prev = (i == 0) ? -1 : (int64_t)skeys[i - 1];
+  for (int64_t q = prev + 1; q <= k; ++q) off[q] = (uint32_t)i;
+  if (i == n - 1)
+    for (int64_t q = k + 1; q <= nkeys; ++q) off[q] = (uint32_t)n;
+}
+
+// Per landmark: track length and smallest camera index.
+__global__ void k_point_stats(const uint32_t* __restrict__ off_pt,
+                              const uint32_t* __restrict__ perm_pt,
+                              const int32_t* __restrict__ cam, int np,
+                              uint32_t* __restrict__ len, uint32_t* __restrict__ mincam) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= np) return;
+  const uint32_t b = off_pt[j], e = off_pt[j + 1];
+  uint32_t mc = 0xffffffffu;
+  for (uint32_t r = b; r < e; ++r) mc = min(mc, (uint32_t)cam[perm_pt[r]]);
+  len[j] = e - b;
+  mincam[j] = mc;
+}
+
+__global__ void k_slot_keys(const uint32_t* __restrict__ len,
+                            const uint32_t* __restrict__ mincam, int np, uint32_t maxlen,
+                            int cam_bits, int use_cam, uint32_t* __restrict__ key) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= np) return;
+  uint32_t k = maxlen - len[j];
+  if (use_cam) k = (k << cam_bits) | mincam[j];
+  key[j] = k;
+}
+
+__global__ void k_slots(const uint32_t* __restrict__ sorted_pts, int np, int np_pad,
+                        const uint32_t* __restrict__ len, uint32_t* __restrict__ slot_pt,
+                        uint32_t* __restrict__ pt_slot, uint32_t* __restrict__ slot_len) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= np_pad) return;
+  if (s < np) {
+    const uint32_t j = sorted_pts[s];
+    slot_pt[s] = j;
+    pt_slot[j] = (uint32_t)s;
+    slot_len[s] = len[j];
+  } else {
+    slot_pt[s] = 0xffffffffu;
+    slot_len[s] = 0;
+  }
+}
+
+__global__ void k_slice_width(const uint32_t* __restrict__ slot_len, int nslices,
+                              uint32_t* __restrict__ w32) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nslices) w32[s] = slot_len[s * SLICE] * SLICE;
+}
+
+__global__ void k_fill_sell(const uint32_t* __restrict__ slot_pt,
+                            const uint32_t* __restrict__ slot_len,
+                            const uint32_t* __restrict__ sell_off,
+                            const uint32_t* __restrict__ off_pt,
+                            const uint32_t* __restrict__ perm_pt,
+                            const int32_t* __restrict__ cam, const double* __restrict__ meas,
+                            int np, int32_t* __restrict__ sell_cam,
+                            float2* __restrict__ m32, double2* __restrict__ m64) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= np) return;
+  const uint32_t j = slot_pt[s];
+  const uint32_t len = slot_len[s];
+  const uint32_t b = off_pt[j];
+  const uint32_t base = sell_off[s / SLICE] + (uint32_t)(s % SLICE);
+  for (uint32_t t = 0; t < len; ++t) {
+    const uint32_t o = perm_pt[b + t];
+    const uint32_t pos = base + t * SLICE;
+    const double u = meas[2 * (size_t)o], v = meas[2 * (size_t)o + 1];
+    sell_cam[pos] = cam[o];
+    m32[pos] = make_float2((float)u, (float)v);
+    m64[pos] = make_double2(u, v);
+  }
+}
+
+__global__ void k_fill_cm(const uint32_t* __restrict__ perm_cam,
+                          const int32_t* __restrict__ pt, const uint32_t* __restrict__ pt_slot,
+                          const double* __restrict__ meas, int64_t n,
+                          uint32_t* __restrict__ cm_slot, float2* __restrict__ m32,
+                          double2* __restrict__ m64) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint32_t o = perm_cam[r];
+  const double u = meas[2 * (size_t)o], v = meas[2 * (size_t)o + 1];
+  cm_slot[r] = pt_slot[pt[o]];
+  m32[r] = make_float2((float)u, (float)v);
+  m64[r] = make_double2(u, v);
+}
+
+__global__ void k_to_u32(const int32_t* __restrict__ src, uint32_t* __restrict__ dst, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (uint32_t)src[i];
+}
+
+int bits_for(uint64_t maxval) {
+  int b = 0;
+  while (b < 32 && (maxval >> b) != 0) ++b;
+  return std::max(b, 1);
+}
+
+// Scratch buffer list freed at the end of build_orders.
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* q : ptrs) cudaFree(q);
+  }
+  template <class T>
+  T* get(size_t count) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    ptrs.push_back(q);
+    return static_cast<T*>(q);
+  }
+};
+
+povar_status scan_exclusive(Problem* p, Scratch& sc, uint32_t* data, int64_t n) {
+  const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
+  if (nb <= 1) {
+    k_scan_block<<<1, RS_THREADS, 0, p->stream>>>(data, n, nullptr);
+    ++p->launches;
+    return check_launch(p, "scan");
+  }
+  uint32_t* sums = sc.get<uint32_t>(nb);
+  if (!sums) return fail(p, POVAR_ENOMEM, "scan scratch");
+  k_scan_block<<<(unsigned)nb, RS_THREADS, 0, p->stream>>>(data, n, sums);
+  ++p->launches;
+  povar_status s = scan_exclusive(p, sc, sums, nb);
+  if (s != POVAR_OK) return s;
+  k_scan_add<<<(unsigned)nb, RS_THREADS, 0, p->stream>>>(data, n, sums);
+  ++p->launches;
+  return check_launch(p, "scan_add");
+}
+
+// Stable sort of (keys, vals) by keys < 2^key_bits. Results end in (*k, *v).
+povar_status radix_sort(Problem* p, Scratch& sc, uint32_t** k, uint32_t** v, int64_t n,
+                        int key_bits) {
+  const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+  uint32_t* k2 = sc.get<uint32_t>(n);
+  uint32_t* v2 = sc.get<uint32_t>(n);
+  uint32_t* hist = sc.get<uint32_t>((size_t)256 * ntiles);
+  if (!k2 || !v2 || !hist) return fail(p, POVAR_ENOMEM, "radix scratch");
+  uint32_t *ka = *k, *va = *v, *kb = k2, *vb = v2;
+  for (int shift = 0; shift < key_bits; shift += 8) {
+    k_radix_hist<<<ntiles, RS_THREADS, 0, p->stream>>>(ka, n, shift, hist, ntiles);
+    ++p->launches;
+    povar_status s = scan_exclusive(p, sc, hist, (int64_t)256 * ntiles);
+    if (s != POVAR_OK) return s;
+    k_radix_scatter<<<ntiles, RS_THREADS, 0, p->stream>>>(ka, va, kb, vb, n, shift, hist,
+                                                         ntiles);
+    ++p->launches;
+    if ((s = check_launch(p, "radix_scatter")) != POVAR_OK) return s;
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  *k = ka;
+  *v = va;
+  return POVAR_OK;
+}
+
+}  // namespace
+
+povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt) {
+  (void)h_pt;
+  Scratch sc;
+  const int64_t n = p->nobs;
+  const unsigned gb = grid_for(n, 256);
+  povar_status s;
+
+  // ---- point-major and camera-major stable orders
+  for (int which = 0; which < 2; ++which) {
+    uint32_t* keys = sc.get<uint32_t>(n);
+    uint32_t* vals = sc.get<uint32_t>(n);
+    if (!keys || !vals) return fail(p, POVAR_ENOMEM, "order scratch");
+    k_to_u32<<<gb, 256, 0, p->stream>>>(which == 0 ? p->d_pt : p->d_cam, keys, n);
+    k_iota<<<gb, 256, 0, p->stream>>>(vals, n);
+    p->launches += 2;
+    const int64_t nkeys = which == 0 ? p->np : p->nc;
+    uint32_t *kk = keys, *vv = vals;
+    if ((s = radix_sort(p, sc, &kk, &vv, n, bits_for((uint64_t)(nkeys - 1)))) != POVAR_OK)
+      return s;
+    uint32_t* perm = which == 0 ? p->perm_pt : p->perm_cam;
+    uint32_t* off = which == 0 ? p->off_pt : p->off_cam;
+    POVAR_CUDA(cudaMemcpyAsync(perm, vv, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                               p->stream));
+    k_offsets<<<gb, 256, 0, p->stream>>>(kk, n, nkeys, off);
+    ++p->launches;
+    if ((s = check_launch(p, "offsets")) != POVAR_OK) return s;
+  }
+
+  // ---- landmark slots sorted by track length (desc), then smallest camera
+  uint32_t* len = sc.get<uint32_t>(p->np);
+  uint32_t* mincam = sc.get<uint32_t>(p->np);
+  uint32_t* skey = sc.get<uint32_t>(p->np);
+  uint32_t* sval = sc.get<uint32_t>(p->np);
+  if (!len || !mincam || !skey || !sval) return fail(p, POVAR_ENOMEM, "slot scratch");
+  const unsigned gp = grid_for(p->np, 256);
+  k_point_stats<<<gp, 256, 0, p->stream>>>(p->off_pt, p->perm_pt, p->d_cam, p->np, len,
+                                           mincam);
+  ++p->launches;
+  std::vector<uint32_t> h_off(p->np + 1);
+  POVAR_CUDA(cudaMemcpyAsync(h_off.data(), p->off_pt, (p->np + 1) * sizeof(uint32_t),
+                             cudaMemcpyDeviceToHost, p->stream));
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  uint32_t maxlen = 0;
+  for (int j = 0; j < p->np; ++j) {
+    const uint32_t l = h_off[j + 1] - h_off[j];
+    if (l == 0) return fail(p, POVAR_EINVAL, "landmark without observations");
+    maxlen = std::max(maxlen, l);
+  }
+  const int len_bits = bits_for(maxlen);
+  const int cam_bits = bits_for((uint64_t)(p->nc - 1));
+  const int use_cam = (len_bits + cam_bits <= 32) ? 1 : 0;
+  k_slot_keys<<<gp, 256, 0, p->stream>>>(len, mincam, p->np, maxlen, cam_bits, use_cam, skey);
+  k_iota<<<gp, 256, 0, p->stream>>>(sval, p->np);
+  p->launches += 2;
+  {
+    uint32_t *kk = skey, *vv = sval;
+    if ((s = radix_sort(p, sc, &kk, &vv, p->np, use_cam ? len_bits + cam_bits : len_bits)) !=
+        POVAR_OK)
+      return s;
+    k_slots<<<grid_for(p->np_pad, 256), 256, 0, p->stream>>>(vv, p->np, p->np_pad, len,
+                                                             p->slot_pt, p->pt_slot,
+                                                             p->slot_len);
+    ++p->launches;
+  }
+  // ---- SELL offsets
+  uint32_t* w = sc.get<uint32_t>(p->nslices + 1);
+  if (!w) return fail(p, POVAR_ENOMEM, "sell scratch");
+  POVAR_CUDA(cudaMemsetAsync(w, 0, (p->nslices + 1) * sizeof(uint32_t), p->stream));
+  k_slice_width<<<grid_for(p->nslices, 256), 256, 0, p->stream>>>(p->slot_len, p->nslices, w);
+  ++p->launches;
+  if ((s = scan_exclusive(p, sc, w, p->nslices + 1)) != POVAR_OK) return s;
+  POVAR_CUDA(cudaMemcpyAsync(p->sell_off, w, (p->nslices + 1) * sizeof(uint32_t),
+                             cudaMemcpyDeviceToDevice, p->stream));
+  uint32_t nsell = 0;
+  POVAR_CUDA(cudaMemcpyAsync(&nsell, w + p->nslices, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                             p->stream));
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  p->nsell = nsell;
+  if ((s = dev_alloc(p, &p->sell_cam, std::max<int64_t>(nsell, 1), "sell_cam")) ||
+      (s = dev_alloc(p, &p->sell_m32, std::max<int64_t>(nsell, 1), "sell_m32")) ||
+      (s = dev_alloc(p, &p->sell_m64, std::max<int64_t>(nsell, 1), "sell_m64")))
+    return s;
+  POVAR_CUDA(cudaMemsetAsync(p->sell_cam, 0xff, nsell * sizeof(int32_t), p->stream));
+  POVAR_CUDA(cudaMemsetAsync(p->sell_m32, 0, nsell * sizeof(float2), p->stream));
+  POVAR_CUDA(cudaMemsetAsync(p->sell_m64, 0, nsell * sizeof(double2), p->stream));
+  k_fill_sell<<<gp, 256, 0, p->stream>>>(p->slot_pt, p->slot_len, p->sell_off, p->off_pt,
+                                         p->perm_pt, p->d_cam, p->d_meas, p->np, p->sell_cam,
+                                         p->sell_m32, p->sell_m64);
+  k_fill_cm<<<gb, 256, 0, p->stream>>>(p->perm_cam, p->d_pt, p->pt_slot, p->d_meas, n,
+                                       p->cm_slot, p->cm_m32, p->cm_m64);
+  p->launches += 2;
+  if ((s = check_launch(p, "fill layouts")) != POVAR_OK) return s;
+
+  // ---- camera-major chunks (host: n_cams entries)
+  std::vector<uint32_t> h_offc(p->nc + 1);
+  POVAR_CUDA(cudaMemcpyAsync(h_offc.data(), p->off_cam, (p->nc + 1) * sizeof(uint32_t),
+                             cudaMemcpyDeviceToHost, p->stream));
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  std::vector<uint32_t> cb;
+  std::vector<int32_t> ccam, cn(p->nc), c0(p->nc);
+  int active = 0;
+  for (int c = 0; c < p->nc; ++c) {
+    const uint32_t b = h_offc[c], e = h_offc[c + 1];
+    c0[c] = (int32_t)ccam.size();
+    cn[c] = (int32_t)((e - b + CHUNK - 1) / CHUNK);
+    if (e > b) ++active;
+    for (uint32_t q = b; q < e; q += CHUNK) {
+      cb.push_back(q);
+      ccam.push_back(c);
+    }
+  }
+  cb.push_back((uint32_t)n);
+  p->nchunks = (int32_t)ccam.size();
+  p->nc_active = active;
+  if ((s = dev_alloc(p, &p->chunk_beg, cb.size(), "chunk_beg")) ||
+      (s = dev_alloc(p, &p->chunk_cam, std::max<size_t>(ccam.size(), 1), "chunk_cam")))
+    return s;
+  POVAR_CUDA(cudaMemcpy(p->chunk_beg, cb.data(), cb.size() * sizeof(uint32_t),
+                        cudaMemcpyHostToDevice));
+  POVAR_CUDA(cudaMemcpy(p->chunk_cam, ccam.data(), ccam.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice));
+  POVAR_CUDA(cudaMemcpy(p->cam_nchunk, cn.data(), p->nc * sizeof(int32_t),
+                        cudaMemcpyHostToDevice));
+  POVAR_CUDA(cudaMemcpy(p->cam_chunk0, c0.data(), p->nc * sizeof(int32_t),
+                        cudaMemcpyHostToDevice));
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  return POVAR_OK;
+}
+
+}  // namespace povar

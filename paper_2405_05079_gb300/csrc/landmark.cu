@@ -1,0 +1,368 @@
+// a2 + a3: closed-form VarPro landmarks and the pOSE cost, in FP64.
+//
+// Eq. update_landmark: with the cameras fixed, every landmark solves its own
+// 3x3 linear least-squares problem. For observation (i, j, m = (u, v)) the
+// pOSE residual (Eq. pose) is r = B(m) (P_i (X_j, 1)) - d(m), so landmark j's
+// normal matrix and right-hand side are
+//     V_j = sum P^T C P,   h_j = sum P^T (C p4 - (eta u, eta v, 0)),
+// with P the left 3x3 of P_i, p4 its last column and C = B^T B =
+//     [[1, 0, -a u], [0, 1, -a v], [-a u, -a v, a (u^2 + v^2)]], a = 1 - eta.
+// Both are affine in (u, v, u^2 + v^2) with per-camera coefficients, so each
+// camera carries a 48-double table (computed once per camera set) and one
+// observation costs 38 FP64 operations. X_j = -V_j^-1 h_j through the
+// Cholesky factor V = L L^T; the kernel also stores F = L^-1 (V^-1 = F^T F),
+// which the series kernels use. A numerically rank-deficient V_j
+// (cond > 1e12) falls back to the Moore-Penrose pseudo-inverse (footnote of
+// Sec. 4.2) from a Jacobi eigen-decomposition.
+// Pass 2 evaluates the four residual rows of every observation of the
+// landmark at (P, X_j) and accumulates F = ||r||^2 (Eq. ba_first_stage) into
+// one FP64 partial per block; a single block then adds the partials in a
+// fixed order, so the cost is deterministic.
+#include "povar_internal.cuh"
+
+namespace povar {
+namespace {
+
+struct SlotBufs {
+  double* X[2];
+  double* F[2];
+  float4* A[2];
+  float4* B[2];
+  float* C[2];
+};
+
+// Ltab layout (48 doubles per camera):
+//  [0,6) R, [6,12) E1, [12,18) E2, [18,24) Fm   (symmetric 3x3: 00 01 02 11 12 22)
+//  [24,27) h0, [27,30) hu, [30,33) hv, [33,36) hw, [36,48) P (row-major 3x4)
+__global__ void k_ltab(const DeviceState* __restrict__ st, int which_rel, double eta,
+                       const double* __restrict__ P0, const double* __restrict__ P1, int nc,
+                       double* __restrict__ Ltab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  if (which_rel == 1 && st->converged) return;
+  const int t = which_rel ? 1 - st->cur : st->cur;
+  const double* P = (t ? P1 : P0) + 12 * (size_t)i;
+  const double a = 1.0 - eta;
+  double p0[3], p1[3], p2[3];
+  for (int c = 0; c < 3; ++c) {
+    p0[c] = P[c];
+    p1[c] = P[4 + c];
+    p2[c] = P[8 + c];
+  }
+  const double q0 = P[3], q1 = P[7], q2 = P[11];
+  double* T = Ltab + 48 * (size_t)i;
+  const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+  for (int e = 0; e < 6; ++e) {
+    const int x = ia[e], y = ib[e];
+    T[e] = p0[x] * p0[y] + p1[x] * p1[y];
+    T[6 + e] = -a * (p0[x] * p2[y] + p2[x] * p0[y]);
+    T[12 + e] = -a * (p1[x] * p2[y] + p2[x] * p1[y]);
+    T[18 + e] = a * p2[x] * p2[y];
+  }
+  for (int c = 0; c < 3; ++c) {
+    T[24 + c] = q0 * p0[c] + q1 * p1[c];
+    T[27 + c] = (-a * q2 - eta) * p0[c] - a * q0 * p2[c];
+    T[30 + c] = (-a * q2 - eta) * p1[c] - a * q1 * p2[c];
+    T[33 + c] = a * q2 * p2[c];
+  }
+  for (int c = 0; c < 12; ++c) T[36 + c] = P[c];
+}
+
+// Symmetric 3x3 packed as (00 01 02 11 12 22).
+__device__ __forceinline__ double sym_at(const double* V, int r, int c) {
+  const int lo = r < c ? r : c, hi = r < c ? c : r;
+  const int idx = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+  return V[idx];
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 (textbook rotation
+// formulas, Golub & Van Loan Sec. 8.5). Returns eigenvalues w and
+// eigenvectors as the columns of Q.
+__device__ __forceinline__ void jacobi3(const double* V, double w[3], double Q[3][3]) {
+  double A[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      A[r][c] = sym_at(V, r, c);
+      Q[r][c] = r == c ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 32; ++sweep) {
+    const double off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+    const double dia = fabs(A[0][0]) + fabs(A[1][1]) + fabs(A[2][2]);
+    if (off <= 1e-300 || off <= 1e-18 * dia) break;
+    for (int pq = 0; pq < 3; ++pq) {
+      const int pp = pq == 2 ? 1 : 0, qq = pq == 0 ? 1 : 2;
+      const double apq = A[pp][qq];
+      if (apq == 0.0) continue;
+      const double theta = (A[qq][qq] - A[pp][pp]) / (2.0 * apq);
+      const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+      const double c = 1.0 / sqrt(tt * tt + 1.0), s = tt * c;
+      for (int k = 0; k < 3; ++k) {
+        const double akp = A[k][pp], akq = A[k][qq];
+        A[k][pp] = c * akp - s * akq;
+        A[k][qq] = s * akp + c * akq;
+      }
+      for (int k = 0; k < 3; ++k) {
+        const double apk = A[pp][k], aqk = A[qq][k];
+        A[pp][k] = c * apk - s * aqk;
+        A[qq][k] = s * apk + c * aqk;
+      }
+      for (int k = 0; k < 3; ++k) {
+        const double qkp = Q[k][pp], qkq = Q[k][qq];
+        Q[k][pp] = c * qkp - s * qkq;
+        Q[k][qq] = s * qkp + c * qkq;
+      }
+    }
+  }
+  w[0] = A[0][0];
+  w[1] = A[1][1];
+  w[2] = A[2][2];
+}
+
+struct Sym3 {
+  double v[6];
+};
+struct Vec3 {
+  double x[3];
+};
+struct PinvOut {
+  double X[3];
+  double F[6];
+  bool deficient;
+};
+
+// Pseudo-inverse path: X = -V^+ h and a lower-triangular F with F^T F = V^+
+// (Cholesky of the index-reversed V^+, zero pivots giving zero columns).
+// `deficient` tells whether V was numerically rank-deficient. Arguments are
+// passed by value so that the caller's accumulators stay in registers.
+__device__ __forceinline__ PinvOut pinv_solve(Sym3 Vs, Vec3 hs) {
+  const double* V = Vs.v;
+  const double* h = hs.x;
+  PinvOut out;
+  double* X = out.X;
+  double* F = out.F;
+  double w[3], Q[3][3];
+  jacobi3(V, w, Q);
+  const double wmax = fmax(w[0], fmax(w[1], w[2]));
+  const double wmin = fmin(w[0], fmin(w[1], w[2]));
+  const bool deficient = !(wmax > 0.0) || wmin <= wmax / PINV_COND;
+  double A[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k)
+        if (w[k] > wmax / PINV_COND && w[k] > 0.0) acc += Q[r][k] * Q[c][k] / w[k];
+      A[r][c] = acc;
+    }
+  for (int r = 0; r < 3; ++r) X[r] = -(A[r][0] * h[0] + A[r][1] * h[1] + A[r][2] * h[2]);
+  // G = chol(J A J), lower; F = J G^T J, i.e. F[a][b] = G[2-b][2-a].
+  double R[3][3], G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) R[r][c] = A[2 - r][2 - c];
+  const double scale = fmax(fmax(fabs(R[0][0]), fabs(R[1][1])), fabs(R[2][2]));
+  for (int k = 0; k < 3; ++k) {
+    double d = R[k][k];
+    for (int q = 0; q < k; ++q) d -= G[k][q] * G[k][q];
+    if (d <= scale * 1e-14) continue;  // zero pivot: column stays zero
+    G[k][k] = sqrt(d);
+    for (int r = k + 1; r < 3; ++r) {
+      double e = R[r][k];
+      for (int q = 0; q < k; ++q) e -= G[r][q] * G[k][q];
+      G[r][k] = e / G[k][k];
+    }
+  }
+  F[0] = G[2][2];  // F00
+  F[1] = G[2][1];  // F10
+  F[2] = G[1][1];  // F11
+  F[3] = G[2][0];  // F20
+  F[4] = G[1][0];  // F21
+  F[5] = G[0][0];  // F22
+  out.deficient = deficient;
+  return out;
+}
+
+__global__ void __launch_bounds__(BLOCK)
+k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
+           const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
+           const int32_t* __restrict__ sell_cam, const double2* __restrict__ sell_m,
+           const double* __restrict__ Ltab, int np, SlotBufs bufs,
+           double* __restrict__ cost_part, int* __restrict__ pinv_part) {
+  if (which_rel == 1 && st->converged) return;
+  const int t = which_rel ? 1 - st->cur : st->cur;
+  const int s = blockIdx.x * BLOCK + threadIdx.x;
+  const double s1 = sqrt(1.0 - eta), s2 = sqrt(eta);
+  double cost = 0.0;
+  int npinv = 0;
+  if (s < np) {
+    const uint32_t len = slot_len[s];
+    const uint32_t base = sell_off[s / SLICE] + (uint32_t)(s % SLICE);
+    double V[6] = {0, 0, 0, 0, 0, 0}, h[3] = {0, 0, 0};
+    for (uint32_t k = 0; k < len; ++k) {
+      const uint32_t pos = base + k * SLICE;
+      const int i = sell_cam[pos];
+      const double2 m = sell_m[pos];
+      const double u = m.x, v = m.y, w = u * u + v * v;
+      const double* T = Ltab + 48 * (size_t)i;
+#pragma unroll
+      for (int e = 0; e < 6; ++e)
+        V[e] += __ldg(T + e) + u * __ldg(T + 6 + e) + v * __ldg(T + 12 + e) +
+                w * __ldg(T + 18 + e);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        h[c] += __ldg(T + 24 + c) + u * __ldg(T + 27 + c) + v * __ldg(T + 30 + c) +
+                w * __ldg(T + 33 + c);
+    }
+    // Cholesky V = L L^T; F = L^-1
+    double X[3], F[6];
+    const double dmax = fmax(V[0], fmax(V[3], V[5]));
+    const double l00 = sqrt(V[0]);
+    const double l10 = V[1] / l00, l20 = V[2] / l00;
+    const double d1 = V[3] - l10 * l10;
+    const double l11 = sqrt(d1);
+    const double l21 = (V[4] - l20 * l10) / l11;
+    const double d2 = V[5] - l20 * l20 - l21 * l21;
+    const double l22 = sqrt(d2);
+    const bool suspect = !(V[0] > 1e-9 * dmax) || !(d1 > 1e-9 * dmax) || !(d2 > 1e-9 * dmax) ||
+                         !(dmax > 0.0);
+    bool deficient = false;
+    if (suspect) {
+      Sym3 vs;
+      Vec3 hs;
+      for (int e = 0; e < 6; ++e) vs.v[e] = V[e];
+      for (int e = 0; e < 3; ++e) hs.x[e] = h[e];
+      const PinvOut o = pinv_solve(vs, hs);
+      deficient = o.deficient;
+      for (int e = 0; e < 3; ++e) X[e] = o.X[e];
+      for (int e = 0; e < 6; ++e) F[e] = o.F[e];
+    }
+    if (!deficient) {
+      const double f00 = 1.0 / l00, f11 = 1.0 / l11, f22 = 1.0 / l22;
+      const double f10 = -l10 * f00 * f11;
+      const double f20 = -(l20 * f00 + l21 * f10) * f22;
+      const double f21 = -l21 * f11 * f22;
+      F[0] = f00; F[1] = f10; F[2] = f11; F[3] = f20; F[4] = f21; F[5] = f22;
+      // z = F h, X = -F^T z
+      const double z0 = f00 * h[0];
+      const double z1 = f10 * h[0] + f11 * h[1];
+      const double z2 = f20 * h[0] + f21 * h[1] + f22 * h[2];
+      X[0] = -(f00 * z0 + f10 * z1 + f20 * z2);
+      X[1] = -(f11 * z1 + f21 * z2);
+      X[2] = -(f22 * z2);
+    }
+    npinv = deficient ? 1 : 0;
+    double* Xo = bufs.X[t] + 3 * (size_t)s;
+    Xo[0] = X[0]; Xo[1] = X[1]; Xo[2] = X[2];
+    double* Fo = bufs.F[t] + 6 * (size_t)s;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) Fo[e] = F[e];
+    bufs.A[t][s] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)F[0]);
+    bufs.B[t][s] = make_float4((float)F[1], (float)F[2], (float)F[3], (float)F[4]);
+    bufs.C[t][s] = (float)F[5];
+    // pass 2: residuals and cost
+    for (uint32_t k = 0; k < len; ++k) {
+      const uint32_t pos = base + k * SLICE;
+      const int i = sell_cam[pos];
+      const double2 m = sell_m[pos];
+      const double* P = Ltab + 48 * (size_t)i + 36;
+      const double y0 = __ldg(P + 0) * X[0] + __ldg(P + 1) * X[1] + __ldg(P + 2) * X[2] + __ldg(P + 3);
+      const double y1 = __ldg(P + 4) * X[0] + __ldg(P + 5) * X[1] + __ldg(P + 6) * X[2] + __ldg(P + 7);
+      const double y2 = __ldg(P + 8) * X[0] + __ldg(P + 9) * X[1] + __ldg(P + 10) * X[2] + __ldg(P + 11);
+      const double r0 = s1 * (y0 - m.x * y2), r1 = s1 * (y1 - m.y * y2);
+      const double r2 = s2 * (y0 - m.x), r3 = s2 * (y1 - m.y);
+      cost += r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3;
+    }
+  } else {
+    // padding slot (the slot arrays are padded to a whole number of blocks)
+    double* Xo = bufs.X[t] + 3 * (size_t)s;
+    Xo[0] = Xo[1] = Xo[2] = 0.0;
+    double* Fo = bufs.F[t] + 6 * (size_t)s;
+    for (int e = 0; e < 6; ++e) Fo[e] = 0.0;
+    bufs.A[t][s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    bufs.B[t][s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    bufs.C[t][s] = 0.f;
+  }
+  // deterministic block reduction
+  __shared__ double red[BLOCK / 32];
+  __shared__ int redi[BLOCK / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cost += __shfl_xor_sync(0xffffffffu, cost, o);
+    npinv += __shfl_xor_sync(0xffffffffu, npinv, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = cost;
+    redi[threadIdx.x >> 5] = npinv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double c = 0.0;
+    int q = 0;
+    for (int w = 0; w < BLOCK / 32; ++w) {
+      c += red[w];
+      q += redi[w];
+    }
+    cost_part[blockIdx.x] = c;
+    pinv_part[blockIdx.x] = q;
+  }
+}
+
+__global__ void k_cost_finish(DeviceState* __restrict__ st, int which_rel,
+                              const double* __restrict__ part, const int* __restrict__ pinv,
+                              int n) {
+  if (which_rel == 1 && st->converged) return;
+  __shared__ double red[256];
+  __shared__ int redi[256];
+  double c = 0.0;
+  int q = 0;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    c += part[i];
+    q += pinv[i];
+  }
+  red[threadIdx.x] = c;
+  redi[threadIdx.x] = q;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[threadIdx.x] += red[threadIdx.x + o];
+      redi[threadIdx.x] += redi[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (which_rel == 0) {
+      st->F = red[0];
+      if (!isfinite(red[0])) st->error = POVAR_ENUMERIC;
+    } else {
+      st->F_new = red[0];
+    }
+    st->n_pinv = redi[0];
+  }
+}
+
+}  // namespace
+
+povar_status launch_landmarks(Problem* p, int which_rel, double eta) {
+  k_ltab<<<grid_for(p->nc, 128), 128, 0, p->stream>>>(p->state, which_rel, eta, p->P64[0],
+                                                      p->P64[1], p->nc, p->Ltab);
+  SlotBufs b;
+  for (int t = 0; t < 2; ++t) {
+    b.X[t] = p->X64[t];
+    b.F[t] = p->F64[t];
+    b.A[t] = p->pdA[t];
+    b.B[t] = p->pdB[t];
+    b.C[t] = p->pdC[t];
+  }
+  k_landmark<<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+      p->state, which_rel, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->Ltab,
+      p->np, b, p->cost_part, p->pinv_part);
+  p->launches += 2;
+  return check_launch(p, "landmark");
+}
+
+povar_status launch_cost_finish(Problem* p, int which_rel) {
+  k_cost_finish<<<1, 256, 0, p->stream>>>(p->state, which_rel, p->cost_part, p->pinv_part,
+                                          p->n_slot_blocks);
+  ++p->launches;
+  return check_launch(p, "cost_finish");
+}
+
+}  // namespace povar

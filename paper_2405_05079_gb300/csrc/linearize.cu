@@ -1,0 +1,306 @@
+// a4: linearization of the pOSE residual at (P, X*(P)) per camera (Sec. 4.1)
+// a5: damped tangent-space camera blocks and their inverses (Sec. 4.3)
+// a6: right-hand side and the first series term x_0 = U~^-1 g (Sec. 4.2)
+//
+// With y = P_i x~_j, the residual of Eq. pose is r = B(m) y - d(m), so
+// J_p = B (x) x~^T and U_i = sum_k C_k (x) x~ x~^T with C = B^T B =
+//   [[1, 0, -a u], [0, 1, -a v], [-a u, -a v, a (u^2 + v^2)]],  a = 1 - eta.
+// Hence U_i is fully determined by four symmetric 4x4 moment sums
+//   S0 = sum x~x~^T, Su = sum u x~x~^T, Sv = sum v x~x~^T, Sw = sum w x~x~^T
+// (w = u^2 + v^2): blocks (0,0) = (1,1) = S0, (0,1) = 0, (0,2) = -a Su,
+// (1,2) = -a Sv, (2,2) = a Sw. b_p,i = sum_k (B^T r_k) (x) x~_j.
+// One warp reduces one camera-major chunk of observations into these 52
+// numbers with shuffles (no atomics); the per-camera kernel adds the chunk
+// partials in chunk order, so the result is deterministic.
+//
+// Tangent space (POVAR_SPHERE): with p^ = P_i / ||P_i|| and Pi = I - p^p^T,
+//   A_i = Pi U_i Pi + lambda Pi + p^ p^T   is SPD and, for any tangent v,
+//   A_i^-1 v = Q (Q^T U_i Q + lambda I)^-1 Q^T v  for every orthonormal basis
+// Q of the tangent space, so G_i = A_i^-1 - p^p^T = Q U~_i^-1 Q^T applies the
+// inverse damped tangent block of Sec. 4.3 in ambient 12-d coordinates.
+// POVAR_EUCLID: G_i = (U_i + lambda I)^-1. The 12x12 Cholesky and inverse are
+// FP64; G is also stored in FP32 for the mixed-precision series.
+#include "povar_internal.cuh"
+
+namespace povar {
+namespace {
+
+template <typename T> struct M2;
+template <> struct M2<float> { using type = float2; };
+template <> struct M2<double> { using type = double2; };
+
+template <typename T>
+__device__ __forceinline__ void load_x(const float4* __restrict__ pdA,
+                                       const double* __restrict__ X64, uint32_t slot,
+                                       T& x0, T& x1, T& x2);
+template <>
+__device__ __forceinline__ void load_x<float>(const float4* __restrict__ pdA,
+                                              const double* __restrict__, uint32_t slot,
+                                              float& x0, float& x1, float& x2) {
+  const float4 a = __ldg(pdA + slot);
+  x0 = a.x; x1 = a.y; x2 = a.z;
+}
+template <>
+__device__ __forceinline__ void load_x<double>(const float4* __restrict__,
+                                               const double* __restrict__ X64, uint32_t slot,
+                                               double& x0, double& x1, double& x2) {
+  const double* x = X64 + 3 * (size_t)slot;
+  x0 = __ldg(x); x1 = __ldg(x + 1); x2 = __ldg(x + 2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_linearize(const DeviceState* __restrict__ st, double eta, int nchunks,
+            const int32_t* __restrict__ chunk_cam, const uint32_t* __restrict__ chunk_beg,
+            const uint32_t* __restrict__ cm_slot, const typename M2<T>::type* __restrict__ cm_m,
+            const double* __restrict__ P0, const double* __restrict__ P1,
+            const float4* __restrict__ pdA0, const float4* __restrict__ pdA1,
+            const double* __restrict__ X0, const double* __restrict__ X1,
+            T* __restrict__ part) {
+  if (st->converged || !st->need_lin) return;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (c >= nchunks) return;
+  const int cur = st->cur;
+  const double* Pd = (cur ? P1 : P0) + 12 * (size_t)chunk_cam[c];
+  const float4* pdA = cur ? pdA1 : pdA0;
+  const double* X64 = cur ? X1 : X0;
+  T P[12];
+#pragma unroll
+  for (int e = 0; e < 12; ++e) P[e] = (T)Pd[e];
+  const T s1 = (T)sqrt(1.0 - eta), s2 = (T)sqrt(eta);
+  T acc[LIN_ACC];
+#pragma unroll
+  for (int e = 0; e < LIN_ACC; ++e) acc[e] = (T)0;
+  const uint32_t b = chunk_beg[c], e_ = chunk_beg[c + 1];
+  for (uint32_t r = b + lane; r < e_; r += 32) {
+    const uint32_t slot = cm_slot[r];
+    const auto m = cm_m[r];
+    const T u = m.x, v = m.y, w = u * u + v * v;
+    T x0, x1, x2;
+    load_x<T>(pdA, X64, slot, x0, x1, x2);
+    const T y0 = P[0] * x0 + P[1] * x1 + P[2] * x2 + P[3];
+    const T y1 = P[4] * x0 + P[5] * x1 + P[6] * x2 + P[7];
+    const T y2 = P[8] * x0 + P[9] * x1 + P[10] * x2 + P[11];
+    const T r0 = s1 * (y0 - u * y2), r1 = s1 * (y1 - v * y2);
+    const T r2 = s2 * (y0 - u), r3 = s2 * (y1 - v);
+    const T g[3] = {s1 * r0 + s2 * r2, s1 * r1 + s2 * r3, -s1 * (u * r0 + v * r1)};
+    const T xt[4] = {x0, x1, x2, (T)1};
+    const T t10[10] = {x0 * x0, x0 * x1, x0 * x2, x0, x1 * x1, x1 * x2, x1, x2 * x2, x2, (T)1};
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      acc[q] += t10[q];
+      acc[10 + q] += u * t10[q];
+      acc[20 + q] += v * t10[q];
+      acc[30 + q] += w * t10[q];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 4; ++bb) acc[40 + 4 * a + bb] += g[a] * xt[bb];
+  }
+#pragma unroll
+  for (int e = 0; e < LIN_ACC; ++e) {
+    T v = acc[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    acc[e] = v;
+  }
+  T* out = part + (size_t)c * LIN_ACC;
+#pragma unroll
+  for (int e = 0; e < LIN_ACC; ++e)
+    if ((e & 31) == lane) out[e] = acc[e];
+}
+
+// index of the unique entry (b, d) of a symmetric 4x4 in the t10 order
+__device__ __forceinline__ int t10_index(int b, int d) {
+  const int lo = b < d ? b : d, hi = b < d ? d : b;
+  // rows: (0,0..3) -> 0..3, (1,1..3) -> 4..6, (2,2..3) -> 7..8, (3,3) -> 9
+  return lo == 0 ? hi : (lo == 1 ? 3 + hi : (lo == 2 ? 5 + hi : 9));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
+                 const int32_t* __restrict__ cam_nchunk, const int32_t* __restrict__ cam_chunk0,
+                 const T* __restrict__ part, const double* __restrict__ P0,
+                 const double* __restrict__ P1, double* __restrict__ U64,
+                 double* __restrict__ bp64, float* __restrict__ camP32,
+                 double* __restrict__ G64, float* __restrict__ G32, T* __restrict__ Y,
+                 T* __restrict__ D, double* __restrict__ camnorm) {
+  if (st->converged) return;
+  __shared__ double smA[4][12][13];
+  __shared__ double smL[4][12][13];
+  __shared__ double smAcc[4][LIN_ACC];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int i = blockIdx.x * 4 + wl;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->stop_series = 0;
+    st->terms_used = 1;
+    st->lam_used = st->lam;
+  }
+  if (i >= nc) return;
+  const int cur = st->cur;
+  const int need_lin = st->need_lin;
+  const double lam = st->lam;
+  const double a = 1.0 - eta;
+  const double* Pc = (cur ? P1 : P0) + 12 * (size_t)i;
+  double (*A)[13] = smA[wl];
+  double (*L)[13] = smL[wl];
+  const double Pl = lane < 12 ? Pc[lane] : 0.0;
+  double bpl = 0.0;
+  if (need_lin) {
+    const int n = cam_nchunk[i], c0 = cam_chunk0[i];
+    for (int e = lane; e < LIN_ACC; e += 32) {
+      double s = 0.0;
+      for (int q = 0; q < n; ++q) s += (double)part[(size_t)(c0 + q) * LIN_ACC + e];
+      smAcc[wl][e] = s;
+    }
+    __syncwarp();
+    if (lane < 12) {
+      const int ra = lane >> 2, rb = lane & 3;
+      for (int q = 0; q < 12; ++q) {
+        const int ca = q >> 2, cd = q & 3;
+        const int t = t10_index(rb, cd);
+        const int lo = ra < ca ? ra : ca, hi = ra < ca ? ca : ra;
+        double val;
+        if (lo == hi && lo < 2) val = smAcc[wl][t];
+        else if (lo == 0 && hi == 1) val = 0.0;
+        else if (lo == 0) val = -a * smAcc[wl][10 + t];
+        else if (lo == 1) val = -a * smAcc[wl][20 + t];
+        else val = a * smAcc[wl][30 + t];
+        A[lane][q] = val;
+        U64[(size_t)i * 144 + lane * 12 + q] = val;
+      }
+      bpl = smAcc[wl][40 + lane];
+      bp64[(size_t)i * 12 + lane] = bpl;
+      camP32[(size_t)i * 12 + lane] = (float)Pl;
+    }
+  } else if (lane < 12) {
+    for (int q = 0; q < 12; ++q) A[lane][q] = U64[(size_t)i * 144 + lane * 12 + q];
+    bpl = bp64[(size_t)i * 12 + lane];
+  }
+  __syncwarp();
+  // tangent projection + damping
+  double ph = 0.0;
+  if (manifold == POVAR_SPHERE) {
+    double nn = Pl * Pl;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    ph = lane < 12 ? Pl / sqrt(nn) : 0.0;
+    double up = 0.0;
+    for (int q = 0; q < 12; ++q) {
+      const double pq = __shfl_sync(0xffffffffu, ph, q);
+      if (lane < 12) up += A[lane][q] * pq;
+    }
+    double cc = ph * up;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, o);
+    __syncwarp();
+    for (int q = 0; q < 12; ++q) {
+      const double pq = __shfl_sync(0xffffffffu, ph, q);
+      const double uq = __shfl_sync(0xffffffffu, up, q);
+      if (lane < 12)
+        A[lane][q] += -up * pq - ph * uq + (cc - lam + 1.0) * ph * pq + (lane == q ? lam : 0.0);
+    }
+  } else if (lane < 12) {
+    A[lane][lane] += lam;
+  }
+  __syncwarp();
+  // Cholesky A = L L^T (lower, in place), lanes own rows
+  bool bad = false;
+  for (int k = 0; k < 12; ++k) {
+    if (lane == k) {
+      const double d = A[k][k];
+      if (!(d > 0.0)) bad = true;
+      A[k][k] = sqrt(fmax(d, 1e-300));
+    }
+    __syncwarp();
+    if (lane > k && lane < 12) A[lane][k] /= A[k][k];
+    __syncwarp();
+    if (lane > k && lane < 12)
+      for (int j = k + 1; j <= lane; ++j) A[lane][j] -= A[lane][k] * A[j][k];
+    __syncwarp();
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) st->error = POVAR_ENUMERIC;
+  // L^-1 by columns (lane c owns column c)
+  if (lane < 12) {
+    const int c = lane;
+    for (int r = 0; r < 12; ++r) {
+      if (r < c) {
+        L[r][c] = 0.0;
+        continue;
+      }
+      double s = (r == c) ? 1.0 : 0.0;
+      for (int k = c; k < r; ++k) s -= A[r][k] * L[k][c];
+      L[r][c] = s / A[r][r];
+    }
+  }
+  __syncwarp();
+  // A^-1 = L^-T L^-1, minus p^p^T on the sphere; x0 = -G b_p
+  double x0 = 0.0;
+  if (lane < 12) {
+    for (int q = 0; q < 12; ++q) {
+      const int k0 = lane > q ? lane : q;
+      double s = 0.0;
+      for (int k = k0; k < 12; ++k) s += L[k][lane] * L[k][q];
+      A[lane][q] = s;  // row `lane` is only read back by this lane below
+    }
+  }
+  __syncwarp();
+  for (int q = 0; q < 12; ++q) {
+    const double pq = __shfl_sync(0xffffffffu, ph, q);
+    const double bq = __shfl_sync(0xffffffffu, bpl, q);
+    if (lane < 12) {
+      double g = A[lane][q];
+      if (manifold == POVAR_SPHERE) g -= ph * pq;
+      G64[(size_t)i * 144 + lane * 12 + q] = g;
+      G32[(size_t)i * 144 + lane * 12 + q] = (float)g;
+      x0 -= g * bq;
+    }
+  }
+  if (lane < 12) {
+    Y[(size_t)i * 12 + lane] = (T)x0;
+    D[(size_t)i * 12 + lane] = (T)x0;
+  }
+  if (lane < 2) camnorm[2 * (size_t)i + lane] = 0.0;
+}
+
+}  // namespace
+
+povar_status launch_linearize(Problem* p, int precision, double eta) {
+  const unsigned g = grid_for(p->nchunks, 8);
+  if (g == 0) return POVAR_OK;
+  if (precision == POVAR_FP64) {
+    k_linearize<double><<<g, 256, 0, p->stream>>>(
+        p->state, eta, p->nchunks, p->chunk_cam, p->chunk_beg, p->cm_slot, p->cm_m64,
+        p->P64[0], p->P64[1], p->pdA[0], p->pdA[1], p->X64[0], p->X64[1],
+        static_cast<double*>(p->part_lin));
+  } else {
+    k_linearize<float><<<g, 256, 0, p->stream>>>(
+        p->state, eta, p->nchunks, p->chunk_cam, p->chunk_beg, p->cm_slot, p->cm_m32,
+        p->P64[0], p->P64[1], p->pdA[0], p->pdA[1], p->X64[0], p->X64[1],
+        static_cast<float*>(p->part_lin));
+  }
+  ++p->launches;
+  return check_launch(p, "linearize");
+}
+
+povar_status launch_camera_prepare(Problem* p, int precision, int manifold, double eta) {
+  const unsigned g = grid_for(p->nc, 4);
+  if (precision == POVAR_FP64) {
+    k_camera_prepare<double><<<g, 128, 0, p->stream>>>(
+        p->state, eta, manifold, p->nc, p->cam_nchunk, p->cam_chunk0,
+        static_cast<const double*>(p->part_lin), p->P64[0], p->P64[1], p->U64, p->bp64,
+        p->camP32, p->G64, p->G32, p->Y64, p->D64, p->camnorm);
+  } else {
+    k_camera_prepare<float><<<g, 128, 0, p->stream>>>(
+        p->state, eta, manifold, p->nc, p->cam_nchunk, p->cam_chunk0,
+        static_cast<const float*>(p->part_lin), p->P64[0], p->P64[1], p->U64, p->bp64,
+        p->camP32, p->G64, p->G32, p->Y32, p->D32, p->camnorm);
+  }
+  ++p->launches;
+  return check_launch(p, "camera_prepare");
+}
+
+}  // namespace povar

@@ -1,0 +1,189 @@
+// Internal declarations shared by the libpovar translation units.
+//
+// Data layout in device memory (one problem):
+//  * Observations are kept in two device orders built once by povar_create:
+//    - point-major "SELL-32" slices: landmarks are renumbered into slots
+//      sorted by track length (descending), 32 consecutive slots form a
+//      slice, and the t-th observation of the slot in lane l of slice s sits
+//      at sell_off[s] + 32 t + l. One thread owns one landmark; the loads of
+//      a warp are fully coalesced and the lanes of a slice have (nearly)
+//      equal track lengths, so there is no divergence.
+//    - camera-major list cut into chunks of <= CHUNK observations that never
+//      cross a camera boundary; one warp reduces one chunk with shuffles and
+//      the last warp of a camera (an atomic ticket) finishes the camera.
+//  * Per camera: P (FP64, double-buffered), the damped inverse G (FP64 and
+//    FP32), U and b_p (FP64), series vectors Y and delta (FP32 and FP64).
+//  * Per landmark slot: X (FP64, double-buffered), the lower-triangular
+//    factor F with F^T F = V^-1 (FP64 and FP32 copies), and the series
+//    record (s = V^-1 W^T y, X) written by the gather pass.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/povar.h"
+
+namespace povar {
+
+constexpr int SLICE = 32;        // landmarks per SELL slice (one warp)
+constexpr int CHUNK = 256;       // observations per camera-major chunk
+constexpr int LIN_ACC = 52;      // linearization accumulators per chunk
+constexpr int BLOCK = 256;       // threads per block for slot kernels
+constexpr double PINV_COND = 1e12;
+
+// Device-resident LM / VarPro controller state (one per problem).
+struct DeviceState {
+  double F;          // cost at the current iterate
+  double F_new;      // cost at the trial iterate
+  double pred;       // predicted decrease of the last step
+  double rho;        // gain ratio of the last step
+  double lam;        // damping for the next step
+  double nu;         // damping growth factor (Madsen-Nielsen)
+  double lam_used;   // damping of the last step
+  double tvt;        // sum_j ||F_j W^T delta||^2 of the last step
+  double ftol;       // relative-decrease stop threshold (0: none)
+  double target;     // target cost (<= 0: none)
+  int cur;           // index (0/1) of the current P / X buffers
+  int iteration;     // steps taken
+  int accepted;      // last step accepted
+  int need_lin;      // linearization must be recomputed
+  int converged;     // stop flag: every step kernel returns immediately
+  int stop_series;   // series early-stop flag (per step)
+  int terms_used;    // series terms used by the last step
+  int error;         // povar_status of a device-detected error
+  int max_iters;     // iteration cap for povar_solve (0: none)
+  int n_pinv;        // landmarks solved by pseudo-inverse at the last solve
+};
+
+// Host-side handle.
+struct Problem {
+  int32_t nc = 0, np = 0;
+  int64_t nobs = 0;
+  int32_t np_pad = 0, nslices = 0, nchunks = 0, nc_active = 0;
+  int64_t nsell = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int64_t launches = 0;
+  double eta_cur = -1.0;   // eta the landmarks / cost were solved for
+  bool fresh = true;       // next step re-initializes the damping
+  int last_precision = POVAR_MIXED_FP32;
+
+  // inputs (device)
+  int32_t* d_cam = nullptr;
+  int32_t* d_pt = nullptr;
+  double* d_meas = nullptr;
+  // orders (a1)
+  uint32_t* perm_pt = nullptr;
+  uint32_t* off_pt = nullptr;
+  uint32_t* perm_cam = nullptr;
+  uint32_t* off_cam = nullptr;
+  // SELL point-major layout
+  uint32_t* slot_pt = nullptr;    // [np_pad] landmark id of a slot (~0u: pad)
+  uint32_t* pt_slot = nullptr;    // [np]
+  uint32_t* slot_len = nullptr;   // [np_pad]
+  uint32_t* sell_off = nullptr;   // [nslices + 1]
+  int32_t* sell_cam = nullptr;    // [nsell] (-1: padding)
+  float2* sell_m32 = nullptr;
+  double2* sell_m64 = nullptr;
+  // camera-major list
+  uint32_t* cm_slot = nullptr;    // [nobs]
+  float2* cm_m32 = nullptr;
+  double2* cm_m64 = nullptr;
+  uint32_t* chunk_beg = nullptr;  // [nchunks + 1]
+  int32_t* chunk_cam = nullptr;   // [nchunks]
+  int32_t* cam_nchunk = nullptr;  // [nc]
+  int32_t* cam_chunk0 = nullptr;  // [nc]
+  uint32_t* cam_ticket = nullptr; // [nc]
+  uint32_t* done_ticket = nullptr;// [1]
+  // cameras
+  double* P64[2] = {nullptr, nullptr};  // [nc*12]
+  double* Ltab = nullptr;               // [nc*48] landmark tables at trial P
+  float* camP32 = nullptr;              // [nc*12] current P, FP32
+  double* U64 = nullptr;                // [nc*144]
+  double* bp64 = nullptr;               // [nc*12]
+  double* G64 = nullptr;                // [nc*144]
+  float* G32 = nullptr;                 // [nc*144]
+  float* Y32 = nullptr;                 // [nc*12]
+  float* D32 = nullptr;                 // [nc*12]
+  double* Y64 = nullptr;
+  double* D64 = nullptr;
+  double* camnorm = nullptr;            // [nc*2]
+  void* part_lin = nullptr;             // [nchunks*LIN_ACC] float or double
+  void* part_ser = nullptr;             // [nchunks*12] float or double
+  // landmark slots
+  double* X64[2] = {nullptr, nullptr};  // [np_pad*3]
+  double* F64[2] = {nullptr, nullptr};  // [np_pad*6] factor F (V^-1 = F^T F)
+  float4* pdA[2] = {nullptr, nullptr};  // (X0, X1, X2, F00)
+  float4* pdB[2] = {nullptr, nullptr};  // (F10, F11, F20, F21)
+  float* pdC[2] = {nullptr, nullptr};   // F22
+  float4* rec32 = nullptr;              // [np_pad*2] (s0 s1 s2 X0)(X1 X2 - -)
+  double2* rec64 = nullptr;             // [np_pad*4] (s0 s1)(s2 X0)(X1 X2)(- -)
+  double* cost_part = nullptr;          // [n slot blocks]
+  double* pred_part = nullptr;          // [n slot blocks]
+  int* pinv_part = nullptr;             // [n slot blocks]
+  int32_t n_slot_blocks = 0;
+  // controller
+  DeviceState* state = nullptr;
+  DeviceState* h_state = nullptr;       // pinned mirror
+  povar_step_report* d_report = nullptr;
+  povar_step_report* h_report = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<void*> allocs;            // every device allocation, freed by destroy
+};
+
+// ------------------------------------------------------------------ helpers
+#define POVAR_CUDA(call)                                                     \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      return ::povar::fail(p, POVAR_ECUDA,                                   \
+                           std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                        \
+  } while (0)
+
+povar_status fail(Problem* p, povar_status s, const std::string& msg);
+povar_status check_launch(Problem* p, const char* what);
+
+// cudaMalloc tracked by the handle (freed by povar_destroy).
+povar_status dev_alloc_bytes(Problem* p, void** ptr, size_t bytes, const char* what);
+template <class T>
+inline povar_status dev_alloc(Problem* p, T** ptr, size_t count, const char* what) {
+  return dev_alloc_bytes(p, reinterpret_cast<void**>(ptr), count * sizeof(T), what);
+}
+
+inline unsigned grid_for(int64_t n, int block) {
+  return (unsigned)((n + block - 1) / block);
+}
+
+// --------------------------------------------------------- csr.cu (a1)
+povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt);
+
+// ---------------------------------------------------- landmark.cu (a2,a3)
+// Landmark tables of the cameras in buffer `which_rel` (0: current, 1: trial)
+// and the closed-form landmarks + cost at those cameras.
+povar_status launch_landmarks(Problem* p, int which_rel, double eta);
+// Reduce the cost partials into state.F (which_rel 0) or state.F_new (1).
+povar_status launch_cost_finish(Problem* p, int which_rel);
+
+// ------------------------------------------------- linearize.cu (a4,a5,a6)
+povar_status launch_linearize(Problem* p, int precision, double eta);
+povar_status launch_camera_prepare(Problem* p, int precision, int manifold,
+                                   double eta);
+
+// ---------------------------------------------------- series.cu (a7,a8)
+povar_status launch_series_term(Problem* p, int precision, double eta,
+                                int term, double eps);
+povar_status launch_pred(Problem* p, int precision, double eta, int manifold, int m);
+
+// ---------------------------------------------------- step.cu (a9,a10)
+povar_status launch_update(Problem* p, int precision, int manifold);
+povar_status launch_controller(Problem* p);
+povar_status launch_init_state(Problem* p, double lambda0, int reset_lm, int reset_all);
+povar_status launch_begin(Problem* p, double ftol, double target, int max_iters);
+povar_status launch_random_cameras(Problem* p, uint64_t seed, int normalize);
+povar_status launch_gather_points(Problem* p, double* d_out);
+
+}  // namespace povar

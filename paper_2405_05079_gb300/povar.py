@@ -1,0 +1,221 @@
+"""Thin ctypes binding of libpovar (C ABI in include/povar.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels. The library is loaded from this package directory (built in-tree by
+``paper_2405_05079_gb300.build``); if it is missing the binding raises -- there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpovar.so")
+
+EUCLID, SPHERE = 0, 1
+FP64, MIXED_FP32 = 0, 1
+
+STATUS = {0: "POVAR_OK", 1: "POVAR_EINVAL", 2: "POVAR_ENOMEM", 3: "POVAR_ECUDA",
+          4: "POVAR_ENUMERIC", 5: "POVAR_ETIMEOUT", 6: "POVAR_ENOTCONVERGED"}
+
+
+class PovarError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("eta", C.c_double), ("lambda0", C.c_double), ("series_eps", C.c_double),
+                ("lambda_l", C.c_double), ("m", C.c_int32), ("manifold", C.c_int32),
+                ("precision", C.c_int32), ("schedule", C.c_int32)]
+
+
+class StepReport(C.Structure):
+    _fields_ = [("cost_before", C.c_double), ("cost_after", C.c_double), ("pred", C.c_double),
+                ("rho", C.c_double), ("lambda_used", C.c_double), ("lambda_next", C.c_double),
+                ("accepted", C.c_int32), ("terms_used", C.c_int32), ("iteration", C.c_int32),
+                ("converged", C.c_int32), ("ms", C.c_float), ("reserved", C.c_float * 3)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libpovar.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"{LIB_PATH} not found: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dp, u64 = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double), C.c_uint64
+    L.povar_create.argtypes = [i32, i32, i64, C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp, vp,
+                               C.POINTER(vp)]
+    L.povar_destroy.argtypes = [vp]
+    L.povar_destroy.restype = None
+    L.povar_last_error.argtypes = [vp]
+    L.povar_last_error.restype = C.c_char_p
+    L.povar_set_cameras.argtypes = [vp, dp, C.c_double]
+    L.povar_init_random.argtypes = [vp, u64, i32, C.c_double]
+    L.povar_get_cameras.argtypes = [vp, dp]
+    L.povar_get_points.argtypes = [vp, dp]
+    L.povar_cost.argtypes = [vp, C.c_double, dp]
+    L.povar_step.argtypes = [vp, C.POINTER(Params), C.POINTER(StepReport)]
+    L.povar_solve.argtypes = [vp, C.POINTER(Params), i32, C.c_double, C.c_double,
+                              C.POINTER(StepReport), C.POINTER(C.c_int32)]
+    u32p = C.POINTER(C.c_uint32)
+    L.povar_get_orders.argtypes = [vp, u32p, u32p, u32p, u32p]
+    L.povar_get_last_step.argtypes = [vp, dp, dp, dp]
+    L.povar_launch_count.argtypes = [vp]
+    L.povar_launch_count.restype = i64
+    L.povar_version.restype = C.c_char_p
+    for name in ("povar_create", "povar_set_cameras", "povar_init_random", "povar_get_cameras",
+                 "povar_get_points", "povar_cost", "povar_step", "povar_solve",
+                 "povar_get_orders", "povar_get_last_step"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def make_params(eta=0.1, lambda0=1e-4, m=10, series_eps=0.0, manifold=SPHERE,
+                precision=MIXED_FP32, schedule=-1) -> Params:
+    return Params(eta=eta, lambda0=lambda0, series_eps=series_eps, lambda_l=0.0, m=m,
+                  manifold=manifold, precision=precision, schedule=schedule)
+
+
+def current_stream_handle() -> int | None:
+    """The current torch CUDA stream as a raw cudaStream_t (None without torch/CUDA)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover - torch is optional for the binding
+        pass
+    return None
+
+
+class Problem:
+    """Owns a ``povar_problem`` handle. Arrays in and out are host numpy arrays."""
+
+    def __init__(self, n_cams: int, n_points: int, cam_idx, pt_idx, meas, stream=None):
+        L = lib()
+        self.n_cams, self.n_points = int(n_cams), int(n_points)
+        cam = np.ascontiguousarray(cam_idx, dtype=np.int32)
+        pt = np.ascontiguousarray(pt_idx, dtype=np.int32)
+        m = np.ascontiguousarray(meas, dtype=np.float64).reshape(-1, 2)
+        self.n_obs = int(cam.shape[0])
+        h = C.c_void_p()
+        st = L.povar_create(self.n_cams, self.n_points, self.n_obs, _ptr(cam, C.c_int32),
+                            _ptr(pt, C.c_int32), _ptr(m, C.c_double),
+                            C.c_void_p(stream) if stream else None, C.byref(h))
+        if st != 0:
+            raise PovarError(st, "povar_create failed")
+        self._h = h
+
+    @classmethod
+    def from_scene(cls, scene, stream=None) -> "Problem":
+        return cls(scene.n_cams, scene.n_points, scene.cam_idx, scene.pt_idx, scene.meas,
+                   stream=stream)
+
+    def _check(self, st: int):
+        if st != 0:
+            raise PovarError(st, lib().povar_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().povar_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_cameras(self, P, eta: float):
+        P = np.ascontiguousarray(P, dtype=np.float64).reshape(self.n_cams, 12)
+        self._check(lib().povar_set_cameras(self._h, _ptr(P, C.c_double), eta))
+
+    def init_random(self, seed: int, manifold: int, eta: float):
+        self._check(lib().povar_init_random(self._h, seed, manifold, eta))
+
+    def cameras(self) -> np.ndarray:
+        out = np.empty((self.n_cams, 12))
+        self._check(lib().povar_get_cameras(self._h, _ptr(out, C.c_double)))
+        return out
+
+    def points(self) -> np.ndarray:
+        out = np.empty((self.n_points, 3))
+        self._check(lib().povar_get_points(self._h, _ptr(out, C.c_double)))
+        return out
+
+    def cost(self, eta: float) -> float:
+        v = C.c_double()
+        self._check(lib().povar_cost(self._h, eta, C.byref(v)))
+        return v.value
+
+    def step(self, params: Params) -> StepReport:
+        rep = StepReport()
+        self._check(lib().povar_step(self._h, C.byref(params), C.byref(rep)))
+        return rep
+
+    def solve(self, params: Params, max_iters=50, ftol=1e-6, target_cost=0.0):
+        rep = StepReport()
+        it = C.c_int32()
+        self._check(lib().povar_solve(self._h, C.byref(params), max_iters, ftol, target_cost,
+                                      C.byref(rep), C.byref(it)))
+        return rep, it.value
+
+    def orders(self):
+        no, np_, nc = self.n_obs, self.n_points, self.n_cams
+        pp = np.empty(no, np.uint32)
+        op = np.empty(np_ + 1, np.uint32)
+        pc = np.empty(no, np.uint32)
+        oc = np.empty(nc + 1, np.uint32)
+        self._check(lib().povar_get_orders(self._h, _ptr(pp, C.c_uint32), _ptr(op, C.c_uint32),
+                                           _ptr(pc, C.c_uint32), _ptr(oc, C.c_uint32)))
+        return pp, op, pc, oc
+
+    def last_step(self):
+        U = np.empty((self.n_cams, 12, 12))
+        bp = np.empty((self.n_cams, 12))
+        d = np.empty((self.n_cams, 12))
+        self._check(lib().povar_get_last_step(self._h, _ptr(U, C.c_double),
+                                              _ptr(bp, C.c_double), _ptr(d, C.c_double)))
+        return U, bp, d
+
+    @property
+    def launch_count(self) -> int:
+        return int(lib().povar_launch_count(self._h))
+
+
+@dataclasses.dataclass
+class SolveResult:
+    report: dict
+    iterations: int
+    cameras: np.ndarray
+    points: np.ndarray
+
+
+def version() -> str:
+    return lib().povar_version().decode()

@@ -1,0 +1,294 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances:
+* integer work (observation orders): bit-exact against a CPU stable sort;
+* FP64 GPU path: 1e-10 relative per step (landmarks, cost, U, b_p, the series
+  step delta, trial cameras, predicted decrease);
+* mixed FP32 path: per step 1e-4 relative on the step (FP32 series), and the
+  converged cost within 1e-5 relative of the oracle's converged cost with
+  normalized cameras within 1e-4.
+"""
+import numpy as np
+import pytest
+
+from oracle import povar_oracle as O
+from paper_2405_05079_gb300 import povar, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def oracle_for(sc):
+    return O.Problem(sc.n_cams, sc.n_points, sc.cam_idx, sc.pt_idx, sc.meas)
+
+
+def ragged_scene():
+    """Edge cases in one scene: 77 landmarks (not a multiple of 32 or 256),
+    one landmark seen by every camera, a camera with no observation, tracks
+    of length 2..12 (ragged SELL slices), landmarks seen only twice."""
+    base = scenes.ring_scene(13, 77, 21, track="uniform3to6", noise_px=1.0, eta=0.2)
+    cam, pt, meas = list(base.cam_idx), list(base.pt_idx), list(base.meas)
+    keep = [k for k in range(len(cam)) if cam[k] != 5]   # camera 5: no observation
+    cam = [cam[k] for k in keep]
+    pt = [pt[k] for k in keep]
+    meas = [meas[k] for k in keep]
+    # landmark 0 seen by every camera except 5 (track length 12)
+    gtc = base.gt_cams
+    X0 = base.gt_points[0]
+    have = {c for c, p in zip(cam, pt) if p == 0}
+    for c in range(13):
+        if c == 5 or c in have:
+            continue
+        y = gtc[c] @ np.r_[X0, 1.0]
+        cam.append(c)
+        pt.append(0)
+        meas.append(y[:2] / y[2])
+    sc = scenes.Scene(name="ragged", seed=21, n_cams=13, n_points=77,
+                      cam_idx=np.array(cam, np.int32), pt_idx=np.array(pt, np.int32),
+                      meas=np.array(meas), eta=0.2, m=8, gt_cams=gtc,
+                      gt_points=base.gt_points)
+    assert np.bincount(sc.pt_idx, minlength=77).min() >= 2
+    assert np.bincount(sc.cam_idx, minlength=13)[5] == 0
+    return sc
+
+
+SCENES = {
+    "tiny": lambda: scenes.tiny_scene(0),
+    "mid": lambda: scenes.mid_scene(0),
+    "ragged": ragged_scene,
+}
+
+
+@pytest.fixture(scope="module", params=list(SCENES))
+def scene(request):
+    return SCENES[request.param]()
+
+
+# ---------------------------------------------------------------- a1 orders
+
+def test_orders_bit_exact(scene):
+    with povar.Problem.from_scene(scene) as pb:
+        pp, op, pc, oc = pb.orders()
+    ref_pp = np.argsort(scene.pt_idx, kind="stable")
+    ref_pc = np.argsort(scene.cam_idx, kind="stable")
+    assert np.array_equal(pp, ref_pp)
+    assert np.array_equal(pc, ref_pc)
+    assert np.array_equal(op, np.searchsorted(scene.pt_idx[ref_pp], np.arange(scene.n_points + 1)))
+    assert np.array_equal(oc, np.searchsorted(scene.cam_idx[ref_pc], np.arange(scene.n_cams + 1)))
+
+
+def test_orders_large_keys_bit_exact():
+    """Keys needing three radix passes, many tiles and a ragged last tile."""
+    rng = np.random.default_rng(5)
+    n_pts, n_cams = 70_001, 300
+    pt = np.concatenate([np.arange(n_pts), rng.integers(0, n_pts, 130_003)]).astype(np.int32)
+    rng.shuffle(pt)
+    cam = rng.integers(0, n_cams, pt.size).astype(np.int32)
+    meas = rng.uniform(-1, 1, (pt.size, 2))
+    with povar.Problem(n_cams, n_pts, cam, pt, meas) as pb:
+        pp, op, pc, oc = pb.orders()
+    assert np.array_equal(pp, np.argsort(pt, kind="stable"))
+    assert np.array_equal(pc, np.argsort(cam, kind="stable"))
+
+
+def test_create_rejects_invalid_input():
+    cam = np.array([0, 1, 2], np.int32)
+    pt = np.array([0, 0, 1], np.int32)
+    meas = np.zeros((3, 2))
+    with pytest.raises(povar.PovarError):
+        povar.Problem(3, 3, cam, pt, meas)          # landmark 2 unobserved
+    with pytest.raises(povar.PovarError):
+        povar.Problem(2, 2, cam, pt, meas)          # camera index out of range
+    bad = meas.copy()
+    bad[1, 0] = np.nan
+    with pytest.raises(povar.PovarError):
+        povar.Problem(3, 2, cam, pt, bad)           # non-finite measurement
+
+
+# ---------------------------------------------------------------- a2 / a3
+
+@pytest.mark.parametrize("normalize", [True, False])
+def test_landmarks_and_cost_fp64(scene, normalize):
+    P0 = scenes.init_cameras(scene.n_cams, 3, normalize=normalize)
+    orc = oracle_for(scene)
+    X = orc.landmarks(P0, scene.eta)
+    F = orc.cost(P0, X, scene.eta)
+    with povar.Problem.from_scene(scene) as pb:
+        pb.set_cameras(P0, scene.eta)
+        Xg = pb.points()
+        Fg = pb.cost(scene.eta)
+        # a different eta re-solves the landmarks
+        Fg2 = pb.cost(0.5)
+    assert rel(Xg, X) <= 1e-10
+    assert abs(Fg - F) <= 1e-10 * F
+    X2 = orc.landmarks(P0, 0.5)
+    assert abs(Fg2 - orc.cost(P0, X2, 0.5)) <= 1e-10 * Fg2
+
+
+# ---------------------------------------------------------------- one step, FP64
+
+@pytest.mark.parametrize("manifold", [O.SPHERE, O.EUCLID])
+def test_one_step_fp64_matches_oracle(scene, manifold):
+    P0 = scenes.init_cameras(scene.n_cams, 4, normalize=True)
+    orc = oracle_for(scene)
+    m = scene.m
+    op = O.Params(eta=scene.eta, m=m, manifold=manifold, series_eps=0.0, lambda0=1e-4)
+    st = orc.init_state(P0, op)
+    ne = orc.normal_equations(st.P, st.X, scene.eta)
+    _, orep = orc.step(st, op)
+    with povar.Problem.from_scene(scene) as pb:
+        pb.set_cameras(P0, scene.eta)
+        rep = pb.step(povar.make_params(eta=scene.eta, m=m, manifold=manifold,
+                                        precision=povar.FP64, lambda0=1e-4))
+        U, bp, d = pb.last_step()
+    assert rel(U, ne.U) <= 1e-10
+    assert rel(bp, ne.b_p.reshape(-1, 12)) <= 1e-10
+    assert rel(d, orep.delta) <= 1e-10
+    assert abs(rep.cost_before - orep.cost_before) <= 1e-10 * orep.cost_before
+    assert abs(rep.cost_after - orep.cost_after) <= 1e-10 * orep.cost_after
+    assert abs(rep.pred - orep.pred) <= 1e-9 * abs(orep.pred)
+    assert rep.accepted == int(orep.accepted)
+    assert rep.terms_used == m
+    assert abs(rep.lambda_next - orep.lambda_next) <= 1e-9 * orep.lambda_next
+
+
+def test_trajectory_fp64_matches_oracle():
+    """Ten damped steps (accepts and rejects) stay at 1e-10 relative per step."""
+    sc = scenes.tiny_scene(0)
+    P0 = scenes.init_cameras(sc.n_cams, 1, normalize=True)
+    orc = oracle_for(sc)
+    op = O.Params(eta=sc.eta, m=sc.m, manifold=O.SPHERE)
+    st = orc.init_state(P0, op)
+    prm = povar.make_params(eta=sc.eta, m=sc.m, manifold=povar.SPHERE, precision=povar.FP64)
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        for _ in range(10):
+            st, orep = orc.step(st, op)
+            rep = pb.step(prm)
+            assert rep.accepted == int(orep.accepted)
+            assert abs(rep.cost_after - orep.cost_after) <= 1e-10 * orep.cost_after
+            assert rel(pb.cameras(), st.P) <= 1e-10
+
+
+def test_series_early_stop_matches_oracle():
+    sc = scenes.tiny_scene(0)
+    P0 = scenes.init_cameras(sc.n_cams, 2, normalize=True)
+    orc = oracle_for(sc)
+    op = O.Params(eta=sc.eta, m=40, manifold=O.SPHERE, series_eps=0.01)
+    st = orc.init_state(P0, op)
+    _, orep = orc.step(st, op)
+    assert orep.terms_used < 40
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        rep = pb.step(povar.make_params(eta=sc.eta, m=40, series_eps=0.01,
+                                        manifold=povar.SPHERE, precision=povar.FP64))
+        _, _, d = pb.last_step()
+    assert rep.terms_used == orep.terms_used
+    assert rel(d, orep.delta) <= 1e-10
+
+
+def test_single_term_is_block_jacobi():
+    """m = 1: the step is U~^-1 g (no series term runs)."""
+    sc = scenes.tiny_scene(0)
+    P0 = scenes.init_cameras(sc.n_cams, 6, normalize=True)
+    orc = oracle_for(sc)
+    op = O.Params(eta=sc.eta, m=1, manifold=O.SPHERE)
+    _, orep = orc.step(orc.init_state(P0, op), op)
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        pb.step(povar.make_params(eta=sc.eta, m=1, manifold=povar.SPHERE, precision=povar.FP64))
+        _, _, d = pb.last_step()
+    assert rel(d, orep.delta) <= 1e-10
+
+
+# ---------------------------------------------------------------- mixed precision
+
+@pytest.mark.parametrize("manifold", [O.SPHERE, O.EUCLID])
+def test_one_step_mixed_close_to_oracle(scene, manifold):
+    P0 = scenes.init_cameras(scene.n_cams, 4, normalize=True)
+    orc = oracle_for(scene)
+    op = O.Params(eta=scene.eta, m=scene.m, manifold=manifold)
+    _, orep = orc.step(orc.init_state(P0, op), op)
+    with povar.Problem.from_scene(scene) as pb:
+        pb.set_cameras(P0, scene.eta)
+        rep = pb.step(povar.make_params(eta=scene.eta, m=scene.m, manifold=manifold,
+                                        precision=povar.MIXED_FP32))
+        _, _, d = pb.last_step()
+    assert rel(d, orep.delta) <= 1e-3
+    assert abs(rep.cost_before - orep.cost_before) <= 1e-10 * orep.cost_before
+    assert abs(rep.cost_after - orep.cost_after) <= 1e-4 * orep.cost_after
+
+
+@pytest.mark.parametrize("name", ["tiny", "mid"])
+def test_solve_reaches_oracle_converged_cost(name):
+    """Both GPU precisions, run to convergence from the same start as the
+    oracle's stored converged solution (tests/golden/converged_<name>.json,
+    written by tests/golden/make_golden.py from the oracle only), reach its
+    cost within 1e-5 relative, with normalized cameras within 1e-4."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    f"converged_{name}.json")))
+    sc = scenes.scene_by_name(name, g["scene_seed"])
+    P0 = scenes.init_cameras(sc.n_cams, g["init_seed"], normalize=True)
+    Fstar = g["series"]["F"]
+    Po = np.array(g["series"]["P"])
+    Po /= np.linalg.norm(Po, axis=1, keepdims=True)
+    for prec in (povar.FP64, povar.MIXED_FP32):
+        with povar.Problem.from_scene(sc) as pb:
+            pb.set_cameras(P0, sc.eta)
+            pb.solve(povar.make_params(eta=sc.eta, m=sc.m, manifold=povar.SPHERE,
+                                       precision=prec, lambda0=g["lambda0"]),
+                     max_iters=g["series"]["iterations"] + 200, ftol=g["ftol"])
+            F = pb.cost(sc.eta)
+            P = pb.cameras()
+        assert abs(F - Fstar) <= 1e-5 * Fstar, (prec, F, Fstar)
+        Pn = P / np.linalg.norm(P, axis=1, keepdims=True)
+        assert np.abs(Pn - Po).max() <= 1e-4, (prec, np.abs(Pn - Po).max())
+
+
+# ---------------------------------------------------------------- init_random
+
+def philox4x32_10(ctr, key):
+    """Numpy Philox4x32-10 (Salmon et al., SC'11) for checking the device RNG."""
+    M0, M1, W0, W1 = 0xD2511F53, 0xCD9E8D57, 0x9E3779B9, 0xBB67AE85
+    c = [int(x) for x in ctr]
+    k0, k1 = int(key[0]), int(key[1])
+    for _ in range(10):
+        p0 = M0 * c[0]
+        p1 = M1 * c[2]
+        c = [((p1 >> 32) ^ c[1] ^ k0) & 0xFFFFFFFF, p1 & 0xFFFFFFFF,
+             ((p0 >> 32) ^ c[3] ^ k1) & 0xFFFFFFFF, p0 & 0xFFFFFFFF]
+        k0 = (k0 + W0) & 0xFFFFFFFF
+        k1 = (k1 + W1) & 0xFFFFFFFF
+    return c
+
+
+def test_init_random_philox_box_muller():
+    sc = scenes.tiny_scene(0)
+    seed = 0x1234_5678_9ABC
+    with povar.Problem.from_scene(sc) as pb:
+        pb.init_random(seed, povar.EUCLID, sc.eta)
+        P = pb.cameras()
+        pb.init_random(seed, povar.SPHERE, sc.eta)
+        Ps = pb.cameras()
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    ref = np.empty((sc.n_cams, 12))
+    for i in range(sc.n_cams):
+        z = []
+        for q in range(3):
+            w = philox4x32_10((i, q, 0, 0), key)
+            for h in range(2):
+                u1 = (w[2 * h] + 1.0) * 2.0 ** -32
+                u2 = (w[2 * h + 1] + 1.0) * 2.0 ** -32
+                r = np.sqrt(-2.0 * np.log(u1))
+                z += [r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)]
+        ref[i] = z
+    assert np.allclose(P, ref, rtol=1e-12, atol=1e-12)
+    assert np.allclose(Ps, ref / np.linalg.norm(ref, axis=1, keepdims=True), rtol=1e-12,
+                       atol=1e-12)

@@ -1,0 +1,48 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point that include/povar.h declares (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "povar.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(povar_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2405_05079_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("povar_create", "povar_destroy", "povar_step", "povar_solve", "povar_cost",
+              "povar_set_cameras", "povar_init_random", "povar_get_cameras",
+              "povar_get_points", "povar_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_version_string_without_gpu(libpath):
+    from paper_2405_05079_gb300 import povar
+    assert "sm_103a" in povar.version()
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2405_05079_gb300 import povar
+    monkeypatch.setattr(povar, "_lib", None)
+    monkeypatch.setattr(povar, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not found"):
+        povar.lib()
