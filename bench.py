@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark: time to 1e-5 relative pOSE cost of the PoVar solver on GB300.
+
+One timed step is one full first-stage solve of the large synthetic scene
+(1,800 cameras on a trajectory, 1,000,000 landmarks, ~5,000,000 observations,
+0.5 px noise, 1% outliers; a stand-in for BAL venice-1672) from the random
+camera initialization of the paper's experiments until the pOSE cost is
+within 1e-5 relative of F*, the FP64 CPU oracle's converged cost from the same
+start (tests/golden/converged_large.json). Solver settings follow Sec. 5.2 of
+the paper: eta = 0.1, lambda0 = 1e-4, series order 20 (m = 21 terms) with
+threshold 0.01; mixed precision (FP32 series / linearization, FP64 landmark
+elimination, 12x12 inverses, cost and gain ratio).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun (N > 1) every rank solves its
+own replica of the workload (the solve does not shard: replicas only).
+"""
+from __future__ import annotations
+
+import os
+
+_CORES = os.cpu_count() or 1
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, str(_CORES))
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import re  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2405_05079_gb300 import scenes  # noqa: E402
+
+METRIC = "time to 1e-5 rel pOSE cost"
+REL_TARGET = 1e-5
+SAMPLE_POINTS = 20_000          # landmarks in the CPU-oracle sample
+
+
+def workload_scene(name: str):
+    return scenes.scene_by_name(name, 0)
+
+
+def load_golden(name: str) -> dict:
+    path = os.path.join(ROOT, "tests", "golden", f"converged_{name}.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+def oracle_iters_to_target(g: dict, target: float) -> int:
+    for i, (F, _, _) in enumerate(g["series"]["trace"]):
+        if F <= target:
+            return i + 1
+    return len(g["series"]["trace"])
+
+
+def solver_params(povar, g: dict, precision: int):
+    return povar.make_params(eta=g["eta"], lambda0=g["lambda0"], m=g["m"],
+                             series_eps=g["series_eps"], manifold=povar.EUCLID,
+                             precision=precision)
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        try:
+            rows = [ln.split(",") for ln in open(self.path).read().strip().splitlines()]
+        except OSError:
+            rows = []
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- roofline
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def series_bytes_per_term(n_obs: int, n_points: int) -> int:
+    """Algorithmic bytes of one series term in FP32: per observation a 4-byte
+    camera index and an 8-byte measurement; per landmark X (12 B), the
+    factor of V^-1 (24 B) and a 4-byte offset."""
+    return 12 * n_obs + 40 * n_points
+
+
+def landmark_flops_per_launch(n_obs: int, n_points: int) -> int:
+    """FP64 operations of one landmark + cost launch: 38 per observation for
+    V_j and h_j, 24 per observation for the residual and cost, ~60 per
+    landmark for the Cholesky solve and the factor."""
+    return 62 * n_obs + 60 * n_points
+
+
+def ncu_traffic(kernel_file: str, key: str):
+    """Per-launch DRAM bytes recorded in profiles/ for a kernel source, or None
+    when the source changed since the capture."""
+    prof = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    src = os.path.join(ROOT, "paper_2405_05079_gb300", "csrc", kernel_file)
+    try:
+        text = open(prof).read()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m = re.search(rf"^{key}\s+sha={h}\s+bytes_per_launch=(\d+)", text, re.M)
+    return int(m.group(1)) if m else None
+
+
+# ----------------------------------------------------------------- CPU oracle sample
+
+def cpu_oracle_sample(scene, g: dict, target: float, steps: int = 2) -> dict:
+    """Time the FP64 CPU oracle (matrix-free step, as it stands) on a bounded
+    sample of the workload: SAMPLE_POINTS landmarks with all their
+    observations and every camera. The per-step time is scaled by the
+    observation count to the full scene and multiplied by the number of
+    oracle iterations the converged reference needed to reach the target."""
+    from oracle import povar_oracle as O
+    rng = np.random.default_rng(7)
+    keep = np.sort(rng.choice(scene.n_points, size=min(SAMPLE_POINTS, scene.n_points),
+                              replace=False))
+    sub = scene.subset_points(keep)
+    P0 = scenes.init_cameras(scene.n_cams, 1, normalize=True)
+    pr = O.MatrixFreeProblem(sub.n_cams, sub.n_points, sub.cam_idx, sub.pt_idx, sub.meas)
+    prm = O.Params(eta=g["eta"], m=g["m"], series_eps=g["series_eps"], manifold=O.EUCLID,
+                   lambda0=g["lambda0"])
+    t0 = time.perf_counter()
+    st = pr.init_state(P0, prm)
+    per = []
+    for _ in range(steps):
+        t = time.perf_counter()
+        st, _ = pr.step(st, prm)
+        per.append(time.perf_counter() - t)
+    wall = time.perf_counter() - t0
+    sec_step = float(np.median(per)) * scene.n_obs / sub.n_obs
+    iters = oracle_iters_to_target(g, target)
+    return {"value": sec_step * iters, "unit": "s", "cores": _CORES, "kind": "oracle",
+            "sample": (f"FP64 numpy oracle (matrix-free step) on {sub.n_points} of "
+                       f"{scene.n_points} landmarks ({sub.n_obs} of {scene.n_obs} obs, all "
+                       f"{scene.n_cams} cameras): median of {steps} LM steps "
+                       f"= {np.median(per):.3f} s, scaled x{scene.n_obs / sub.n_obs:.1f} by "
+                       f"observations, x{iters} oracle iterations to target; "
+                       f"{wall:.1f} s of CPU work; BLAS threads {_CORES}"),
+            "sec_per_step_full": sec_step, "iters": iters}
+
+
+# ----------------------------------------------------------------- our arm
+
+def run_ours(args, rank: int, world: int) -> dict | None:
+    import torch
+    from paper_2405_05079_gb300 import povar
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sc = workload_scene(args.workload)
+    g = load_golden(args.workload)
+    Fstar = g["series"]["F"]
+    target = Fstar * (1.0 + REL_TARGET)
+    P0 = scenes.init_cameras(sc.n_cams, g["init_seed"], normalize=True)
+    stream = torch.cuda.current_stream(dev)
+    prec = povar.FP64 if args.precision == "fp64" else povar.MIXED_FP32
+    params = solver_params(povar, g, prec)
+    pb = povar.Problem.from_scene(sc, stream=stream.cuda_stream)
+    dP0 = torch.tensor(P0, dtype=torch.float64, device=dev)
+    pb.set_profiling(True)
+
+    def one_solve():
+        pb.set_cameras_device(dP0.data_ptr(), g["eta"])
+        rep, iters = pb.solve(params, max_iters=args.max_iters, ftol=0.0, target_cost=target)
+        return rep, iters
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize(dev)
+    pb.profile(reset=True)
+    launches0 = pb.launch_count
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    results = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev.index) as clk:
+        ev[0].record(stream)
+        for k in range(args.steps):
+            rep, iters = one_solve()
+            ev[k + 1].record(stream)
+            results.append((rep.cost_after if rep.accepted else rep.cost_before, iters,
+                            rep.terms_used))
+        torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    launches = pb.launch_count - launches0
+    per_solve = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    phases, nsteps = pb.profile(reset=True)
+    clocks = clk.summary()
+    final_cost = pb.cost(g["eta"])
+
+    # ---- e2e: the user's call sequence with host buffers
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        times = []
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            with povar.Problem.from_scene(sc, stream=stream.cuda_stream) as q:
+                q.set_cameras(P0, g["eta"])
+                q.solve(params, max_iters=args.max_iters, ftol=0.0, target_cost=target)
+                Pout = q.cameras()
+                Fout = q.cost(g["eta"])
+            times.append(time.perf_counter() - t0)
+            assert np.isfinite(Pout).all() and np.isfinite(Fout)
+        h2d = sc.n_obs * (4 + 4 + 16) + sc.n_cams * 96
+        d2h = sc.n_cams * 96 + 8
+        e2e = {"value": float(np.mean(times)), "unit": "s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "note": "povar_create (H2D + observation orders) + set_cameras + solve + "
+                       "get_cameras + cost, host arrays, wall clock"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+    pk = measured_peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    iters_total = sum(r[1] for r in results)
+    steps_timed = max(nsteps, 1)
+    ms_series = phases["series"]
+    # series terms actually run per LM step (early stop by threshold)
+    terms_per_step = float(np.mean([r[2] for r in results])) if results else float(params.m)
+    bytes_term = series_bytes_per_term(sc.n_obs, sc.n_points)
+    series_gbs = (bytes_term * max(terms_per_step - 1, 1) * steps_timed) / (ms_series * 1e-3) / 1e9
+    flops_lm = landmark_flops_per_launch(sc.n_obs, sc.n_points)
+    lm_gflops = flops_lm * steps_timed / (phases["landmarks"] * 1e-3) / 1e9
+    fp64_peak = 1250.0   # GFLOP/s: nominal GB300 FP64 (152 SMs x 2 FMA/clk at max clock)
+    roof_series = {"bound": "hbm", "achieved": round(series_gbs, 1), "peak": hbm,
+                   "unit": "GB/s", "frac": round(series_gbs / hbm, 4),
+                   "traffic": ncu_traffic("series.cu", "series_term"),
+                   "kernel": "series term (k_series_gather + k_series_scatter)",
+                   "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
+                   "frac_of_8TBs": round(series_gbs / 8000.0, 4)}
+    roof_lm = {"bound": "alu", "achieved": round(lm_gflops, 1), "peak": fp64_peak,
+               "unit": "GFLOP/s", "frac": round(lm_gflops / fp64_peak, 4),
+               "traffic": ncu_traffic("landmark.cu", "landmark"),
+               "kernel": "k_landmark (FP64 landmark elimination + cost)",
+               "peak_source": "nominal FP64 of the recipe (1.25 TFLOP/s)"}
+    dominant = roof_series if ms_series >= phases["landmarks"] else roof_lm
+    secs = total_ms / 1e3 / args.steps
+    reached = all(r[0] <= target for r in results)
+    out = {
+        "metric": METRIC, "value": round(secs, 5), "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == povar.MIXED_FP32 else "f64", "data": "synthetic",
+        "config": {"workload": (f"{args.workload}: {sc.n_cams} cams, {sc.n_points} landmarks, "
+                                f"{sc.n_obs} obs (trajectory scene, 1% outliers)"),
+                   "precision": args.precision, "manifold": "euclid (first stage, Sec. 3.2)",
+                   "eta": g["eta"], "m": g["m"], "series_eps": g["series_eps"],
+                   "lambda0": g["lambda0"], "target_cost": target, "F_star_oracle": Fstar,
+                   "l2": "inputs (~0.5 GB resident) larger than the 129 MB L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": dominant,
+        "roofline_series": roof_series,
+        "roofline_landmark": roof_lm,
+        "phases_ms_per_lm_step": {k: round(v / steps_timed, 4) for k, v in phases.items()},
+        "lm_iterations_per_solve": iters_total / max(len(results), 1),
+        "series_terms_per_step": terms_per_step,
+        "reached_target": bool(reached),
+        "final_cost": final_cost,
+        "per_solve_ms": [round(x, 3) for x in per_solve],
+        "solves_per_s_all_ranks": round(world * args.steps / (total_ms / 1e3), 3),
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        cb = cpu_oracle_sample(sc, g, target)
+        out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+# ----------------------------------------------------------------- reference arm
+
+def run_reference(args, rank: int) -> dict | None:
+    if rank != 0:
+        return None
+    sc = workload_scene(args.workload)
+    g = load_golden(args.workload)
+    target = g["series"]["F"] * (1.0 + REL_TARGET)
+    vals = []
+    last = None
+    for _ in range(args.warmup + args.steps):
+        last = cpu_oracle_sample(sc, g, target, steps=1)
+        vals.append(last["value"])
+    v = float(np.mean(vals[args.warmup:]))
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {sc.n_cams} cams, {sc.n_points} "
+                                   f"landmarks, {sc.n_obs} obs", "precision": "fp64 (CPU)"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": _CORES,
+                             "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="large", choices=("large", "mid", "tiny"))
+    ap.add_argument("--precision", default="mixed", choices=("mixed", "fp64"))
+    ap.add_argument("--max-iters", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    out = run_reference(args, rank) if args.impl == "reference" else run_ours(args, rank, world)
+    if out is not None and rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

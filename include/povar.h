@@ -70,7 +70,12 @@ enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1 };
  *  precision  POVAR_FP64: every kernel in FP64.
  *             POVAR_MIXED_FP32: series and linearization in FP32; landmark
  *             elimination, 12x12 inverses, cost and gain ratio in FP64.
- *  schedule   -1 = library default; 0 = point-gather / camera-scatter. */
+ *  schedule   series schedule: 0 = landmark-major gather pass + camera-major
+ *             scatter pass; 1 = one fused landmark-major pass whose camera
+ *             contributions are reduced across the lanes of a warp that
+ *             share a camera; -1 = chosen at creation (1 when the observation
+ *             layout yields at most one partial sum per two observations).
+ *             Both schedules compute the same series. */
 typedef struct {
   double eta;
   double lambda0;
@@ -127,7 +132,9 @@ const char* povar_last_error(const povar_problem* p);
 
 /* Set the cameras (n_cams x 12 row-major doubles) and re-solve every
  * landmark in closed form (Eq. update_landmark) at pOSE weight eta. Resets
- * the damping state: the next step starts from params->lambda0. */
+ * the damping state: the next step starts from params->lambda0. P may be a
+ * host pointer (checked for finite values) or a device pointer of the
+ * handle's device (copied device to device, not checked). */
 povar_status povar_set_cameras(povar_problem* p, const double* P, double eta);
 
 /* Random initialization of the paper's experiments (Sec. 5.2): every camera
@@ -177,6 +184,22 @@ povar_status povar_get_orders(povar_problem* p, uint32_t* perm_pt, uint32_t* off
  * unit sphere in POVAR_SPHERE mode). Any pointer may be NULL. */
 povar_status povar_get_last_step(povar_problem* p, double* U_out, double* bp_out,
                                  double* delta_out);
+
+/* Phase timing with CUDA events recorded on the handle's stream around each
+ * phase of every step (no extra host synchronization). Phases, in order:
+ * 0 linearization, 1 damped camera blocks + first term, 2 series terms,
+ * 3 predicted decrease, 4 camera update, 5 landmarks + cost at the trial
+ * cameras, 6 controller. povar_get_profile writes, per phase, the summed
+ * device milliseconds (ms_out[POVAR_NPHASES]) and the number of timed steps
+ * (steps_out, may be NULL), and zeroes the counters when reset != 0.
+ * Timing applies to povar_step and povar_solve issued while enabled; in
+ * povar_solve, which runs each step as one CUDA graph, the phase events are
+ * part of the graph and the steps that end at a host synchronization point
+ * (every fourth step and the last one) are sampled. */
+enum { POVAR_NPHASES = 7 };
+povar_status povar_set_profiling(povar_problem* p, int32_t enable);
+povar_status povar_get_profile(povar_problem* p, double* ms_out, int64_t* steps_out,
+                               int32_t reset);
 
 /* Number of kernel launches this handle has issued so far. */
 int64_t povar_launch_count(const povar_problem* p);

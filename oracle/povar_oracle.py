@@ -36,7 +36,8 @@ Readings where the paper is silent or garbled (each also listed in the design doc):
   when ||x_k||_2 <= eps * ||delta_k||_2; eps = 0 runs exactly m terms.
 * D_p = I; the damping update is the Madsen-Nielsen rule (on accept:
   lambda *= max(1/3, 1 - (2 rho - 1)^3), nu = 2; on reject: lambda *= nu,
-  nu *= 2); a step is accepted iff the cost decreases.
+  nu *= 2), with lambda kept >= LAMBDA_MIN = 1e-8; a step is accepted iff
+  the cost decreases.
 * The predicted decrease is pred = 2 g^T d - d^T (S - lambda I) d.
 * vec(P) is row-major (rows p1, p2, p3 of the 3x4 camera).
 * Rank-deficient V_j: pseudo-inverse when cond(V_j) > 1e12 (footnote of
@@ -58,6 +59,8 @@ import scipy.sparse as sp
 EUCLID = 0
 SPHERE = 1
 PINV_COND = 1e12
+LAMBDA_MIN = 1e-8    # damping floor (convention; the paper gives no bound)
+LAMBDA_MAX = 1e30    # damping ceiling: the solve stops as diverged above it
 
 
 # ---------------------------------------------------------------------------
@@ -295,9 +298,20 @@ def reduced_system(ne: NormalEquations, Q, lam):
 
 
 def exact_step(rs: ReducedSystem):
-    """delta = S^{-1} g by dense Cholesky (S is SPD: S >= lambda I)."""
-    c = sla.cho_factor(rs.S, lower=True)
-    return sla.cho_solve(c, rs.g)
+    """delta = S^{-1} g by dense Cholesky (S is SPD: S >= lambda I).
+
+    When S is so ill-conditioned (cond ~ 1e16, e.g. a landmark drifting to
+    infinity after the cost has converged) that rounding makes it
+    numerically indefinite, the solve falls back to the eigen-decomposition
+    of S with every eigenvalue floored at lambda, the bound S >= lambda I
+    holds in exact arithmetic."""
+    try:
+        c = sla.cho_factor(rs.S, lower=True)
+        return sla.cho_solve(c, rs.g)
+    except np.linalg.LinAlgError:
+        w, E = np.linalg.eigh(rs.S)
+        w = np.maximum(w, rs.lam)
+        return E @ ((E.T @ rs.g) / w)
 
 
 def series_step(rs: ReducedSystem, m, eps=0.0):
@@ -410,7 +424,7 @@ class Problem:
                          accepted=bool(accepted), terms_used=terms, delta=dP,
                          P_trial=P_new)
         if accepted:
-            lam = st.lam * max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3)
+            lam = max(st.lam * max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3), LAMBDA_MIN)
             new = State(P=P_new, X=X_new, F=F_new, lam=lam, nu=2.0,
                         iteration=st.iteration + 1)
         else:
@@ -436,6 +450,108 @@ class Problem:
                     break
                 if (rep.cost_before - rep.cost_after) < ftol * rep.cost_before:
                     break
-            if st.lam > 1e30:
+            if st.lam > LAMBDA_MAX:
                 break
         return st, reports
+
+
+# ---------------------------------------------------------------------------
+# Matrix-free variant for scenes whose dense S does not fit (series mode only)
+# ---------------------------------------------------------------------------
+
+class MatrixFreeProblem(Problem):
+    """The same damped VarPro step as ``Problem.step`` in series mode, with
+    the camera-landmark block W applied observation by observation
+    (W = sum_k J_p,k^T J_l,k placed at camera i(k), landmark j(k)) instead of
+    through the sparse Jacobian and the dense Schur complement. U, V, b_p,
+    b_l are the same per-observation sums J^T J and J^T r. Observation sums
+    are formed with sparse 0/1 incidence matrices (a library product).
+    Pinned against ``Problem.step`` on small scenes (tests/test_oracle_pins.py).
+    """
+
+    CHUNK = 250_000
+
+    def __init__(self, n_cams, n_points, cam_idx, pt_idx, meas):
+        super().__init__(n_cams, n_points, cam_idx, pt_idx, meas)
+        n = len(self.cam_idx)
+        ones = np.ones(n)
+        self.A_cam = sp.csr_matrix((ones, (self.cam_idx, np.arange(n))), shape=(self.n_cams, n))
+        self.A_pt = sp.csr_matrix((ones, (self.pt_idx, np.arange(n))), shape=(self.n_points, n))
+
+    def blocks(self, P, X, eta):
+        """U (n_cams,12,12), b_p (n_cams,12), V (n_points,3,3), b_l, J_p, J_l."""
+        n = len(self.cam_idx)
+        r = pose_residuals(P, X, self.cam_idx, self.pt_idx, self.meas, eta)
+        Jp, Jl = jacobian_blocks(P, X, self.cam_idx, self.pt_idx, self.meas, eta)
+        U = np.zeros((self.n_cams, 144))
+        for a in range(0, n, self.CHUNK):
+            b = min(n, a + self.CHUNK)
+            outer = np.einsum("nra,nrb->nab", Jp[a:b], Jp[a:b]).reshape(b - a, 144)
+            U += self.A_cam[:, a:b] @ outer
+        b_p = self.A_cam @ np.einsum("nra,nr->na", Jp, r)
+        V = (self.A_pt @ np.einsum("nra,nrb->nab", Jl, Jl).reshape(n, 9)).reshape(-1, 3, 3)
+        b_l = self.A_pt @ np.einsum("nra,nr->na", Jl, r)
+        return U.reshape(-1, 12, 12), b_p, V, b_l, Jp, Jl
+
+    def step(self, st: State, params: Params):
+        if params.solver != "series":
+            raise ValueError("MatrixFreeProblem only runs the series solver")
+        eta, lam = params.eta, st.lam
+        U, b_p, V, b_l, Jp, Jl = self.blocks(st.P, st.X, eta)
+        Vinv, _ = sym_inverse_batch(V)
+        Q = tangent_bases(st.P, params.manifold)
+        k = Q.shape[2]
+        Ut = np.einsum("nai,nab,nbj->nij", Q, U, Q) + lam * np.eye(k)[None]
+        Utinv = np.linalg.inv(Ut)
+        ci, pj = self.cam_idx, self.pt_idx
+
+        def Wt(xc):          # (n_cams, 12) ambient -> (n_points, 3)
+            y = np.einsum("nra,na->nr", Jp, xc[ci])
+            return self.A_pt @ np.einsum("nrb,nr->nb", Jl, y)
+
+        def W(s):            # (n_points, 3) -> (n_cams, 12)
+            y = np.einsum("nrb,nb->nr", Jl, s[pj])
+            return self.A_cam @ np.einsum("nra,nr->na", Jp, y)
+
+        def lift(xt):        # tangent coordinates -> ambient
+            return np.einsum("nab,nb->na", Q, xt)
+
+        def proj(xa):        # ambient -> tangent coordinates (Q^T)
+            return np.einsum("nab,na->nb", Q, xa)
+
+        def Vi(t):
+            return np.einsum("nab,nb->na", Vinv, t)
+
+        g = -(proj(b_p) - proj(W(Vi(b_l))))
+        x = np.einsum("nab,nb->na", Utinv, g)
+        delta = x.copy()
+        terms = 1
+        for _ in range(1, params.m):
+            x = np.einsum("nab,nb->na", Utinv, proj(W(Vi(Wt(lift(x))))))
+            delta += x
+            terms += 1
+            if params.series_eps > 0 and (np.linalg.norm(x) <=
+                                          params.series_eps * np.linalg.norm(delta)):
+                break
+        dP = lift(delta)
+        S0d = np.einsum("nab,nb->na", Ut, delta) - lam * delta - proj(W(Vi(Wt(dP))))
+        pred = float(2.0 * np.sum(g * delta) - np.sum(delta * S0d))
+        P_new = st.P + dP
+        if params.manifold == SPHERE:
+            P_new = P_new / np.linalg.norm(P_new, axis=1, keepdims=True)
+        X_new = self.landmarks(P_new, eta)
+        F_new = self.cost(P_new, X_new, eta)
+        rho = (st.F - F_new) / pred if pred > 0 else 0.0
+        accepted = F_new < st.F
+        rep = StepReport(cost_before=st.F, cost_after=F_new, pred=pred, rho=rho,
+                         lambda_used=lam, lambda_next=0.0, accepted=bool(accepted),
+                         terms_used=terms, delta=dP, P_trial=P_new)
+        if accepted:
+            lam_n = max(lam * max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3), LAMBDA_MIN)
+            new = State(P=P_new, X=X_new, F=F_new, lam=lam_n, nu=2.0,
+                        iteration=st.iteration + 1)
+        else:
+            new = State(P=st.P, X=st.X, F=st.F, lam=lam * st.nu, nu=2.0 * st.nu,
+                        iteration=st.iteration + 1)
+        rep.lambda_next = new.lam
+        return new, rep

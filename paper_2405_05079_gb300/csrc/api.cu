@@ -43,10 +43,13 @@ povar_status dev_alloc_bytes(Problem* p, void** ptr, size_t bytes, const char* w
 
 namespace {
 
+void collect_profile(Problem* p);
+
 povar_status sync_state(Problem* p) {
   POVAR_CUDA(cudaMemcpyAsync(p->h_state, p->state, sizeof(DeviceState), cudaMemcpyDeviceToHost,
                              p->stream));
   POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  if (!p->prof_steps.empty()) collect_profile(p);
   return POVAR_OK;
 }
 
@@ -62,7 +65,7 @@ povar_status check_params(Problem* p, const povar_params* q) {
     return fail(p, POVAR_EINVAL, "unknown manifold");
   if (q->precision != POVAR_FP64 && q->precision != POVAR_MIXED_FP32)
     return fail(p, POVAR_EINVAL, "unknown precision");
-  if (q->schedule < -1 || q->schedule > 0) return fail(p, POVAR_EINVAL, "unknown schedule");
+  if (q->schedule < -1 || q->schedule > 1) return fail(p, POVAR_EINVAL, "unknown schedule");
   return POVAR_OK;
 }
 
@@ -76,25 +79,156 @@ povar_status refresh_landmarks(Problem* p, double eta) {
   return POVAR_OK;
 }
 
-// Enqueue one damped VarPro iteration (no host synchronization).
-povar_status enqueue_step(Problem* p, const povar_params* q) {
+// Record a phase-boundary event of the current step (profiling only).
+povar_status mark(Problem* p, std::vector<size_t>* marks) {
+  if (!marks) return POVAR_OK;
+  if (p->prof_next >= p->prof_events.size()) {
+    cudaEvent_t e;
+    POVAR_CUDA(cudaEventCreate(&e));
+    p->prof_events.push_back(e);
+  }
+  const size_t k = p->prof_next++;
+  POVAR_CUDA(cudaEventRecord(p->prof_events[k], p->stream));
+  marks->push_back(k);
+  return POVAR_OK;
+}
+
+// Fold the recorded (and completed: the caller synchronized) step events
+// into the per-phase sums and recycle the pool.
+void collect_profile(Problem* p) {
+  for (const auto& m : p->prof_steps) {
+    if (m.size() != POVAR_NPHASES + 1) continue;
+    for (int ph = 0; ph < POVAR_NPHASES; ++ph) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p->prof_events[m[ph]], p->prof_events[m[ph + 1]]) ==
+          cudaSuccess)
+        p->prof_ms[ph] += ms;
+    }
+    ++p->prof_count;
+  }
+  cudaGetLastError();
+  p->prof_steps.clear();
+  p->prof_next = 0;
+}
+
+// Host decisions before a step: damping initialization after new cameras,
+// landmark refresh when eta changed. Enqueues on p->stream.
+povar_status prepare_step(Problem* p, const povar_params* q) {
   povar_status s;
   if (p->fresh) {
     if ((s = launch_init_state(p, q->lambda0, 1, 0)) != POVAR_OK) return s;
     p->fresh = false;
   }
   if (q->eta != p->eta_cur && (s = refresh_landmarks(p, q->eta)) != POVAR_OK) return s;
+  return POVAR_OK;
+}
+
+// The fixed kernel sequence of one damped VarPro iteration (a4 .. a10). It
+// depends only on q and device state, so it can be captured in a graph.
+povar_status enqueue_step_kernels(Problem* p, const povar_params* q, std::vector<size_t>* mk,
+                                  const cudaEvent_t* fixed = nullptr) {
+  povar_status s;
   const int prec = q->precision;
+  const int sched = q->schedule < 0 ? p->schedule_default : q->schedule;
+  int nmark = 0;
+  // phase boundary: a pooled event (eager profiling) or a fixed event node
+  // (profiling inside the step graph)
+  auto mark = [&](Problem* pp, std::vector<size_t>* m) -> povar_status {
+    if (fixed) {
+      const cudaError_t e =
+          cudaEventRecordWithFlags(fixed[nmark++], pp->stream, cudaEventRecordExternal);
+      return e == cudaSuccess ? POVAR_OK : fail(pp, POVAR_ECUDA, cudaGetErrorString(e));
+    }
+    return ::povar::mark(pp, m);
+  };
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_linearize(p, prec, q->eta)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_camera_prepare(p, prec, q->manifold, q->eta)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
   for (int k = 1; k < q->m; ++k)
-    if ((s = launch_series_term(p, prec, q->eta, k, q->series_eps)) != POVAR_OK) return s;
+    if ((s = launch_series_term(p, prec, q->eta, k, q->series_eps, sched)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_pred(p, prec, q->eta, q->manifold, q->m)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_update(p, prec, q->manifold)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_landmarks(p, 1, q->eta)) != POVAR_OK) return s;
   if ((s = launch_cost_finish(p, 1)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_controller(p)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
   p->last_precision = prec;
+  return POVAR_OK;
+}
+
+// Enqueue one damped VarPro iteration (no host synchronization).
+povar_status enqueue_step(Problem* p, const povar_params* q) {
+  povar_status s;
+  std::vector<size_t>* mk = nullptr;
+  if (p->profiling) {
+    p->prof_steps.emplace_back();
+    mk = &p->prof_steps.back();
+  }
+  if ((s = prepare_step(p, q)) != POVAR_OK) return s;
+  return enqueue_step_kernels(p, q, mk);
+}
+
+// Add the phase times of the last completed graph launch (the caller has
+// synchronized the graph stream).
+void sample_graph_profile(Problem* p) {
+  if (!p->g_profiled) return;
+  float ms[POVAR_NPHASES];
+  for (int ph = 0; ph < POVAR_NPHASES; ++ph)
+    if (cudaEventElapsedTime(&ms[ph], p->gprof[ph], p->gprof[ph + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+  for (int ph = 0; ph < POVAR_NPHASES; ++ph) p->prof_ms[ph] += ms[ph];
+  ++p->prof_count;
+}
+
+bool same_params(const povar_params& a, const povar_params& b) {
+  return a.eta == b.eta && a.series_eps == b.series_eps && a.m == b.m &&
+         a.manifold == b.manifold && a.precision == b.precision && a.schedule == b.schedule;
+}
+
+// Graph of one step on p->gstream (captured once per parameter set).
+povar_status step_graph(Problem* p, const povar_params* q) {
+  const int sched = q->schedule < 0 ? p->schedule_default : q->schedule;
+  if (p->gexec && same_params(p->gkey, *q) && p->gkey_sched == sched &&
+      p->g_profiled == p->profiling)
+    return POVAR_OK;
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  cudaStream_t user = p->stream;
+  p->stream = p->gstream;
+  const int64_t l0 = p->launches;
+  cudaError_t e = cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal);
+  povar_status s = POVAR_OK;
+  if (e == cudaSuccess) s = enqueue_step_kernels(p, q, nullptr, p->profiling ? p->gprof : nullptr);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(p->gstream, &g);
+  p->stream = user;
+  p->g_launches = p->launches - l0;
+  p->launches = l0;
+  if (e != cudaSuccess || e2 != cudaSuccess || s != POVAR_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return s != POVAR_OK ? s : fail(p, POVAR_ECUDA, "step graph capture failed");
+  }
+  e = cudaGraphInstantiate(&p->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    p->gexec = nullptr;
+    cudaGetLastError();
+    return fail(p, POVAR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  p->gkey = *q;
+  p->gkey_sched = sched;
+  p->g_profiled = p->profiling;
   return POVAR_OK;
 }
 
@@ -127,6 +261,15 @@ void povar_destroy(povar_problem* pp) {
   if (p->h_report) cudaFreeHost(p->h_report);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
+  for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->gstream) {
+    cudaStreamSynchronize(p->gstream);
+    cudaStreamDestroy(p->gstream);
+  }
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  for (int ph = 0; ph <= POVAR_NPHASES; ++ph)
+    if (p->gprof[ph]) cudaEventDestroy(p->gprof[ph]);
   delete pp;
 }
 
@@ -181,7 +324,8 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
   ALLOC(p->P64[0], nc * 12);
   ALLOC(p->P64[1], nc * 12);
   ALLOC(p->Ltab, nc * 48);
-  ALLOC(p->camP32, nc * 12);
+  ALLOC(p->camP32[0], nc * 12);
+  ALLOC(p->camP32[1], nc * 12);
   ALLOC(p->U64, nc * 144);
   ALLOC(p->bp64, nc * 12);
   ALLOC(p->G64, nc * 144);
@@ -200,9 +344,9 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
   }
   ALLOC(p->rec32, npd * 2);
   ALLOC(p->rec64, npd * 4);
-  ALLOC(p->cost_part, (size_t)p->n_slot_blocks);
-  ALLOC(p->pred_part, (size_t)p->n_slot_blocks);
-  ALLOC(p->pinv_part, (size_t)p->n_slot_blocks);
+  ALLOC(p->cost_part, npd / 32);
+  ALLOC(p->pred_part, npd / 32);
+  ALLOC(p->pinv_part, npd / 32);
   ALLOC(p->state, 1);
   ALLOC(p->d_report, 1);
 #define CK(call)                                                             \
@@ -218,6 +362,9 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
   CK(cudaMallocHost(&p->h_report, sizeof(povar_step_report)));
   CK(cudaEventCreate(&p->ev0));
   CK(cudaEventCreate(&p->ev1));
+  CK(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+  for (int ph = 0; ph <= POVAR_NPHASES; ++ph) CK(cudaEventCreate(&p->gprof[ph]));
   CK(cudaMemcpyAsync(p->d_cam, cam_idx, no * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream));
   CK(cudaMemcpyAsync(p->d_pt, pt_idx, no * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream));
   CK(cudaMemcpyAsync(p->d_meas, meas, 2 * no * sizeof(double), cudaMemcpyHostToDevice,
@@ -235,6 +382,8 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
   }
   ALLOC(*reinterpret_cast<char**>(&p->part_lin), (size_t)std::max(p->nchunks, 1) * povar::LIN_ACC * sizeof(double));
   ALLOC(*reinterpret_cast<char**>(&p->part_ser), (size_t)std::max(p->nchunks, 1) * 12 * sizeof(double));
+  // fused schedule when at most half as many run partials as observations
+  p->schedule_default = (2 * p->npart <= p->nobs) ? 1 : 0;
 #undef ALLOC
 #undef CK
   if ((s = povar::launch_init_state(p, 1e-4, 1, 1)) != POVAR_OK ||
@@ -251,12 +400,19 @@ povar_status povar_set_cameras(povar_problem* pp, const double* P, double eta) {
   Problem* p = &pp->impl;
   if (!P) return povar::fail(p, POVAR_EINVAL, "P is NULL");
   if (!(eta >= 0.0 && eta <= 1.0)) return povar::fail(p, POVAR_EINVAL, "eta must be in [0, 1]");
-  for (int64_t e = 0; e < (int64_t)p->nc * 12; ++e)
-    if (!std::isfinite(P[e])) return povar::fail(p, POVAR_EINVAL, "non-finite camera");
+  cudaPointerAttributes attr;
+  bool on_device = false;
+  if (cudaPointerGetAttributes(&attr, P) == cudaSuccess)
+    on_device = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+  cudaGetLastError();
+  if (!on_device)
+    for (int64_t e = 0; e < (int64_t)p->nc * 12; ++e)
+      if (!std::isfinite(P[e])) return povar::fail(p, POVAR_EINVAL, "non-finite camera");
   povar_status s;
   if ((s = povar::launch_init_state(p, 1e-4, 1, 1)) != POVAR_OK) return s;
   POVAR_CUDA(cudaMemcpyAsync(p->P64[0], P, (size_t)p->nc * 12 * sizeof(double),
-                             cudaMemcpyHostToDevice, p->stream));
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             p->stream));
   if ((s = povar::refresh_landmarks(p, eta)) != POVAR_OK) return s;
   p->fresh = true;
   if ((s = povar::sync_state(p)) != POVAR_OK) return s;
@@ -349,11 +505,45 @@ povar_status povar_solve(povar_problem* pp, const povar_params* params, int32_t 
   if ((s = povar::launch_begin(p, ftol, target_cost, max_iters)) != POVAR_OK) return s;
   POVAR_CUDA(cudaEventRecord(p->ev0, p->stream));
   const int check_every = 4;
-  for (int it = 0; it < max_iters; ++it) {
-    if ((s = povar::enqueue_step(p, params)) != POVAR_OK) return s;
-    if ((it + 1) % check_every == 0 && it + 1 < max_iters) {
-      if ((s = povar::sync_state(p)) != POVAR_OK) return s;
-      if (p->h_state->converged) break;
+  if (p->use_graphs) {
+    // one graph launch per step on the library stream, joined to the
+    // caller's stream with events before and after
+    if ((s = povar::prepare_step(p, params)) != POVAR_OK) return s;
+    if ((s = povar::step_graph(p, params)) != POVAR_OK) return s;
+    POVAR_CUDA(cudaEventRecord(p->ev_join, p->stream));
+    POVAR_CUDA(cudaStreamWaitEvent(p->gstream, p->ev_join, 0));
+    cudaStream_t user = p->stream;
+    p->stream = p->gstream;
+    for (int it = 0; it < max_iters; ++it) {
+      const cudaError_t e = cudaGraphLaunch(p->gexec, p->gstream);
+      if (e != cudaSuccess) {
+        p->stream = user;
+        return povar::fail(p, POVAR_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+      }
+      p->launches += p->g_launches;
+      if ((it + 1) % check_every == 0 && it + 1 < max_iters) {
+        if ((s = povar::sync_state(p)) != POVAR_OK) {
+          p->stream = user;
+          return s;
+        }
+        povar::sample_graph_profile(p);
+        if (p->h_state->converged) break;
+      }
+    }
+    if (p->g_profiled) {
+      POVAR_CUDA(cudaStreamSynchronize(p->gstream));
+      povar::sample_graph_profile(p);
+    }
+    POVAR_CUDA(cudaEventRecord(p->ev_join, p->gstream));
+    p->stream = user;
+    POVAR_CUDA(cudaStreamWaitEvent(p->stream, p->ev_join, 0));
+  } else {
+    for (int it = 0; it < max_iters; ++it) {
+      if ((s = povar::enqueue_step(p, params)) != POVAR_OK) return s;
+      if ((it + 1) % check_every == 0 && it + 1 < max_iters) {
+        if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+        if (p->h_state->converged) break;
+      }
     }
   }
   POVAR_CUDA(cudaEventRecord(p->ev1, p->stream));
@@ -366,6 +556,31 @@ povar_status povar_solve(povar_problem* pp, const povar_params* params, int32_t 
   if (iters_out) *iters_out = p->h_state->iteration - it0;
   if (p->h_state->error)
     return povar::fail(p, (povar_status)p->h_state->error, "device reported an error");
+  return POVAR_OK;
+}
+
+povar_status povar_set_profiling(povar_problem* pp, int32_t enable) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  povar_status s;
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  p->profiling = enable != 0;
+  return POVAR_OK;
+}
+
+povar_status povar_get_profile(povar_problem* pp, double* ms_out, int64_t* steps_out,
+                               int32_t reset) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  povar_status s;
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  if (ms_out)
+    for (int ph = 0; ph < POVAR_NPHASES; ++ph) ms_out[ph] = p->prof_ms[ph];
+  if (steps_out) *steps_out = p->prof_count;
+  if (reset) {
+    for (int ph = 0; ph < POVAR_NPHASES; ++ph) p->prof_ms[ph] = 0.0;
+    p->prof_count = 0;
+  }
   return POVAR_OK;
 }
 

@@ -158,36 +158,29 @@ __global__ void k_point_stats(const uint32_t* __restrict__ off_pt,
   mincam[j] = mc;
 }
 
+// Slot key: smallest camera first, then track length descending. Landmarks
+// whose tracks start at the same camera are adjacent, so when tracks are
+// contiguous runs of cameras (video, trajectories) the lanes of a slice visit
+// the same camera at the same track position; within one start camera the
+// lengths descend, so a slice's lanes have nearly equal track lengths.
 __global__ void k_slot_keys(const uint32_t* __restrict__ len,
                             const uint32_t* __restrict__ mincam, int np, uint32_t maxlen,
-                            int cam_bits, int use_cam, uint32_t* __restrict__ key) {
+                            int len_bits, int use_cam, uint32_t* __restrict__ key) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= np) return;
   uint32_t k = maxlen - len[j];
-  if (use_cam) k = (k << cam_bits) | mincam[j];
+  if (use_cam) k |= mincam[j] << len_bits;
   key[j] = k;
 }
 
-__global__ void k_slots(const uint32_t* __restrict__ sorted_pts, int np, int np_pad,
-                        const uint32_t* __restrict__ len, uint32_t* __restrict__ slot_pt,
-                        uint32_t* __restrict__ pt_slot, uint32_t* __restrict__ slot_len) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= np_pad) return;
-  if (s < np) {
-    const uint32_t j = sorted_pts[s];
-    slot_pt[s] = j;
-    pt_slot[j] = (uint32_t)s;
-    slot_len[s] = len[j];
-  } else {
-    slot_pt[s] = 0xffffffffu;
-    slot_len[s] = 0;
-  }
-}
-
+// Slice width = longest track among its 32 slots (times 32 entries per row).
 __global__ void k_slice_width(const uint32_t* __restrict__ slot_len, int nslices,
                               uint32_t* __restrict__ w32) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < nslices) w32[s] = slot_len[s * SLICE] * SLICE;
+  if (s >= nslices) return;
+  uint32_t w = 0;
+  for (int l = 0; l < SLICE; ++l) w = max(w, slot_len[s * SLICE + l]);
+  w32[s] = w * SLICE;
 }
 
 __global__ void k_fill_sell(const uint32_t* __restrict__ slot_pt,
@@ -226,6 +219,16 @@ __global__ void k_fill_cm(const uint32_t* __restrict__ perm_cam,
   cm_slot[r] = pt_slot[pt[o]];
   m32[r] = make_float2((float)u, (float)v);
   m64[r] = make_double2(u, v);
+}
+
+// keys[r] = pt[perm[r]], vals[r] = perm[r]
+__global__ void k_keys_through(const int32_t* __restrict__ pt, const uint32_t* __restrict__ perm,
+                               int64_t n, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint32_t o = perm[r];
+  keys[r] = (uint32_t)pt[o];
+  vals[r] = o;
 }
 
 __global__ void k_to_u32(const int32_t* __restrict__ src, uint32_t* __restrict__ dst, int64_t n) {
@@ -300,6 +303,8 @@ povar_status radix_sort(Problem* p, Scratch& sc, uint32_t** k, uint32_t** v, int
 
 }  // namespace
 
+povar_status build_runs(Problem* p);
+
 povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt) {
   (void)h_pt;
   Scratch sc;
@@ -328,7 +333,22 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
     if ((s = check_launch(p, "offsets")) != POVAR_OK) return s;
   }
 
-  // ---- landmark slots sorted by track length (desc), then smallest camera
+  // ---- observations of each landmark in camera order (stable sort of the
+  //      camera-major order by landmark): the SELL rows follow this order
+  uint32_t* perm_ptcam = nullptr;
+  {
+    uint32_t* keys = sc.get<uint32_t>(n);
+    uint32_t* vals = sc.get<uint32_t>(n);
+    if (!keys || !vals) return fail(p, POVAR_ENOMEM, "order scratch");
+    k_keys_through<<<gb, 256, 0, p->stream>>>(p->d_pt, p->perm_cam, n, keys, vals);
+    ++p->launches;
+    uint32_t *kk = keys, *vv = vals;
+    if ((s = radix_sort(p, sc, &kk, &vv, n, bits_for((uint64_t)(p->np - 1)))) != POVAR_OK)
+      return s;
+    perm_ptcam = vv;
+  }
+
+  // ---- landmark slots: smallest camera first, then track length (desc)
   uint32_t* len = sc.get<uint32_t>(p->np);
   uint32_t* mincam = sc.get<uint32_t>(p->np);
   uint32_t* skey = sc.get<uint32_t>(p->np);
@@ -351,7 +371,7 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
   const int len_bits = bits_for(maxlen);
   const int cam_bits = bits_for((uint64_t)(p->nc - 1));
   const int use_cam = (len_bits + cam_bits <= 32) ? 1 : 0;
-  k_slot_keys<<<gp, 256, 0, p->stream>>>(len, mincam, p->np, maxlen, cam_bits, use_cam, skey);
+  k_slot_keys<<<gp, 256, 0, p->stream>>>(len, mincam, p->np, maxlen, len_bits, use_cam, skey);
   k_iota<<<gp, 256, 0, p->stream>>>(sval, p->np);
   p->launches += 2;
   {
@@ -359,10 +379,32 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
     if ((s = radix_sort(p, sc, &kk, &vv, p->np, use_cam ? len_bits + cam_bits : len_bits)) !=
         POVAR_OK)
       return s;
-    k_slots<<<grid_for(p->np_pad, 256), 256, 0, p->stream>>>(vv, p->np, p->np_pad, len,
-                                                             p->slot_pt, p->pt_slot,
-                                                             p->slot_len);
-    ++p->launches;
+    // Slices of the sorted order are then ordered by width (longest track
+    // first, stable), keeping the last partial slice in place, so that the
+    // eight slices of a block have similar widths. Pads stay at the end.
+    std::vector<uint32_t> order(p->np), h_len(p->np);
+    POVAR_CUDA(cudaMemcpy(order.data(), vv, p->np * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    POVAR_CUDA(cudaMemcpy(h_len.data(), len, p->np * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    const int nfull = p->np / SLICE;
+    std::vector<uint32_t> width(nfull, 0);
+    for (int sl = 0; sl < nfull; ++sl)
+      for (int l = 0; l < SLICE; ++l) width[sl] = std::max(width[sl], h_len[order[sl * SLICE + l]]);
+    std::vector<int> sl_order(nfull);
+    for (int sl = 0; sl < nfull; ++sl) sl_order[sl] = sl;
+    std::stable_sort(sl_order.begin(), sl_order.end(),
+                     [&](int x, int y) { return width[x] > width[y]; });
+    std::vector<uint32_t> slot_pt(p->np_pad, 0xffffffffu), slot_len(p->np_pad, 0),
+        pt_slot(p->np);
+    for (int sl = 0; sl < nfull; ++sl)
+      for (int l = 0; l < SLICE; ++l) slot_pt[sl * SLICE + l] = order[sl_order[sl] * SLICE + l];
+    for (int q = nfull * SLICE; q < p->np; ++q) slot_pt[q] = order[q];
+    for (int q = 0; q < p->np; ++q) {
+      slot_len[q] = h_len[slot_pt[q]];
+      pt_slot[slot_pt[q]] = (uint32_t)q;
+    }
+    POVAR_CUDA(cudaMemcpy(p->slot_pt, slot_pt.data(), p->np_pad * 4, cudaMemcpyHostToDevice));
+    POVAR_CUDA(cudaMemcpy(p->slot_len, slot_len.data(), p->np_pad * 4, cudaMemcpyHostToDevice));
+    POVAR_CUDA(cudaMemcpy(p->pt_slot, pt_slot.data(), (size_t)p->np * 4, cudaMemcpyHostToDevice));
   }
   // ---- SELL offsets
   uint32_t* w = sc.get<uint32_t>(p->nslices + 1);
@@ -386,7 +428,7 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
   POVAR_CUDA(cudaMemsetAsync(p->sell_m32, 0, nsell * sizeof(float2), p->stream));
   POVAR_CUDA(cudaMemsetAsync(p->sell_m64, 0, nsell * sizeof(double2), p->stream));
   k_fill_sell<<<gp, 256, 0, p->stream>>>(p->slot_pt, p->slot_len, p->sell_off, p->off_pt,
-                                         p->perm_pt, p->d_cam, p->d_meas, p->np, p->sell_cam,
+                                         perm_ptcam, p->d_cam, p->d_meas, p->np, p->sell_cam,
                                          p->sell_m32, p->sell_m64);
   k_fill_cm<<<gb, 256, 0, p->stream>>>(p->perm_cam, p->d_pt, p->pt_slot, p->d_meas, n,
                                        p->cm_slot, p->cm_m32, p->cm_m64);
@@ -426,6 +468,75 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
   POVAR_CUDA(cudaMemcpy(p->cam_chunk0, c0.data(), p->nc * sizeof(int32_t),
                         cudaMemcpyHostToDevice));
   POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  return build_runs(p);
+}
+
+// Run structure of the fused series schedule. For each slice s and track
+// position t (a "slice row", index sell_off[s] / 32 + t) the cameras of the
+// 32 lanes are known at creation time. A row is "uniform" when every valid
+// lane has the same camera (one partial sum, reduced over the whole warp);
+// otherwise it is split into runs of consecutive lanes with equal camera
+// (one partial per run with a valid camera). row_mask = 0 marks a uniform
+// row; otherwise bit l is set when lane l starts a run (bit 0 always set).
+// row_base is the index of the row's first partial. The partials of camera
+// i are listed, in increasing index, at cam_part_idx[cam_part_off[i] ..).
+povar_status build_runs(Problem* p) {
+  povar_status s;
+  const int64_t nrows = p->nsell / SLICE;
+  std::vector<int32_t> cam(p->nsell);
+  std::vector<uint32_t> off(p->nslices + 1);
+  POVAR_CUDA(cudaMemcpy(cam.data(), p->sell_cam, p->nsell * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost));
+  POVAR_CUDA(cudaMemcpy(off.data(), p->sell_off, (p->nslices + 1) * sizeof(uint32_t),
+                        cudaMemcpyDeviceToHost));
+  std::vector<uint32_t> mask(std::max<int64_t>(nrows, 1)), base(std::max<int64_t>(nrows, 1));
+  std::vector<int32_t> pcam;
+  pcam.reserve(nrows + nrows / 4);
+  for (int64_t row = 0; row < nrows; ++row) {
+    const int32_t* c = cam.data() + row * SLICE;
+    int32_t c0 = -1;
+    bool uniform = true;
+    for (int l = 0; l < SLICE; ++l) {
+      if (c[l] < 0) continue;
+      if (c0 < 0) c0 = c[l];
+      else if (c[l] != c0) uniform = false;
+    }
+    base[row] = (uint32_t)pcam.size();
+    if (uniform && c0 >= 0) {
+      mask[row] = 0;
+      pcam.push_back(c0);
+      continue;
+    }
+    uint32_t m = 0;
+    for (int l = 0; l < SLICE; ++l) {
+      if (l == 0 || c[l] != c[l - 1]) {
+        m |= 1u << l;
+        if (c[l] >= 0) pcam.push_back(c[l]);
+      }
+    }
+    mask[row] = m;
+  }
+  const int64_t npart = (int64_t)pcam.size();
+  std::vector<uint32_t> poff(p->nc + 1, 0), pidx(std::max<int64_t>(npart, 1));
+  for (int32_t c : pcam) ++poff[c + 1];
+  for (int c = 0; c < p->nc; ++c) poff[c + 1] += poff[c];
+  {
+    std::vector<uint32_t> cursor(poff.begin(), poff.end() - 1);
+    for (int64_t q = 0; q < npart; ++q) pidx[cursor[pcam[q]]++] = (uint32_t)q;
+  }
+  p->nrows = nrows;
+  p->npart = npart;
+  if ((s = dev_alloc(p, &p->row_mask, mask.size(), "row_mask")) ||
+      (s = dev_alloc(p, &p->row_base, base.size(), "row_base")) ||
+      (s = dev_alloc(p, &p->cam_part_off, poff.size(), "cam_part_off")) ||
+      (s = dev_alloc(p, &p->cam_part_idx, pidx.size(), "cam_part_idx")) ||
+      (s = dev_alloc_bytes(p, &p->part_run, std::max<int64_t>(npart, 1) * 12 * sizeof(double),
+                           "part_run")))
+    return s;
+  POVAR_CUDA(cudaMemcpy(p->row_mask, mask.data(), mask.size() * 4, cudaMemcpyHostToDevice));
+  POVAR_CUDA(cudaMemcpy(p->row_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice));
+  POVAR_CUDA(cudaMemcpy(p->cam_part_off, poff.data(), poff.size() * 4, cudaMemcpyHostToDevice));
+  POVAR_CUDA(cudaMemcpy(p->cam_part_idx, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice));
   return POVAR_OK;
 }
 

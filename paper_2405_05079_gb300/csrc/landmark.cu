@@ -14,10 +14,13 @@
 // which the series kernels use. A numerically rank-deficient V_j
 // (cond > 1e12) falls back to the Moore-Penrose pseudo-inverse (footnote of
 // Sec. 4.2) from a Jacobi eigen-decomposition.
-// Pass 2 evaluates the four residual rows of every observation of the
-// landmark at (P, X_j) and accumulates F = ||r||^2 (Eq. ba_first_stage) into
-// one FP64 partial per block; a single block then adds the partials in a
-// fixed order, so the cost is deterministic.
+// The cost needs no second pass: with r_k = A_k X + c_k (A_k = B P,
+// c_k = B p4 - d), sum_k ||r_k||^2 = X^T V X + 2 h^T X + sum_k ||c_k||^2, and
+// at X = -V^+ h (h lies in the range of V) this is sum_k ||c_k||^2 + h^T X.
+// ||c_k||^2 = A0 + u A1 + v A2 + (u^2 + v^2) A3 with per-camera A0..A3, so it
+// is accumulated in pass 1 with four more FP64 operations per observation.
+// F = ||r||^2 (Eq. ba_first_stage) is summed into one FP64 partial per warp
+// and a single block adds the partials in a fixed order (deterministic).
 #include "povar_internal.cuh"
 
 namespace povar {
@@ -33,15 +36,19 @@ struct SlotBufs {
 
 // Ltab layout (48 doubles per camera):
 //  [0,6) R, [6,12) E1, [12,18) E2, [18,24) Fm   (symmetric 3x3: 00 01 02 11 12 22)
-//  [24,27) h0, [27,30) hu, [30,33) hv, [33,36) hw, [36,48) P (row-major 3x4)
+//  [24,27) h0, [27,30) hu, [30,33) hv, [33,36) hw, [36,40) A0..A3 (||c||^2),
+//  [40,48) unused
 __global__ void k_ltab(const DeviceState* __restrict__ st, int which_rel, double eta,
                        const double* __restrict__ P0, const double* __restrict__ P1, int nc,
-                       double* __restrict__ Ltab) {
+                       double* __restrict__ Ltab, float* __restrict__ C0,
+                       float* __restrict__ C1) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc) return;
   if (which_rel == 1 && st->converged) return;
   const int t = which_rel ? 1 - st->cur : st->cur;
   const double* P = (t ? P1 : P0) + 12 * (size_t)i;
+  float* Pf = (t ? C1 : C0) + 12 * (size_t)i;  // FP32 copy used by the FP32 kernels
+  for (int c = 0; c < 12; ++c) Pf[c] = (float)P[c];
   const double a = 1.0 - eta;
   double p0[3], p1[3], p2[3];
   for (int c = 0; c < 3; ++c) {
@@ -65,7 +72,10 @@ __global__ void k_ltab(const DeviceState* __restrict__ st, int which_rel, double
     T[30 + c] = (-a * q2 - eta) * p1[c] - a * q1 * p2[c];
     T[33 + c] = a * q2 * p2[c];
   }
-  for (int c = 0; c < 12; ++c) T[36 + c] = P[c];
+  T[36] = q0 * q0 + q1 * q1;
+  T[37] = -2.0 * q0 * (a * q2 + eta);
+  T[38] = -2.0 * q1 * (a * q2 + eta);
+  T[39] = a * q2 * q2 + eta;
 }
 
 // Symmetric 3x3 packed as (00 01 02 11 12 22).
@@ -189,38 +199,41 @@ k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
   if (which_rel == 1 && st->converged) return;
   const int t = which_rel ? 1 - st->cur : st->cur;
   const int s = blockIdx.x * BLOCK + threadIdx.x;
-  const double s1 = sqrt(1.0 - eta), s2 = sqrt(eta);
   double cost = 0.0;
   int npinv = 0;
   if (s < np) {
     const uint32_t len = slot_len[s];
     const uint32_t base = sell_off[s / SLICE] + (uint32_t)(s % SLICE);
-    double V[6] = {0, 0, 0, 0, 0, 0}, h[3] = {0, 0, 0};
+    double V[6] = {0, 0, 0, 0, 0, 0}, h[3] = {0, 0, 0}, cc = 0.0;
     for (uint32_t k = 0; k < len; ++k) {
       const uint32_t pos = base + k * SLICE;
       const int i = sell_cam[pos];
       const double2 m = sell_m[pos];
       const double u = m.x, v = m.y, w = u * u + v * v;
-      const double* T = Ltab + 48 * (size_t)i;
+      const double2* T = reinterpret_cast<const double2*>(Ltab + 48 * (size_t)i);
+      double tb[40];
 #pragma unroll
-      for (int e = 0; e < 6; ++e)
-        V[e] += __ldg(T + e) + u * __ldg(T + 6 + e) + v * __ldg(T + 12 + e) +
-                w * __ldg(T + 18 + e);
+      for (int q = 0; q < 20; ++q) {
+        const double2 x = __ldg(T + q);
+        tb[2 * q] = x.x;
+        tb[2 * q + 1] = x.y;
+      }
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        h[c] += __ldg(T + 24 + c) + u * __ldg(T + 27 + c) + v * __ldg(T + 30 + c) +
-                w * __ldg(T + 33 + c);
+      for (int e = 0; e < 6; ++e) V[e] += tb[e] + u * tb[6 + e] + v * tb[12 + e] + w * tb[18 + e];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) h[c] += tb[24 + c] + u * tb[27 + c] + v * tb[30 + c] + w * tb[33 + c];
+      cc += tb[36] + u * tb[37] + v * tb[38] + w * tb[39];
     }
-    // Cholesky V = L L^T; F = L^-1
+    // Cholesky V = L L^T through reciprocal square roots; F = L^-1
     double X[3], F[6];
     const double dmax = fmax(V[0], fmax(V[3], V[5]));
-    const double l00 = sqrt(V[0]);
-    const double l10 = V[1] / l00, l20 = V[2] / l00;
+    const double f00 = rsqrt(V[0]);
+    const double l10 = V[1] * f00, l20 = V[2] * f00;
     const double d1 = V[3] - l10 * l10;
-    const double l11 = sqrt(d1);
-    const double l21 = (V[4] - l20 * l10) / l11;
+    const double f11 = rsqrt(d1);
+    const double l21 = (V[4] - l20 * l10) * f11;
     const double d2 = V[5] - l20 * l20 - l21 * l21;
-    const double l22 = sqrt(d2);
+    const double f22 = rsqrt(d2);
     const bool suspect = !(V[0] > 1e-9 * dmax) || !(d1 > 1e-9 * dmax) || !(d2 > 1e-9 * dmax) ||
                          !(dmax > 0.0);
     bool deficient = false;
@@ -235,7 +248,6 @@ k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
       for (int e = 0; e < 6; ++e) F[e] = o.F[e];
     }
     if (!deficient) {
-      const double f00 = 1.0 / l00, f11 = 1.0 / l11, f22 = 1.0 / l22;
       const double f10 = -l10 * f00 * f11;
       const double f20 = -(l20 * f00 + l21 * f10) * f22;
       const double f21 = -l21 * f11 * f22;
@@ -257,19 +269,7 @@ k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
     bufs.A[t][s] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)F[0]);
     bufs.B[t][s] = make_float4((float)F[1], (float)F[2], (float)F[3], (float)F[4]);
     bufs.C[t][s] = (float)F[5];
-    // pass 2: residuals and cost
-    for (uint32_t k = 0; k < len; ++k) {
-      const uint32_t pos = base + k * SLICE;
-      const int i = sell_cam[pos];
-      const double2 m = sell_m[pos];
-      const double* P = Ltab + 48 * (size_t)i + 36;
-      const double y0 = __ldg(P + 0) * X[0] + __ldg(P + 1) * X[1] + __ldg(P + 2) * X[2] + __ldg(P + 3);
-      const double y1 = __ldg(P + 4) * X[0] + __ldg(P + 5) * X[1] + __ldg(P + 6) * X[2] + __ldg(P + 7);
-      const double y2 = __ldg(P + 8) * X[0] + __ldg(P + 9) * X[1] + __ldg(P + 10) * X[2] + __ldg(P + 11);
-      const double r0 = s1 * (y0 - m.x * y2), r1 = s1 * (y1 - m.y * y2);
-      const double r2 = s2 * (y0 - m.x), r3 = s2 * (y1 - m.y);
-      cost += r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3;
-    }
+    cost = cc + h[0] * X[0] + h[1] * X[1] + h[2] * X[2];
   } else {
     // padding slot (the slot arrays are padded to a whole number of blocks)
     double* Xo = bufs.X[t] + 3 * (size_t)s;
@@ -280,28 +280,16 @@ k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
     bufs.B[t][s] = make_float4(0.f, 0.f, 0.f, 0.f);
     bufs.C[t][s] = 0.f;
   }
-  // deterministic block reduction
-  __shared__ double red[BLOCK / 32];
-  __shared__ int redi[BLOCK / 32];
+  // one deterministic partial per warp (no block barrier: slices finish
+  // independently)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     cost += __shfl_xor_sync(0xffffffffu, cost, o);
     npinv += __shfl_xor_sync(0xffffffffu, npinv, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5] = cost;
-    redi[threadIdx.x >> 5] = npinv;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double c = 0.0;
-    int q = 0;
-    for (int w = 0; w < BLOCK / 32; ++w) {
-      c += red[w];
-      q += redi[w];
-    }
-    cost_part[blockIdx.x] = c;
-    pinv_part[blockIdx.x] = q;
+    cost_part[s / 32] = cost;
+    pinv_part[s / 32] = npinv;
   }
 }
 
@@ -342,7 +330,8 @@ __global__ void k_cost_finish(DeviceState* __restrict__ st, int which_rel,
 
 povar_status launch_landmarks(Problem* p, int which_rel, double eta) {
   k_ltab<<<grid_for(p->nc, 128), 128, 0, p->stream>>>(p->state, which_rel, eta, p->P64[0],
-                                                      p->P64[1], p->nc, p->Ltab);
+                                                      p->P64[1], p->nc, p->Ltab, p->camP32[0],
+                                                      p->camP32[1]);
   SlotBufs b;
   for (int t = 0; t < 2; ++t) {
     b.X[t] = p->X64[t];
@@ -360,7 +349,7 @@ povar_status launch_landmarks(Problem* p, int which_rel, double eta) {
 
 povar_status launch_cost_finish(Problem* p, int which_rel) {
   k_cost_finish<<<1, 256, 0, p->stream>>>(p->state, which_rel, p->cost_part, p->pinv_part,
-                                          p->n_slot_blocks);
+                                          p->np_pad / 32);
   ++p->launches;
   return check_launch(p, "cost_finish");
 }

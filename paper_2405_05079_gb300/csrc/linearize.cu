@@ -50,10 +50,10 @@ __device__ __forceinline__ void load_x<double>(const float4* __restrict__,
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_linearize(const DeviceState* __restrict__ st, double eta, int nchunks,
+k_linearize(const DeviceState* __restrict__ st, T s1, T s2, int nchunks,
             const int32_t* __restrict__ chunk_cam, const uint32_t* __restrict__ chunk_beg,
             const uint32_t* __restrict__ cm_slot, const typename M2<T>::type* __restrict__ cm_m,
-            const double* __restrict__ P0, const double* __restrict__ P1,
+            const T* __restrict__ P0, const T* __restrict__ P1,
             const float4* __restrict__ pdA0, const float4* __restrict__ pdA1,
             const double* __restrict__ X0, const double* __restrict__ X1,
             T* __restrict__ part) {
@@ -62,13 +62,12 @@ k_linearize(const DeviceState* __restrict__ st, double eta, int nchunks,
   const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (c >= nchunks) return;
   const int cur = st->cur;
-  const double* Pd = (cur ? P1 : P0) + 12 * (size_t)chunk_cam[c];
+  const T* Pd = (cur ? P1 : P0) + 12 * (size_t)chunk_cam[c];
   const float4* pdA = cur ? pdA1 : pdA0;
   const double* X64 = cur ? X1 : X0;
   T P[12];
 #pragma unroll
-  for (int e = 0; e < 12; ++e) P[e] = (T)Pd[e];
-  const T s1 = (T)sqrt(1.0 - eta), s2 = (T)sqrt(eta);
+  for (int e = 0; e < 12; ++e) P[e] = Pd[e];
   T acc[LIN_ACC];
 #pragma unroll
   for (int e = 0; e < LIN_ACC; ++e) acc[e] = (T)0;
@@ -125,8 +124,7 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
                  const int32_t* __restrict__ cam_nchunk, const int32_t* __restrict__ cam_chunk0,
                  const T* __restrict__ part, const double* __restrict__ P0,
                  const double* __restrict__ P1, double* __restrict__ U64,
-                 double* __restrict__ bp64, float* __restrict__ camP32,
-                 double* __restrict__ G64, float* __restrict__ G32, T* __restrict__ Y,
+                 double* __restrict__ bp64, double* __restrict__ G64, float* __restrict__ G32, T* __restrict__ Y,
                  T* __restrict__ D, double* __restrict__ camnorm) {
   if (st->converged) return;
   __shared__ double smA[4][12][13];
@@ -174,7 +172,6 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
       }
       bpl = smAcc[wl][40 + lane];
       bp64[(size_t)i * 12 + lane] = bpl;
-      camP32[(size_t)i * 12 + lane] = (float)Pl;
     }
   } else if (lane < 12) {
     for (int q = 0; q < 12; ++q) A[lane][q] = U64[(size_t)i * 144 + lane * 12 + q];
@@ -273,14 +270,14 @@ povar_status launch_linearize(Problem* p, int precision, double eta) {
   if (g == 0) return POVAR_OK;
   if (precision == POVAR_FP64) {
     k_linearize<double><<<g, 256, 0, p->stream>>>(
-        p->state, eta, p->nchunks, p->chunk_cam, p->chunk_beg, p->cm_slot, p->cm_m64,
-        p->P64[0], p->P64[1], p->pdA[0], p->pdA[1], p->X64[0], p->X64[1],
+        p->state, sqrt(1.0 - eta), sqrt(eta), p->nchunks, p->chunk_cam, p->chunk_beg, p->cm_slot,
+        p->cm_m64, p->P64[0], p->P64[1], p->pdA[0], p->pdA[1], p->X64[0], p->X64[1],
         static_cast<double*>(p->part_lin));
   } else {
     k_linearize<float><<<g, 256, 0, p->stream>>>(
-        p->state, eta, p->nchunks, p->chunk_cam, p->chunk_beg, p->cm_slot, p->cm_m32,
-        p->P64[0], p->P64[1], p->pdA[0], p->pdA[1], p->X64[0], p->X64[1],
-        static_cast<float*>(p->part_lin));
+        p->state, (float)sqrt(1.0 - eta), (float)sqrt(eta), p->nchunks, p->chunk_cam,
+        p->chunk_beg, p->cm_slot, p->cm_m32, p->camP32[0], p->camP32[1], p->pdA[0], p->pdA[1],
+        p->X64[0], p->X64[1], static_cast<float*>(p->part_lin));
   }
   ++p->launches;
   return check_launch(p, "linearize");
@@ -292,12 +289,12 @@ povar_status launch_camera_prepare(Problem* p, int precision, int manifold, doub
     k_camera_prepare<double><<<g, 128, 0, p->stream>>>(
         p->state, eta, manifold, p->nc, p->cam_nchunk, p->cam_chunk0,
         static_cast<const double*>(p->part_lin), p->P64[0], p->P64[1], p->U64, p->bp64,
-        p->camP32, p->G64, p->G32, p->Y64, p->D64, p->camnorm);
+        p->G64, p->G32, p->Y64, p->D64, p->camnorm);
   } else {
     k_camera_prepare<float><<<g, 128, 0, p->stream>>>(
         p->state, eta, manifold, p->nc, p->cam_nchunk, p->cam_chunk0,
         static_cast<const float*>(p->part_lin), p->P64[0], p->P64[1], p->U64, p->bp64,
-        p->camP32, p->G64, p->G32, p->Y32, p->D32, p->camnorm);
+        p->G64, p->G32, p->Y32, p->D32, p->camnorm);
   }
   ++p->launches;
   return check_launch(p, "camera_prepare");

@@ -3,11 +3,12 @@
 // Data layout in device memory (one problem):
 //  * Observations are kept in two device orders built once by povar_create:
 //    - point-major "SELL-32" slices: landmarks are renumbered into slots
-//      sorted by track length (descending), 32 consecutive slots form a
-//      slice, and the t-th observation of the slot in lane l of slice s sits
-//      at sell_off[s] + 32 t + l. One thread owns one landmark; the loads of
-//      a warp are fully coalesced and the lanes of a slice have (nearly)
-//      equal track lengths, so there is no divergence.
+//      sorted by their smallest camera, then by track length (descending);
+//      32 consecutive slots form a slice, and the t-th observation (in
+//      camera order) of the slot in lane l of slice s sits at
+//      sell_off[s] + 32 t + l. One thread owns one landmark; the loads of a
+//      warp are coalesced, and when tracks are contiguous camera windows the
+//      lanes of a slice row share one camera (warp-broadcast camera loads).
 //    - camera-major list cut into chunks of <= CHUNK observations that never
 //      cross a camera boundary; one warp reduces one chunk with shuffles and
 //      the last warp of a camera (an atomic ticket) finishes the camera.
@@ -33,6 +34,8 @@ constexpr int CHUNK = 256;       // observations per camera-major chunk
 constexpr int LIN_ACC = 52;      // linearization accumulators per chunk
 constexpr int BLOCK = 256;       // threads per block for slot kernels
 constexpr double PINV_COND = 1e12;
+constexpr double LAMBDA_MIN = 1e-8;   // damping floor
+constexpr double LAMBDA_MAX = 1e30;   // damping ceiling (solve reported as diverged)
 
 // Device-resident LM / VarPro controller state (one per problem).
 struct DeviceState {
@@ -98,10 +101,18 @@ struct Problem {
   int32_t* cam_chunk0 = nullptr;  // [nc]
   uint32_t* cam_ticket = nullptr; // [nc]
   uint32_t* done_ticket = nullptr;// [1]
+  // fused-schedule run structure (see build_runs in csr.cu)
+  int64_t nrows = 0, npart = 0;
+  uint32_t* row_mask = nullptr;     // [nrows]
+  uint32_t* row_base = nullptr;     // [nrows]
+  uint32_t* cam_part_off = nullptr; // [nc + 1]
+  uint32_t* cam_part_idx = nullptr; // [npart]
+  void* part_run = nullptr;         // [npart * 12] float or double
+  int schedule_default = 1;         // chosen at creation from the run statistics
   // cameras
   double* P64[2] = {nullptr, nullptr};  // [nc*12]
   double* Ltab = nullptr;               // [nc*48] landmark tables at trial P
-  float* camP32 = nullptr;              // [nc*12] current P, FP32
+  float* camP32[2] = {nullptr, nullptr};  // [nc*12] FP32 copies of P64[0], P64[1]
   double* U64 = nullptr;                // [nc*144]
   double* bp64 = nullptr;               // [nc*12]
   double* G64 = nullptr;                // [nc*144]
@@ -121,9 +132,9 @@ struct Problem {
   float* pdC[2] = {nullptr, nullptr};   // F22
   float4* rec32 = nullptr;              // [np_pad*2] (s0 s1 s2 X0)(X1 X2 - -)
   double2* rec64 = nullptr;             // [np_pad*4] (s0 s1)(s2 X0)(X1 X2)(- -)
-  double* cost_part = nullptr;          // [n slot blocks]
-  double* pred_part = nullptr;          // [n slot blocks]
-  int* pinv_part = nullptr;             // [n slot blocks]
+  double* cost_part = nullptr;          // [np_pad / 32] one per warp
+  double* pred_part = nullptr;          // [np_pad / 32] one per warp
+  int* pinv_part = nullptr;             // [np_pad / 32] one per warp
   int32_t n_slot_blocks = 0;
   // controller
   DeviceState* state = nullptr;
@@ -131,6 +142,24 @@ struct Problem {
   povar_step_report* d_report = nullptr;
   povar_step_report* h_report = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // phase profiling: events recorded at phase boundaries of every step
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_events;   // pool
+  size_t prof_next = 0;                   // next free event in the pool
+  std::vector<std::vector<size_t>> prof_steps;  // event indices of pending steps
+  double prof_ms[POVAR_NPHASES] = {0};
+  int64_t prof_count = 0;
+  // CUDA graph of one step (povar_solve): captured on a library stream that
+  // joins the caller's stream through events; cached per parameter set
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_join = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  povar_params gkey{};
+  int gkey_sched = -2;
+  int64_t g_launches = 0;               // kernels per graph launch
+  bool g_profiled = false;              // graph carries the phase events below
+  cudaEvent_t gprof[POVAR_NPHASES + 1] = {};  // phase boundaries inside the graph
+  bool use_graphs = true;
   std::vector<void*> allocs;            // every device allocation, freed by destroy
 };
 
@@ -174,8 +203,9 @@ povar_status launch_camera_prepare(Problem* p, int precision, int manifold,
                                    double eta);
 
 // ---------------------------------------------------- series.cu (a7,a8)
+// schedule 0: point gather + camera-major scatter; 1: fused runs
 povar_status launch_series_term(Problem* p, int precision, double eta,
-                                int term, double eps);
+                                int term, double eps, int schedule);
 povar_status launch_pred(Problem* p, int precision, double eta, int manifold, int m);
 
 // ---------------------------------------------------- step.cu (a9,a10)

@@ -98,7 +98,7 @@ __device__ __forceinline__ void load_rec(const float4*, const double2* rec64, ui
 // ||F_j t_j||^2 into one FP64 partial per block.
 template <typename T, bool PRED>
 __global__ void __launch_bounds__(BLOCK)
-k_series_gather(const DeviceState* __restrict__ st, double eta,
+k_series_gather(const DeviceState* __restrict__ st, T a,
                 const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
                 const int32_t* __restrict__ sell_cam,
                 const typename Vt<T>::m2* __restrict__ sell_m, const T* __restrict__ camPa,
@@ -111,16 +111,23 @@ k_series_gather(const DeviceState* __restrict__ st, double eta,
   const int s = blockIdx.x * BLOCK + threadIdx.x;
   const PointData<T>& pd = st->cur ? pd1 : pd0;
   const T* __restrict__ camP = st->cur ? camPb : camPa;
-  const T a = (T)(1.0 - eta);
   const uint32_t len = slot_len[s];
   const uint32_t base = sell_off[s / SLICE] + (uint32_t)(s % SLICE);
   T X[3], F[6];
   load_point<T>(pd, s, X, F);
   T t0 = 0, t1 = 0, t2 = 0;
+  // pass 1, software-pipelined: the next observation's camera index and
+  // measurement are loaded while the current one is processed
+  using M2 = typename Vt<T>::m2;
+  int i_n = len > 0 ? sell_cam[base] : 0;
+  M2 m_n = len > 0 ? sell_m[base] : M2{0, 0};
   for (uint32_t k = 0; k < len; ++k) {
-    const uint32_t pos = base + k * SLICE;
-    const int i = sell_cam[pos];
-    const auto m = sell_m[pos];
+    const int i = i_n;
+    const auto m = m_n;
+    if (k + 1 < len) {
+      i_n = sell_cam[base + (k + 1) * SLICE];
+      m_n = sell_m[base + (k + 1) * SLICE];
+    }
     T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
     load_row<T>(vec, i, 0, Y0);
     load_row<T>(vec, i, 1, Y1);
@@ -145,17 +152,11 @@ k_series_gather(const DeviceState* __restrict__ st, double eta,
   const T z1 = F[1] * t0 + F[2] * t1;
   const T z2 = F[3] * t0 + F[4] * t1 + F[5] * t2;
   if (PRED) {
-    double q = (double)z0 * z0 + (double)z1 * z1 + (double)z2 * z2;
-    __shared__ double red[BLOCK / 32];
+    // per-warp sum in the series precision; partials are added in FP64
+    T q = z0 * z0 + z1 * z1 + z2 * z2;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = q;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double c = 0.0;
-      for (int w = 0; w < BLOCK / 32; ++w) c += red[w];
-      pred_part[blockIdx.x] = c;
-    }
+    if ((threadIdx.x & 31) == 0) pred_part[s / 32] = (double)q;
   } else {
     T S[3];
     S[0] = F[0] * z0 + F[1] * z1 + F[3] * z2;
@@ -165,9 +166,81 @@ k_series_gather(const DeviceState* __restrict__ st, double eta,
   }
 }
 
+// Per-camera end of a series term, run by one warp whose lanes 0..11 hold
+// z_i: x_i = G_i z_i, delta_i += x_i, Y_i = x_i; with the threshold rule
+// (eps > 0) the last camera to finish (atomic ticket over `n_tickets`
+// cameras) adds the per-camera norms in camera order and sets the stop flag.
+template <typename T>
+__device__ __forceinline__ void camera_update(int i, int lane, T z, const T* __restrict__ G,
+                                              T* __restrict__ Y, T* __restrict__ D, double& yy,
+                                              double& dd) {
+  T x = 0;
+#pragma unroll
+  for (int q = 0; q < 12; ++q) {
+    const T zq = __shfl_sync(0xffffffffu, z, q);
+    if (lane < 12) x += G[144 * (size_t)i + 12 * lane + q] * zq;
+  }
+  T y2 = 0, d2 = 0;
+  if (lane < 12) {
+    const T d = D[12 * (size_t)i + lane] + x;
+    D[12 * (size_t)i + lane] = d;
+    Y[12 * (size_t)i + lane] = x;
+    y2 = x * x;
+    d2 = d * d;
+  }
+  // warp sums in the series precision, converted once
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+  }
+  yy = (double)y2;
+  dd = (double)d2;
+}
+
+template <typename T>
+__device__ __forceinline__ void finish_camera(DeviceState* __restrict__ st, int i, int lane, T z,
+                                              int term, double eps, int n_tickets,
+                                              const T* __restrict__ G,
+                                              double* __restrict__ camnorm,
+                                              uint32_t* __restrict__ done_ticket,
+                                              T* __restrict__ Y, T* __restrict__ D, int nc) {
+  double yy, dd;
+  camera_update<T>(i, lane, z, G, Y, D, yy, dd);
+  if (eps > 0.0) {
+    if (lane == 0) {
+      camnorm[2 * (size_t)i] = yy;
+      camnorm[2 * (size_t)i + 1] = dd;
+    }
+    __threadfence();
+    unsigned t2 = 0;
+    if (lane == 0) t2 = atomicAdd(done_ticket, 1u);
+    t2 = __shfl_sync(0xffffffffu, t2, 0);
+    if (t2 != (unsigned)(n_tickets - 1)) return;
+    __threadfence();
+    double sy = 0.0, sd = 0.0;
+    for (int q = lane; q < nc; q += 32) {
+      sy += __ldcg(camnorm + 2 * (size_t)q);
+      sd += __ldcg(camnorm + 2 * (size_t)q + 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    }
+    if (lane == 0) {
+      *done_ticket = 0;
+      if (sy <= eps * eps * sd) {
+        st->stop_series = 1;
+        st->terms_used = term + 1;
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_series_scatter(DeviceState* __restrict__ st, double eta, int term, double eps, int nchunks,
+k_series_scatter(DeviceState* __restrict__ st, T a, int term, double eps, int nchunks,
                  int nc, int nc_active, const int32_t* __restrict__ chunk_cam,
                  const uint32_t* __restrict__ chunk_beg, const int32_t* __restrict__ cam_nchunk,
                  const int32_t* __restrict__ cam_chunk0, const uint32_t* __restrict__ cm_slot,
@@ -181,7 +254,6 @@ k_series_scatter(DeviceState* __restrict__ st, double eta, int term, double eps,
   const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (c >= nchunks) return;
   const int i = chunk_cam[c];
-  const T a = (T)(1.0 - eta);
   const T* __restrict__ camP = st->cur ? camPb : camPa;
   T P[3][3];
 #pragma unroll
@@ -241,53 +313,285 @@ k_series_scatter(DeviceState* __restrict__ st, double eta, int term, double eps,
       z = s;
     }
   }
-  // x_i = G_i z_i, delta_i += x_i
-  T x = 0;
+  finish_camera<T>(st, i, lane, z, term, eps, nc_active, G, camnorm, done_ticket, Y, D, nc);
+}
+
+
+// ---------------------------------------------------------------------------
+// Fused schedule: one pass over the SELL slices per series term.
+//   pass 1 (lane = landmark j): t_j = sum_k Pbar_i^T C_k (Y_i x~_j),
+//                               s_j = F_j^T F_j t_j
+//   pass 2 (lanes in lockstep over track positions k): the contribution
+//       vec((C_k Pbar_i s_j) x~_j^T) of every lane is reduced over the lanes
+//       that share its camera -- the whole warp for a uniform slice row, a
+//       run of consecutive lanes otherwise -- and written as one partial
+//       per run. The run layout is fixed at creation, so every partial has a
+//       fixed slot and the per-camera sums below are deterministic.
+// ---------------------------------------------------------------------------
+
+// Sum of v[0..11] over the 32 lanes by recursive halving (18 shuffles).
+// Afterwards lanes 0, 8, 16, 24 hold totals (vbase .. vbase + 2) in r[0..2].
+template <typename T>
+__device__ __forceinline__ void warp_reduce12(const T v[12], int lane, T r[3], int& vbase) {
+  const bool hiA = lane & 16, hiB = lane & 8;
+  T r6[6];
 #pragma unroll
-  for (int q = 0; q < 12; ++q) {
-    const T zq = __shfl_sync(0xffffffffu, z, q);
-    if (lane < 12) x += G[144 * (size_t)i + 12 * lane + q] * zq;
+  for (int j = 0; j < 6; ++j) {
+    const T send = hiA ? v[j] : v[j + 6];
+    const T keep = hiA ? v[j + 6] : v[j];
+    r6[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
-  double yy = 0.0, dd = 0.0;
-  if (lane < 12) {
-    const T d = D[12 * (size_t)i + lane] + x;
-    D[12 * (size_t)i + lane] = d;
-    Y[12 * (size_t)i + lane] = x;
-    yy = (double)x * x;
-    dd = (double)d * d;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const T send = hiB ? r6[j] : r6[j + 3];
+    const T keep = hiB ? r6[j + 3] : r6[j];
+    r[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
-  if (eps > 0.0) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      yy += __shfl_xor_sync(0xffffffffu, yy, o);
-      dd += __shfl_xor_sync(0xffffffffu, dd, o);
+  for (int j = 0; j < 3; ++j) {
+    r[j] += __shfl_xor_sync(0xffffffffu, r[j], 4);
+    r[j] += __shfl_xor_sync(0xffffffffu, r[j], 2);
+    r[j] += __shfl_xor_sync(0xffffffffu, r[j], 1);
+  }
+  vbase = (hiA ? 6 : 0) + (hiB ? 3 : 0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BLOCK)
+k_series_fused(const DeviceState* __restrict__ st, T a,
+               const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
+               const int32_t* __restrict__ sell_cam,
+               const typename Vt<T>::m2* __restrict__ sell_m, const T* __restrict__ camPa,
+               const T* __restrict__ camPb, const T* __restrict__ vec, PointData<T> pd0,
+               PointData<T> pd1, const uint32_t* __restrict__ row_mask,
+               const uint32_t* __restrict__ row_base, T* __restrict__ part) {
+  if (st->converged || st->stop_series) return;
+  const int s = blockIdx.x * BLOCK + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const PointData<T>& pd = st->cur ? pd1 : pd0;
+  const T* __restrict__ camP = st->cur ? camPb : camPa;
+  const uint32_t sbeg = sell_off[s / SLICE];
+  const uint32_t width = (sell_off[s / SLICE + 1] - sbeg) / SLICE;
+  const uint32_t len = slot_len[s];
+  const uint32_t base = sbeg + (uint32_t)lane;
+  T X[3], F[6];
+  load_point<T>(pd, s, X, F);
+  T t0 = 0, t1 = 0, t2 = 0;
+  // pass 1, software-pipelined: the next observation's camera index and
+  // measurement are loaded while the current one is processed
+  using M2 = typename Vt<T>::m2;
+  int i_n = len > 0 ? sell_cam[base] : 0;
+  M2 m_n = len > 0 ? sell_m[base] : M2{0, 0};
+  for (uint32_t k = 0; k < len; ++k) {
+    const int i = i_n;
+    const auto m = m_n;
+    if (k + 1 < len) {
+      i_n = sell_cam[base + (k + 1) * SLICE];
+      m_n = sell_m[base + (k + 1) * SLICE];
     }
-    if (lane == 0) {
-      camnorm[2 * (size_t)i] = yy;
-      camnorm[2 * (size_t)i + 1] = dd;
+    T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
+    load_row<T>(vec, i, 0, Y0);
+    load_row<T>(vec, i, 1, Y1);
+    load_row<T>(vec, i, 2, Y2);
+    load_row<T>(camP, i, 0, P0);
+    load_row<T>(camP, i, 1, P1);
+    load_row<T>(camP, i, 2, P2);
+    const T e0 = Y0[0] * X[0] + Y0[1] * X[1] + Y0[2] * X[2] + Y0[3];
+    const T e1 = Y1[0] * X[0] + Y1[1] * X[1] + Y1[2] * X[2] + Y1[3];
+    const T e2 = Y2[0] * X[0] + Y2[1] * X[1] + Y2[2] * X[2] + Y2[3];
+    const T au = a * (T)m.x, av = a * (T)m.y;
+    const T aw = au * (T)m.x + av * (T)m.y;
+    const T c0 = e0 - au * e2;
+    const T c1 = e1 - av * e2;
+    const T c2 = aw * e2 - au * e0 - av * e1;
+    t0 += P0[0] * c0 + P1[0] * c1 + P2[0] * c2;
+    t1 += P0[1] * c0 + P1[1] * c1 + P2[1] * c2;
+    t2 += P0[2] * c0 + P1[2] * c1 + P2[2] * c2;
+  }
+  const T z0 = F[0] * t0;
+  const T z1 = F[1] * t0 + F[2] * t1;
+  const T z2 = F[3] * t0 + F[4] * t1 + F[5] * t2;
+  const T S0 = F[0] * z0 + F[1] * z1 + F[3] * z2;
+  const T S1 = F[2] * z1 + F[4] * z2;
+  const T S2 = F[5] * z2;
+  const uint32_t row0 = sbeg / SLICE;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  // pass 2, software-pipelined over the slice rows (row metadata and the
+  // lane's camera index of the next row are loaded ahead)
+  int ip = width > 0 && len > 0 ? sell_cam[base] : -1;
+  M2 mp = width > 0 ? sell_m[base] : M2{0, 0};
+  uint32_t maskp = width > 0 ? __ldg(row_mask + row0) : 0u;
+  uint32_t basep = width > 0 ? __ldg(row_base + row0) : 0u;
+  for (uint32_t k = 0; k < width; ++k) {
+    const int i = ip;
+    const auto m = mp;
+    const uint32_t mask = maskp, pbase = basep;
+    if (k + 1 < width) {
+      const uint32_t pn = base + (k + 1) * SLICE;
+      ip = k + 1 < len ? sell_cam[pn] : -1;
+      mp = sell_m[pn];
+      maskp = __ldg(row_mask + row0 + k + 1);
+      basep = __ldg(row_base + row0 + k + 1);
     }
-    __threadfence();
-    unsigned t2 = 0;
-    if (lane == 0) t2 = atomicAdd(done_ticket, 1u);
-    t2 = __shfl_sync(0xffffffffu, t2, 0);
-    if (t2 != (unsigned)(nc_active - 1)) return;
-    __threadfence();
-    double sy = 0.0, sd = 0.0;
-    for (int q = lane; q < nc; q += 32) {
-      sy += __ldcg(camnorm + 2 * (size_t)q);
-      sd += __ldcg(camnorm + 2 * (size_t)q + 1);
-    }
+    T v[12];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sy += __shfl_xor_sync(0xffffffffu, sy, o);
-      sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    for (int e = 0; e < 12; ++e) v[e] = 0;
+    if (i >= 0) {
+      T P0[4], P1[4], P2[4];
+      load_row<T>(camP, i, 0, P0);
+      load_row<T>(camP, i, 1, P1);
+      load_row<T>(camP, i, 2, P2);
+      const T w0 = P0[0] * S0 + P0[1] * S1 + P0[2] * S2;
+      const T w1 = P1[0] * S0 + P1[1] * S1 + P1[2] * S2;
+      const T w2 = P2[0] * S0 + P2[1] * S1 + P2[2] * S2;
+      const T au = a * (T)m.x, av = a * (T)m.y;
+      const T aw = au * (T)m.x + av * (T)m.y;
+      const T q0 = w0 - au * w2;
+      const T q1 = w1 - av * w2;
+      const T q2 = aw * w2 - au * w0 - av * w1;
+      v[0] = q0 * X[0]; v[1] = q0 * X[1]; v[2] = q0 * X[2]; v[3] = q0;
+      v[4] = q1 * X[0]; v[5] = q1 * X[1]; v[6] = q1 * X[2]; v[7] = q1;
+      v[8] = q2 * X[0]; v[9] = q2 * X[1]; v[10] = q2 * X[2]; v[11] = q2;
     }
-    if (lane == 0) {
-      *done_ticket = 0;
-      if (sy <= eps * eps * sd) {
-        st->stop_series = 1;
-        st->terms_used = term + 1;
+    if (mask == 0u) {
+      T r[3];
+      int vb;
+      warp_reduce12<T>(v, lane, r, vb);
+      if ((lane & 7) == 0) {
+        T* out = part + (size_t)pbase * 12 + vb;
+        out[0] = r[0]; out[1] = r[1]; out[2] = r[2];
       }
+    } else {
+      const uint32_t nb = lane < 31 ? (mask >> (lane + 1)) : 0u;
+      bool ok[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const int o = 1 << q;
+        ok[q] = (lane + o < 32) && ((nb & ((1u << o) - 1u)) == 0u);
+      }
+#pragma unroll
+      for (int e = 0; e < 12; ++e) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const T other = __shfl_down_sync(0xffffffffu, v[e], 1 << q);
+          if (ok[q]) v[e] += other;
+        }
+      }
+      const uint32_t valid = __ballot_sync(0xffffffffu, i >= 0);
+      const uint32_t starts = mask & valid;
+      if ((starts >> lane) & 1u) {
+        T* out = part + ((size_t)pbase + __popc(starts & lt_mask)) * 12;
+#pragma unroll
+        for (int e = 0; e < 12; ++e) out[e] = v[e];
+      }
+    }
+  }
+}
+
+// Per camera (one warp): z_i = sum of its partials in index order, then the
+// camera update. With the threshold rule, each block writes the sum of its
+// eight cameras' norms and the last block (atomic ticket) adds the block sums
+// in block order and sets the stop flag.
+template <typename T> struct Rec12;
+template <> struct Rec12<float> {
+  static __device__ __forceinline__ void add(const float* src, float acc[12]) {
+    const float4* q = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float4 x = __ldcg(q + r);
+      acc[4 * r] += x.x; acc[4 * r + 1] += x.y; acc[4 * r + 2] += x.z; acc[4 * r + 3] += x.w;
+    }
+  }
+};
+template <> struct Rec12<double> {
+  static __device__ __forceinline__ void add(const double* src, double acc[12]) {
+    const double2* q = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      const double2 x = __ldcg(q + r);
+      acc[2 * r] += x.x; acc[2 * r + 1] += x.y;
+    }
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
+               const uint32_t* __restrict__ cam_part_off, const uint32_t* __restrict__ cam_part_idx,
+               const T* __restrict__ part, const T* __restrict__ G, double* __restrict__ blocksum,
+               uint32_t* __restrict__ done_ticket, T* __restrict__ Y, T* __restrict__ D) {
+  if (st->converged || st->stop_series) return;
+  __shared__ double sh_yy[8], sh_dd[8];
+  __shared__ int sh_last;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int i = blockIdx.x * 8 + wl;
+  double yy = 0.0, dd = 0.0;
+  if (i < nc) {
+    T acc[12];
+#pragma unroll
+    for (int e = 0; e < 12; ++e) acc[e] = 0;
+    const uint32_t b = cam_part_off[i], e_ = cam_part_off[i + 1];
+    uint32_t q = b + lane;
+    for (; q + 32 < e_; q += 64) {
+      const uint32_t i0 = __ldg(cam_part_idx + q), i1 = __ldg(cam_part_idx + q + 32);
+      Rec12<T>::add(part + (size_t)i0 * 12, acc);
+      Rec12<T>::add(part + (size_t)i1 * 12, acc);
+    }
+    if (q < e_) Rec12<T>::add(part + (size_t)__ldg(cam_part_idx + q) * 12, acc);
+#pragma unroll
+    for (int e = 0; e < 12; ++e) {
+      T v = acc[e];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      acc[e] = v;
+    }
+    T z = 0;
+#pragma unroll
+    for (int e = 0; e < 12; ++e)
+      if (lane == e) z = acc[e];
+    camera_update<T>(i, lane, z, G, Y, D, yy, dd);
+  }
+  if (eps <= 0.0) return;
+  if (lane == 0) {
+    sh_yy[wl] = yy;
+    sh_dd[wl] = dd;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double by = 0.0, bd = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      by += sh_yy[w];
+      bd += sh_dd[w];
+    }
+    blocksum[2 * (size_t)blockIdx.x] = by;
+    blocksum[2 * (size_t)blockIdx.x + 1] = bd;
+    __threadfence();
+    sh_last = atomicAdd(done_ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!sh_last) return;
+  __threadfence();
+  __shared__ double ry[256], rd[256];
+  double sy = 0.0, sd = 0.0;
+  for (unsigned q = threadIdx.x; q < gridDim.x; q += 256) {
+    sy += __ldcg(blocksum + 2 * (size_t)q);
+    sd += __ldcg(blocksum + 2 * (size_t)q + 1);
+  }
+  ry[threadIdx.x] = sy;
+  rd[threadIdx.x] = sd;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      ry[threadIdx.x] += ry[threadIdx.x + o];
+      rd[threadIdx.x] += rd[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *done_ticket = 0;
+    if (ry[0] <= eps * eps * rd[0]) {
+      st->stop_series = 1;
+      st->terms_used = term + 1;
     }
   }
 }
@@ -311,28 +615,44 @@ __global__ void k_project_delta(const DeviceState* __restrict__ st, int nc,
   for (int e = 0; e < 12; ++e) D[12 * (size_t)i + e] = (T)((double)D[12 * (size_t)i + e] - f * P[e]);
 }
 
+// Per camera (one warp): d^T U d and b_p^T d in FP64 into camnorm[2i], [2i+1].
 template <typename T>
+__global__ void __launch_bounds__(256)
+k_pred_cam(const DeviceState* __restrict__ st, int nc, const double* __restrict__ U64,
+           const double* __restrict__ bp64, const T* __restrict__ D,
+           double* __restrict__ camsum) {
+  if (st->converged) return;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= nc) return;
+  const double d = lane < 12 ? (double)D[12 * (size_t)i + lane] : 0.0;
+  double su = 0.0;
+  for (int q = 0; q < 12; ++q) {
+    const double dq = __shfl_sync(0xffffffffu, d, q);
+    if (lane < 12) su += U64[144 * (size_t)i + 12 * lane + q] * dq;
+  }
+  double du = d * su;
+  double bd = lane < 12 ? bp64[12 * (size_t)i + lane] * d : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    du += __shfl_xor_sync(0xffffffffu, du, o);
+    bd += __shfl_xor_sync(0xffffffffu, bd, o);
+  }
+  if (lane == 0) {
+    camsum[2 * (size_t)i] = du;
+    camsum[2 * (size_t)i + 1] = bd;
+  }
+}
+
+// pred = -2 b_p^T d - d^T U d + sum_j ||F_j W^T d||^2, fixed-order sums.
 __global__ void k_pred_finish(DeviceState* __restrict__ st, int nc, int nparts, int m,
                               const double* __restrict__ pred_part,
-                              const double* __restrict__ U64, const double* __restrict__ bp64,
-                              const T* __restrict__ D) {
+                              const double* __restrict__ camsum) {
   if (st->converged) return;
   __shared__ double red[256];
-  double tv = 0.0;
-  for (int q = threadIdx.x; q < nparts; q += 256) tv += pred_part[q];
-  double du = 0.0, bd = 0.0;
-  for (int i = threadIdx.x; i < nc; i += 256) {
-    double d[12];
-    for (int e = 0; e < 12; ++e) d[e] = (double)D[12 * (size_t)i + e];
-    const double* U = U64 + 144 * (size_t)i;
-    for (int r = 0; r < 12; ++r) {
-      double s = 0.0;
-      for (int q = 0; q < 12; ++q) s += U[12 * r + q] * d[q];
-      du += d[r] * s;
-      bd += bp64[12 * (size_t)i + r] * d[r];
-    }
-  }
-  double v = -2.0 * bd - du + tv;
+  double v = 0.0;
+  for (int q = threadIdx.x; q < nparts; q += 256) v += pred_part[q];
+  for (int i = threadIdx.x; i < nc; i += 256) v -= camsum[2 * (size_t)i] + 2.0 * camsum[2 * (size_t)i + 1];
   red[threadIdx.x] = v;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -358,30 +678,57 @@ PointData<T> point_data(Problem* p, int t) {
 
 }  // namespace
 
-povar_status launch_series_term(Problem* p, int precision, double eta, int term, double eps) {
+povar_status launch_series_term(Problem* p, int precision, double eta, int term, double eps,
+                                int schedule) {
+  const double a64 = 1.0 - eta;   // C_k = B_k^T B_k coefficient, 1 - eta
+  const float a32 = (float)a64;
+  if (schedule == 1) {
+    const unsigned ga = grid_for(p->nc, 8);
+    if (precision == POVAR_FP64) {
+      k_series_fused<double><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+          p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0],
+          p->P64[1], p->Y64, point_data<double>(p, 0), point_data<double>(p, 1), p->row_mask,
+          p->row_base, static_cast<double*>(p->part_run));
+      k_series_apply<double><<<ga, 256, 0, p->stream>>>(
+          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
+          static_cast<const double*>(p->part_run), p->G64, p->camnorm, p->done_ticket, p->Y64,
+          p->D64);
+    } else {
+      k_series_fused<float><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+          p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
+          p->camP32[1], p->Y32, point_data<float>(p, 0), point_data<float>(p, 1), p->row_mask,
+          p->row_base, static_cast<float*>(p->part_run));
+      k_series_apply<float><<<ga, 256, 0, p->stream>>>(
+          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
+          static_cast<const float*>(p->part_run), p->G32, p->camnorm, p->done_ticket, p->Y32,
+          p->D32);
+    }
+    p->launches += 2;
+    return check_launch(p, "series_term (fused)");
+  }
   const unsigned gs = grid_for(p->nchunks, 8);
   if (precision == POVAR_FP64) {
     k_series_gather<double, false><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
-        p->state, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1], p->Y64,
+        p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1], p->Y64,
         point_data<double>(p, 0), point_data<double>(p, 1), p->rec32, p->rec64, nullptr);
   } else {
     k_series_gather<float, false><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
-        p->state, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32, p->camP32, p->Y32,
+        p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0], p->camP32[1], p->Y32,
         point_data<float>(p, 0), point_data<float>(p, 1), p->rec32, p->rec64, nullptr);
   }
   ++p->launches;
   if (gs > 0) {
     if (precision == POVAR_FP64) {
       k_series_scatter<double><<<gs, 256, 0, p->stream>>>(
-          p->state, eta, term, eps, p->nchunks, p->nc, p->nc_active, p->chunk_cam,
+          p->state, a64, term, eps, p->nchunks, p->nc, p->nc_active, p->chunk_cam,
           p->chunk_beg, p->cam_nchunk, p->cam_chunk0, p->cm_slot, p->cm_m64, p->P64[0],
           p->P64[1], p->rec32, p->rec64, p->G64, static_cast<double*>(p->part_ser), p->cam_ticket,
           p->done_ticket, p->camnorm, p->Y64, p->D64);
     } else {
       k_series_scatter<float><<<gs, 256, 0, p->stream>>>(
-          p->state, eta, term, eps, p->nchunks, p->nc, p->nc_active, p->chunk_cam,
-          p->chunk_beg, p->cam_nchunk, p->cam_chunk0, p->cm_slot, p->cm_m32, p->camP32,
-          p->camP32, p->rec32, p->rec64, p->G32, static_cast<float*>(p->part_ser), p->cam_ticket,
+          p->state, a32, term, eps, p->nchunks, p->nc, p->nc_active, p->chunk_cam,
+          p->chunk_beg, p->cam_nchunk, p->cam_chunk0, p->cm_slot, p->cm_m32, p->camP32[0],
+          p->camP32[1], p->rec32, p->rec64, p->G32, static_cast<float*>(p->part_ser), p->cam_ticket,
           p->done_ticket, p->camnorm, p->Y32, p->D32);
     }
     ++p->launches;
@@ -390,27 +737,33 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
 }
 
 povar_status launch_pred(Problem* p, int precision, double eta, int manifold, int m) {
+  const double a64 = 1.0 - eta;
+  const float a32 = (float)a64;
   const unsigned gc = grid_for(p->nc, 128);
   if (precision == POVAR_FP64) {
     if (manifold == POVAR_SPHERE)
       k_project_delta<double><<<gc, 128, 0, p->stream>>>(p->state, p->nc, p->P64[0],
                                                          p->P64[1], p->D64);
     k_series_gather<double, true><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
-        p->state, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1], p->D64,
+        p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1], p->D64,
         point_data<double>(p, 0), point_data<double>(p, 1), p->rec32, p->rec64, p->pred_part);
-    k_pred_finish<double><<<1, 256, 0, p->stream>>>(p->state, p->nc, p->n_slot_blocks, m,
-                                                    p->pred_part, p->U64, p->bp64, p->D64);
+    k_pred_cam<double><<<grid_for(p->nc, 8), 256, 0, p->stream>>>(p->state, p->nc, p->U64,
+                                                                   p->bp64, p->D64, p->camnorm);
+    k_pred_finish<<<1, 256, 0, p->stream>>>(p->state, p->nc, p->np_pad / 32, m, p->pred_part,
+                                            p->camnorm);
   } else {
     if (manifold == POVAR_SPHERE)
       k_project_delta<float><<<gc, 128, 0, p->stream>>>(p->state, p->nc, p->P64[0], p->P64[1],
                                                         p->D32);
     k_series_gather<float, true><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
-        p->state, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32, p->camP32, p->D32,
+        p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0], p->camP32[1], p->D32,
         point_data<float>(p, 0), point_data<float>(p, 1), p->rec32, p->rec64, p->pred_part);
-    k_pred_finish<float><<<1, 256, 0, p->stream>>>(p->state, p->nc, p->n_slot_blocks, m,
-                                                   p->pred_part, p->U64, p->bp64, p->D32);
+    k_pred_cam<float><<<grid_for(p->nc, 8), 256, 0, p->stream>>>(p->state, p->nc, p->U64,
+                                                                  p->bp64, p->D32, p->camnorm);
+    k_pred_finish<<<1, 256, 0, p->stream>>>(p->state, p->nc, p->np_pad / 32, m, p->pred_part,
+                                            p->camnorm);
   }
-  p->launches += manifold == POVAR_SPHERE ? 3 : 2;
+  p->launches += manifold == POVAR_SPHERE ? 4 : 3;
   return check_launch(p, "pred");
 }
 

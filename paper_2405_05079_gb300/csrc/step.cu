@@ -4,7 +4,8 @@
 //     controller, on the device so that a whole solve runs without host
 //     round-trips (Sec. 5.2 fixes lambda0 = 1e-4, 50 iterations, ftol 1e-6;
 //     the damping rule is Madsen-Nielsen: on accept lambda *= max(1/3,
-//     1 - (2 rho - 1)^3), nu = 2; on reject lambda *= nu, nu *= 2).
+//     1 - (2 rho - 1)^3), nu = 2; on reject lambda *= nu, nu *= 2; lambda is
+//     kept >= LAMBDA_MIN and a damping above LAMBDA_MAX stops the solve).
 // Also: state initialization, device random cameras (Philox4x32-10 of
 //     Salmon et al., SC'11, with the Box-Muller transform) and the landmark
 //     gather back to the caller's numbering.
@@ -51,7 +52,7 @@ __global__ void k_controller(DeviceState* __restrict__ st, povar_step_report* __
   int conv = 0;
   if (accepted) {
     const double x = 2.0 * rho - 1.0;
-    st->lam = st->lam * fmax(1.0 / 3.0, 1.0 - x * x * x);
+    st->lam = fmax(st->lam * fmax(1.0 / 3.0, 1.0 - x * x * x), LAMBDA_MIN);
     st->nu = 2.0;
     st->cur = 1 - st->cur;
     st->F = Fn;
@@ -64,7 +65,7 @@ __global__ void k_controller(DeviceState* __restrict__ st, povar_step_report* __
     st->need_lin = 0;
   }
   if (st->max_iters > 0 && st->iteration >= st->max_iters) conv = 1;
-  if (!(st->lam < 1e30)) {
+  if (!(st->lam < LAMBDA_MAX)) {
     st->error = POVAR_ENOTCONVERGED;
     conv = 1;
   }

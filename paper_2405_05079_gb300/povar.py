@@ -76,12 +76,15 @@ def lib() -> C.CDLL:
     u32p = C.POINTER(C.c_uint32)
     L.povar_get_orders.argtypes = [vp, u32p, u32p, u32p, u32p]
     L.povar_get_last_step.argtypes = [vp, dp, dp, dp]
+    L.povar_set_profiling.argtypes = [vp, i32]
+    L.povar_get_profile.argtypes = [vp, dp, C.POINTER(C.c_int64), i32]
     L.povar_launch_count.argtypes = [vp]
     L.povar_launch_count.restype = i64
     L.povar_version.restype = C.c_char_p
     for name in ("povar_create", "povar_set_cameras", "povar_init_random", "povar_get_cameras",
                  "povar_get_points", "povar_cost", "povar_step", "povar_solve",
-                 "povar_get_orders", "povar_get_last_step"):
+                 "povar_get_orders", "povar_get_last_step", "povar_set_profiling",
+                 "povar_get_profile"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -155,6 +158,24 @@ class Problem:
     def set_cameras(self, P, eta: float):
         P = np.ascontiguousarray(P, dtype=np.float64).reshape(self.n_cams, 12)
         self._check(lib().povar_set_cameras(self._h, _ptr(P, C.c_double), eta))
+
+    def set_cameras_device(self, ptr: int, eta: float):
+        """Cameras from a device buffer (n_cams x 12 doubles) on the handle's device."""
+        self._check(lib().povar_set_cameras(self._h, C.cast(C.c_void_p(ptr),
+                                                            C.POINTER(C.c_double)), eta))
+
+    PHASES = ("linearize", "camera_blocks", "series", "pred", "update", "landmarks",
+              "controller")
+
+    def set_profiling(self, enable: bool):
+        self._check(lib().povar_set_profiling(self._h, 1 if enable else 0))
+
+    def profile(self, reset: bool = False):
+        ms = np.zeros(len(self.PHASES))
+        n = C.c_int64()
+        self._check(lib().povar_get_profile(self._h, _ptr(ms, C.c_double), C.byref(n),
+                                            1 if reset else 0))
+        return dict(zip(self.PHASES, ms.tolist())), n.value
 
     def init_random(self, seed: int, manifold: int, eta: float):
         self._check(lib().povar_init_random(self._h, seed, manifold, eta))

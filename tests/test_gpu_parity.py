@@ -61,6 +61,8 @@ SCENES = {
     "tiny": lambda: scenes.tiny_scene(0),
     "mid": lambda: scenes.mid_scene(0),
     "ragged": ragged_scene,
+    # contiguous camera windows: the fused schedule's warp-uniform rows
+    "traj": lambda: scenes.trajectory_scene(120, 6000, 3, eta=0.1, m=8, name="traj"),
 }
 
 
@@ -132,8 +134,9 @@ def test_landmarks_and_cost_fp64(scene, normalize):
 
 # ---------------------------------------------------------------- one step, FP64
 
+@pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("manifold", [O.SPHERE, O.EUCLID])
-def test_one_step_fp64_matches_oracle(scene, manifold):
+def test_one_step_fp64_matches_oracle(scene, manifold, schedule):
     P0 = scenes.init_cameras(scene.n_cams, 4, normalize=True)
     orc = oracle_for(scene)
     m = scene.m
@@ -144,7 +147,8 @@ def test_one_step_fp64_matches_oracle(scene, manifold):
     with povar.Problem.from_scene(scene) as pb:
         pb.set_cameras(P0, scene.eta)
         rep = pb.step(povar.make_params(eta=scene.eta, m=m, manifold=manifold,
-                                        precision=povar.FP64, lambda0=1e-4))
+                                        precision=povar.FP64, lambda0=1e-4,
+                                        schedule=schedule))
         U, bp, d = pb.last_step()
     assert rel(U, ne.U) <= 1e-10
     assert rel(bp, ne.b_p.reshape(-1, 12)) <= 1e-10
@@ -175,7 +179,8 @@ def test_trajectory_fp64_matches_oracle():
             assert rel(pb.cameras(), st.P) <= 1e-10
 
 
-def test_series_early_stop_matches_oracle():
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_series_early_stop_matches_oracle(schedule):
     sc = scenes.tiny_scene(0)
     P0 = scenes.init_cameras(sc.n_cams, 2, normalize=True)
     orc = oracle_for(sc)
@@ -186,7 +191,8 @@ def test_series_early_stop_matches_oracle():
     with povar.Problem.from_scene(sc) as pb:
         pb.set_cameras(P0, sc.eta)
         rep = pb.step(povar.make_params(eta=sc.eta, m=40, series_eps=0.01,
-                                        manifold=povar.SPHERE, precision=povar.FP64))
+                                        manifold=povar.SPHERE, precision=povar.FP64,
+                                        schedule=schedule))
         _, _, d = pb.last_step()
     assert rep.terms_used == orep.terms_used
     assert rel(d, orep.delta) <= 1e-10
@@ -208,8 +214,9 @@ def test_single_term_is_block_jacobi():
 
 # ---------------------------------------------------------------- mixed precision
 
+@pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("manifold", [O.SPHERE, O.EUCLID])
-def test_one_step_mixed_close_to_oracle(scene, manifold):
+def test_one_step_mixed_close_to_oracle(scene, manifold, schedule):
     P0 = scenes.init_cameras(scene.n_cams, 4, normalize=True)
     orc = oracle_for(scene)
     op = O.Params(eta=scene.eta, m=scene.m, manifold=manifold)
@@ -217,7 +224,7 @@ def test_one_step_mixed_close_to_oracle(scene, manifold):
     with povar.Problem.from_scene(scene) as pb:
         pb.set_cameras(P0, scene.eta)
         rep = pb.step(povar.make_params(eta=scene.eta, m=scene.m, manifold=manifold,
-                                        precision=povar.MIXED_FP32))
+                                        precision=povar.MIXED_FP32, schedule=schedule))
         _, _, d = pb.last_step()
     assert rel(d, orep.delta) <= 1e-3
     assert abs(rep.cost_before - orep.cost_before) <= 1e-10 * orep.cost_before
@@ -292,3 +299,37 @@ def test_init_random_philox_box_muller():
     assert np.allclose(P, ref, rtol=1e-12, atol=1e-12)
     assert np.allclose(Ps, ref / np.linalg.norm(ref, axis=1, keepdims=True), rtol=1e-12,
                        atol=1e-12)
+
+
+def test_schedules_agree_bitwise_in_fp64_up_to_rounding():
+    """Both series schedules compute the same step (FP64, trajectory scene)."""
+    sc = SCENES["traj"]()
+    P0 = scenes.init_cameras(sc.n_cams, 4, normalize=True)
+    out = []
+    for sched in (0, 1):
+        with povar.Problem.from_scene(sc) as pb:
+            pb.set_cameras(P0, sc.eta)
+            pb.step(povar.make_params(eta=sc.eta, m=12, manifold=povar.EUCLID,
+                                      precision=povar.FP64, schedule=sched))
+            out.append(pb.last_step()[2])
+    assert rel(out[1], out[0]) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [povar.FP64, povar.MIXED_FP32])
+def test_graph_solve_equals_eager_steps(precision):
+    """povar_solve runs every step as one captured CUDA graph; the kernels and
+    reduction orders are the same as the eager povar_step path, so the
+    iterates agree bit for bit."""
+    sc = SCENES["traj"]()
+    P0 = scenes.init_cameras(sc.n_cams, 2, normalize=True)
+    prm = povar.make_params(eta=sc.eta, m=9, series_eps=0.01, manifold=povar.EUCLID,
+                            precision=precision)
+    with povar.Problem.from_scene(sc) as a, povar.Problem.from_scene(sc) as b:
+        a.set_cameras(P0, sc.eta)
+        b.set_cameras(P0, sc.eta)
+        for _ in range(6):
+            a.step(prm)
+        rep, iters = b.solve(prm, max_iters=6, ftol=0.0)
+        assert iters == 6
+        assert np.array_equal(a.cameras(), b.cameras())
+        assert a.cost(sc.eta) == b.cost(sc.eta)

@@ -346,3 +346,25 @@ def test_affine_factorization_special_case():
     prm = O.Params(eta=1.0, m=10, manifold=O.EUCLID, solver="exact", lambda0=1e-4)
     st, _ = pr.solve(P0, prm, max_iters=100, ftol=1e-14)
     assert abs(st.F - Fstar) <= 1e-8 * Fstar
+
+
+# --------------------------------------------------------------- matrix-free variant
+
+@pytest.mark.parametrize("manifold", [O.EUCLID, O.SPHERE])
+def test_matrix_free_step_equals_dense_step(tiny, manifold):
+    """The matrix-free oracle step (used for scenes whose dense S does not
+    fit) reproduces the explicit-S step, including the b_l term off the
+    landmark optimum and the early-stop rule."""
+    pr, P, X, eta = _state(tiny)
+    mf = O.MatrixFreeProblem(pr.n_cams, pr.n_points, pr.cam_idx, pr.pt_idx, pr.meas)
+    for eps, m in ((0.0, 7), (0.05, 30)):
+        prm = O.Params(eta=eta, m=m, manifold=manifold, series_eps=eps, lambda0=1e-3)
+        st = pr.init_state(P, prm)
+        st_off = O.State(P=st.P, X=st.X + 0.01, F=st.F, lam=st.lam)
+        for s0 in (st, st_off):
+            _, a = pr.step(s0, prm)
+            _, b = mf.step(s0, prm)
+            assert a.terms_used == b.terms_used
+            assert np.allclose(b.delta, a.delta, rtol=1e-9, atol=1e-12 * np.abs(a.delta).max())
+            assert abs(a.cost_after - b.cost_after) <= 1e-10 * a.cost_after
+            assert abs(a.pred - b.pred) <= 1e-8 * abs(a.pred)
