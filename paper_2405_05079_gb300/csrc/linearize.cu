@@ -178,48 +178,72 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
     bpl = bp64[(size_t)i * 12 + lane];
   }
   __syncwarp();
-  // tangent projection + damping
+  // Damped block and its Cholesky factor. If rounding leaves the block not
+  // numerically positive definite (an FP32-accumulated U with a huge
+  // condition number), the damping of this camera is raised -- to at least
+  // 1e-12 of its largest diagonal entry, then x100 per attempt, at most 8
+  // attempts -- and the event is counted in the device state.
+  double umax = lane < 12 ? A[lane][lane] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) umax = fmax(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+  double lam_eff = lam;
+  bool bad = true;
+  int attempt = 0;
   double ph = 0.0;
-  if (manifold == POVAR_SPHERE) {
-    double nn = Pl * Pl;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-    ph = lane < 12 ? Pl / sqrt(nn) : 0.0;
-    double up = 0.0;
-    for (int q = 0; q < 12; ++q) {
-      const double pq = __shfl_sync(0xffffffffu, ph, q);
-      if (lane < 12) up += A[lane][q] * pq;
-    }
-    double cc = ph * up;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, o);
-    __syncwarp();
-    for (int q = 0; q < 12; ++q) {
-      const double pq = __shfl_sync(0xffffffffu, ph, q);
-      const double uq = __shfl_sync(0xffffffffu, up, q);
+  for (; attempt < 8 && bad; ++attempt) {
+    if (attempt > 0) {
+      lam_eff = fmax(lam_eff * 100.0, 1e-12 * umax);
       if (lane < 12)
-        A[lane][q] += -up * pq - ph * uq + (cc - lam + 1.0) * ph * pq + (lane == q ? lam : 0.0);
+        for (int q = 0; q < 12; ++q) A[lane][q] = U64[(size_t)i * 144 + lane * 12 + q];
+      __syncwarp();
     }
-  } else if (lane < 12) {
-    A[lane][lane] += lam;
-  }
-  __syncwarp();
-  // Cholesky A = L L^T (lower, in place), lanes own rows
-  bool bad = false;
-  for (int k = 0; k < 12; ++k) {
-    if (lane == k) {
-      const double d = A[k][k];
-      if (!(d > 0.0)) bad = true;
-      A[k][k] = sqrt(fmax(d, 1e-300));
+    // tangent projection + damping
+    if (manifold == POVAR_SPHERE) {
+      double nn = Pl * Pl;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+      ph = lane < 12 ? Pl / sqrt(nn) : 0.0;
+      double up = 0.0;
+      for (int q = 0; q < 12; ++q) {
+        const double pq = __shfl_sync(0xffffffffu, ph, q);
+        if (lane < 12) up += A[lane][q] * pq;
+      }
+      double cc = ph * up;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, o);
+      __syncwarp();
+      for (int q = 0; q < 12; ++q) {
+        const double pq = __shfl_sync(0xffffffffu, ph, q);
+        const double uq = __shfl_sync(0xffffffffu, up, q);
+        if (lane < 12)
+          A[lane][q] += -up * pq - ph * uq + (cc - lam_eff + 1.0) * ph * pq +
+                        (lane == q ? lam_eff : 0.0);
+      }
+    } else if (lane < 12) {
+      A[lane][lane] += lam_eff;
     }
     __syncwarp();
-    if (lane > k && lane < 12) A[lane][k] /= A[k][k];
-    __syncwarp();
-    if (lane > k && lane < 12)
-      for (int j = k + 1; j <= lane; ++j) A[lane][j] -= A[lane][k] * A[j][k];
-    __syncwarp();
+    // Cholesky A = L L^T (lower, in place), lanes own rows
+    bool lbad = false;
+    for (int k = 0; k < 12; ++k) {
+      if (lane == k) {
+        const double d = A[k][k];
+        if (!(d > 0.0)) lbad = true;
+        A[k][k] = sqrt(fmax(d, 1e-300));
+      }
+      __syncwarp();
+      if (lane > k && lane < 12) A[lane][k] /= A[k][k];
+      __syncwarp();
+      if (lane > k && lane < 12)
+        for (int j = k + 1; j <= lane; ++j) A[lane][j] -= A[lane][k] * A[j][k];
+      __syncwarp();
+    }
+    bad = __any_sync(0xffffffffu, lbad);
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) st->error = POVAR_ENUMERIC;
+  if (lane == 0) {
+    if (bad) st->error = POVAR_ENUMERIC;
+    else if (attempt > 1) atomicAdd(&st->n_regularized, 1);
+  }
   // L^-1 by columns (lane c owns column c)
   if (lane < 12) {
     const int c = lane;

@@ -59,6 +59,7 @@ struct DeviceState {
   int error;         // povar_status of a device-detected error
   int max_iters;     // iteration cap for povar_solve (0: none)
   int n_pinv;        // landmarks solved by pseudo-inverse at the last solve
+  int n_regularized; // camera blocks whose damping had to be raised (cumulative)
 };
 
 // Host-side handle.
