@@ -330,9 +330,9 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
   ALLOC(p->bp64, nc * 12);
   ALLOC(p->G64, nc * 144);
   ALLOC(p->G32, nc * 144);
-  ALLOC(p->Y32, nc * 12);
+  ALLOC(p->Y32, 2 * nc * 12);
   ALLOC(p->D32, nc * 12);
-  ALLOC(p->Y64, nc * 12);
+  ALLOC(p->Y64, 2 * nc * 12);
   ALLOC(p->D64, nc * 12);
   ALLOC(p->camnorm, nc * 2);
   for (int t = 0; t < 2; ++t) {

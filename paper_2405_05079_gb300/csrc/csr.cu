@@ -526,10 +526,13 @@ povar_status build_runs(Problem* p) {
   }
   p->nrows = nrows;
   p->npart = npart;
+  p->nc_parts = 0;
+  for (int c = 0; c < p->nc; ++c) p->nc_parts += poff[c + 1] > poff[c] ? 1 : 0;
   if ((s = dev_alloc(p, &p->row_mask, mask.size(), "row_mask")) ||
       (s = dev_alloc(p, &p->row_base, base.size(), "row_base")) ||
       (s = dev_alloc(p, &p->cam_part_off, poff.size(), "cam_part_off")) ||
       (s = dev_alloc(p, &p->cam_part_idx, pidx.size(), "cam_part_idx")) ||
+      (s = dev_alloc(p, &p->cam_count, (size_t)p->nc, "cam_count")) ||
       (s = dev_alloc_bytes(p, &p->part_run, std::max<int64_t>(npart, 1) * 12 * sizeof(double),
                            "part_run")))
     return s;
@@ -537,6 +540,7 @@ povar_status build_runs(Problem* p) {
   POVAR_CUDA(cudaMemcpy(p->row_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice));
   POVAR_CUDA(cudaMemcpy(p->cam_part_off, poff.data(), poff.size() * 4, cudaMemcpyHostToDevice));
   POVAR_CUDA(cudaMemcpy(p->cam_part_idx, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice));
+  POVAR_CUDA(cudaMemset(p->cam_count, 0, (size_t)p->nc * 4));
   return POVAR_OK;
 }
 

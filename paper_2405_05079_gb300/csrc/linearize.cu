@@ -281,7 +281,8 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
     }
   }
   if (lane < 12) {
-    Y[(size_t)i * 12 + lane] = (T)x0;
+    Y[(size_t)i * 12 + lane] = (T)x0;                    // term parity 0
+    Y[((size_t)nc + i) * 12 + lane] = (T)0;              // term parity 1
     D[(size_t)i * 12 + lane] = (T)x0;
   }
   if (lane < 2) camnorm[2 * (size_t)i + lane] = 0.0;

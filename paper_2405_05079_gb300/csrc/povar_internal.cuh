@@ -109,6 +109,8 @@ struct Problem {
   uint32_t* cam_part_off = nullptr; // [nc + 1]
   uint32_t* cam_part_idx = nullptr; // [npart]
   void* part_run = nullptr;         // [npart * 12] float or double
+  uint32_t* cam_count = nullptr;    // [nc] partials written in the current term
+  int32_t nc_parts = 0;             // cameras with at least one partial
   int schedule_default = 1;         // chosen at creation from the run statistics
   // cameras
   double* P64[2] = {nullptr, nullptr};  // [nc*12]
@@ -118,9 +120,9 @@ struct Problem {
   double* bp64 = nullptr;               // [nc*12]
   double* G64 = nullptr;                // [nc*144]
   float* G32 = nullptr;                 // [nc*144]
-  float* Y32 = nullptr;                 // [nc*12]
+  float* Y32 = nullptr;                 // [2*nc*12] series vector, double-buffered by term parity
   float* D32 = nullptr;                 // [nc*12]
-  double* Y64 = nullptr;
+  double* Y64 = nullptr;                // [2*nc*12]
   double* D64 = nullptr;
   double* camnorm = nullptr;            // [nc*2]
   void* part_lin = nullptr;             // [nchunks*LIN_ACC] float or double

@@ -170,16 +170,37 @@ k_series_gather(const DeviceState* __restrict__ st, T a,
 // z_i: x_i = G_i z_i, delta_i += x_i, Y_i = x_i; with the threshold rule
 // (eps > 0) the last camera to finish (atomic ticket over `n_tickets`
 // cameras) adds the per-camera norms in camera order and sets the stop flag.
+template <typename T> struct Row12;
+template <> struct Row12<float> {
+  static __device__ __forceinline__ void load(const float* src, float r[12]) {
+    const float4* q = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 x = __ldg(q + k);
+      r[4 * k] = x.x; r[4 * k + 1] = x.y; r[4 * k + 2] = x.z; r[4 * k + 3] = x.w;
+    }
+  }
+};
+template <> struct Row12<double> {
+  static __device__ __forceinline__ void load(const double* src, double r[12]) {
+    const double2* q = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double2 x = __ldg(q + k);
+      r[2 * k] = x.x; r[2 * k + 1] = x.y;
+    }
+  }
+};
+
 template <typename T>
 __device__ __forceinline__ void camera_update(int i, int lane, T z, const T* __restrict__ G,
                                               T* __restrict__ Y, T* __restrict__ D, double& yy,
                                               double& dd) {
+  T g[12];
+  Row12<T>::load(G + 144 * (size_t)i + 12 * (lane < 12 ? lane : 0), g);
   T x = 0;
 #pragma unroll
-  for (int q = 0; q < 12; ++q) {
-    const T zq = __shfl_sync(0xffffffffu, z, q);
-    if (lane < 12) x += G[144 * (size_t)i + 12 * lane + q] * zq;
-  }
+  for (int q = 0; q < 12; ++q) x += g[q] * __shfl_sync(0xffffffffu, z, q);
   T y2 = 0, d2 = 0;
   if (lane < 12) {
     const T d = D[12 * (size_t)i + lane] + x;
@@ -515,81 +536,78 @@ template <> struct Rec12<double> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
                const uint32_t* __restrict__ cam_part_off, const uint32_t* __restrict__ cam_part_idx,
-               const T* __restrict__ part, const T* __restrict__ G, double* __restrict__ blocksum,
+               const T* __restrict__ part, const T* __restrict__ G, double* __restrict__ camnorm,
                uint32_t* __restrict__ done_ticket, T* __restrict__ Y, T* __restrict__ D) {
+  // one block of 4 warps per camera: each warp adds a strided quarter of the
+  // camera's partials, the four warp sums are combined in a fixed order
   if (st->converged || st->stop_series) return;
-  __shared__ double sh_yy[8], sh_dd[8];
+  __shared__ T sh[4][12];
   __shared__ int sh_last;
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int i = blockIdx.x * 8 + wl;
-  double yy = 0.0, dd = 0.0;
-  if (i < nc) {
-    T acc[12];
+  const int i = blockIdx.x;
+  T acc[12];
 #pragma unroll
-    for (int e = 0; e < 12; ++e) acc[e] = 0;
-    const uint32_t b = cam_part_off[i], e_ = cam_part_off[i + 1];
-    uint32_t q = b + lane;
-    for (; q + 32 < e_; q += 64) {
-      const uint32_t i0 = __ldg(cam_part_idx + q), i1 = __ldg(cam_part_idx + q + 32);
-      Rec12<T>::add(part + (size_t)i0 * 12, acc);
-      Rec12<T>::add(part + (size_t)i1 * 12, acc);
-    }
-    if (q < e_) Rec12<T>::add(part + (size_t)__ldg(cam_part_idx + q) * 12, acc);
-#pragma unroll
-    for (int e = 0; e < 12; ++e) {
-      T v = acc[e];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[e] = v;
-    }
-    T z = 0;
-#pragma unroll
-    for (int e = 0; e < 12; ++e)
-      if (lane == e) z = acc[e];
-    camera_update<T>(i, lane, z, G, Y, D, yy, dd);
+  for (int e = 0; e < 12; ++e) acc[e] = 0;
+  const uint32_t b = cam_part_off[i], e_ = cam_part_off[i + 1];
+  uint32_t q = b + threadIdx.x;
+  for (; q + 128 < e_; q += 256) {
+    const uint32_t i0 = __ldg(cam_part_idx + q), i1 = __ldg(cam_part_idx + q + 128);
+    Rec12<T>::add(part + (size_t)i0 * 12, acc);
+    Rec12<T>::add(part + (size_t)i1 * 12, acc);
   }
+  if (q < e_) Rec12<T>::add(part + (size_t)__ldg(cam_part_idx + q) * 12, acc);
+#pragma unroll
+  for (int e = 0; e < 12; ++e) {
+    T v = acc[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    acc[e] = v;
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int e = 0; e < 12; ++e) sh[wl][e] = acc[e];
+  __syncthreads();
+  if (wl != 0) return;
+  T z = 0;
+  if (lane < 12) z = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
+  double yy, dd;
+  camera_update<T>(i, lane, z, G, Y, D, yy, dd);
   if (eps <= 0.0) return;
   if (lane == 0) {
-    sh_yy[wl] = yy;
-    sh_dd[wl] = dd;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double by = 0.0, bd = 0.0;
-    for (int w = 0; w < 8; ++w) {
-      by += sh_yy[w];
-      bd += sh_dd[w];
-    }
-    blocksum[2 * (size_t)blockIdx.x] = by;
-    blocksum[2 * (size_t)blockIdx.x + 1] = bd;
+    camnorm[2 * (size_t)i] = yy;
+    camnorm[2 * (size_t)i + 1] = dd;
     __threadfence();
-    sh_last = atomicAdd(done_ticket, 1u) == gridDim.x - 1;
+    sh_last = atomicAdd(done_ticket, 1u) == (unsigned)(nc - 1);
   }
-  __syncthreads();
+  __syncwarp();
   if (!sh_last) return;
   __threadfence();
-  __shared__ double ry[256], rd[256];
   double sy = 0.0, sd = 0.0;
-  for (unsigned q = threadIdx.x; q < gridDim.x; q += 256) {
-    sy += __ldcg(blocksum + 2 * (size_t)q);
-    sd += __ldcg(blocksum + 2 * (size_t)q + 1);
-  }
-  ry[threadIdx.x] = sy;
-  rd[threadIdx.x] = sd;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      ry[threadIdx.x] += ry[threadIdx.x + o];
-      rd[threadIdx.x] += rd[threadIdx.x + o];
+  for (int c0 = 0; c0 < nc; c0 += 32 * 8) {
+    double vy[8], vd[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + u * 32 + lane;
+      vy[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c) : 0.0;
+      vd[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c + 1) : 0.0;
     }
-    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      sy += vy[u];
+      sd += vd[u];
+    }
   }
-  if (threadIdx.x == 0) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    sd += __shfl_xor_sync(0xffffffffu, sd, o);
+  }
+  if (lane == 0) {
     *done_ticket = 0;
-    if (ry[0] <= eps * eps * rd[0]) {
+    if (sy <= eps * eps * sd) {
       st->stop_series = 1;
       st->terms_used = term + 1;
     }
@@ -682,25 +700,28 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
                                 int schedule) {
   const double a64 = 1.0 - eta;   // C_k = B_k^T B_k coefficient, 1 - eta
   const float a32 = (float)a64;
+  // the series vector is double-buffered by term parity
+  const size_t yoff_in = ((term - 1) & 1) * (size_t)p->nc * 12;
+  const size_t yoff_out = (term & 1) * (size_t)p->nc * 12;
   if (schedule == 1) {
-    const unsigned ga = grid_for(p->nc, 8);
+    const unsigned ga = (unsigned)p->nc;
     if (precision == POVAR_FP64) {
       k_series_fused<double><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
           p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0],
-          p->P64[1], p->Y64, point_data<double>(p, 0), point_data<double>(p, 1), p->row_mask,
+          p->P64[1], p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1), p->row_mask,
           p->row_base, static_cast<double*>(p->part_run));
-      k_series_apply<double><<<ga, 256, 0, p->stream>>>(
+      k_series_apply<double><<<ga, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
-          static_cast<const double*>(p->part_run), p->G64, p->camnorm, p->done_ticket, p->Y64,
+          static_cast<const double*>(p->part_run), p->G64, p->camnorm, p->done_ticket, p->Y64 + yoff_out,
           p->D64);
     } else {
       k_series_fused<float><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
           p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
-          p->camP32[1], p->Y32, point_data<float>(p, 0), point_data<float>(p, 1), p->row_mask,
+          p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1), p->row_mask,
           p->row_base, static_cast<float*>(p->part_run));
-      k_series_apply<float><<<ga, 256, 0, p->stream>>>(
+      k_series_apply<float><<<ga, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
-          static_cast<const float*>(p->part_run), p->G32, p->camnorm, p->done_ticket, p->Y32,
+          static_cast<const float*>(p->part_run), p->G32, p->camnorm, p->done_ticket, p->Y32 + yoff_out,
           p->D32);
     }
     p->launches += 2;
@@ -709,11 +730,11 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
   const unsigned gs = grid_for(p->nchunks, 8);
   if (precision == POVAR_FP64) {
     k_series_gather<double, false><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
-        p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1], p->Y64,
+        p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1], p->Y64 + yoff_in,
         point_data<double>(p, 0), point_data<double>(p, 1), p->rec32, p->rec64, nullptr);
   } else {
     k_series_gather<float, false><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
-        p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0], p->camP32[1], p->Y32,
+        p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0], p->camP32[1], p->Y32 + yoff_in,
         point_data<float>(p, 0), point_data<float>(p, 1), p->rec32, p->rec64, nullptr);
   }
   ++p->launches;
@@ -723,13 +744,13 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
           p->state, a64, term, eps, p->nchunks, p->nc, p->nc_active, p->chunk_cam,
           p->chunk_beg, p->cam_nchunk, p->cam_chunk0, p->cm_slot, p->cm_m64, p->P64[0],
           p->P64[1], p->rec32, p->rec64, p->G64, static_cast<double*>(p->part_ser), p->cam_ticket,
-          p->done_ticket, p->camnorm, p->Y64, p->D64);
+          p->done_ticket, p->camnorm, p->Y64 + yoff_out, p->D64);
     } else {
       k_series_scatter<float><<<gs, 256, 0, p->stream>>>(
           p->state, a32, term, eps, p->nchunks, p->nc, p->nc_active, p->chunk_cam,
           p->chunk_beg, p->cam_nchunk, p->cam_chunk0, p->cm_slot, p->cm_m32, p->camP32[0],
           p->camP32[1], p->rec32, p->rec64, p->G32, static_cast<float*>(p->part_ser), p->cam_ticket,
-          p->done_ticket, p->camnorm, p->Y32, p->D32);
+          p->done_ticket, p->camnorm, p->Y32 + yoff_out, p->D32);
     }
     ++p->launches;
   }
