@@ -71,11 +71,13 @@ enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1 };
  *             POVAR_MIXED_FP32: series and linearization in FP32; landmark
  *             elimination, 12x12 inverses, cost and gain ratio in FP64.
  *  schedule   series schedule: 0 = landmark-major gather pass + camera-major
- *             scatter pass; 1 = one fused landmark-major pass whose camera
- *             contributions are reduced across the lanes of a warp that
- *             share a camera; -1 = chosen at creation (1 when the observation
- *             layout yields at most one partial sum per two observations).
- *             Both schedules compute the same series. */
+ *             scatter pass over observation chunks; 1 = one fused
+ *             landmark-major pass whose camera contributions are reduced
+ *             across the lanes of a warp that share a camera; 2 =
+ *             landmark-major gather pass + camera-major pass over the
+ *             landmark slice rows that contain each camera; -1 = chosen at
+ *             creation from the observation layout. All schedules compute
+ *             the same series. */
 typedef struct {
   double eta;
   double lambda0;

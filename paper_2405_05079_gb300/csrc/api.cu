@@ -65,7 +65,7 @@ povar_status check_params(Problem* p, const povar_params* q) {
     return fail(p, POVAR_EINVAL, "unknown manifold");
   if (q->precision != POVAR_FP64 && q->precision != POVAR_MIXED_FP32)
     return fail(p, POVAR_EINVAL, "unknown precision");
-  if (q->schedule < -1 || q->schedule > 1) return fail(p, POVAR_EINVAL, "unknown schedule");
+  if (q->schedule < -1 || q->schedule > 2) return fail(p, POVAR_EINVAL, "unknown schedule");
   return POVAR_OK;
 }
 

@@ -516,6 +516,46 @@ povar_status build_runs(Problem* p) {
     }
     mask[row] = m;
   }
+  // camera-row lists: every distinct valid camera of every slice row
+  std::vector<uint32_t> voff(p->nc + 1, 0);
+  std::vector<std::pair<uint32_t, uint32_t>> vis;  // (camera, row) in row order
+  {
+    std::vector<uint32_t> row_slice(std::max<int64_t>(nrows, 1), 0);
+    for (int sl = 0; sl < p->nslices; ++sl)
+      for (uint32_t r = off[sl] / SLICE; r < off[sl + 1] / SLICE; ++r) row_slice[r] = sl;
+    vis.reserve(nrows + nrows / 4);
+    int32_t seen[SLICE];
+    for (int64_t row = 0; row < nrows; ++row) {
+      const int32_t* c = cam.data() + row * SLICE;
+      int nseen = 0;
+      for (int l = 0; l < SLICE; ++l) {
+        if (c[l] < 0) continue;
+        bool dup = false;
+        for (int q = 0; q < nseen; ++q) dup |= seen[q] == c[l];
+        if (!dup) {
+          seen[nseen++] = c[l];
+          vis.emplace_back((uint32_t)c[l], (uint32_t)row);
+        }
+      }
+    }
+    for (const auto& v : vis) ++voff[v.first + 1];
+    for (int c = 0; c < p->nc; ++c) voff[c + 1] += voff[c];
+    std::vector<uint32_t> cursor(voff.begin(), voff.end() - 1);
+    std::vector<uint32_t> pos0(std::max<size_t>(vis.size(), 1)), slot0(std::max<size_t>(vis.size(), 1));
+    for (const auto& v : vis) {
+      const uint32_t q = cursor[v.first]++;
+      pos0[q] = v.second * SLICE;
+      slot0[q] = row_slice[v.second] * SLICE;
+    }
+    p->nvisits = (int64_t)vis.size();
+    if ((s = dev_alloc(p, &p->cam_row_off, voff.size(), "cam_row_off")) ||
+        (s = dev_alloc(p, &p->cam_row_pos0, pos0.size(), "cam_row_pos0")) ||
+        (s = dev_alloc(p, &p->cam_row_slot0, slot0.size(), "cam_row_slot0")))
+      return s;
+    POVAR_CUDA(cudaMemcpy(p->cam_row_off, voff.data(), voff.size() * 4, cudaMemcpyHostToDevice));
+    POVAR_CUDA(cudaMemcpy(p->cam_row_pos0, pos0.data(), pos0.size() * 4, cudaMemcpyHostToDevice));
+    POVAR_CUDA(cudaMemcpy(p->cam_row_slot0, slot0.data(), slot0.size() * 4, cudaMemcpyHostToDevice));
+  }
   const int64_t npart = (int64_t)pcam.size();
   std::vector<uint32_t> poff(p->nc + 1, 0), pidx(std::max<int64_t>(npart, 1));
   for (int32_t c : pcam) ++poff[c + 1];
@@ -532,7 +572,6 @@ povar_status build_runs(Problem* p) {
       (s = dev_alloc(p, &p->row_base, base.size(), "row_base")) ||
       (s = dev_alloc(p, &p->cam_part_off, poff.size(), "cam_part_off")) ||
       (s = dev_alloc(p, &p->cam_part_idx, pidx.size(), "cam_part_idx")) ||
-      (s = dev_alloc(p, &p->cam_count, (size_t)p->nc, "cam_count")) ||
       (s = dev_alloc_bytes(p, &p->part_run, std::max<int64_t>(npart, 1) * 12 * sizeof(double),
                            "part_run")))
     return s;
@@ -540,7 +579,6 @@ povar_status build_runs(Problem* p) {
   POVAR_CUDA(cudaMemcpy(p->row_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice));
   POVAR_CUDA(cudaMemcpy(p->cam_part_off, poff.data(), poff.size() * 4, cudaMemcpyHostToDevice));
   POVAR_CUDA(cudaMemcpy(p->cam_part_idx, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice));
-  POVAR_CUDA(cudaMemset(p->cam_count, 0, (size_t)p->nc * 4));
   return POVAR_OK;
 }
 

@@ -109,8 +109,13 @@ struct Problem {
   uint32_t* cam_part_off = nullptr; // [nc + 1]
   uint32_t* cam_part_idx = nullptr; // [npart]
   void* part_run = nullptr;         // [npart * 12] float or double
-  uint32_t* cam_count = nullptr;    // [nc] partials written in the current term
   int32_t nc_parts = 0;             // cameras with at least one partial
+  // camera-row schedule: for camera i, the slice rows that contain it, as the
+  // SELL position and the slot of lane 0 of the row (rows in index order)
+  int64_t nvisits = 0;
+  uint32_t* cam_row_off = nullptr;  // [nc + 1]
+  uint32_t* cam_row_pos0 = nullptr; // [nvisits]
+  uint32_t* cam_row_slot0 = nullptr;// [nvisits]
   int schedule_default = 1;         // chosen at creation from the run statistics
   // cameras
   double* P64[2] = {nullptr, nullptr};  // [nc*12]

@@ -116,36 +116,43 @@ k_series_gather(const DeviceState* __restrict__ st, T a,
   T X[3], F[6];
   load_point<T>(pd, s, X, F);
   T t0 = 0, t1 = 0, t2 = 0;
-  // pass 1, software-pipelined: the next observation's camera index and
-  // measurement are loaded while the current one is processed
+  // observations in chunks of RB: the chunk's camera indices and
+  // measurements are loaded together so that RB rows are in flight per warp
   using M2 = typename Vt<T>::m2;
-  int i_n = len > 0 ? sell_cam[base] : 0;
-  M2 m_n = len > 0 ? sell_m[base] : M2{0, 0};
-  for (uint32_t k = 0; k < len; ++k) {
-    const int i = i_n;
-    const auto m = m_n;
-    if (k + 1 < len) {
-      i_n = sell_cam[base + (k + 1) * SLICE];
-      m_n = sell_m[base + (k + 1) * SLICE];
+  constexpr int RB = 4;
+  for (uint32_t k0 = 0; k0 < len; k0 += RB) {
+    int ci[RB];
+    M2 mi[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const bool in = k0 + u < len;
+      ci[u] = in ? sell_cam[base + (k0 + u) * SLICE] : 0;
+      mi[u] = in ? sell_m[base + (k0 + u) * SLICE] : M2{0, 0};
     }
-    T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
-    load_row<T>(vec, i, 0, Y0);
-    load_row<T>(vec, i, 1, Y1);
-    load_row<T>(vec, i, 2, Y2);
-    load_row<T>(camP, i, 0, P0);
-    load_row<T>(camP, i, 1, P1);
-    load_row<T>(camP, i, 2, P2);
-    const T e0 = Y0[0] * X[0] + Y0[1] * X[1] + Y0[2] * X[2] + Y0[3];
-    const T e1 = Y1[0] * X[0] + Y1[1] * X[1] + Y1[2] * X[2] + Y1[3];
-    const T e2 = Y2[0] * X[0] + Y2[1] * X[1] + Y2[2] * X[2] + Y2[3];
-    const T au = a * (T)m.x, av = a * (T)m.y;
-    const T aw = au * (T)m.x + av * (T)m.y;
-    const T c0 = e0 - au * e2;
-    const T c1 = e1 - av * e2;
-    const T c2 = aw * e2 - au * e0 - av * e1;
-    t0 += P0[0] * c0 + P1[0] * c1 + P2[0] * c2;
-    t1 += P0[1] * c0 + P1[1] * c1 + P2[1] * c2;
-    t2 += P0[2] * c0 + P1[2] * c1 + P2[2] * c2;
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      if (k0 + u >= len) break;
+      const int i = ci[u];
+      const auto m = mi[u];
+      T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
+      load_row<T>(vec, i, 0, Y0);
+      load_row<T>(vec, i, 1, Y1);
+      load_row<T>(vec, i, 2, Y2);
+      load_row<T>(camP, i, 0, P0);
+      load_row<T>(camP, i, 1, P1);
+      load_row<T>(camP, i, 2, P2);
+      const T e0 = Y0[0] * X[0] + Y0[1] * X[1] + Y0[2] * X[2] + Y0[3];
+      const T e1 = Y1[0] * X[0] + Y1[1] * X[1] + Y1[2] * X[2] + Y1[3];
+      const T e2 = Y2[0] * X[0] + Y2[1] * X[1] + Y2[2] * X[2] + Y2[3];
+      const T au = a * (T)m.x, av = a * (T)m.y;
+      const T aw = au * (T)m.x + av * (T)m.y;
+      const T c0 = e0 - au * e2;
+      const T c1 = e1 - av * e2;
+      const T c2 = aw * e2 - au * e0 - av * e1;
+      t0 += P0[0] * c0 + P1[0] * c1 + P2[0] * c2;
+      t1 += P0[1] * c0 + P1[1] * c1 + P2[1] * c2;
+      t2 += P0[2] * c0 + P1[2] * c1 + P2[2] * c2;
+    }
   }
   // z = F t (F lower-triangular, V^-1 = F^T F)
   const T z0 = F[0] * t0;
@@ -398,36 +405,43 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
   T X[3], F[6];
   load_point<T>(pd, s, X, F);
   T t0 = 0, t1 = 0, t2 = 0;
-  // pass 1, software-pipelined: the next observation's camera index and
-  // measurement are loaded while the current one is processed
+  // pass 1 in chunks of RB observations: the chunk's camera indices and
+  // measurements are loaded together so that RB rows are in flight per warp
   using M2 = typename Vt<T>::m2;
-  int i_n = len > 0 ? sell_cam[base] : 0;
-  M2 m_n = len > 0 ? sell_m[base] : M2{0, 0};
-  for (uint32_t k = 0; k < len; ++k) {
-    const int i = i_n;
-    const auto m = m_n;
-    if (k + 1 < len) {
-      i_n = sell_cam[base + (k + 1) * SLICE];
-      m_n = sell_m[base + (k + 1) * SLICE];
+  constexpr int RB = 4;
+  for (uint32_t k0 = 0; k0 < len; k0 += RB) {
+    int ci[RB];
+    M2 mi[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const bool in = k0 + u < len;
+      ci[u] = in ? sell_cam[base + (k0 + u) * SLICE] : 0;
+      mi[u] = in ? sell_m[base + (k0 + u) * SLICE] : M2{0, 0};
     }
-    T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
-    load_row<T>(vec, i, 0, Y0);
-    load_row<T>(vec, i, 1, Y1);
-    load_row<T>(vec, i, 2, Y2);
-    load_row<T>(camP, i, 0, P0);
-    load_row<T>(camP, i, 1, P1);
-    load_row<T>(camP, i, 2, P2);
-    const T e0 = Y0[0] * X[0] + Y0[1] * X[1] + Y0[2] * X[2] + Y0[3];
-    const T e1 = Y1[0] * X[0] + Y1[1] * X[1] + Y1[2] * X[2] + Y1[3];
-    const T e2 = Y2[0] * X[0] + Y2[1] * X[1] + Y2[2] * X[2] + Y2[3];
-    const T au = a * (T)m.x, av = a * (T)m.y;
-    const T aw = au * (T)m.x + av * (T)m.y;
-    const T c0 = e0 - au * e2;
-    const T c1 = e1 - av * e2;
-    const T c2 = aw * e2 - au * e0 - av * e1;
-    t0 += P0[0] * c0 + P1[0] * c1 + P2[0] * c2;
-    t1 += P0[1] * c0 + P1[1] * c1 + P2[1] * c2;
-    t2 += P0[2] * c0 + P1[2] * c1 + P2[2] * c2;
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      if (k0 + u >= len) break;
+      const int i = ci[u];
+      const auto m = mi[u];
+      T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
+      load_row<T>(vec, i, 0, Y0);
+      load_row<T>(vec, i, 1, Y1);
+      load_row<T>(vec, i, 2, Y2);
+      load_row<T>(camP, i, 0, P0);
+      load_row<T>(camP, i, 1, P1);
+      load_row<T>(camP, i, 2, P2);
+      const T e0 = Y0[0] * X[0] + Y0[1] * X[1] + Y0[2] * X[2] + Y0[3];
+      const T e1 = Y1[0] * X[0] + Y1[1] * X[1] + Y1[2] * X[2] + Y1[3];
+      const T e2 = Y2[0] * X[0] + Y2[1] * X[1] + Y2[2] * X[2] + Y2[3];
+      const T au = a * (T)m.x, av = a * (T)m.y;
+      const T aw = au * (T)m.x + av * (T)m.y;
+      const T c0 = e0 - au * e2;
+      const T c1 = e1 - av * e2;
+      const T c2 = aw * e2 - au * e0 - av * e1;
+      t0 += P0[0] * c0 + P1[0] * c1 + P2[0] * c2;
+      t1 += P0[1] * c0 + P1[1] * c1 + P2[1] * c2;
+      t2 += P0[2] * c0 + P1[2] * c1 + P2[2] * c2;
+    }
   }
   const T z0 = F[0] * t0;
   const T z1 = F[1] * t0 + F[2] * t1;
@@ -437,23 +451,27 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
   const T S2 = F[5] * z2;
   const uint32_t row0 = sbeg / SLICE;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  // pass 2, software-pipelined over the slice rows (row metadata and the
-  // lane's camera index of the next row are loaded ahead)
-  int ip = width > 0 && len > 0 ? sell_cam[base] : -1;
-  M2 mp = width > 0 ? sell_m[base] : M2{0, 0};
-  uint32_t maskp = width > 0 ? __ldg(row_mask + row0) : 0u;
-  uint32_t basep = width > 0 ? __ldg(row_base + row0) : 0u;
-  for (uint32_t k = 0; k < width; ++k) {
-    const int i = ip;
-    const auto m = mp;
-    const uint32_t mask = maskp, pbase = basep;
-    if (k + 1 < width) {
-      const uint32_t pn = base + (k + 1) * SLICE;
-      ip = k + 1 < len ? sell_cam[pn] : -1;
-      mp = sell_m[pn];
-      maskp = __ldg(row_mask + row0 + k + 1);
-      basep = __ldg(row_base + row0 + k + 1);
+  // pass 2 in chunks of RB slice rows: the rows' camera indices,
+  // measurements and run metadata are loaded together
+  for (uint32_t k0 = 0; k0 < width; k0 += RB) {
+    int ci[RB];
+    M2 mi[RB];
+    uint32_t mk[RB], bk[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const bool rin = k0 + u < width;
+      const bool in = k0 + u < len;
+      ci[u] = in ? sell_cam[base + (k0 + u) * SLICE] : -1;
+      mi[u] = in ? sell_m[base + (k0 + u) * SLICE] : M2{0, 0};
+      mk[u] = rin ? __ldg(row_mask + row0 + k0 + u) : 0u;
+      bk[u] = rin ? __ldg(row_base + row0 + k0 + u) : 0u;
     }
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+    if (k0 + u >= width) break;
+    const int i = ci[u];
+    const auto m = mi[u];
+    const uint32_t mask = mk[u], pbase = bk[u];
     T v[12];
 #pragma unroll
     for (int e = 0; e < 12; ++e) v[e] = 0;
@@ -505,6 +523,7 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
 #pragma unroll
         for (int e = 0; e < 12; ++e) out[e] = v[e];
       }
+    }
     }
   }
 }
@@ -569,6 +588,126 @@ k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
   if (lane == 0)
 #pragma unroll
     for (int e = 0; e < 12; ++e) sh[wl][e] = acc[e];
+  __syncthreads();
+  if (wl != 0) return;
+  T z = 0;
+  if (lane < 12) z = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
+  double yy, dd;
+  camera_update<T>(i, lane, z, G, Y, D, yy, dd);
+  if (eps <= 0.0) return;
+  if (lane == 0) {
+    camnorm[2 * (size_t)i] = yy;
+    camnorm[2 * (size_t)i + 1] = dd;
+    __threadfence();
+    sh_last = atomicAdd(done_ticket, 1u) == (unsigned)(nc - 1);
+  }
+  __syncwarp();
+  if (!sh_last) return;
+  __threadfence();
+  double sy = 0.0, sd = 0.0;
+  for (int c0 = 0; c0 < nc; c0 += 32 * 8) {
+    double vy[8], vd[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + u * 32 + lane;
+      vy[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c) : 0.0;
+      vd[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c + 1) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      sy += vy[u];
+      sd += vd[u];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    sd += __shfl_xor_sync(0xffffffffu, sd, o);
+  }
+  if (lane == 0) {
+    *done_ticket = 0;
+    if (sy <= eps * eps * sd) {
+      st->stop_series = 1;
+      st->terms_used = term + 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Camera-row schedule (2): after the landmark-major gather has written every
+// landmark's record (s_j, X_j), one block per camera walks the slice rows
+// that contain the camera (rows in index order, strided over the 4 warps).
+// Each lane adds the contribution vec((C_k Pbar_i s_j) x~_j^T) of its own
+// landmark when that landmark's observation in the row is of this camera, so
+// contributions accumulate in registers across rows; the block reduces once
+// per camera, in a fixed order, and applies the camera update.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_series_camrows(DeviceState* __restrict__ st, T a, int term, double eps, int nc,
+                 const uint32_t* __restrict__ cam_row_off,
+                 const uint32_t* __restrict__ cam_row_pos0,
+                 const uint32_t* __restrict__ cam_row_slot0, const int32_t* __restrict__ sell_cam,
+                 const typename Vt<T>::m2* __restrict__ sell_m, const T* __restrict__ camPa,
+                 const T* __restrict__ camPb, const float4* __restrict__ rec32,
+                 const double2* __restrict__ rec64, const T* __restrict__ G,
+                 double* __restrict__ camnorm, uint32_t* __restrict__ done_ticket,
+                 T* __restrict__ Y, T* __restrict__ D) {
+  if (st->converged || st->stop_series) return;
+  __shared__ T sh[4][12];
+  __shared__ int sh_last;
+  using M2 = typename Vt<T>::m2;
+  constexpr int RB = 4;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int i = blockIdx.x;
+  const T* __restrict__ camP = st->cur ? camPb : camPa;
+  T P0[4], P1[4], P2[4];
+  load_row<T>(camP, i, 0, P0);
+  load_row<T>(camP, i, 1, P1);
+  load_row<T>(camP, i, 2, P2);
+  T acc[12];
+#pragma unroll
+  for (int e = 0; e < 12; ++e) acc[e] = 0;
+  const uint32_t b = cam_row_off[i], e_ = cam_row_off[i + 1];
+  for (uint32_t q0 = b + wl; q0 < e_; q0 += 4 * RB) {
+    uint32_t pos[RB], slot[RB];
+    int cv[RB];
+    M2 mv[RB];
+    T S[RB][3], X[RB][3];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const uint32_t q = q0 + 4 * u;
+      const bool in = q < e_;
+      pos[u] = in ? __ldg(cam_row_pos0 + q) + lane : 0u;
+      slot[u] = in ? __ldg(cam_row_slot0 + q) + lane : 0u;
+      cv[u] = in ? sell_cam[pos[u]] : -1;
+      mv[u] = in ? sell_m[pos[u]] : M2{0, 0};
+      if (in) load_rec(rec32, rec64, slot[u], S[u], X[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      if (cv[u] != i) continue;
+      const T w0 = P0[0] * S[u][0] + P0[1] * S[u][1] + P0[2] * S[u][2];
+      const T w1 = P1[0] * S[u][0] + P1[1] * S[u][1] + P1[2] * S[u][2];
+      const T w2 = P2[0] * S[u][0] + P2[1] * S[u][1] + P2[2] * S[u][2];
+      const T au = a * (T)mv[u].x, av = a * (T)mv[u].y;
+      const T aw = au * (T)mv[u].x + av * (T)mv[u].y;
+      const T q0v = w0 - au * w2;
+      const T q1v = w1 - av * w2;
+      const T q2v = aw * w2 - au * w0 - av * w1;
+      acc[0] += q0v * X[u][0]; acc[1] += q0v * X[u][1]; acc[2] += q0v * X[u][2]; acc[3] += q0v;
+      acc[4] += q1v * X[u][0]; acc[5] += q1v * X[u][1]; acc[6] += q1v * X[u][2]; acc[7] += q1v;
+      acc[8] += q2v * X[u][0]; acc[9] += q2v * X[u][1]; acc[10] += q2v * X[u][2]; acc[11] += q2v;
+    }
+  }
+  T r[3];
+  int vb;
+  warp_reduce12<T>(acc, lane, r, vb);
+  if ((lane & 7) == 0) {
+    sh[wl][vb] = r[0];
+    sh[wl][vb + 1] = r[1];
+    sh[wl][vb + 2] = r[2];
+  }
   __syncthreads();
   if (wl != 0) return;
   T z = 0;
@@ -703,6 +842,29 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
   // the series vector is double-buffered by term parity
   const size_t yoff_in = ((term - 1) & 1) * (size_t)p->nc * 12;
   const size_t yoff_out = (term & 1) * (size_t)p->nc * 12;
+  if (schedule == 2) {
+    if (precision == POVAR_FP64) {
+      k_series_gather<double, false><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+          p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1],
+          p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1), p->rec32,
+          p->rec64, nullptr);
+      k_series_camrows<double><<<p->nc, 128, 0, p->stream>>>(
+          p->state, a64, term, eps, p->nc, p->cam_row_off, p->cam_row_pos0, p->cam_row_slot0,
+          p->sell_cam, p->sell_m64, p->P64[0], p->P64[1], p->rec32, p->rec64, p->G64,
+          p->camnorm, p->done_ticket, p->Y64 + yoff_out, p->D64);
+    } else {
+      k_series_gather<float, false><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+          p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
+          p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1),
+          p->rec32, p->rec64, nullptr);
+      k_series_camrows<float><<<p->nc, 128, 0, p->stream>>>(
+          p->state, a32, term, eps, p->nc, p->cam_row_off, p->cam_row_pos0, p->cam_row_slot0,
+          p->sell_cam, p->sell_m32, p->camP32[0], p->camP32[1], p->rec32, p->rec64, p->G32,
+          p->camnorm, p->done_ticket, p->Y32 + yoff_out, p->D32);
+    }
+    p->launches += 2;
+    return check_launch(p, "series_term (camera rows)");
+  }
   if (schedule == 1) {
     const unsigned ga = (unsigned)p->nc;
     if (precision == POVAR_FP64) {
