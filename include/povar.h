@@ -203,6 +203,15 @@ povar_status povar_set_profiling(povar_problem* p, int32_t enable);
 povar_status povar_get_profile(povar_problem* p, double* ms_out, int64_t* steps_out,
                                int32_t reset);
 
+/* Series-schedule autotuner. The first povar_solve with params->schedule
+ * = -1 times two series terms of every schedule (0, 1, 2) on the live
+ * state with CUDA events and keeps the fastest for that precision; later
+ * solves and povar_step with schedule -1 use it. povar_get_tuning returns the
+ * chosen schedule (-1 before tuning) and the three measured times in
+ * milliseconds (ms_out[3], may be NULL). */
+povar_status povar_get_tuning(povar_problem* p, int32_t precision, int32_t* schedule_out,
+                              float* ms_out);
+
 /* Number of kernel launches this handle has issued so far. */
 int64_t povar_launch_count(const povar_problem* p);
 

@@ -129,7 +129,8 @@ povar_status enqueue_step_kernels(Problem* p, const povar_params* q, std::vector
                                   const cudaEvent_t* fixed = nullptr) {
   povar_status s;
   const int prec = q->precision;
-  const int sched = q->schedule < 0 ? p->schedule_default : q->schedule;
+  const int tuned = p->tuned_schedule[q->precision == POVAR_FP64 ? 0 : 1];
+  const int sched = q->schedule >= 0 ? q->schedule : (tuned >= 0 ? tuned : p->schedule_default);
   int nmark = 0;
   // phase boundary: a pooled event (eager profiling) or a fixed event node
   // (profiling inside the step graph)
@@ -188,6 +189,42 @@ void sample_graph_profile(Problem* p) {
   ++p->prof_count;
 }
 
+// Series-schedule autotuner: on the live state of the first step, time two
+// series terms of every schedule with CUDA events and keep the fastest for
+// this precision. The damped blocks are re-prepared afterwards, so the solve
+// continues from exactly the state it would have had without tuning.
+povar_status autotune_schedule(Problem* p, const povar_params* q) {
+  const int prec = q->precision == POVAR_FP64 ? 0 : 1;
+  if (p->tuned_schedule[prec] >= 0) return POVAR_OK;
+  povar_status s;
+  if ((s = prepare_step(p, q)) != POVAR_OK) return s;
+  if ((s = launch_linearize(p, q->precision, q->eta)) != POVAR_OK) return s;
+  cudaEvent_t ev[4];
+  for (int k = 0; k < 4; ++k) POVAR_CUDA(cudaEventCreate(&ev[k]));
+  int best = 1;
+  float best_ms = 1e30f;
+  for (int sched = 0; sched < 3; ++sched) {
+    if ((s = launch_camera_prepare(p, q->precision, q->manifold, q->eta)) != POVAR_OK) break;
+    POVAR_CUDA(cudaEventRecord(ev[0], p->stream));
+    for (int k = 1; k <= 2 && s == POVAR_OK; ++k)
+      s = launch_series_term(p, q->precision, q->eta, k, 0.0, sched);
+    if (s != POVAR_OK) break;
+    POVAR_CUDA(cudaEventRecord(ev[1], p->stream));
+    POVAR_CUDA(cudaEventSynchronize(ev[1]));
+    float ms = 0.f;
+    POVAR_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    p->tune_ms[prec][sched] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = sched;
+    }
+  }
+  for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
+  if (s != POVAR_OK) return s;
+  p->tuned_schedule[prec] = best;
+  return POVAR_OK;
+}
+
 bool same_params(const povar_params& a, const povar_params& b) {
   return a.eta == b.eta && a.series_eps == b.series_eps && a.m == b.m &&
          a.manifold == b.manifold && a.precision == b.precision && a.schedule == b.schedule;
@@ -195,7 +232,8 @@ bool same_params(const povar_params& a, const povar_params& b) {
 
 // Graph of one step on p->gstream (captured once per parameter set).
 povar_status step_graph(Problem* p, const povar_params* q) {
-  const int sched = q->schedule < 0 ? p->schedule_default : q->schedule;
+  const int tuned = p->tuned_schedule[q->precision == POVAR_FP64 ? 0 : 1];
+  const int sched = q->schedule >= 0 ? q->schedule : (tuned >= 0 ? tuned : p->schedule_default);
   if (p->gexec && same_params(p->gkey, *q) && p->gkey_sched == sched &&
       p->g_profiled == p->profiling)
     return POVAR_OK;
@@ -509,6 +547,7 @@ povar_status povar_solve(povar_problem* pp, const povar_params* params, int32_t 
     // one graph launch per step on the library stream, joined to the
     // caller's stream with events before and after
     if ((s = povar::prepare_step(p, params)) != POVAR_OK) return s;
+    if (params->schedule < 0 && (s = povar::autotune_schedule(p, params)) != POVAR_OK) return s;
     if ((s = povar::step_graph(p, params)) != POVAR_OK) return s;
     POVAR_CUDA(cudaEventRecord(p->ev_join, p->stream));
     POVAR_CUDA(cudaStreamWaitEvent(p->gstream, p->ev_join, 0));
@@ -581,6 +620,19 @@ povar_status povar_get_profile(povar_problem* pp, double* ms_out, int64_t* steps
     for (int ph = 0; ph < POVAR_NPHASES; ++ph) p->prof_ms[ph] = 0.0;
     p->prof_count = 0;
   }
+  return POVAR_OK;
+}
+
+povar_status povar_get_tuning(povar_problem* pp, int32_t precision, int32_t* schedule_out,
+                              float* ms_out) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  if (precision != POVAR_FP64 && precision != POVAR_MIXED_FP32)
+    return povar::fail(p, POVAR_EINVAL, "unknown precision");
+  const int k = precision == POVAR_FP64 ? 0 : 1;
+  if (schedule_out) *schedule_out = p->tuned_schedule[k];
+  if (ms_out)
+    for (int q = 0; q < 3; ++q) ms_out[q] = p->tune_ms[k][q];
   return POVAR_OK;
 }
 

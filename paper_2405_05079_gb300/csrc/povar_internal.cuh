@@ -117,6 +117,8 @@ struct Problem {
   uint32_t* cam_row_pos0 = nullptr; // [nvisits]
   uint32_t* cam_row_slot0 = nullptr;// [nvisits]
   int schedule_default = 1;         // chosen at creation from the run statistics
+  int tuned_schedule[2] = {-1, -1}; // autotuned series schedule per precision (-1: not yet)
+  float tune_ms[2][3] = {};         // measured ms of two series terms per schedule
   // cameras
   double* P64[2] = {nullptr, nullptr};  // [nc*12]
   double* Ltab = nullptr;               // [nc*48] landmark tables at trial P

@@ -78,13 +78,14 @@ def lib() -> C.CDLL:
     L.povar_get_last_step.argtypes = [vp, dp, dp, dp]
     L.povar_set_profiling.argtypes = [vp, i32]
     L.povar_get_profile.argtypes = [vp, dp, C.POINTER(C.c_int64), i32]
+    L.povar_get_tuning.argtypes = [vp, i32, C.POINTER(C.c_int32), C.POINTER(C.c_float)]
     L.povar_launch_count.argtypes = [vp]
     L.povar_launch_count.restype = i64
     L.povar_version.restype = C.c_char_p
     for name in ("povar_create", "povar_set_cameras", "povar_init_random", "povar_get_cameras",
                  "povar_get_points", "povar_cost", "povar_step", "povar_solve",
                  "povar_get_orders", "povar_get_last_step", "povar_set_profiling",
-                 "povar_get_profile"):
+                 "povar_get_profile", "povar_get_tuning"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -224,6 +225,12 @@ class Problem:
         self._check(lib().povar_get_last_step(self._h, _ptr(U, C.c_double),
                                               _ptr(bp, C.c_double), _ptr(d, C.c_double)))
         return U, bp, d
+
+    def tuning(self, precision: int):
+        sched = C.c_int32()
+        ms = (C.c_float * 3)()
+        self._check(lib().povar_get_tuning(self._h, precision, C.byref(sched), ms))
+        return sched.value, list(ms)
 
     @property
     def launch_count(self) -> int:

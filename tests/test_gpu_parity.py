@@ -364,7 +364,7 @@ def test_graph_solve_equals_eager_steps(precision):
     sc = SCENES["traj"]()
     P0 = scenes.init_cameras(sc.n_cams, 2, normalize=True)
     prm = povar.make_params(eta=sc.eta, m=9, series_eps=0.01, manifold=povar.EUCLID,
-                            precision=precision)
+                            precision=precision, schedule=1)
     with povar.Problem.from_scene(sc) as a, povar.Problem.from_scene(sc) as b:
         a.set_cameras(P0, sc.eta)
         b.set_cameras(P0, sc.eta)
@@ -374,3 +374,24 @@ def test_graph_solve_equals_eager_steps(precision):
         assert iters == 6
         assert np.array_equal(a.cameras(), b.cameras())
         assert a.cost(sc.eta) == b.cost(sc.eta)
+
+
+def test_autotuner_picks_a_schedule_without_changing_the_solve():
+    """The schedule autotuner runs on the live state of the first solve and
+    restores it: the tuned solve equals a solve with the chosen schedule."""
+    sc = SCENES["traj"]()
+    P0 = scenes.init_cameras(sc.n_cams, 5, normalize=True)
+    auto = povar.make_params(eta=sc.eta, m=8, manifold=povar.EUCLID, precision=povar.FP64,
+                             schedule=-1)
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        pb.solve(auto, max_iters=4, ftol=0.0)
+        sched, ms = pb.tuning(povar.FP64)
+        P_auto = pb.cameras()
+    assert sched in (0, 1, 2) and all(t > 0 for t in ms)
+    fixed = povar.make_params(eta=sc.eta, m=8, manifold=povar.EUCLID, precision=povar.FP64,
+                              schedule=sched)
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        pb.solve(fixed, max_iters=4, ftol=0.0)
+        assert np.array_equal(pb.cameras(), P_auto)
