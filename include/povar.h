@@ -215,6 +215,34 @@ povar_status povar_get_tuning(povar_problem* p, int32_t precision, int32_t* sche
 /* Number of kernel launches this handle has issued so far. */
 int64_t povar_launch_count(const povar_problem* p);
 
+/* ---- batches of independent problems ----
+ * Many independent problems of uneven sizes, given as concatenated arrays
+ * with per-problem sizes: problem k has n_cams[k] cameras, n_points[k]
+ * landmarks and n_obs[k] observations; its observations follow those of
+ * problems 0..k-1 in cam_idx / pt_idx / meas (2 doubles each), with indices
+ * local to the problem. Cameras of all problems are concatenated likewise
+ * (12 doubles per camera). povar_batch_solve runs every iteration of every
+ * problem as one CUDA-graph launch whose child graphs are the problems' step
+ * graphs (no dependencies between problems, so their kernels overlap); each
+ * problem stops on its own device-side convergence flag; the host checks the
+ * flags every fourth iteration. Results are identical to solving each
+ * problem alone with the same parameters and schedule. target_costs,
+ * reports and iters_out hold one entry per problem (each may be NULL). */
+typedef struct povar_batch povar_batch;
+povar_status povar_batch_create(int32_t n_problems, const int32_t* n_cams,
+                                const int32_t* n_points, const int64_t* n_obs,
+                                const int32_t* cam_idx, const int32_t* pt_idx,
+                                const double* meas, void* cuda_stream, povar_batch** out);
+void povar_batch_destroy(povar_batch* b);
+const char* povar_batch_last_error(const povar_batch* b);
+povar_problem* povar_batch_problem(povar_batch* b, int32_t k);
+povar_status povar_batch_set_cameras(povar_batch* b, const double* P, double eta);
+povar_status povar_batch_get_cameras(povar_batch* b, double* P_out);
+povar_status povar_batch_cost(povar_batch* b, double eta, double* costs_out);
+povar_status povar_batch_solve(povar_batch* b, const povar_params* params, int32_t max_iters,
+                               double ftol, const double* target_costs,
+                               povar_step_report* reports, int32_t* iters_out);
+
 /* Library version string. */
 const char* povar_version(void);
 

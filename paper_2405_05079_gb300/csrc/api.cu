@@ -258,7 +258,8 @@ povar_status step_graph(Problem* p, const povar_params* q) {
     return s != POVAR_OK ? s : fail(p, POVAR_ECUDA, "step graph capture failed");
   }
   e = cudaGraphInstantiate(&p->gexec, g, 0);
-  cudaGraphDestroy(g);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->graph = g;
   if (e != cudaSuccess) {
     p->gexec = nullptr;
     cudaGetLastError();
@@ -301,6 +302,7 @@ void povar_destroy(povar_problem* pp) {
   if (p->ev1) cudaEventDestroy(p->ev1);
   for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
   if (p->gstream) {
     cudaStreamSynchronize(p->gstream);
     cudaStreamDestroy(p->gstream);
@@ -678,6 +680,171 @@ povar_status povar_get_last_step(povar_problem* pp, double* U_out, double* bp_ou
   }
   POVAR_CUDA(cudaStreamSynchronize(p->stream));
   return POVAR_OK;
+}
+
+// ---------------------------------------------------------------- batches
+
+struct povar_batch {
+  std::vector<povar_problem*> probs;
+  std::vector<int32_t> cam0;            // first camera of each problem
+  int32_t nc_total = 0;
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  povar_params key{};
+  bool built = false;
+  std::string err;
+};
+
+static povar_status batch_fail(povar_batch* b, povar_status s, const std::string& m) {
+  if (b) b->err = m;
+  return s;
+}
+
+const char* povar_batch_last_error(const povar_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void povar_batch_destroy(povar_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (povar_problem* q : b->probs) povar_destroy(q);
+  delete b;
+}
+
+povar_status povar_batch_create(int32_t n_problems, const int32_t* n_cams, const int32_t* n_points,
+                                const int64_t* n_obs, const int32_t* cam_idx, const int32_t* pt_idx,
+                                const double* meas, void* cuda_stream, povar_batch** out) {
+  if (!out) return POVAR_EINVAL;
+  *out = nullptr;
+  if (n_problems < 1 || !n_cams || !n_points || !n_obs || !cam_idx || !pt_idx || !meas)
+    return POVAR_EINVAL;
+  povar_batch* b = new (std::nothrow) povar_batch();
+  if (!b) return POVAR_ENOMEM;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  int64_t o = 0;
+  for (int32_t k = 0; k < n_problems; ++k) {
+    povar_problem* q = nullptr;
+    const povar_status s = povar_create(n_cams[k], n_points[k], n_obs[k], cam_idx + o, pt_idx + o,
+                                        meas + 2 * o, cuda_stream, &q);
+    if (s != POVAR_OK) {
+      povar_batch_destroy(b);
+      return s;
+    }
+    b->probs.push_back(q);
+    b->cam0.push_back(b->nc_total);
+    b->nc_total += n_cams[k];
+    o += n_obs[k];
+  }
+  *out = b;
+  return POVAR_OK;
+}
+
+povar_problem* povar_batch_problem(povar_batch* b, int32_t k) {
+  if (!b || k < 0 || k >= (int32_t)b->probs.size()) return nullptr;
+  return b->probs[k];
+}
+
+povar_status povar_batch_set_cameras(povar_batch* b, const double* P, double eta) {
+  if (!b || !P) return POVAR_EINVAL;
+  for (size_t k = 0; k < b->probs.size(); ++k) {
+    const povar_status s = povar_set_cameras(b->probs[k], P + 12 * (size_t)b->cam0[k], eta);
+    if (s != POVAR_OK) return batch_fail(b, s, povar_last_error(b->probs[k]));
+  }
+  return POVAR_OK;
+}
+
+povar_status povar_batch_get_cameras(povar_batch* b, double* P_out) {
+  if (!b || !P_out) return POVAR_EINVAL;
+  for (size_t k = 0; k < b->probs.size(); ++k) {
+    const povar_status s = povar_get_cameras(b->probs[k], P_out + 12 * (size_t)b->cam0[k]);
+    if (s != POVAR_OK) return batch_fail(b, s, povar_last_error(b->probs[k]));
+  }
+  return POVAR_OK;
+}
+
+povar_status povar_batch_cost(povar_batch* b, double eta, double* costs_out) {
+  if (!b || !costs_out) return POVAR_EINVAL;
+  for (size_t k = 0; k < b->probs.size(); ++k) {
+    const povar_status s = povar_cost(b->probs[k], eta, costs_out + k);
+    if (s != POVAR_OK) return batch_fail(b, s, povar_last_error(b->probs[k]));
+  }
+  return POVAR_OK;
+}
+
+povar_status povar_batch_solve(povar_batch* b, const povar_params* params, int32_t max_iters,
+                               double ftol, const double* target_costs,
+                               povar_step_report* reports, int32_t* iters_out) {
+  if (!b) return POVAR_EINVAL;
+  if (max_iters < 1) return batch_fail(b, POVAR_EINVAL, "max_iters must be >= 1");
+  povar_status s;
+  const size_t n = b->probs.size();
+  std::vector<int> it0(n);
+  bool rebuild = !b->built || !povar::same_params(b->key, *params);
+  for (size_t k = 0; k < n; ++k) {
+    Problem* p = &b->probs[k]->impl;
+    if ((s = povar::check_params(p, params)) != POVAR_OK) return batch_fail(b, s, p->err);
+    if ((s = povar::sync_state(p)) != POVAR_OK) return batch_fail(b, s, p->err);
+    it0[k] = p->h_state->iteration;
+    if ((s = povar::launch_begin(p, ftol, target_costs ? target_costs[k] : 0.0, max_iters)) !=
+        POVAR_OK)
+      return batch_fail(b, s, p->err);
+    if ((s = povar::prepare_step(p, params)) != POVAR_OK) return batch_fail(b, s, p->err);
+    cudaGraphExec_t before = p->gexec;
+    if ((s = povar::step_graph(p, params)) != POVAR_OK) return batch_fail(b, s, p->err);
+    rebuild |= p->gexec != before;
+  }
+  if (rebuild) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&b->graph, 0);
+    for (size_t k = 0; k < n && e == cudaSuccess; ++k) {
+      cudaGraphNode_t node;
+      e = cudaGraphAddChildGraphNode(&node, b->graph, nullptr, 0, b->probs[k]->impl.graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b->built = false;
+      return batch_fail(b, POVAR_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    b->key = *params;
+    b->built = true;
+  }
+  const int check_every = 4;
+  for (int it = 0; it < max_iters; ++it) {
+    const cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess)
+      return batch_fail(b, POVAR_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    for (povar_problem* q : b->probs) q->impl.launches += q->impl.g_launches;
+    if ((it + 1) % check_every == 0 && it + 1 < max_iters) {
+      bool all = true;
+      for (povar_problem* q : b->probs) {
+        Problem* p = &q->impl;
+        if (cudaMemcpyAsync(p->h_state, p->state, sizeof(povar::DeviceState),
+                            cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+          return batch_fail(b, POVAR_ECUDA, "state copy");
+      }
+      if (cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return batch_fail(b, POVAR_ECUDA, "stream sync");
+      for (povar_problem* q : b->probs) all &= q->impl.h_state->converged != 0;
+      if (all) break;
+    }
+  }
+  povar_status worst = POVAR_OK;
+  for (size_t k = 0; k < n; ++k) {
+    Problem* p = &b->probs[k]->impl;
+    if (cudaMemcpyAsync(p->h_report, p->d_report, sizeof(povar_step_report),
+                        cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+      return batch_fail(b, POVAR_ECUDA, "report copy");
+    if ((s = povar::sync_state(p)) != POVAR_OK) return batch_fail(b, s, p->err);
+    if (reports) povar::fill_report(p, reports + k, 0.f);
+    if (iters_out) iters_out[k] = p->h_state->iteration - it0[k];
+    if (p->h_state->error && worst == POVAR_OK) worst = (povar_status)p->h_state->error;
+  }
+  return worst == POVAR_OK ? POVAR_OK : batch_fail(b, worst, "a problem reported a device error");
 }
 
 }  // extern "C"

@@ -164,6 +164,7 @@ struct Problem {
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_join = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;          // the captured step (kept for batch graphs)
   povar_params gkey{};
   int gkey_sched = -2;
   int64_t g_launches = 0;               // kernels per graph launch

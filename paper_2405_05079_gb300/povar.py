@@ -82,6 +82,23 @@ def lib() -> C.CDLL:
     L.povar_launch_count.argtypes = [vp]
     L.povar_launch_count.restype = i64
     L.povar_version.restype = C.c_char_p
+    L.povar_batch_create.argtypes = [i32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32), dp, vp, C.POINTER(vp)]
+    L.povar_batch_destroy.argtypes = [vp]
+    L.povar_batch_destroy.restype = None
+    L.povar_batch_last_error.argtypes = [vp]
+    L.povar_batch_last_error.restype = C.c_char_p
+    L.povar_batch_problem.argtypes = [vp, i32]
+    L.povar_batch_problem.restype = vp
+    L.povar_batch_set_cameras.argtypes = [vp, dp, C.c_double]
+    L.povar_batch_get_cameras.argtypes = [vp, dp]
+    L.povar_batch_cost.argtypes = [vp, C.c_double, dp]
+    L.povar_batch_solve.argtypes = [vp, C.POINTER(Params), i32, C.c_double, dp,
+                                    C.POINTER(StepReport), C.POINTER(C.c_int32)]
+    for name in ("povar_batch_create", "povar_batch_set_cameras", "povar_batch_get_cameras",
+                 "povar_batch_cost", "povar_batch_solve"):
+        getattr(L, name).restype = C.c_int
     for name in ("povar_create", "povar_set_cameras", "povar_init_random", "povar_get_cameras",
                  "povar_get_points", "povar_cost", "povar_step", "povar_solve",
                  "povar_get_orders", "povar_get_last_step", "povar_set_profiling",
@@ -235,6 +252,75 @@ class Problem:
     @property
     def launch_count(self) -> int:
         return int(lib().povar_launch_count(self._h))
+
+
+class Batch:
+    """Independent problems solved together (one CUDA-graph launch per iteration)."""
+
+    def __init__(self, scenes_list, stream=None):
+        L = lib()
+        self.n = len(scenes_list)
+        nc = np.array([s.n_cams for s in scenes_list], np.int32)
+        npnt = np.array([s.n_points for s in scenes_list], np.int32)
+        nob = np.array([s.n_obs for s in scenes_list], np.int64)
+        cam = np.ascontiguousarray(np.concatenate([s.cam_idx for s in scenes_list]), np.int32)
+        pt = np.ascontiguousarray(np.concatenate([s.pt_idx for s in scenes_list]), np.int32)
+        m = np.ascontiguousarray(np.concatenate([s.meas for s in scenes_list]), np.float64)
+        self.n_cams = nc
+        self.cam0 = np.concatenate([[0], np.cumsum(nc)])
+        h = C.c_void_p()
+        st = L.povar_batch_create(self.n, _ptr(nc, C.c_int32), _ptr(npnt, C.c_int32),
+                                  _ptr(nob, C.c_int64), _ptr(cam, C.c_int32), _ptr(pt, C.c_int32),
+                                  _ptr(m, C.c_double), C.c_void_p(stream) if stream else None,
+                                  C.byref(h))
+        if st != 0:
+            raise PovarError(st, "povar_batch_create failed")
+        self._h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise PovarError(st, lib().povar_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().povar_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_cameras(self, P_list, eta):
+        P = np.ascontiguousarray(np.concatenate([np.asarray(p).reshape(-1, 12) for p in P_list]),
+                                 np.float64)
+        self._check(lib().povar_batch_set_cameras(self._h, _ptr(P, C.c_double), eta))
+
+    def cameras(self):
+        out = np.empty((int(self.cam0[-1]), 12))
+        self._check(lib().povar_batch_get_cameras(self._h, _ptr(out, C.c_double)))
+        return [out[self.cam0[k]:self.cam0[k + 1]] for k in range(self.n)]
+
+    def costs(self, eta):
+        out = np.empty(self.n)
+        self._check(lib().povar_batch_cost(self._h, eta, _ptr(out, C.c_double)))
+        return out
+
+    def solve(self, params, max_iters=50, ftol=1e-6, target_costs=None):
+        reps = (StepReport * self.n)()
+        its = np.zeros(self.n, np.int32)
+        tc = None if target_costs is None else np.ascontiguousarray(target_costs, np.float64)
+        self._check(lib().povar_batch_solve(self._h, C.byref(params), max_iters, ftol,
+                                            None if tc is None else _ptr(tc, C.c_double), reps,
+                                            _ptr(its, C.c_int32)))
+        return list(reps), its
 
 
 @dataclasses.dataclass

@@ -395,3 +395,26 @@ def test_autotuner_picks_a_schedule_without_changing_the_solve():
         pb.set_cameras(P0, sc.eta)
         pb.solve(fixed, max_iters=4, ftol=0.0)
         assert np.array_equal(pb.cameras(), P_auto)
+
+
+def test_batch_solve_equals_each_problem_alone():
+    """Problems of uneven sizes solved as one batch (one graph launch per
+    iteration) give bit-identical results to solving each alone."""
+    scs = [SCENES["tiny"](), SCENES["traj"](), SCENES["ragged"](),
+           scenes.ring_scene(7, 300, 9, eta=0.1)]
+    P0s = [scenes.init_cameras(s.n_cams, 10 + k, normalize=True) for k, s in enumerate(scs)]
+    for prec in (povar.FP64, povar.MIXED_FP32):
+        prm = povar.make_params(eta=0.1, m=10, series_eps=0.01, manifold=povar.EUCLID,
+                                precision=prec, schedule=0)
+        with povar.Batch(scs) as b:
+            b.set_cameras(P0s, 0.1)
+            reps, its = b.solve(prm, max_iters=12, ftol=1e-9)
+            Pb = b.cameras()
+            Fb = b.costs(0.1)
+        for k, sc in enumerate(scs):
+            with povar.Problem.from_scene(sc) as pb:
+                pb.set_cameras(P0s[k], 0.1)
+                rep, it = pb.solve(prm, max_iters=12, ftol=1e-9)
+                assert it == its[k]
+                assert np.array_equal(pb.cameras(), Pb[k])
+                assert pb.cost(0.1) == Fb[k]
