@@ -242,6 +242,23 @@ int bits_for(uint64_t maxval) {
   return std::max(b, 1);
 }
 
+// Copies of the set-up tables between host vectors and the device run on the
+// problem's stream and are waited for: a plain cudaMemcpy runs on the legacy
+// default stream, which is not ordered with a caller's non-blocking stream,
+// so it could read a table before the set-up kernels have written it, or a
+// kernel could read a table before its upload has landed.
+template <class T>
+povar_status copy_sync(Problem* p, T* dst, const T* src, size_t count, cudaMemcpyKind kind) {
+  POVAR_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), kind, p->stream));
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  return POVAR_OK;
+}
+#define POVAR_COPY(dst, src, count, kind)                                    \
+  do {                                                                       \
+    const povar_status cs_ = copy_sync(p, dst, src, count, kind);            \
+    if (cs_ != POVAR_OK) return cs_;                                         \
+  } while (0)
+
 // Scratch buffer list freed at the end of build_orders.
 struct Scratch {
   std::vector<void*> ptrs;
@@ -383,8 +400,8 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
     // first, stable), keeping the last partial slice in place, so that the
     // eight slices of a block have similar widths. Pads stay at the end.
     std::vector<uint32_t> order(p->np), h_len(p->np);
-    POVAR_CUDA(cudaMemcpy(order.data(), vv, p->np * sizeof(uint32_t), cudaMemcpyDeviceToHost));
-    POVAR_CUDA(cudaMemcpy(h_len.data(), len, p->np * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    POVAR_COPY(order.data(), vv, p->np, cudaMemcpyDeviceToHost);
+    POVAR_COPY(h_len.data(), len, p->np, cudaMemcpyDeviceToHost);
     const int nfull = p->np / SLICE;
     std::vector<uint32_t> width(nfull, 0);
     for (int sl = 0; sl < nfull; ++sl)
@@ -402,9 +419,9 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
       slot_len[q] = h_len[slot_pt[q]];
       pt_slot[slot_pt[q]] = (uint32_t)q;
     }
-    POVAR_CUDA(cudaMemcpy(p->slot_pt, slot_pt.data(), p->np_pad * 4, cudaMemcpyHostToDevice));
-    POVAR_CUDA(cudaMemcpy(p->slot_len, slot_len.data(), p->np_pad * 4, cudaMemcpyHostToDevice));
-    POVAR_CUDA(cudaMemcpy(p->pt_slot, pt_slot.data(), (size_t)p->np * 4, cudaMemcpyHostToDevice));
+    POVAR_COPY(p->slot_pt, slot_pt.data(), p->np_pad, cudaMemcpyHostToDevice);
+    POVAR_COPY(p->slot_len, slot_len.data(), p->np_pad, cudaMemcpyHostToDevice);
+    POVAR_COPY(p->pt_slot, pt_slot.data(), (size_t)p->np, cudaMemcpyHostToDevice);
   }
   // ---- SELL offsets
   uint32_t* w = sc.get<uint32_t>(p->nslices + 1);
@@ -459,14 +476,10 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
   if ((s = dev_alloc(p, &p->chunk_beg, cb.size(), "chunk_beg")) ||
       (s = dev_alloc(p, &p->chunk_cam, std::max<size_t>(ccam.size(), 1), "chunk_cam")))
     return s;
-  POVAR_CUDA(cudaMemcpy(p->chunk_beg, cb.data(), cb.size() * sizeof(uint32_t),
-                        cudaMemcpyHostToDevice));
-  POVAR_CUDA(cudaMemcpy(p->chunk_cam, ccam.data(), ccam.size() * sizeof(int32_t),
-                        cudaMemcpyHostToDevice));
-  POVAR_CUDA(cudaMemcpy(p->cam_nchunk, cn.data(), p->nc * sizeof(int32_t),
-                        cudaMemcpyHostToDevice));
-  POVAR_CUDA(cudaMemcpy(p->cam_chunk0, c0.data(), p->nc * sizeof(int32_t),
-                        cudaMemcpyHostToDevice));
+  POVAR_COPY(p->chunk_beg, cb.data(), cb.size(), cudaMemcpyHostToDevice);
+  POVAR_COPY(p->chunk_cam, ccam.data(), ccam.size(), cudaMemcpyHostToDevice);
+  POVAR_COPY(p->cam_nchunk, cn.data(), p->nc, cudaMemcpyHostToDevice);
+  POVAR_COPY(p->cam_chunk0, c0.data(), p->nc, cudaMemcpyHostToDevice);
   POVAR_CUDA(cudaStreamSynchronize(p->stream));
   return build_runs(p);
 }
@@ -485,10 +498,8 @@ povar_status build_runs(Problem* p) {
   const int64_t nrows = p->nsell / SLICE;
   std::vector<int32_t> cam(p->nsell);
   std::vector<uint32_t> off(p->nslices + 1);
-  POVAR_CUDA(cudaMemcpy(cam.data(), p->sell_cam, p->nsell * sizeof(int32_t),
-                        cudaMemcpyDeviceToHost));
-  POVAR_CUDA(cudaMemcpy(off.data(), p->sell_off, (p->nslices + 1) * sizeof(uint32_t),
-                        cudaMemcpyDeviceToHost));
+  POVAR_COPY(cam.data(), p->sell_cam, p->nsell, cudaMemcpyDeviceToHost);
+  POVAR_COPY(off.data(), p->sell_off, (p->nslices + 1), cudaMemcpyDeviceToHost);
   std::vector<uint32_t> mask(std::max<int64_t>(nrows, 1)), base(std::max<int64_t>(nrows, 1));
   std::vector<int32_t> pcam;
   pcam.reserve(nrows + nrows / 4);
@@ -552,9 +563,9 @@ povar_status build_runs(Problem* p) {
         (s = dev_alloc(p, &p->cam_row_pos0, pos0.size(), "cam_row_pos0")) ||
         (s = dev_alloc(p, &p->cam_row_slot0, slot0.size(), "cam_row_slot0")))
       return s;
-    POVAR_CUDA(cudaMemcpy(p->cam_row_off, voff.data(), voff.size() * 4, cudaMemcpyHostToDevice));
-    POVAR_CUDA(cudaMemcpy(p->cam_row_pos0, pos0.data(), pos0.size() * 4, cudaMemcpyHostToDevice));
-    POVAR_CUDA(cudaMemcpy(p->cam_row_slot0, slot0.data(), slot0.size() * 4, cudaMemcpyHostToDevice));
+    POVAR_COPY(p->cam_row_off, voff.data(), voff.size(), cudaMemcpyHostToDevice);
+    POVAR_COPY(p->cam_row_pos0, pos0.data(), pos0.size(), cudaMemcpyHostToDevice);
+    POVAR_COPY(p->cam_row_slot0, slot0.data(), slot0.size(), cudaMemcpyHostToDevice);
   }
   const int64_t npart = (int64_t)pcam.size();
   std::vector<uint32_t> poff(p->nc + 1, 0), pidx(std::max<int64_t>(npart, 1));
@@ -575,10 +586,10 @@ povar_status build_runs(Problem* p) {
       (s = dev_alloc_bytes(p, &p->part_run, std::max<int64_t>(npart, 1) * 12 * sizeof(double),
                            "part_run")))
     return s;
-  POVAR_CUDA(cudaMemcpy(p->row_mask, mask.data(), mask.size() * 4, cudaMemcpyHostToDevice));
-  POVAR_CUDA(cudaMemcpy(p->row_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice));
-  POVAR_CUDA(cudaMemcpy(p->cam_part_off, poff.data(), poff.size() * 4, cudaMemcpyHostToDevice));
-  POVAR_CUDA(cudaMemcpy(p->cam_part_idx, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice));
+  POVAR_COPY(p->row_mask, mask.data(), mask.size(), cudaMemcpyHostToDevice);
+  POVAR_COPY(p->row_base, base.data(), base.size(), cudaMemcpyHostToDevice);
+  POVAR_COPY(p->cam_part_off, poff.data(), poff.size(), cudaMemcpyHostToDevice);
+  POVAR_COPY(p->cam_part_idx, pidx.data(), pidx.size(), cudaMemcpyHostToDevice);
   return POVAR_OK;
 }
 
