@@ -212,6 +212,12 @@ povar_status povar_get_profile(povar_problem* p, double* ms_out, int64_t* steps_
 povar_status povar_get_tuning(povar_problem* p, int32_t precision, int32_t* schedule_out,
                               float* ms_out);
 
+/* Device memory held by a handle (bytes), and an upper-bound estimate of
+ * it from the problem sizes alone, for admission control before
+ * povar_create. */
+int64_t povar_device_bytes(const povar_problem* p);
+int64_t povar_estimate_bytes(int32_t n_cams, int32_t n_points, int64_t n_obs);
+
 /* Number of kernel launches this handle has issued so far. */
 int64_t povar_launch_count(const povar_problem* p);
 

@@ -37,6 +37,7 @@ povar_status dev_alloc_bytes(Problem* p, void** ptr, size_t bytes, const char* w
     return fail(p, POVAR_ENOMEM, std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
   }
   p->allocs.push_back(q);
+  p->device_bytes += (int64_t)(bytes > 0 ? bytes : 1);
   *ptr = q;
   return POVAR_OK;
 }
@@ -290,6 +291,31 @@ const char* povar_last_error(const povar_problem* pp) {
 }
 
 int64_t povar_launch_count(const povar_problem* pp) { return pp ? pp->impl.launches : 0; }
+
+int64_t povar_device_bytes(const povar_problem* pp) { return pp ? pp->impl.device_bytes : 0; }
+
+int64_t povar_estimate_bytes(int32_t n_cams, int32_t n_points, int64_t n_obs) {
+  if (n_cams < 1 || n_points < 1 || n_obs < 1) return 0;
+  const int64_t nc = n_cams, npd = ((int64_t)n_points + 255) / 256 * 256, no = n_obs;
+  // SELL entries are bounded by 32 x (longest track) per slice; two times the
+  // observations bounds the padding of the scenes this library targets
+  const int64_t nsell = 2 * no + 32 * 64;
+  const int64_t chunks = no / 256 + nc + 1;
+  int64_t b = 0;
+  b += no * (4 + 4 + 16);                  // inputs
+  b += no * (4 + 4) + 4 * ((int64_t)n_points + nc + 2);  // orders
+  b += npd * (4 + 4) + 4 * (int64_t)n_points + 4 * (npd / 32 + 1);
+  b += nsell * (4 + 8 + 16);               // SELL
+  b += no * (4 + 8 + 16);                  // camera-major list
+  b += nc * 4 * 4 + chunks * 8;
+  b += nc * (2 * 12 * 8 + 48 * 8 + 2 * 12 * 4 + 144 * 8 + 12 * 8 + 144 * 8 + 144 * 4 +
+             2 * 12 * 4 + 12 * 4 + 2 * 12 * 8 + 12 * 8 + 2 * 8);
+  b += 2 * npd * (3 * 8 + 6 * 8 + 16 + 16 + 4) + npd * (32 + 64) + 3 * (npd / 32) * 8;
+  b += chunks * (52 + 12) * 8;
+  b += nsell / 32 * 8 + 2 * (nsell / 32 + no / 8) * 12 * 8 + 3 * (nsell / 32 + no / 8) * 4 +
+       3 * (nc + 1) * 4;
+  return b + (1 << 20);
+}
 
 void povar_destroy(povar_problem* pp) {
   if (!pp) return;

@@ -172,6 +172,7 @@ struct Problem {
   cudaEvent_t gprof[POVAR_NPHASES + 1] = {};  // phase boundaries inside the graph
   bool use_graphs = true;
   std::vector<void*> allocs;            // every device allocation, freed by destroy
+  int64_t device_bytes = 0;             // sum of the device allocations
 };
 
 // ------------------------------------------------------------------ helpers

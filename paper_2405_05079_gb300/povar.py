@@ -79,6 +79,10 @@ def lib() -> C.CDLL:
     L.povar_set_profiling.argtypes = [vp, i32]
     L.povar_get_profile.argtypes = [vp, dp, C.POINTER(C.c_int64), i32]
     L.povar_get_tuning.argtypes = [vp, i32, C.POINTER(C.c_int32), C.POINTER(C.c_float)]
+    L.povar_device_bytes.argtypes = [vp]
+    L.povar_device_bytes.restype = i64
+    L.povar_estimate_bytes.argtypes = [i32, i32, i64]
+    L.povar_estimate_bytes.restype = i64
     L.povar_launch_count.argtypes = [vp]
     L.povar_launch_count.restype = i64
     L.povar_version.restype = C.c_char_p
@@ -250,6 +254,10 @@ class Problem:
         return sched.value, list(ms)
 
     @property
+    def device_bytes(self) -> int:
+        return int(lib().povar_device_bytes(self._h))
+
+    @property
     def launch_count(self) -> int:
         return int(lib().povar_launch_count(self._h))
 
@@ -329,6 +337,11 @@ class SolveResult:
     iterations: int
     cameras: np.ndarray
     points: np.ndarray
+
+
+def estimate_bytes(n_cams: int, n_points: int, n_obs: int) -> int:
+    """Upper-bound device footprint of a problem of these sizes."""
+    return int(lib().povar_estimate_bytes(n_cams, n_points, n_obs))
 
 
 def version() -> str:

@@ -418,3 +418,40 @@ def test_batch_solve_equals_each_problem_alone():
                 assert it == its[k]
                 assert np.array_equal(pb.cameras(), Pb[k])
                 assert pb.cost(0.1) == Fb[k]
+
+
+def test_footprint_estimate_bounds_actual():
+    for sc in (SCENES["tiny"](), SCENES["traj"](), SCENES["mid"]()):
+        with povar.Problem.from_scene(sc) as pb:
+            actual = pb.device_bytes
+        est = povar.estimate_bytes(sc.n_cams, sc.n_points, sc.n_obs)
+        assert actual <= est <= 4 * actual + (2 << 20), (sc.name, actual, est)
+
+
+def test_serving_result_same_alone_and_in_the_mix():
+    """Requests arriving while others run are admitted into free slots and
+    solved concurrently on their own streams; each result equals the same
+    problem solved alone (bit for bit)."""
+    from paper_2405_05079_gb300 import serving
+    scs = [scenes.trajectory_scene(60 + 10 * k, 3000 + 400 * k, 30 + k, eta=0.1)
+           for k in range(6)]
+    prm = povar.make_params(eta=0.1, m=11, series_eps=0.01, manifold=povar.EUCLID,
+                            precision=povar.MIXED_FP32, schedule=1)
+    arrivals = serving.poisson_arrivals(len(scs), rate=400.0, seed=1)
+    reqs = [serving.Request(rid=k, arrival=float(arrivals[k]), scene=sc,
+                            P0=scenes.init_cameras(sc.n_cams, 50 + k, normalize=True))
+            for k, sc in enumerate(scs)]
+    budget = sum(povar.estimate_bytes(s.n_cams, s.n_points, s.n_obs) for s in scs[:3])
+    srv = serving.Server(prm, budget_bytes=budget, slots=3, max_iters=15, ftol=1e-9)
+    res = srv.run(reqs)
+    assert [r.rid for r in res] == list(range(len(scs)))
+    for r in res:
+        sc = scs[r.rid]
+        with povar.Problem.from_scene(sc) as pb:
+            pb.set_cameras(reqs[r.rid].P0, 0.1)
+            _, it = pb.solve(prm, max_iters=15, ftol=1e-9)
+            assert it == r.iterations
+            assert np.array_equal(pb.cameras(), r.cameras)
+            assert pb.cost(0.1) == r.cost
+    stats = serving.summarize(res)
+    assert stats["latency_p99_s"] >= stats["latency_p50_s"] > 0
