@@ -14,11 +14,12 @@
 // which the series kernels use. A numerically rank-deficient V_j
 // (cond > 1e12) falls back to the Moore-Penrose pseudo-inverse (footnote of
 // Sec. 4.2) from a Jacobi eigen-decomposition.
-// The cost needs no second pass: with r_k = A_k X + c_k (A_k = B P,
-// c_k = B p4 - d), sum_k ||r_k||^2 = X^T V X + 2 h^T X + sum_k ||c_k||^2, and
-// at X = -V^+ h (h lies in the range of V) this is sum_k ||c_k||^2 + h^T X.
-// ||c_k||^2 = A0 + u A1 + v A2 + (u^2 + v^2) A3 with per-camera A0..A3, so it
-// is accumulated in pass 1 with four more FP64 operations per observation.
+// The cost is then evaluated directly, in a second pass over the landmark's
+// observations: sum_k ||r_k||^2 at the solved X (17 FP64 operations per
+// observation). The shortcut sum_k ||c_k||^2 + h^T X (c_k = B p4 - d, exact at
+// the optimum) is not used: it cancels catastrophically when V_j is
+// ill-conditioned and X_j large (a trial step towards degenerate cameras gave
+// a negative cost that way), while the direct sum is always >= 0 and accurate.
 // F = ||r||^2 (Eq. ba_first_stage) is summed into one FP64 partial per warp
 // and a single block adds the partials in a fixed order (deterministic).
 #include "povar_internal.cuh"
@@ -36,8 +37,7 @@ struct SlotBufs {
 
 // Ltab layout (48 doubles per camera):
 //  [0,6) R, [6,12) E1, [12,18) E2, [18,24) Fm   (symmetric 3x3: 00 01 02 11 12 22)
-//  [24,27) h0, [27,30) hu, [30,33) hv, [33,36) hw, [36,40) A0..A3 (||c||^2),
-//  [40,48) unused
+//  [24,27) h0, [27,30) hu, [30,33) hv, [33,36) hw, [36,48) unused
 __global__ void k_ltab(const DeviceState* __restrict__ st, int which_rel, double eta,
                        const double* __restrict__ P0, const double* __restrict__ P1, int nc,
                        double* __restrict__ Ltab, float* __restrict__ C0,
@@ -72,10 +72,6 @@ __global__ void k_ltab(const DeviceState* __restrict__ st, int which_rel, double
     T[30 + c] = (-a * q2 - eta) * p1[c] - a * q1 * p2[c];
     T[33 + c] = a * q2 * p2[c];
   }
-  T[36] = q0 * q0 + q1 * q1;
-  T[37] = -2.0 * q0 * (a * q2 + eta);
-  T[38] = -2.0 * q1 * (a * q2 + eta);
-  T[39] = a * q2 * q2 + eta;
 }
 
 // Symmetric 3x3 packed as (00 01 02 11 12 22).
@@ -194,7 +190,8 @@ __global__ void __launch_bounds__(BLOCK)
 k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
            const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
            const int32_t* __restrict__ sell_cam, const double2* __restrict__ sell_m,
-           const double* __restrict__ Ltab, int np, SlotBufs bufs,
+           const double* __restrict__ Ltab, const double* __restrict__ P0,
+           const double* __restrict__ P1, int np, SlotBufs bufs,
            double* __restrict__ cost_part, int* __restrict__ pinv_part) {
   if (which_rel == 1 && st->converged) return;
   const int t = which_rel ? 1 - st->cur : st->cur;
@@ -204,16 +201,16 @@ k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
   if (s < np) {
     const uint32_t len = slot_len[s];
     const uint32_t base = sell_off[s / SLICE] + (uint32_t)(s % SLICE);
-    double V[6] = {0, 0, 0, 0, 0, 0}, h[3] = {0, 0, 0}, cc = 0.0;
+    double V[6] = {0, 0, 0, 0, 0, 0}, h[3] = {0, 0, 0};
     for (uint32_t k = 0; k < len; ++k) {
       const uint32_t pos = base + k * SLICE;
       const int i = sell_cam[pos];
       const double2 m = sell_m[pos];
       const double u = m.x, v = m.y, w = u * u + v * v;
       const double2* T = reinterpret_cast<const double2*>(Ltab + 48 * (size_t)i);
-      double tb[40];
+      double tb[36];
 #pragma unroll
-      for (int q = 0; q < 20; ++q) {
+      for (int q = 0; q < 18; ++q) {
         const double2 x = __ldg(T + q);
         tb[2 * q] = x.x;
         tb[2 * q + 1] = x.y;
@@ -222,7 +219,6 @@ k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
       for (int e = 0; e < 6; ++e) V[e] += tb[e] + u * tb[6 + e] + v * tb[12 + e] + w * tb[18 + e];
 #pragma unroll
       for (int c = 0; c < 3; ++c) h[c] += tb[24 + c] + u * tb[27 + c] + v * tb[30 + c] + w * tb[33 + c];
-      cc += tb[36] + u * tb[37] + v * tb[38] + w * tb[39];
     }
     // Cholesky V = L L^T through reciprocal square roots; F = L^-1
     double X[3], F[6];
@@ -269,7 +265,31 @@ k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
     bufs.A[t][s] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)F[0]);
     bufs.B[t][s] = make_float4((float)F[1], (float)F[2], (float)F[3], (float)F[4]);
     bufs.C[t][s] = (float)F[5];
-    cost = cc + h[0] * X[0] + h[1] * X[1] + h[2] * X[2];
+    // r_k = B_k P_i (X, 1) - d_k: with y = P_i (X, 1),
+    // ||r_k||^2 = (1 - eta) ((y0 - u y2)^2 + (y1 - v y2)^2) + eta ((y0 - u)^2 + (y1 - v)^2)
+    const double* __restrict__ Pc = t ? P1 : P0;
+    double e1 = 0.0, e2 = 0.0;
+    for (uint32_t k = 0; k < len; ++k) {
+      const uint32_t pos = base + k * SLICE;
+      const int i = sell_cam[pos];
+      const double2 m = sell_m[pos];
+      const double2* Q = reinterpret_cast<const double2*>(Pc + 12 * (size_t)i);
+      double q[12];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        const double2 x = __ldg(Q + r);
+        q[2 * r] = x.x;
+        q[2 * r + 1] = x.y;
+      }
+      const double y0 = fma(q[0], X[0], fma(q[1], X[1], fma(q[2], X[2], q[3])));
+      const double y1 = fma(q[4], X[0], fma(q[5], X[1], fma(q[6], X[2], q[7])));
+      const double y2 = fma(q[8], X[0], fma(q[9], X[1], fma(q[10], X[2], q[11])));
+      const double a0 = fma(-m.x, y2, y0), a1 = fma(-m.y, y2, y1);
+      const double b0 = y0 - m.x, b1 = y1 - m.y;
+      e1 = fma(a0, a0, fma(a1, a1, e1));
+      e2 = fma(b0, b0, fma(b1, b1, e2));
+    }
+    cost = (1.0 - eta) * e1 + eta * e2;
   } else {
     // padding slot (the slot arrays are padded to a whole number of blocks)
     double* Xo = bufs.X[t] + 3 * (size_t)s;
@@ -342,7 +362,7 @@ povar_status launch_landmarks(Problem* p, int which_rel, double eta) {
   }
   k_landmark<<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
       p->state, which_rel, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->Ltab,
-      p->np, b, p->cost_part, p->pinv_part);
+      p->P64[0], p->P64[1], p->np, b, p->cost_part, p->pinv_part);
   p->launches += 2;
   return check_launch(p, "landmark");
 }
