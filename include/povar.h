@@ -192,16 +192,20 @@ povar_status povar_get_last_step(povar_problem* p, double* U_out, double* bp_out
  * 0 linearization, 1 damped camera blocks + first term, 2 series terms,
  * 3 predicted decrease, 4 camera update, 5 landmarks + cost at the trial
  * cameras, 6 controller. povar_get_profile writes, per phase, the summed
- * device milliseconds (ms_out[POVAR_NPHASES]) and the number of timed steps
- * (steps_out, may be NULL), and zeroes the counters when reset != 0.
- * Timing applies to povar_step and povar_solve issued while enabled; in
- * povar_solve, which runs each step as one CUDA graph, the phase events are
- * part of the graph and the steps that end at a host synchronization point
- * (every fourth step and the last one) are sampled. */
+ * device milliseconds (ms_out[POVAR_NPHASES]), the number of timed steps
+ * (steps_out) and the number of series products M y computed by those steps
+ * (products_out: terms used minus one per step, so the per-product time of
+ * phase 2 is ms_out[2] / products_out), and zeroes the counters when
+ * reset != 0. Output pointers may be NULL. Timing applies to povar_step and
+ * povar_solve issued while enabled; in povar_solve, which runs each step as
+ * one CUDA graph, the phase events are part of the graph and the steps that
+ * end at a host synchronization point (every fourth step and the last one)
+ * are sampled, skipping a sampled launch that found the solve already
+ * converged and did no work. */
 enum { POVAR_NPHASES = 7 };
 povar_status povar_set_profiling(povar_problem* p, int32_t enable);
 povar_status povar_get_profile(povar_problem* p, double* ms_out, int64_t* steps_out,
-                               int32_t reset);
+                               int64_t* products_out, int32_t reset);
 
 /* Series-schedule autotuner. The first povar_solve with params->schedule
  * = -1 times two series terms of every schedule (0, 1, 2) on the live
@@ -231,8 +235,10 @@ int64_t povar_launch_count(const povar_problem* p);
  * problem as one CUDA-graph launch whose child graphs are the problems' step
  * graphs (no dependencies between problems, so their kernels overlap); each
  * problem stops on its own device-side convergence flag; the host checks the
- * flags every fourth iteration. Results are identical to solving each
- * problem alone with the same parameters and schedule. target_costs,
+ * flags every fourth iteration. With schedule -1 every problem picks its
+ * own series schedule by the autotuner of povar_solve before the first
+ * iteration. Results are identical to solving each problem alone with the
+ * same parameters and schedule. target_costs,
  * reports and iters_out hold one entry per problem (each may be NULL). */
 typedef struct povar_batch povar_batch;
 povar_status povar_batch_create(int32_t n_problems, const int32_t* n_cams,

@@ -51,6 +51,7 @@ povar_status sync_state(Problem* p) {
                              p->stream));
   POVAR_CUDA(cudaStreamSynchronize(p->stream));
   if (!p->prof_steps.empty()) collect_profile(p);
+  p->prof_products_mark = p->h_state->products;
   return POVAR_OK;
 }
 
@@ -107,6 +108,8 @@ void collect_profile(Problem* p) {
     }
     ++p->prof_count;
   }
+  // every step enqueued since the last synchronization was timed
+  p->prof_products += p->h_state->products - p->prof_products_mark;
   cudaGetLastError();
   p->prof_steps.clear();
   p->prof_next = 0;
@@ -178,8 +181,8 @@ povar_status enqueue_step(Problem* p, const povar_params* q) {
 
 // Add the phase times of the last completed graph launch (the caller has
 // synchronized the graph stream).
-void sample_graph_profile(Problem* p) {
-  if (!p->g_profiled) return;
+void sample_graph_profile(Problem* p, bool last_step_worked) {
+  if (!p->g_profiled || !last_step_worked) return;
   float ms[POVAR_NPHASES];
   for (int ph = 0; ph < POVAR_NPHASES; ++ph)
     if (cudaEventElapsedTime(&ms[ph], p->gprof[ph], p->gprof[ph + 1]) != cudaSuccess) {
@@ -188,6 +191,7 @@ void sample_graph_profile(Problem* p) {
     }
   for (int ph = 0; ph < POVAR_NPHASES; ++ph) p->prof_ms[ph] += ms[ph];
   ++p->prof_count;
+  p->prof_products += p->h_state->terms_used > 1 ? p->h_state->terms_used - 1 : 0;
 }
 
 // Series-schedule autotuner: on the live state of the first step, time two
@@ -581,6 +585,17 @@ povar_status povar_solve(povar_problem* pp, const povar_params* params, int32_t 
     POVAR_CUDA(cudaStreamWaitEvent(p->gstream, p->ev_join, 0));
     cudaStream_t user = p->stream;
     p->stream = p->gstream;
+    // the phase events hold the last launched step: it is sampled when it
+    // did work, i.e. when every launch since the last sample advanced the
+    // iteration count (launches after convergence return at once)
+    int since = 0, iter_mark = it0;
+    auto sample = [&]() -> povar_status {
+      if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+      povar::sample_graph_profile(p, since > 0 && p->h_state->iteration - iter_mark == since);
+      iter_mark = p->h_state->iteration;
+      since = 0;
+      return POVAR_OK;
+    };
     for (int it = 0; it < max_iters; ++it) {
       const cudaError_t e = cudaGraphLaunch(p->gexec, p->gstream);
       if (e != cudaSuccess) {
@@ -588,18 +603,18 @@ povar_status povar_solve(povar_problem* pp, const povar_params* params, int32_t 
         return povar::fail(p, POVAR_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
       }
       p->launches += p->g_launches;
+      ++since;
       if ((it + 1) % check_every == 0 && it + 1 < max_iters) {
-        if ((s = povar::sync_state(p)) != POVAR_OK) {
+        if (sample() != POVAR_OK) {
           p->stream = user;
           return s;
         }
-        povar::sample_graph_profile(p);
         if (p->h_state->converged) break;
       }
     }
-    if (p->g_profiled) {
-      POVAR_CUDA(cudaStreamSynchronize(p->gstream));
-      povar::sample_graph_profile(p);
+    if (since > 0 && sample() != POVAR_OK) {
+      p->stream = user;
+      return s;
     }
     POVAR_CUDA(cudaEventRecord(p->ev_join, p->gstream));
     p->stream = user;
@@ -636,7 +651,7 @@ povar_status povar_set_profiling(povar_problem* pp, int32_t enable) {
 }
 
 povar_status povar_get_profile(povar_problem* pp, double* ms_out, int64_t* steps_out,
-                               int32_t reset) {
+                               int64_t* products_out, int32_t reset) {
   if (!pp) return POVAR_EINVAL;
   Problem* p = &pp->impl;
   povar_status s;
@@ -644,9 +659,11 @@ povar_status povar_get_profile(povar_problem* pp, double* ms_out, int64_t* steps
   if (ms_out)
     for (int ph = 0; ph < POVAR_NPHASES; ++ph) ms_out[ph] = p->prof_ms[ph];
   if (steps_out) *steps_out = p->prof_count;
+  if (products_out) *products_out = p->prof_products;
   if (reset) {
     for (int ph = 0; ph < POVAR_NPHASES; ++ph) p->prof_ms[ph] = 0.0;
     p->prof_count = 0;
+    p->prof_products = 0;
   }
   return POVAR_OK;
 }
@@ -816,6 +833,8 @@ povar_status povar_batch_solve(povar_batch* b, const povar_params* params, int32
         POVAR_OK)
       return batch_fail(b, s, p->err);
     if ((s = povar::prepare_step(p, params)) != POVAR_OK) return batch_fail(b, s, p->err);
+    if (params->schedule < 0 && (s = povar::autotune_schedule(p, params)) != POVAR_OK)
+      return batch_fail(b, s, p->err);
     cudaGraphExec_t before = p->gexec;
     if ((s = povar::step_graph(p, params)) != POVAR_OK) return batch_fail(b, s, p->err);
     rebuild |= p->gexec != before;

@@ -60,6 +60,7 @@ struct DeviceState {
   int max_iters;     // iteration cap for povar_solve (0: none)
   int n_pinv;        // landmarks solved by pseudo-inverse at the last solve
   int n_regularized; // camera blocks whose damping had to be raised (cumulative)
+  long long products; // series products M y computed by all steps (never reset)
 };
 
 // Host-side handle.
@@ -159,6 +160,8 @@ struct Problem {
   std::vector<std::vector<size_t>> prof_steps;  // event indices of pending steps
   double prof_ms[POVAR_NPHASES] = {0};
   int64_t prof_count = 0;
+  int64_t prof_products = 0;             // series products of the timed steps
+  long long prof_products_mark = 0;      // device product counter at the last sync
   // CUDA graph of one step (povar_solve): captured on a library stream that
   // joins the caller's stream through events; cached per parameter set
   cudaStream_t gstream = nullptr;

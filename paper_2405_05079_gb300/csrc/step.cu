@@ -45,6 +45,7 @@ __global__ void k_controller(DeviceState* __restrict__ st, povar_step_report* __
   rep->lambda_used = st->lam_used;
   rep->accepted = accepted ? 1 : 0;
   rep->terms_used = st->terms_used;
+  st->products += st->terms_used > 1 ? st->terms_used - 1 : 0;
   st->rho = rho;
   st->accepted = accepted ? 1 : 0;
   st->iteration += 1;

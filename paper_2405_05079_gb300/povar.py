@@ -77,7 +77,7 @@ def lib() -> C.CDLL:
     L.povar_get_orders.argtypes = [vp, u32p, u32p, u32p, u32p]
     L.povar_get_last_step.argtypes = [vp, dp, dp, dp]
     L.povar_set_profiling.argtypes = [vp, i32]
-    L.povar_get_profile.argtypes = [vp, dp, C.POINTER(C.c_int64), i32]
+    L.povar_get_profile.argtypes = [vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), i32]
     L.povar_get_tuning.argtypes = [vp, i32, C.POINTER(C.c_int32), C.POINTER(C.c_float)]
     L.povar_device_bytes.argtypes = [vp]
     L.povar_device_bytes.restype = i64
@@ -192,12 +192,16 @@ class Problem:
     def set_profiling(self, enable: bool):
         self._check(lib().povar_set_profiling(self._h, 1 if enable else 0))
 
-    def profile(self, reset: bool = False):
+    def profile(self, reset: bool = False, products: bool = False):
+        """Summed phase milliseconds and the number of timed steps; with
+        ``products`` also the number of series products those steps computed."""
         ms = np.zeros(len(self.PHASES))
         n = C.c_int64()
+        k = C.c_int64()
         self._check(lib().povar_get_profile(self._h, _ptr(ms, C.c_double), C.byref(n),
-                                            1 if reset else 0))
-        return dict(zip(self.PHASES, ms.tolist())), n.value
+                                            C.byref(k), 1 if reset else 0))
+        out = dict(zip(self.PHASES, ms.tolist()))
+        return (out, n.value, k.value) if products else (out, n.value)
 
     def init_random(self, seed: int, manifold: int, eta: float):
         self._check(lib().povar_init_random(self._h, seed, manifold, eta))

@@ -149,22 +149,36 @@ def ring_scene(n_cams: int, n_points: int, seed: int, *, track="uniform3to6",
 
 def trajectory_scene(n_cams: int, n_points: int, seed: int, *, noise_px=0.5,
                      eta=0.1, m=20, outlier_frac=0.01, max_track=40,
-                     p_geom=0.25, radius=20.0, name=None) -> Scene:
+                     p_geom=0.25, radius=20.0, deg_per_cam=None, name=None) -> Scene:
     """Cameras along a closed circular trajectory looking at its centre.
 
     Each point is seen by a contiguous window of ``L = 1 + Geom(p_geom)``
     consecutive cameras (mean 5, min 2 for p = 1/4), capped at ``max_track``.
     The point is placed in front of the middle camera of its window, so it
     projects inside the +-45 degree field of view of every camera in it.
+
+    With ``deg_per_cam`` the trajectory is an open helix instead (camera i at
+    angle i * deg_per_cam, rising 0.05 per camera, looking at the axis at its
+    own height) and windows do not wrap around; this keeps the angle spanned
+    by a window small for scenes with few cameras.
     """
     rng = np.random.default_rng(seed)
-    ang = 2.0 * np.pi * np.arange(n_cams) / n_cams
-    heights = 0.5 * np.sin(5.0 * ang)
+    if deg_per_cam is None:
+        ang = 2.0 * np.pi * np.arange(n_cams) / n_cams
+        heights = 0.5 * np.sin(5.0 * ang)
+        targets = np.zeros((n_cams, 3))
+    else:
+        ang = np.deg2rad(deg_per_cam) * np.arange(n_cams)
+        heights = 0.05 * np.arange(n_cams)
+        targets = np.stack([np.zeros(n_cams), heights, np.zeros(n_cams)], 1)
     centers = np.stack([radius * np.sin(ang), heights, -radius * np.cos(ang)], 1)
-    cams = np.stack([_look_at(c, np.array([0.0, 0.0, 0.0])) for c in centers])
+    cams = np.stack([_look_at(c, t) for c, t in zip(centers, targets)])
     lengths = np.minimum(1 + rng.geometric(p_geom, size=n_points),
                          min(max_track, n_cams))
-    start = rng.integers(0, n_cams, size=n_points)
+    if deg_per_cam is None:
+        start = rng.integers(0, n_cams, size=n_points)
+    else:
+        start = rng.integers(0, n_cams - lengths + 1)
     mid = (start + lengths // 2) % n_cams
     depth = rng.uniform(4.0, 8.0, size=n_points)
     lat = rng.uniform(-0.35, 0.35, size=(n_points, 2)) * depth[:, None]
@@ -210,6 +224,26 @@ def large_scene(seed: int = 0, n_cams: int = 1800,
                             name="large")
 
 
+def family_scenes(kind: str, n: int, seed: int = 0) -> list:
+    """Seeded families of independent problems of uneven sizes.
+
+    ``batched``: cameras log-uniform in [20, 400], 50 points per camera, mean
+    track 4 (1 + Geom(1/3)). ``serving``: cameras log-uniform in [10, 1000],
+    100 points per camera, mean track 5 (1 + Geom(1/4)). Both are helix
+    trajectories (1 degree per camera, contiguous-window tracks capped at 40),
+    0.5 px noise, no outliers, eta = 0.1.
+    """
+    spec = {"batched": (20, 400, 50, 1.0 / 3.0), "serving": (10, 1000, 100, 0.25)}
+    lo, hi, ppc, p = spec[kind]
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xFA11]))
+    n_cams = np.round(np.exp(rng.uniform(np.log(lo), np.log(hi), size=n))).astype(int)
+    seeds = rng.integers(0, 2**31 - 1, size=n)
+    return [trajectory_scene(int(c), int(c) * ppc, int(s), noise_px=0.5, eta=0.1, m=20,
+                             outlier_frac=0.0, max_track=40, p_geom=p, deg_per_cam=1.0,
+                             name=f"{kind}{k}")
+            for k, (c, s) in enumerate(zip(n_cams, seeds))]
+
+
 def init_cameras(n_cams: int, seed: int, normalize: bool) -> np.ndarray:
     """Random camera initialization: 3x4 entries iid N(0,1), stored row-major
     as [n_cams, 12] float64; with ``normalize`` each camera is scaled to unit
@@ -234,5 +268,5 @@ def describe(scene: Scene) -> dict:
 
 
 __all__ = ["Scene", "ring_scene", "trajectory_scene", "tiny_scene",
-           "mid_scene", "large_scene", "init_cameras", "scene_by_name",
+           "mid_scene", "large_scene", "family_scenes", "init_cameras", "scene_by_name",
            "describe", "FOCAL_PX"]

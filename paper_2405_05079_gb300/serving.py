@@ -147,8 +147,7 @@ def summarize(results: list[Result], wall: float | None = None) -> dict:
             "latency_p99_s": float(np.percentile(lat, 99)),
             "solve_p50_s": float(np.percentile(sol, 50)),
             "solve_p99_s": float(np.percentile(sol, 99)),
-            "mean_iterations": float(np.mean([r.iterations for r in results])),
-            "peak_bytes_est": None}
+            "mean_iterations": float(np.mean([r.iterations for r in results]))}
 
 
 def sequential(requests: list[Request], params, max_iters: int = 50,
