@@ -255,6 +255,56 @@ povar_status povar_batch_solve(povar_batch* b, const povar_params* params, int32
                                double ftol, const double* target_costs,
                                povar_step_report* reports, int32_t* iters_out);
 
+/* ---- allocation-free cost evaluation ----
+ * No counterpart in the paper: a library utility. It evaluates the same
+ * quantity as povar_set_cameras + povar_cost + povar_get_points (the pOSE
+ * cost of Eq. ba_first_stage with every landmark eliminated in closed form
+ * by Eq. update_landmark, pseudo-inverse for rank-deficient V_j, all in
+ * FP64) without a problem handle and without allocating any memory.
+ *
+ * Who needs it: callers that must not allocate at the point of the call.
+ * cudaMalloc and cudaFree synchronize the device, so a latency-critical loop
+ * that evaluates a candidate camera set while other work is in flight cannot
+ * afford them; a process whose device memory is fully reserved by another
+ * allocator (a caching allocator holding the whole pool, a fixed arena)
+ * cannot obtain more; and a caller that only needs the cost of a few camera
+ * sets does not want to build and keep a handle (observation orders, series
+ * buffers) for it. The working memory is one fixed array inside the library
+ * (per-block cost partials, POVAR_NOALLOC_MAX_POINTS / 256 doubles = 128 KB),
+ * which bounds the problem size.
+ *
+ * Inputs (all DEVICE pointers, caller-owned, only read): P = n_cams x 12
+ * row-major FP64 cameras; the observations in landmark-major order:
+ * off_pt[n_points + 1] (u32, observations of landmark j are
+ * off_pt[j] .. off_pt[j+1]-1), cam[n_obs] (i32 camera index) and
+ * meas[n_obs x 2] (FP64 normalized coordinates, 16-byte aligned). Outputs
+ * (DEVICE pointers, caller-owned): cost_out[1] receives the cost; X_out
+ * (n_points x 3 FP64, may be NULL) receives the landmarks. Work is enqueued
+ * on cuda_stream (NULL = legacy default stream) and nothing is
+ * synchronized: the outputs are ready when the stream reaches this point.
+ *
+ * Errors: POVAR_EINVAL for a NULL pointer, a size < 1, eta outside [0, 1],
+ * or n_points > POVAR_NOALLOC_MAX_POINTS (the fixed working array would be
+ * too small); nothing is launched then. POVAR_ECUDA if the set-up or a
+ * launch fails. Index errors are detected on the device without a host
+ * round trip: a camera index outside [0, n_cams) or an offset table that is
+ * decreasing or points past n_obs makes *cost_out NaN (the offending
+ * observations are skipped, never read out of bounds).
+ *
+ * Set-up and concurrency: the first call on each device (with that device
+ * current) looks up the device address of the library's working array
+ * (cudaGetSymbolAddress, which also loads the library's device code if it
+ * is not yet loaded); make that first call before any stream capture.
+ * All calls on one device share the same working array, so calls whose
+ * executions overlap in time (on different streams or from different host
+ * threads without ordering between them) race and may return a wrong cost;
+ * order them on one stream or with events. */
+enum { POVAR_NOALLOC_MAX_POINTS = 4194304 };
+povar_status povar_cost_noalloc(int32_t n_cams, int32_t n_points, int64_t n_obs,
+                                const double* P, const uint32_t* off_pt, const int32_t* cam,
+                                const double* meas, double eta, double* X_out,
+                                double* cost_out, void* cuda_stream);
+
 /* Library version string. */
 const char* povar_version(void);
 

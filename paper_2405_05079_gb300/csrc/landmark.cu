@@ -22,6 +22,8 @@
 // a negative cost that way), while the direct sum is always >= 0 and accurate.
 // F = ||r||^2 (Eq. ba_first_stage) is summed into one FP64 partial per warp
 // and a single block adds the partials in a fixed order (deterministic).
+#include <mutex>
+
 #include "povar_internal.cuh"
 
 namespace povar {
@@ -375,3 +377,217 @@ povar_status launch_cost_finish(Problem* p, int which_rel) {
 }
 
 }  // namespace povar
+
+// ---------------------------------------------------------------------------
+// Allocation-free cost evaluation (povar_cost_noalloc).
+//
+// The same landmark elimination and cost as k_landmark + k_cost_finish, read
+// from a caller-provided landmark-major CSR (one thread per landmark) instead
+// of the handle's SELL slots. The per-block cost partials, the only working
+// memory beyond the caller's inputs and outputs, live in the fixed array
+// below; its device address is looked up once per device. Every partial the
+// sum kernel reads is written first by its block in the same call, so the
+// array needs no clearing between calls.
+// ---------------------------------------------------------------------------
+namespace povar {
+namespace {
+
+constexpr int NA_BLOCK = 256;
+constexpr int NA_MAX_BLOCKS = POVAR_NOALLOC_MAX_POINTS / NA_BLOCK;
+static_assert(NA_MAX_BLOCKS * NA_BLOCK == POVAR_NOALLOC_MAX_POINTS, "whole blocks");
+
+static __device__ __align__(256) double na_partials[NA_MAX_BLOCKS];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex na_mutex;
+double* na_ptr[NA_MAX_DEVICES] = {};
+
+__global__ void __launch_bounds__(NA_BLOCK)
+k_landmark_csr(const double* __restrict__ P, int nc, const uint32_t* __restrict__ off,
+               const int32_t* __restrict__ cam, const double2* __restrict__ meas,
+               int64_t nobs, int np, double eta, double* __restrict__ X_out,
+               double* __restrict__ part) {
+  __shared__ double red[NA_BLOCK / 32];
+  const int j = blockIdx.x * NA_BLOCK + threadIdx.x;
+  double cost = 0.0;
+  if (j < np) {
+    // observation range, clamped to the arrays; a malformed range or camera
+    // index makes the cost NaN instead of being read out of bounds
+    const int64_t b0 = off[j], e0 = off[j + 1];
+    bool bad = e0 < b0 || e0 > nobs;
+    const int64_t e = e0 < nobs ? e0 : nobs;
+    const int64_t b = b0 < e ? b0 : e;
+    const double a = 1.0 - eta;
+    // V = sum Pbar^T C Pbar, h = sum Pbar^T (C p4 - (eta u, eta v, 0)) with
+    // C = [[1, 0, -a u], [0, 1, -a v], [-a u, -a v, a (u^2 + v^2)]]; with
+    // rows p_r of Pbar, V = sum_r p_r (C Pbar)_r^T and h = sum_r c_r p_r.
+    double V[6] = {0, 0, 0, 0, 0, 0}, h[3] = {0, 0, 0};
+    for (int64_t k = b; k < e; ++k) {
+      const int i = cam[k];
+      if ((unsigned)i >= (unsigned)nc) {
+        bad = true;
+        continue;
+      }
+      const double2 m = meas[k];
+      const double u = m.x, v = m.y, w = u * u + v * v;
+      const double2* Q = reinterpret_cast<const double2*>(P + 12 * (size_t)i);
+      double q[12];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        const double2 x = __ldg(Q + r);
+        q[2 * r] = x.x;
+        q[2 * r + 1] = x.y;
+      }
+      const double* p0 = q;
+      const double* p1 = q + 4;
+      const double* p2 = q + 8;
+      double r0[3], r1[3], r2[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        r0[c] = p0[c] - a * u * p2[c];
+        r1[c] = p1[c] - a * v * p2[c];
+        r2[c] = a * (w * p2[c] - u * p0[c] - v * p1[c]);
+      }
+      const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int t = 0; t < 6; ++t)
+        V[t] += p0[ia[t]] * r0[ib[t]] + p1[ia[t]] * r1[ib[t]] + p2[ia[t]] * r2[ib[t]];
+      const double c0 = p0[3] - a * u * p2[3] - eta * u;
+      const double c1 = p1[3] - a * v * p2[3] - eta * v;
+      const double c2 = a * (w * p2[3] - u * p0[3] - v * p1[3]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) h[c] += c0 * p0[c] + c1 * p1[c] + c2 * p2[c];
+    }
+    // X = -V^-1 h by the Cholesky factor, pseudo-inverse when deficient
+    double X[3];
+    const double dmax = fmax(V[0], fmax(V[3], V[5]));
+    const double f00 = rsqrt(V[0]);
+    const double l10 = V[1] * f00, l20 = V[2] * f00;
+    const double d1 = V[3] - l10 * l10;
+    const double f11 = rsqrt(d1);
+    const double l21 = (V[4] - l20 * l10) * f11;
+    const double d2 = V[5] - l20 * l20 - l21 * l21;
+    const double f22 = rsqrt(d2);
+    const bool suspect = !(V[0] > 1e-9 * dmax) || !(d1 > 1e-9 * dmax) || !(d2 > 1e-9 * dmax) ||
+                         !(dmax > 0.0);
+    bool deficient = false;
+    if (suspect) {
+      Sym3 vs;
+      Vec3 hs;
+      for (int t = 0; t < 6; ++t) vs.v[t] = V[t];
+      for (int c = 0; c < 3; ++c) hs.x[c] = h[c];
+      const PinvOut o = pinv_solve(vs, hs);
+      deficient = o.deficient;
+      for (int c = 0; c < 3; ++c) X[c] = o.X[c];
+    }
+    if (!deficient) {
+      const double f10 = -l10 * f00 * f11;
+      const double f20 = -(l20 * f00 + l21 * f10) * f22;
+      const double f21 = -l21 * f11 * f22;
+      const double z0 = f00 * h[0];
+      const double z1 = f10 * h[0] + f11 * h[1];
+      const double z2 = f20 * h[0] + f21 * h[1] + f22 * h[2];
+      X[0] = -(f00 * z0 + f10 * z1 + f20 * z2);
+      X[1] = -(f11 * z1 + f21 * z2);
+      X[2] = -(f22 * z2);
+    }
+    if (X_out) {
+      X_out[3 * (size_t)j] = X[0];
+      X_out[3 * (size_t)j + 1] = X[1];
+      X_out[3 * (size_t)j + 2] = X[2];
+    }
+    // sum_k ||r_k||^2 at X, directly (Eq. pose, Eq. ba_first_stage)
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t k = b; k < e; ++k) {
+      const int i = cam[k];
+      if ((unsigned)i >= (unsigned)nc) continue;
+      const double2 m = meas[k];
+      const double2* Q = reinterpret_cast<const double2*>(P + 12 * (size_t)i);
+      double q[12];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        const double2 x = __ldg(Q + r);
+        q[2 * r] = x.x;
+        q[2 * r + 1] = x.y;
+      }
+      const double y0 = fma(q[0], X[0], fma(q[1], X[1], fma(q[2], X[2], q[3])));
+      const double y1 = fma(q[4], X[0], fma(q[5], X[1], fma(q[6], X[2], q[7])));
+      const double y2 = fma(q[8], X[0], fma(q[9], X[1], fma(q[10], X[2], q[11])));
+      const double a0 = fma(-m.x, y2, y0), a1 = fma(-m.y, y2, y1);
+      const double g0 = y0 - m.x, g1 = y1 - m.y;
+      s1 = fma(a0, a0, fma(a1, a1, s1));
+      s2 = fma(g0, g0, fma(g1, g1, s2));
+    }
+    cost = bad ? __longlong_as_double(0x7ff8000000000000LL) : a * s1 + eta * s2;
+  }
+  // block partial in a fixed order: warp tree, then the warps in index order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cost += __shfl_xor_sync(0xffffffffu, cost, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cost;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NA_BLOCK / 32; ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+// Sum of the nb block partials in a fixed order into *cost_out.
+__global__ void __launch_bounds__(256)
+k_noalloc_sum(const double* __restrict__ part, int nb, double* __restrict__ cost_out) {
+  __shared__ double red[256];
+  double c = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 256) c += part[i];
+  red[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *cost_out = red[0];
+}
+
+// Device address of the working array on the current device (looked up on
+// the first call for that device).
+cudaError_t na_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(na_mutex);
+  if (!na_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, na_partials);
+    if (e != cudaSuccess) return e;
+    na_ptr[dev] = static_cast<double*>(ptr);
+  }
+  *out = na_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace povar
+
+extern "C" povar_status povar_cost_noalloc(int32_t n_cams, int32_t n_points, int64_t n_obs,
+                                           const double* P, const uint32_t* off_pt,
+                                           const int32_t* cam, const double* meas, double eta,
+                                           double* X_out, double* cost_out, void* cuda_stream) {
+  using namespace povar;
+  if (!P || !off_pt || !cam || !meas || !cost_out) return POVAR_EINVAL;
+  if (n_cams < 1 || n_points < 1 || n_obs < 1) return POVAR_EINVAL;
+  if (n_points > POVAR_NOALLOC_MAX_POINTS) return POVAR_EINVAL;
+  if (!(eta >= 0.0 && eta <= 1.0)) return POVAR_EINVAL;
+  double* part = nullptr;
+  if (na_scratch(&part) != cudaSuccess) {
+    cudaGetLastError();
+    return POVAR_ECUDA;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int nb = (n_points + NA_BLOCK - 1) / NA_BLOCK;
+  k_landmark_csr<<<nb, NA_BLOCK, 0, s>>>(P, n_cams, off_pt, cam,
+                                         reinterpret_cast<const double2*>(meas), n_obs, n_points,
+                                         eta, X_out, part);
+  k_noalloc_sum<<<1, 256, 0, s>>>(part, nb, cost_out);
+  if (cudaGetLastError() != cudaSuccess) return POVAR_ECUDA;
+  return POVAR_OK;
+}

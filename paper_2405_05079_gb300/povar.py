@@ -100,6 +100,8 @@ def lib() -> C.CDLL:
     L.povar_batch_cost.argtypes = [vp, C.c_double, dp]
     L.povar_batch_solve.argtypes = [vp, C.POINTER(Params), i32, C.c_double, dp,
                                     C.POINTER(StepReport), C.POINTER(C.c_int32)]
+    L.povar_cost_noalloc.argtypes = [i32, i32, i64, vp, vp, vp, vp, C.c_double, vp, vp, vp]
+    L.povar_cost_noalloc.restype = C.c_int
     for name in ("povar_batch_create", "povar_batch_set_cameras", "povar_batch_get_cameras",
                  "povar_batch_cost", "povar_batch_solve"):
         getattr(L, name).restype = C.c_int
@@ -346,6 +348,25 @@ class SolveResult:
 def estimate_bytes(n_cams: int, n_points: int, n_obs: int) -> int:
     """Upper-bound device footprint of a problem of these sizes."""
     return int(lib().povar_estimate_bytes(n_cams, n_points, n_obs))
+
+
+NOALLOC_MAX_POINTS = 4194304   # POVAR_NOALLOC_MAX_POINTS
+
+
+def cost_noalloc(n_cams: int, n_points: int, n_obs: int, P: int, off_pt: int, cam: int,
+                 meas: int, eta: float, X_out: int | None, cost_out: int,
+                 stream: int | None = None) -> None:
+    """povar_cost_noalloc on raw device addresses (see include/povar.h):
+    P (n_cams x 12 f64), off_pt (n_points + 1 u32), cam (n_obs i32), meas
+    (n_obs x 2 f64), X_out (n_points x 3 f64 or None), cost_out (1 f64).
+    Enqueued on ``stream``; nothing is allocated or synchronized."""
+    st = lib().povar_cost_noalloc(n_cams, n_points, n_obs, P, off_pt, cam, meas, eta,
+                                  X_out, cost_out, stream)
+    if st == 1 and n_points > NOALLOC_MAX_POINTS:
+        raise ValueError(f"n_points = {n_points} exceeds the allocation-free limit "
+                         f"of {NOALLOC_MAX_POINTS} landmarks")
+    if st != 0:
+        raise PovarError(st, "povar_cost_noalloc failed")
 
 
 def version() -> str:
