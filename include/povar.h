@@ -75,9 +75,12 @@ enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1 };
  *             landmark-major pass whose camera contributions are reduced
  *             across the lanes of a warp that share a camera; 2 =
  *             landmark-major gather pass + camera-major pass over the
- *             landmark slice rows that contain each camera; -1 = chosen at
- *             creation from the observation layout. All schedules compute
- *             the same series. */
+ *             landmark slice rows that contain each camera; 3 = the fused
+ *             pass of 1 with one warp per group of up to four slices whose
+ *             landmarks share their first camera, one reduction per group
+ *             row when all of its lanes see one camera; -1 = autotuned (see
+ *             povar_get_tuning). All schedules compute the same series. */
+enum { POVAR_NSCHEDULES = 4 };
 typedef struct {
   double eta;
   double lambda0;
@@ -208,11 +211,11 @@ povar_status povar_get_profile(povar_problem* p, double* ms_out, int64_t* steps_
                                int64_t* products_out, int32_t reset);
 
 /* Series-schedule autotuner. The first povar_solve with params->schedule
- * = -1 times two series terms of every schedule (0, 1, 2) on the live
- * state with CUDA events and keeps the fastest for that precision; later
- * solves and povar_step with schedule -1 use it. povar_get_tuning returns the
- * chosen schedule (-1 before tuning) and the three measured times in
- * milliseconds (ms_out[3], may be NULL). */
+ * = -1 times two series terms of every schedule (0 .. POVAR_NSCHEDULES-1)
+ * on the live state with CUDA events and keeps the fastest for that
+ * precision; later solves and povar_step with schedule -1 use it.
+ * povar_get_tuning returns the chosen schedule (-1 before tuning) and the
+ * measured times in milliseconds (ms_out[POVAR_NSCHEDULES], may be NULL). */
 povar_status povar_get_tuning(povar_problem* p, int32_t precision, int32_t* schedule_out,
                               float* ms_out);
 

@@ -67,7 +67,8 @@ povar_status check_params(Problem* p, const povar_params* q) {
     return fail(p, POVAR_EINVAL, "unknown manifold");
   if (q->precision != POVAR_FP64 && q->precision != POVAR_MIXED_FP32)
     return fail(p, POVAR_EINVAL, "unknown precision");
-  if (q->schedule < -1 || q->schedule > 2) return fail(p, POVAR_EINVAL, "unknown schedule");
+  if (q->schedule < -1 || q->schedule >= POVAR_NSCHEDULES)
+    return fail(p, POVAR_EINVAL, "unknown schedule");
   return POVAR_OK;
 }
 
@@ -208,7 +209,7 @@ povar_status autotune_schedule(Problem* p, const povar_params* q) {
   for (int k = 0; k < 4; ++k) POVAR_CUDA(cudaEventCreate(&ev[k]));
   int best = 1;
   float best_ms = 1e30f;
-  for (int sched = 0; sched < 3; ++sched) {
+  for (int sched = 0; sched < POVAR_NSCHEDULES; ++sched) {
     if ((s = launch_camera_prepare(p, q->precision, q->manifold, q->eta)) != POVAR_OK) break;
     POVAR_CUDA(cudaEventRecord(ev[0], p->stream));
     for (int k = 1; k <= 2 && s == POVAR_OK; ++k)
@@ -316,8 +317,14 @@ int64_t povar_estimate_bytes(int32_t n_cams, int32_t n_points, int64_t n_obs) {
              2 * 12 * 4 + 12 * 4 + 2 * 12 * 8 + 12 * 8 + 2 * 8);
   b += 2 * npd * (3 * 8 + 6 * 8 + 16 + 16 + 4) + npd * (32 + 64) + 3 * (npd / 32) * 8;
   b += chunks * (52 + 12) * 8;
-  b += nsell / 32 * 8 + 2 * (nsell / 32 + no / 8) * 12 * 8 + 3 * (nsell / 32 + no / 8) * 4 +
-       3 * (nc + 1) * 4;
+  // every run partial and every camera-row visit holds at least one
+  // observation, so n_obs bounds their counts
+  // fused schedule: run mask and base per slice row, partials and their index
+  b += (nsell / 32) * 8 + no * (12 * 8 + 4) + (nc + 1) * 4;
+  // camera-row schedule: visit lists
+  b += no * 8 + (nc + 1) * 4;
+  // grouped schedule: group tables, group rows, slice-row runs, partials
+  b += 2 * (npd / 32 + 1) * 4 + (nsell / 32) * 16 + no * (12 * 8 + 4) + (nc + 1) * 4;
   return b + (1 << 20);
 }
 
@@ -677,7 +684,7 @@ povar_status povar_get_tuning(povar_problem* pp, int32_t precision, int32_t* sch
   const int k = precision == POVAR_FP64 ? 0 : 1;
   if (schedule_out) *schedule_out = p->tuned_schedule[k];
   if (ms_out)
-    for (int q = 0; q < 3; ++q) ms_out[q] = p->tune_ms[k][q];
+    for (int q = 0; q < POVAR_NSCHEDULES; ++q) ms_out[q] = p->tune_ms[k][q];
   return POVAR_OK;
 }
 

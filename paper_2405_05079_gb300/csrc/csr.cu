@@ -396,20 +396,44 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
     if ((s = radix_sort(p, sc, &kk, &vv, p->np, use_cam ? len_bits + cam_bits : len_bits)) !=
         POVAR_OK)
       return s;
-    // Slices of the sorted order are then ordered by width (longest track
-    // first, stable), keeping the last partial slice in place, so that the
-    // eight slices of a block have similar widths. Pads stay at the end.
-    std::vector<uint32_t> order(p->np), h_len(p->np);
+    // Full slices of the sorted order are grouped: up to GROUP consecutive
+    // slices whose first landmarks share the smallest camera (their rows
+    // then tend to see the same camera, row by row). Groups are ordered by
+    // width (longest track first, stable) so that the warps of a block get
+    // similar work; the last partial slice and the pads stay at the end,
+    // one group each.
+    std::vector<uint32_t> order(p->np), h_len(p->np), h_min(p->np);
     POVAR_COPY(order.data(), vv, p->np, cudaMemcpyDeviceToHost);
     POVAR_COPY(h_len.data(), len, p->np, cudaMemcpyDeviceToHost);
+    POVAR_COPY(h_min.data(), mincam, p->np, cudaMemcpyDeviceToHost);
     const int nfull = p->np / SLICE;
     std::vector<uint32_t> width(nfull, 0);
     for (int sl = 0; sl < nfull; ++sl)
       for (int l = 0; l < SLICE; ++l) width[sl] = std::max(width[sl], h_len[order[sl * SLICE + l]]);
-    std::vector<int> sl_order(nfull);
-    for (int sl = 0; sl < nfull; ++sl) sl_order[sl] = sl;
-    std::stable_sort(sl_order.begin(), sl_order.end(),
-                     [&](int x, int y) { return width[x] > width[y]; });
+    std::vector<std::pair<int, int>> groups;  // [first, last) sorted slices
+    for (int sl = 0; sl < nfull;) {
+      int e = sl + 1;
+      while (e < nfull && e - sl < GROUP && h_min[order[e * SLICE]] == h_min[order[sl * SLICE]]) ++e;
+      groups.emplace_back(sl, e);
+      sl = e;
+    }
+    std::vector<uint32_t> gwidth(groups.size(), 0);
+    for (size_t g = 0; g < groups.size(); ++g)
+      for (int sl = groups[g].first; sl < groups[g].second; ++sl)
+        gwidth[g] = std::max(gwidth[g], width[sl]);
+    std::vector<int> g_order(groups.size());
+    for (size_t g = 0; g < groups.size(); ++g) g_order[g] = (int)g;
+    std::stable_sort(g_order.begin(), g_order.end(),
+                     [&](int x, int y) { return gwidth[x] > gwidth[y]; });
+    std::vector<int> sl_order;
+    sl_order.reserve(nfull);
+    p->h_grp_slice0.assign(1, 0u);
+    for (int g : g_order) {
+      for (int sl = groups[g].first; sl < groups[g].second; ++sl) sl_order.push_back(sl);
+      p->h_grp_slice0.push_back((uint32_t)sl_order.size());
+    }
+    for (int sl = nfull; sl < p->nslices; ++sl) p->h_grp_slice0.push_back((uint32_t)sl + 1);
+    p->ngroups = (int32_t)p->h_grp_slice0.size() - 1;
     std::vector<uint32_t> slot_pt(p->np_pad, 0xffffffffu), slot_len(p->np_pad, 0),
         pt_slot(p->np);
     for (int sl = 0; sl < nfull; ++sl)
@@ -493,6 +517,9 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
 // row; otherwise bit l is set when lane l starts a run (bit 0 always set).
 // row_base is the index of the row's first partial. The partials of camera
 // i are listed, in increasing index, at cam_part_idx[cam_part_off[i] ..).
+povar_status build_group_runs(Problem* p, const std::vector<int32_t>& cam,
+                              const std::vector<uint32_t>& off);
+
 povar_status build_runs(Problem* p) {
   povar_status s;
   const int64_t nrows = p->nsell / SLICE;
@@ -590,6 +617,113 @@ povar_status build_runs(Problem* p) {
   POVAR_COPY(p->row_base, base.data(), base.size(), cudaMemcpyHostToDevice);
   POVAR_COPY(p->cam_part_off, poff.data(), poff.size(), cudaMemcpyHostToDevice);
   POVAR_COPY(p->cam_part_idx, pidx.data(), pidx.size(), cudaMemcpyHostToDevice);
+  return build_group_runs(p, cam, off);
+}
+
+// Run structure of the grouped schedule. Group g holds the slices
+// h_grp_slice0[g] .. h_grp_slice0[g+1]-1; its rows t = 0 .. (widest slice)-1
+// are numbered from grp_row0[g]. A group row whose valid lanes (over all of
+// the group's slices that reach row t) all see one camera is "uniform": one
+// partial, at grow_base, camera in grow_cam. For any other group row,
+// grow_cam = -1 and every slice row in it gets the run description of the
+// fused schedule (srow_mask, srow_base) in the grouped partial space. The
+// partials of camera i are listed at cam_part3_idx[cam_part3_off[i] ..).
+povar_status build_group_runs(Problem* p, const std::vector<int32_t>& cam,
+                              const std::vector<uint32_t>& off) {
+  povar_status s;
+  const int ng = p->ngroups;
+  const int64_t nrows = p->nsell / SLICE;
+  std::vector<uint32_t> grow0(ng + 1, 0), gbase, smask(std::max<int64_t>(nrows, 1), 0),
+      sbase(std::max<int64_t>(nrows, 1), 0);
+  std::vector<int32_t> gcam, pcam;
+  for (int g = 0; g < ng; ++g) {
+    const uint32_t s0 = p->h_grp_slice0[g], s1 = p->h_grp_slice0[g + 1];
+    uint32_t W = 0;
+    for (uint32_t sl = s0; sl < s1; ++sl) W = std::max(W, (off[sl + 1] - off[sl]) / SLICE);
+    grow0[g] = (uint32_t)gcam.size();
+    for (uint32_t t = 0; t < W; ++t) {
+      int32_t c0 = -1;
+      bool uniform = true;
+      for (uint32_t sl = s0; sl < s1; ++sl) {
+        if (t >= (off[sl + 1] - off[sl]) / SLICE) continue;
+        const int32_t* c = cam.data() + (size_t)off[sl] + (size_t)t * SLICE;
+        for (int l = 0; l < SLICE; ++l) {
+          if (c[l] < 0) continue;
+          if (c0 < 0) c0 = c[l];
+          else if (c[l] != c0) uniform = false;
+        }
+      }
+      if (uniform && c0 >= 0) {
+        gcam.push_back(c0);
+        gbase.push_back((uint32_t)pcam.size());
+        pcam.push_back(c0);
+        continue;
+      }
+      gcam.push_back(-1);
+      gbase.push_back(0);
+      for (uint32_t sl = s0; sl < s1; ++sl) {
+        if (t >= (off[sl + 1] - off[sl]) / SLICE) continue;
+        const int64_t row = off[sl] / SLICE + t;
+        const int32_t* c = cam.data() + row * SLICE;
+        int32_t r0 = -1;
+        bool ru = true;
+        for (int l = 0; l < SLICE; ++l) {
+          if (c[l] < 0) continue;
+          if (r0 < 0) r0 = c[l];
+          else if (c[l] != r0) ru = false;
+        }
+        sbase[row] = (uint32_t)pcam.size();
+        if (ru && r0 >= 0) {
+          smask[row] = 0;
+          pcam.push_back(r0);
+          continue;
+        }
+        uint32_t m = 0;
+        for (int l = 0; l < SLICE; ++l) {
+          if (l == 0 || c[l] != c[l - 1]) {
+            m |= 1u << l;
+            if (c[l] >= 0) pcam.push_back(c[l]);
+          }
+        }
+        smask[row] = m;
+      }
+    }
+  }
+  grow0[ng] = (uint32_t)gcam.size();
+  const int64_t npart = (int64_t)pcam.size();
+  std::vector<uint32_t> poff(p->nc + 1, 0), pidx(std::max<int64_t>(npart, 1));
+  for (int32_t c : pcam) ++poff[c + 1];
+  for (int c = 0; c < p->nc; ++c) poff[c + 1] += poff[c];
+  {
+    std::vector<uint32_t> cursor(poff.begin(), poff.end() - 1);
+    for (int64_t q = 0; q < npart; ++q) pidx[cursor[pcam[q]]++] = (uint32_t)q;
+  }
+  p->ngrows = (int64_t)gcam.size();
+  p->npart3 = npart;
+  if (gcam.empty()) {
+    gcam.push_back(-1);
+    gbase.push_back(0);
+  }
+  if ((s = dev_alloc(p, &p->grp_slice0, p->h_grp_slice0.size(), "grp_slice0")) ||
+      (s = dev_alloc(p, &p->grp_row0, grow0.size(), "grp_row0")) ||
+      (s = dev_alloc(p, &p->grow_cam, gcam.size(), "grow_cam")) ||
+      (s = dev_alloc(p, &p->grow_base, gbase.size(), "grow_base")) ||
+      (s = dev_alloc(p, &p->srow_mask, smask.size(), "srow_mask")) ||
+      (s = dev_alloc(p, &p->srow_base, sbase.size(), "srow_base")) ||
+      (s = dev_alloc(p, &p->cam_part3_off, poff.size(), "cam_part3_off")) ||
+      (s = dev_alloc(p, &p->cam_part3_idx, pidx.size(), "cam_part3_idx")) ||
+      (s = dev_alloc_bytes(p, &p->part3, std::max<int64_t>(npart, 1) * 12 * sizeof(double),
+                           "part3")))
+    return s;
+  POVAR_COPY(p->grp_slice0, p->h_grp_slice0.data(), p->h_grp_slice0.size(),
+             cudaMemcpyHostToDevice);
+  POVAR_COPY(p->grp_row0, grow0.data(), grow0.size(), cudaMemcpyHostToDevice);
+  POVAR_COPY(p->grow_cam, gcam.data(), gcam.size(), cudaMemcpyHostToDevice);
+  POVAR_COPY(p->grow_base, gbase.data(), gbase.size(), cudaMemcpyHostToDevice);
+  POVAR_COPY(p->srow_mask, smask.data(), smask.size(), cudaMemcpyHostToDevice);
+  POVAR_COPY(p->srow_base, sbase.data(), sbase.size(), cudaMemcpyHostToDevice);
+  POVAR_COPY(p->cam_part3_off, poff.data(), poff.size(), cudaMemcpyHostToDevice);
+  POVAR_COPY(p->cam_part3_idx, pidx.data(), pidx.size(), cudaMemcpyHostToDevice);
   return POVAR_OK;
 }
 

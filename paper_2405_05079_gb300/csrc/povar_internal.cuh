@@ -33,6 +33,7 @@ constexpr int SLICE = 32;        // landmarks per SELL slice (one warp)
 constexpr int CHUNK = 256;       // observations per camera-major chunk
 constexpr int LIN_ACC = 52;      // linearization accumulators per chunk
 constexpr int BLOCK = 256;       // threads per block for slot kernels
+constexpr int GROUP = 4;         // slices per warp in the grouped series schedule
 constexpr double PINV_COND = 1e12;
 constexpr double LAMBDA_MIN = 1e-8;   // damping floor
 constexpr double LAMBDA_MAX = 1e30;   // damping ceiling (solve reported as diverged)
@@ -117,9 +118,25 @@ struct Problem {
   uint32_t* cam_row_off = nullptr;  // [nc + 1]
   uint32_t* cam_row_pos0 = nullptr; // [nvisits]
   uint32_t* cam_row_slot0 = nullptr;// [nvisits]
+  // grouped schedule (3): one warp handles up to GROUP consecutive slices
+  // whose first landmarks share the smallest camera; a group row (row t of
+  // all the group's slices) whose valid lanes all see one camera yields a
+  // single partial; other group rows fall back to per-slice-row runs
+  int32_t ngroups = 0;
+  int64_t ngrows = 0, npart3 = 0;
+  std::vector<uint32_t> h_grp_slice0;   // [ngroups + 1] (host)
+  uint32_t* grp_slice0 = nullptr;       // [ngroups + 1] first slice of each group
+  uint32_t* grp_row0 = nullptr;         // [ngroups + 1] first group row of each group
+  int32_t* grow_cam = nullptr;          // [ngrows] camera of a group-uniform row, else -1
+  uint32_t* grow_base = nullptr;        // [ngrows] partial of a group-uniform row
+  uint32_t* srow_mask = nullptr;        // [nrows] runs of slice rows in non-uniform group rows
+  uint32_t* srow_base = nullptr;        // [nrows]
+  uint32_t* cam_part3_off = nullptr;    // [nc + 1]
+  uint32_t* cam_part3_idx = nullptr;    // [npart3]
+  void* part3 = nullptr;                // [npart3 * 12] float or double
   int schedule_default = 1;         // chosen at creation from the run statistics
   int tuned_schedule[2] = {-1, -1}; // autotuned series schedule per precision (-1: not yet)
-  float tune_ms[2][3] = {};         // measured ms of two series terms per schedule
+  float tune_ms[2][POVAR_NSCHEDULES] = {};  // measured ms of two series terms per schedule
   // cameras
   double* P64[2] = {nullptr, nullptr};  // [nc*12]
   double* Ltab = nullptr;               // [nc*48] landmark tables at trial P

@@ -822,6 +822,290 @@ __global__ void k_pred_finish(DeviceState* __restrict__ st, int nc, int nparts, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Grouped schedule (3). One warp handles a group of up to GROUP slices whose
+// landmarks share their smallest camera, lane l holding landmark l of every
+// slice of the group. Row t of the group is row t of each of its slices; in
+// a "uniform" group row every valid lane of every slice observes the same
+// camera (known from the table, so its rows are loaded once, before any
+// observation data), and the camera contributions of all the group's
+// landmarks are summed in registers and reduced across the warp once,
+// into one partial. Other group rows are handled slice row by slice row
+// exactly as in the fused schedule.
+// ---------------------------------------------------------------------------
+// t += Pbar^T C (Y x~) for one observation (W^T-gather)
+template <typename T>
+__device__ __forceinline__ void gather_obs(const T Y0[4], const T Y1[4], const T Y2[4],
+                                           const T P0[4], const T P1[4], const T P2[4], T a,
+                                           T mu, T mv, const T X[3], T t[3]) {
+  const T e0 = Y0[0] * X[0] + Y0[1] * X[1] + Y0[2] * X[2] + Y0[3];
+  const T e1 = Y1[0] * X[0] + Y1[1] * X[1] + Y1[2] * X[2] + Y1[3];
+  const T e2 = Y2[0] * X[0] + Y2[1] * X[1] + Y2[2] * X[2] + Y2[3];
+  const T au = a * mu, av = a * mv;
+  const T aw = au * mu + av * mv;
+  const T c0 = e0 - au * e2;
+  const T c1 = e1 - av * e2;
+  const T c2 = aw * e2 - au * e0 - av * e1;
+  t[0] += P0[0] * c0 + P1[0] * c1 + P2[0] * c2;
+  t[1] += P0[1] * c0 + P1[1] * c1 + P2[1] * c2;
+  t[2] += P0[2] * c0 + P1[2] * c1 + P2[2] * c2;
+}
+
+// v += vec((C Pbar s) x~^T) for one observation (W-scatter)
+template <typename T>
+__device__ __forceinline__ void scatter_obs(const T P0[4], const T P1[4], const T P2[4], T a,
+                                            T mu, T mv, const T S[3], const T X[3], T v[12]) {
+  const T w0 = P0[0] * S[0] + P0[1] * S[1] + P0[2] * S[2];
+  const T w1 = P1[0] * S[0] + P1[1] * S[1] + P1[2] * S[2];
+  const T w2 = P2[0] * S[0] + P2[1] * S[1] + P2[2] * S[2];
+  const T au = a * mu, av = a * mv;
+  const T aw = au * mu + av * mv;
+  const T q0 = w0 - au * w2;
+  const T q1 = w1 - av * w2;
+  const T q2 = aw * w2 - au * w0 - av * w1;
+  v[0] += q0 * X[0]; v[1] += q0 * X[1]; v[2] += q0 * X[2]; v[3] += q0;
+  v[4] += q1 * X[0]; v[5] += q1 * X[1]; v[6] += q1 * X[2]; v[7] += q1;
+  v[8] += q2 * X[0]; v[9] += q2 * X[1]; v[10] += q2 * X[2]; v[11] += q2;
+}
+
+// Segmented sum of v over the runs of equal camera that start at the set
+// bits of mask; the run starting at a valid lane stores its sum as the next
+// partial from pbase (valid run starts in lane order).
+template <typename T>
+__device__ __forceinline__ void store_runs(T v[12], uint32_t mask, bool valid, uint32_t pbase,
+                                           int lane, T* __restrict__ part) {
+  const uint32_t nb = lane < 31 ? (mask >> (lane + 1)) : 0u;
+  bool ok[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int o = 1 << q;
+    ok[q] = (lane + o < 32) && ((nb & ((1u << o) - 1u)) == 0u);
+  }
+#pragma unroll
+  for (int e = 0; e < 12; ++e) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const T other = __shfl_down_sync(0xffffffffu, v[e], 1 << q);
+      if (ok[q]) v[e] += other;
+    }
+  }
+  const uint32_t starts = mask & __ballot_sync(0xffffffffu, valid);
+  if ((starts >> lane) & 1u) {
+    T* out = part + ((size_t)pbase + __popc(starts & ((1u << lane) - 1u))) * 12;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) out[e] = v[e];
+  }
+}
+
+// Per warp, 32 group rows at a time: the rows' cameras are read with one
+// coalesced load (lane r holds the camera of row r0 + r) and the rows Y_i, P_i
+// of every uniform row's camera are staged in shared memory by the lanes in
+// parallel, so the row loop waits on no dependent global load; the
+// measurements of the next row are loaded while the current one is computed.
+template <typename T>
+struct GroupStage {
+  T cam[BLOCK / SLICE][SLICE][24];  // per warp, per staged row: Y rows (12) then P rows (12)
+};
+
+template <typename T>
+__device__ __forceinline__ void stage_rows(T (*dst)[24], const int32_t* __restrict__ grow_cam,
+                                           uint32_t rbeg, uint32_t nrow, const T* __restrict__ vec,
+                                           const T* __restrict__ camP, bool with_y, int lane,
+                                           int& gc) {
+  __syncwarp();  // every lane is done with the previously staged rows
+  gc = lane < (int)nrow ? __ldg(grow_cam + rbeg + lane) : -1;
+  if (gc >= 0) {
+    T row[4];
+    if (with_y) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        load_row<T>(vec, gc, q, row);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dst[lane][4 * q + e] = row[e];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      load_row<T>(camP, gc, q, row);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) dst[lane][12 + 4 * q + e] = row[e];
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BLOCK, 2)
+k_series_grouped(const DeviceState* __restrict__ st, T a,
+                 const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
+                 const int32_t* __restrict__ sell_cam,
+                 const typename Vt<T>::m2* __restrict__ sell_m, const T* __restrict__ camPa,
+                 const T* __restrict__ camPb, const T* __restrict__ vec, PointData<T> pd0,
+                 PointData<T> pd1, const uint32_t* __restrict__ grp_slice0,
+                 const uint32_t* __restrict__ grp_row0, int ngroups,
+                 const int32_t* __restrict__ grow_cam, const uint32_t* __restrict__ grow_base,
+                 const uint32_t* __restrict__ srow_mask, const uint32_t* __restrict__ srow_base,
+                 T* __restrict__ part) {
+  __shared__ __align__(16) GroupStage<T> stage;
+  if (st->converged || st->stop_series) return;
+  const int wl = (int)(threadIdx.x >> 5);
+  const int g = blockIdx.x * (BLOCK / SLICE) + wl;
+  if (g >= ngroups) return;  // whole warp (no block-level barrier below)
+  const int lane = threadIdx.x & 31;
+  using M2 = typename Vt<T>::m2;
+  T (*sm)[24] = stage.cam[wl];
+  const PointData<T>& pd = st->cur ? pd1 : pd0;
+  const T* __restrict__ camP = st->cur ? camPb : camPa;
+  const uint32_t s0 = grp_slice0[g];
+  const int ns = (int)(grp_slice0[g + 1] - s0);
+  const uint32_t r0 = grp_row0[g], W = grp_row0[g + 1] - r0;
+  uint32_t sb[GROUP], wid[GROUP], len[GROUP];
+  T X[GROUP][3], t[GROUP][3];
+#pragma unroll
+  for (int k = 0; k < GROUP; ++k) {
+    sb[k] = 0;
+    wid[k] = 0;
+    len[k] = 0;
+    X[k][0] = X[k][1] = X[k][2] = 0;
+    t[k][0] = t[k][1] = t[k][2] = 0;
+    if (k < ns) {
+      const uint32_t s = s0 + (uint32_t)k;
+      sb[k] = sell_off[s];
+      wid[k] = (sell_off[s + 1] - sb[k]) / SLICE;
+      len[k] = slot_len[s * SLICE + lane];
+      T Fk[6];
+      load_point<T>(pd, (int)(s * SLICE) + lane, X[k], Fk);
+    }
+  }
+  // pass 1: t_j = sum over the landmark's observations of Pbar^T C (Y x~_j)
+  M2 mn[GROUP];
+#pragma unroll
+  for (int k = 0; k < GROUP; ++k) mn[k] = 0u < len[k] ? sell_m[sb[k] + lane] : M2{0, 0};
+  int gc = -1;
+  for (uint32_t r = 0; r < W; ++r) {
+    const uint32_t rl = r & (SLICE - 1);
+    if (rl == 0) stage_rows<T>(sm, grow_cam, r0 + r, min(W - r, (uint32_t)SLICE), vec, camP, true,
+                               lane, gc);
+    const int c = __shfl_sync(0xffffffffu, gc, (int)rl);
+    M2 m[GROUP];
+#pragma unroll
+    for (int k = 0; k < GROUP; ++k) {
+      m[k] = mn[k];
+      mn[k] = r + 1 < len[k] ? sell_m[sb[k] + lane + (r + 1) * SLICE] : M2{0, 0};
+    }
+    if (c >= 0) {
+      const T* q = sm[rl];
+      T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        Y0[e] = q[e]; Y1[e] = q[4 + e]; Y2[e] = q[8 + e];
+        P0[e] = q[12 + e]; P1[e] = q[16 + e]; P2[e] = q[20 + e];
+      }
+#pragma unroll
+      for (int k = 0; k < GROUP; ++k)
+        if (r < len[k]) gather_obs<T>(Y0, Y1, Y2, P0, P1, P2, a, (T)m[k].x, (T)m[k].y, X[k], t[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < GROUP; ++k) {
+        if (r >= len[k]) continue;
+        const int i = sell_cam[sb[k] + lane + r * SLICE];
+        T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
+        load_row<T>(vec, i, 0, Y0);
+        load_row<T>(vec, i, 1, Y1);
+        load_row<T>(vec, i, 2, Y2);
+        load_row<T>(camP, i, 0, P0);
+        load_row<T>(camP, i, 1, P1);
+        load_row<T>(camP, i, 2, P2);
+        gather_obs<T>(Y0, Y1, Y2, P0, P1, P2, a, (T)m[k].x, (T)m[k].y, X[k], t[k]);
+      }
+    }
+  }
+  // s_j = V_j^-1 t_j = F^T (F t_j)
+  T S[GROUP][3];
+#pragma unroll
+  for (int k = 0; k < GROUP; ++k) {
+    T Xk[3], F[6] = {0, 0, 0, 0, 0, 0};
+    if (k < ns) load_point<T>(pd, (int)((s0 + (uint32_t)k) * SLICE) + lane, Xk, F);
+    const T z0 = F[0] * t[k][0];
+    const T z1 = F[1] * t[k][0] + F[2] * t[k][1];
+    const T z2 = F[3] * t[k][0] + F[4] * t[k][1] + F[5] * t[k][2];
+    S[k][0] = F[0] * z0 + F[1] * z1 + F[3] * z2;
+    S[k][1] = F[2] * z1 + F[4] * z2;
+    S[k][2] = F[5] * z2;
+  }
+  // pass 2: camera contributions vec((C Pbar s_j) x~_j^T); the staged rows of
+  // the first 32 group rows are still in place when W <= 32
+#pragma unroll
+  for (int k = 0; k < GROUP; ++k) mn[k] = 0u < len[k] ? sell_m[sb[k] + lane] : M2{0, 0};
+  for (uint32_t r = 0; r < W; ++r) {
+    const uint32_t rl = r & (SLICE - 1);
+    if (rl == 0 && W > (uint32_t)SLICE)
+      stage_rows<T>(sm, grow_cam, r0 + r, min(W - r, (uint32_t)SLICE), vec, camP, false, lane,
+                    gc);
+    const int c = __shfl_sync(0xffffffffu, gc, (int)rl);
+    M2 m[GROUP];
+#pragma unroll
+    for (int k = 0; k < GROUP; ++k) {
+      m[k] = mn[k];
+      mn[k] = r + 1 < len[k] ? sell_m[sb[k] + lane + (r + 1) * SLICE] : M2{0, 0};
+    }
+    if (c >= 0) {
+      const T* q = sm[rl];
+      T P0[4], P1[4], P2[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        P0[e] = q[12 + e]; P1[e] = q[16 + e]; P2[e] = q[20 + e];
+      }
+      T v[12];
+#pragma unroll
+      for (int e = 0; e < 12; ++e) v[e] = 0;
+#pragma unroll
+      for (int k = 0; k < GROUP; ++k)
+        if (r < len[k]) scatter_obs<T>(P0, P1, P2, a, (T)m[k].x, (T)m[k].y, S[k], X[k], v);
+      T red[3];
+      int vb;
+      warp_reduce12<T>(v, lane, red, vb);
+      if ((lane & 7) == 0) {
+        T* out = part + (size_t)__ldg(grow_base + r0 + r) * 12 + vb;
+        out[0] = red[0];
+        out[1] = red[1];
+        out[2] = red[2];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < GROUP; ++k) {
+        if (r >= wid[k]) continue;  // warp-uniform
+        const uint32_t row = sb[k] / SLICE + r;
+        const uint32_t mask = __ldg(srow_mask + row), pbase = __ldg(srow_base + row);
+        const int i = r < len[k] ? sell_cam[sb[k] + lane + r * SLICE] : -1;
+        T v[12];
+#pragma unroll
+        for (int e = 0; e < 12; ++e) v[e] = 0;
+        if (i >= 0) {
+          T P0[4], P1[4], P2[4];
+          load_row<T>(camP, i, 0, P0);
+          load_row<T>(camP, i, 1, P1);
+          load_row<T>(camP, i, 2, P2);
+          scatter_obs<T>(P0, P1, P2, a, (T)m[k].x, (T)m[k].y, S[k], X[k], v);
+        }
+        if (mask == 0u) {
+          T red[3];
+          int vb;
+          warp_reduce12<T>(v, lane, red, vb);
+          if ((lane & 7) == 0) {
+            T* out = part + (size_t)pbase * 12 + vb;
+            out[0] = red[0];
+            out[1] = red[1];
+            out[2] = red[2];
+          }
+        } else {
+          store_runs<T>(v, mask, i >= 0, pbase, lane, part);
+        }
+      }
+    }
+  }
+}
+
 template <typename T>
 PointData<T> point_data(Problem* p, int t) {
   PointData<T> pd;
@@ -864,6 +1148,34 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
     }
     p->launches += 2;
     return check_launch(p, "series_term (camera rows)");
+  }
+  if (schedule == 3) {
+    const unsigned gg = (unsigned)((p->ngroups + BLOCK / SLICE - 1) / (BLOCK / SLICE));
+    if (precision == POVAR_FP64) {
+      if (gg > 0)
+        k_series_grouped<double><<<gg, BLOCK, 0, p->stream>>>(
+            p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0],
+            p->P64[1], p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1),
+            p->grp_slice0, p->grp_row0, p->ngroups, p->grow_cam, p->grow_base, p->srow_mask,
+            p->srow_base, static_cast<double*>(p->part3));
+      k_series_apply<double><<<p->nc, 128, 0, p->stream>>>(
+          p->state, term, eps, p->nc, p->cam_part3_off, p->cam_part3_idx,
+          static_cast<const double*>(p->part3), p->G64, p->camnorm, p->done_ticket,
+          p->Y64 + yoff_out, p->D64);
+    } else {
+      if (gg > 0)
+        k_series_grouped<float><<<gg, BLOCK, 0, p->stream>>>(
+            p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
+            p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1),
+            p->grp_slice0, p->grp_row0, p->ngroups, p->grow_cam, p->grow_base, p->srow_mask,
+            p->srow_base, static_cast<float*>(p->part3));
+      k_series_apply<float><<<p->nc, 128, 0, p->stream>>>(
+          p->state, term, eps, p->nc, p->cam_part3_off, p->cam_part3_idx,
+          static_cast<const float*>(p->part3), p->G32, p->camnorm, p->done_ticket,
+          p->Y32 + yoff_out, p->D32);
+    }
+    p->launches += gg > 0 ? 2 : 1;
+    return check_launch(p, "series_term (grouped)");
   }
   if (schedule == 1) {
     const unsigned ga = (unsigned)p->nc;

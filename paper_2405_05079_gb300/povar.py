@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libpovar.so")
 
 EUCLID, SPHERE = 0, 1
 FP64, MIXED_FP32 = 0, 1
+NSCHEDULES = 4            # POVAR_NSCHEDULES
 
 STATUS = {0: "POVAR_OK", 1: "POVAR_EINVAL", 2: "POVAR_ENOMEM", 3: "POVAR_ECUDA",
           4: "POVAR_ENUMERIC", 5: "POVAR_ETIMEOUT", 6: "POVAR_ENOTCONVERGED"}
@@ -255,7 +256,7 @@ class Problem:
 
     def tuning(self, precision: int):
         sched = C.c_int32()
-        ms = (C.c_float * 3)()
+        ms = (C.c_float * NSCHEDULES)()
         self._check(lib().povar_get_tuning(self._h, precision, C.byref(sched), ms))
         return sched.value, list(ms)
 
