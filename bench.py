@@ -72,10 +72,10 @@ def oracle_iters_to_target(g: dict, target: float) -> int:
     return len(g["series"]["trace"])
 
 
-def solver_params(povar, g: dict, precision: int):
+def solver_params(povar, g: dict, precision: int, schedule: int = -1):
     return povar.make_params(eta=g["eta"], lambda0=g["lambda0"], m=g["m"],
                              series_eps=g["series_eps"], manifold=povar.EUCLID,
-                             precision=precision)
+                             precision=precision, schedule=schedule)
 
 
 # ----------------------------------------------------------------- clocks
@@ -164,8 +164,8 @@ def landmark_flops_per_launch(n_obs: int, n_points: int) -> int:
 
 
 def ncu_traffic(kernel_file: str, key: str):
-    """Per-launch DRAM bytes recorded in profiles/ for a kernel source, or None
-    when the source changed since the capture."""
+    """Per-launch DRAM bytes recorded in profiles/ncu_traffic.txt for a kernel
+    source (one ncu capture), or None when the source changed since."""
     prof = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     src = os.path.join(ROOT, "paper_2405_05079_gb300", "csrc", kernel_file)
     try:
@@ -233,7 +233,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     P0 = scenes.init_cameras(sc.n_cams, g["init_seed"], normalize=True)
     stream = torch.cuda.current_stream(dev)
     prec = povar.FP64 if args.precision == "fp64" else povar.MIXED_FP32
-    params = solver_params(povar, g, prec)
+    params = solver_params(povar, g, prec, args.schedule)
     pb = povar.Problem.from_scene(sc, stream=stream.cuda_stream)
     dP0 = torch.tensor(P0, dtype=torch.float64, device=dev)
     pb.set_profiling(True)
@@ -272,6 +272,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         total_ms = float(t.item())
     phases, nsteps, nproducts = pb.profile(reset=True, products=True)
     sched, tune_ms = pb.tuning(prec)
+    if args.schedule >= 0:
+        sched = args.schedule
     clocks = clk.summary()
     final_cost = pb.cost(g["eta"])
 
@@ -317,7 +319,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     fp64_peak = 1250.0   # GFLOP/s: nominal GB300 FP64 (152 SMs x 2 FMA/clk at max clock)
     roof_series = {"bound": "hbm", "achieved": round(series_gbs, 1), "peak": hbm,
                    "unit": "GB/s", "frac": round(series_gbs / hbm, 4),
-                   "traffic": ncu_traffic("series.cu", "series_term"),
+                   "traffic": ncu_traffic("series.cu", f"series_product_s{sched}"),
                    "kernel": SERIES_KERNELS.get(sched, "series term"),
                    "schedule": sched,
                    "us_per_product": round(ms_series * 1e3 / products, 2),
@@ -548,6 +550,9 @@ def main(argv=None):
     ap.add_argument("--rate", type=float, default=40.0, help="serving: arrivals per second")
     ap.add_argument("--precision", default="mixed", choices=("mixed", "fp64"))
     ap.add_argument("--max-iters", type=int, default=200)
+    ap.add_argument("--schedule", type=int, default=-1,
+                    help="series schedule (-1: autotuned; a profiler distorts the tuning "
+                         "timings, so profiled runs pin the schedule the plain run chose)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
