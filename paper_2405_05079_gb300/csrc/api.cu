@@ -79,6 +79,7 @@ povar_status refresh_landmarks(Problem* p, double eta) {
   if ((s = launch_cost_finish(p, 0)) != POVAR_OK) return s;
   if ((s = launch_init_state(p, 0.0, 0, 0)) != POVAR_OK) return s;  // need_lin = 1
   p->eta_cur = eta;
+  p->lm_df = false;
   return POVAR_OK;
 }
 
@@ -125,6 +126,12 @@ povar_status prepare_step(Problem* p, const povar_params* q) {
     p->fresh = false;
   }
   if (q->eta != p->eta_cur && (s = refresh_landmarks(p, q->eta)) != POVAR_OK) return s;
+  // mixed steps solve their trial landmarks in double-float and leave the
+  // FP64 factor unwritten; an FP64 step after them starts from landmarks
+  // re-solved in FP64 at the current cameras
+  if (q->precision == POVAR_FP64 && p->lm_df && (s = refresh_landmarks(p, q->eta)) != POVAR_OK)
+    return s;
+  if (q->precision == POVAR_MIXED_FP32) p->lm_df = true;
   return POVAR_OK;
 }
 
@@ -159,7 +166,7 @@ povar_status enqueue_step_kernels(Problem* p, const povar_params* q, std::vector
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_update(p, prec, q->manifold)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
-  if ((s = launch_landmarks(p, 1, q->eta)) != POVAR_OK) return s;
+  if ((s = launch_landmarks(p, 1, q->eta, prec)) != POVAR_OK) return s;
   if ((s = launch_cost_finish(p, 1)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_controller(p)) != POVAR_OK) return s;
@@ -310,9 +317,10 @@ int64_t povar_estimate_bytes(int32_t n_cams, int32_t n_points, int64_t n_obs) {
   b += no * (4 + 4 + 16);                  // inputs
   b += no * (4 + 4) + 4 * ((int64_t)n_points + nc + 2);  // orders
   b += npd * (4 + 4) + 4 * (int64_t)n_points + 4 * (npd / 32 + 1);
-  b += nsell * (4 + 8 + 16);               // SELL
+  b += nsell * (4 + 8 + 16 + 16);          // SELL (camera, measurements f32 / f64 / double-float)
   b += no * (4 + 8 + 16);                  // camera-major list
   b += nc * 4 * 4 + chunks * 8;
+  b += nc * 48 * 8;                        // double-float landmark tables
   b += nc * (2 * 12 * 8 + 48 * 8 + 2 * 12 * 4 + 144 * 8 + 12 * 8 + 144 * 8 + 144 * 4 +
              2 * 12 * 4 + 12 * 4 + 2 * 12 * 8 + 12 * 8 + 2 * 8);
   b += 2 * npd * (3 * 8 + 6 * 8 + 16 + 16 + 4) + npd * (32 + 64) + 3 * (npd / 32) * 8;
@@ -401,6 +409,7 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
   ALLOC(p->P64[0], nc * 12);
   ALLOC(p->P64[1], nc * 12);
   ALLOC(p->Ltab, nc * 48);
+  ALLOC(p->Ltab_df, nc * 48);
   ALLOC(p->camP32[0], nc * 12);
   ALLOC(p->camP32[1], nc * 12);
   ALLOC(p->U64, nc * 144);

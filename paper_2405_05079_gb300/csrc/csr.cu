@@ -174,6 +174,16 @@ __global__ void k_slot_keys(const uint32_t* __restrict__ len,
 }
 
 // Slice width = longest track among its 32 slots (times 32 entries per row).
+// SELL measurements split into double-float pairs (u_hi, u_lo, v_hi, v_lo)
+// for the double-float landmark kernel (padding entries are zero).
+__global__ void k_split_meas(const double2* __restrict__ m, int64_t n, float4* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 x = m[i];
+  const float uh = (float)x.x, vh = (float)x.y;
+  out[i] = make_float4(uh, (float)(x.x - (double)uh), vh, (float)(x.y - (double)vh));
+}
+
 __global__ void k_slice_width(const uint32_t* __restrict__ slot_len, int nslices,
                               uint32_t* __restrict__ w32) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -463,7 +473,8 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
   p->nsell = nsell;
   if ((s = dev_alloc(p, &p->sell_cam, std::max<int64_t>(nsell, 1), "sell_cam")) ||
       (s = dev_alloc(p, &p->sell_m32, std::max<int64_t>(nsell, 1), "sell_m32")) ||
-      (s = dev_alloc(p, &p->sell_m64, std::max<int64_t>(nsell, 1), "sell_m64")))
+      (s = dev_alloc(p, &p->sell_m64, std::max<int64_t>(nsell, 1), "sell_m64")) ||
+      (s = dev_alloc(p, &p->sell_mdf, std::max<int64_t>(nsell, 1), "sell_mdf")))
     return s;
   POVAR_CUDA(cudaMemsetAsync(p->sell_cam, 0xff, nsell * sizeof(int32_t), p->stream));
   POVAR_CUDA(cudaMemsetAsync(p->sell_m32, 0, nsell * sizeof(float2), p->stream));
@@ -473,7 +484,9 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
                                          p->sell_m32, p->sell_m64);
   k_fill_cm<<<gb, 256, 0, p->stream>>>(p->perm_cam, p->d_pt, p->pt_slot, p->d_meas, n,
                                        p->cm_slot, p->cm_m32, p->cm_m64);
-  p->launches += 2;
+  k_split_meas<<<grid_for((int64_t)nsell, 256), 256, 0, p->stream>>>(p->sell_m64, nsell,
+                                                                    p->sell_mdf);
+  p->launches += 3;
   if ((s = check_launch(p, "fill layouts")) != POVAR_OK) return s;
 
   // ---- camera-major chunks (host: n_cams entries)

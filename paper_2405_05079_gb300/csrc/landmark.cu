@@ -24,6 +24,7 @@
 // and a single block adds the partials in a fixed order (deterministic).
 #include <mutex>
 
+#include "df64.cuh"
 #include "povar_internal.cuh"
 
 namespace povar {
@@ -42,8 +43,8 @@ struct SlotBufs {
 //  [24,27) h0, [27,30) hu, [30,33) hv, [33,36) hw, [36,48) unused
 __global__ void k_ltab(const DeviceState* __restrict__ st, int which_rel, double eta,
                        const double* __restrict__ P0, const double* __restrict__ P1, int nc,
-                       double* __restrict__ Ltab, float* __restrict__ C0,
-                       float* __restrict__ C1) {
+                       double* __restrict__ Ltab, float2* __restrict__ Ldf,
+                       float* __restrict__ C0, float* __restrict__ C1) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc) return;
   if (which_rel == 1 && st->converged) return;
@@ -73,6 +74,16 @@ __global__ void k_ltab(const DeviceState* __restrict__ st, int which_rel, double
     T[27 + c] = (-a * q2 - eta) * p0[c] - a * q0 * p2[c];
     T[30 + c] = (-a * q2 - eta) * p1[c] - a * q1 * p2[c];
     T[33 + c] = a * q2 * p2[c];
+  }
+  // double-float copy: the 36 table entries, then P itself (12)
+  float2* D = Ldf + 48 * (size_t)i;
+  for (int e = 0; e < 36; ++e) {
+    const float hi = (float)T[e];
+    D[e] = make_float2(hi, (float)(T[e] - (double)hi));
+  }
+  for (int e = 0; e < 12; ++e) {
+    const float hi = (float)P[e];
+    D[36 + e] = make_float2(hi, (float)(P[e] - (double)hi));
   }
 }
 
@@ -315,6 +326,175 @@ k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
   }
 }
 
+// The same elimination and direct cost as k_landmark with the arithmetic of
+// both per-observation passes and of the per-landmark Cholesky solve in
+// double-float (about 48 bits; df64.cuh), for the mixed-precision solve:
+// the FP64 pipe, which bounds k_landmark, is left almost idle. A landmark
+// whose Cholesky pivots flag a near rank-deficient V_j takes the FP64
+// pseudo-inverse path of k_landmark. Writes X (FP64), the FP32 copies used
+// by the FP32 kernels and the cost partials; the FP64 factor F64 is not
+// written (an FP64 step re-solves the landmarks with k_landmark first).
+__global__ void __launch_bounds__(BLOCK)
+k_landmark_df(const DeviceState* __restrict__ st, int which_rel, double eta,
+              const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
+              const int32_t* __restrict__ sell_cam, const float4* __restrict__ sell_mdf,
+              const float2* __restrict__ Ldf, int np, SlotBufs bufs,
+              double* __restrict__ cost_part, int* __restrict__ pinv_part) {
+  if (which_rel == 1 && st->converged) return;
+  const int t = which_rel ? 1 - st->cur : st->cur;
+  const int s = blockIdx.x * BLOCK + threadIdx.x;
+  double cost = 0.0;
+  int npinv = 0;
+  if (s < np) {
+    const uint32_t len = slot_len[s];
+    const uint32_t base = sell_off[s / SLICE] + (uint32_t)(s % SLICE);
+    df64 V[6], h[3];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) V[e] = {0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h[c] = {0.f, 0.f};
+    for (uint32_t k = 0; k < len; ++k) {
+      const uint32_t pos = base + k * SLICE;
+      const int i = sell_cam[pos];
+      const float4 m = sell_mdf[pos];
+      const df64 u = {m.x, m.y}, v = {m.z, m.w};
+      df64 w = df_mul(v, v);
+      df_acc_mul(w, u, u);
+      w = df_norm(w);
+      const float4* T4 = reinterpret_cast<const float4*>(Ldf + 48 * (size_t)i);
+      df64 tb[36];
+#pragma unroll
+      for (int q = 0; q < 18; ++q) {
+        const float4 x = __ldg(T4 + q);
+        tb[2 * q] = {x.x, x.y};
+        tb[2 * q + 1] = {x.z, x.w};
+      }
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        df_acc(V[e], tb[e]);
+        df_acc_mul(V[e], u, tb[6 + e]);
+        df_acc_mul(V[e], v, tb[12 + e]);
+        df_acc_mul(V[e], w, tb[18 + e]);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        df_acc(h[c], tb[24 + c]);
+        df_acc_mul(h[c], u, tb[27 + c]);
+        df_acc_mul(h[c], v, tb[30 + c]);
+        df_acc_mul(h[c], w, tb[33 + c]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 6; ++e) V[e] = df_norm(V[e]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h[c] = df_norm(h[c]);
+    // Cholesky V = L L^T through reciprocal square roots; F = L^-1
+    const df64 f00 = df_rsqrt(V[0]);
+    const df64 l10 = df_mul(V[1], f00), l20 = df_mul(V[2], f00);
+    const df64 d1 = df_sub(V[3], df_mul(l10, l10));
+    const df64 f11 = df_rsqrt(d1);
+    const df64 l21 = df_mul(df_sub(V[4], df_mul(l20, l10)), f11);
+    const df64 d2 = df_sub(df_sub(V[5], df_mul(l20, l20)), df_mul(l21, l21));
+    const df64 f22 = df_rsqrt(d2);
+    const float dmax = fmaxf(V[0].hi, fmaxf(V[3].hi, V[5].hi));
+    const bool suspect = !(V[0].hi > 1e-9f * dmax) || !(d1.hi > 1e-9f * dmax) ||
+                         !(d2.hi > 1e-9f * dmax) || !(dmax > 0.f);
+    df64 X[3];
+    float F[6];
+    double X64v[3], F64v[6];
+    bool deficient = false;
+    if (suspect) {
+      Sym3 vs;
+      Vec3 hs;
+      for (int e = 0; e < 6; ++e) vs.v[e] = df_to_double(V[e]);
+      for (int c = 0; c < 3; ++c) hs.x[c] = df_to_double(h[c]);
+      const PinvOut o = pinv_solve(vs, hs);
+      deficient = o.deficient;
+      for (int c = 0; c < 3; ++c) X64v[c] = o.X[c];
+      for (int e = 0; e < 6; ++e) F64v[e] = o.F[e];
+    }
+    if (!deficient) {
+      const df64 f10 = df_neg(df_mul(df_mul(l10, f00), f11));
+      const df64 f20 = df_neg(df_mul(df_add(df_mul(l20, f00), df_mul(l21, f10)), f22));
+      const df64 f21 = df_neg(df_mul(df_mul(l21, f11), f22));
+      // z = F h, X = -F^T z
+      const df64 z0 = df_mul(f00, h[0]);
+      const df64 z1 = df_add(df_mul(f10, h[0]), df_mul(f11, h[1]));
+      const df64 z2 = df_add(df_add(df_mul(f20, h[0]), df_mul(f21, h[1])), df_mul(f22, h[2]));
+      X[0] = df_neg(df_add(df_add(df_mul(f00, z0), df_mul(f10, z1)), df_mul(f20, z2)));
+      X[1] = df_neg(df_add(df_mul(f11, z1), df_mul(f21, z2)));
+      X[2] = df_neg(df_mul(f22, z2));
+      F[0] = f00.hi; F[1] = f10.hi; F[2] = f11.hi; F[3] = f20.hi; F[4] = f21.hi; F[5] = f22.hi;
+      for (int c = 0; c < 3; ++c) X64v[c] = df_to_double(X[c]);
+    } else {
+      for (int c = 0; c < 3; ++c) X[c] = df_from_double(X64v[c]);
+      for (int e = 0; e < 6; ++e) F[e] = (float)F64v[e];
+    }
+    npinv = deficient ? 1 : 0;
+    double* Xo = bufs.X[t] + 3 * (size_t)s;
+    Xo[0] = X64v[0]; Xo[1] = X64v[1]; Xo[2] = X64v[2];
+    bufs.A[t][s] = make_float4(X[0].hi, X[1].hi, X[2].hi, F[0]);
+    bufs.B[t][s] = make_float4(F[1], F[2], F[3], F[4]);
+    bufs.C[t][s] = F[5];
+    // ||r_k||^2 = (1 - eta) ((y0 - u y2)^2 + (y1 - v y2)^2) + eta ((y0 - u)^2 + (y1 - v)^2)
+    // with y = P_i (X, 1), summed in double-float
+    df64 e1 = {0.f, 0.f}, e2 = {0.f, 0.f};
+    for (uint32_t k = 0; k < len; ++k) {
+      const uint32_t pos = base + k * SLICE;
+      const int i = sell_cam[pos];
+      const float4 m = sell_mdf[pos];
+      const df64 nu = {-m.x, -m.y}, nv = {-m.z, -m.w};
+      const float4* Q4 = reinterpret_cast<const float4*>(Ldf + 48 * (size_t)i + 36);
+      df64 q[12];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        const float4 x = __ldg(Q4 + r);
+        q[2 * r] = {x.x, x.y};
+        q[2 * r + 1] = {x.z, x.w};
+      }
+      df64 y[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        df64 acc = q[4 * r + 3];
+        df_acc_mul(acc, q[4 * r], X[0]);
+        df_acc_mul(acc, q[4 * r + 1], X[1]);
+        df_acc_mul(acc, q[4 * r + 2], X[2]);
+        y[r] = df_norm(acc);
+      }
+      df64 a0 = y[0], a1 = y[1];
+      df_acc_mul(a0, nu, y[2]);
+      df_acc_mul(a1, nv, y[2]);
+      a0 = df_norm(a0);
+      a1 = df_norm(a1);
+      df64 b0 = y[0], b1 = y[1];
+      df_acc(b0, nu);
+      df_acc(b1, nv);
+      b0 = df_norm(b0);
+      b1 = df_norm(b1);
+      df_acc_mul(e1, a0, a0);
+      df_acc_mul(e1, a1, a1);
+      df_acc_mul(e2, b0, b0);
+      df_acc_mul(e2, b1, b1);
+    }
+    cost = (1.0 - eta) * df_to_double(df_norm(e1)) + eta * df_to_double(df_norm(e2));
+  } else {
+    double* Xo = bufs.X[t] + 3 * (size_t)s;
+    Xo[0] = Xo[1] = Xo[2] = 0.0;
+    bufs.A[t][s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    bufs.B[t][s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    bufs.C[t][s] = 0.f;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cost += __shfl_xor_sync(0xffffffffu, cost, o);
+    npinv += __shfl_xor_sync(0xffffffffu, npinv, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    cost_part[s / 32] = cost;
+    pinv_part[s / 32] = npinv;
+  }
+}
+
 __global__ void k_cost_finish(DeviceState* __restrict__ st, int which_rel,
                               const double* __restrict__ part, const int* __restrict__ pinv,
                               int n) {
@@ -350,10 +530,10 @@ __global__ void k_cost_finish(DeviceState* __restrict__ st, int which_rel,
 
 }  // namespace
 
-povar_status launch_landmarks(Problem* p, int which_rel, double eta) {
+povar_status launch_landmarks(Problem* p, int which_rel, double eta, int precision) {
   k_ltab<<<grid_for(p->nc, 128), 128, 0, p->stream>>>(p->state, which_rel, eta, p->P64[0],
-                                                      p->P64[1], p->nc, p->Ltab, p->camP32[0],
-                                                      p->camP32[1]);
+                                                      p->P64[1], p->nc, p->Ltab, p->Ltab_df,
+                                                      p->camP32[0], p->camP32[1]);
   SlotBufs b;
   for (int t = 0; t < 2; ++t) {
     b.X[t] = p->X64[t];
@@ -362,9 +542,16 @@ povar_status launch_landmarks(Problem* p, int which_rel, double eta) {
     b.B[t] = p->pdB[t];
     b.C[t] = p->pdC[t];
   }
-  k_landmark<<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
-      p->state, which_rel, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->Ltab,
-      p->P64[0], p->P64[1], p->np, b, p->cost_part, p->pinv_part);
+  // trial landmarks of a mixed-precision step in double-float; every other
+  // evaluation (and every FP64 step) in FP64
+  if (which_rel == 1 && precision == POVAR_MIXED_FP32)
+    k_landmark_df<<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+        p->state, which_rel, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_mdf,
+        p->Ltab_df, p->np, b, p->cost_part, p->pinv_part);
+  else
+    k_landmark<<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+        p->state, which_rel, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->Ltab,
+        p->P64[0], p->P64[1], p->np, b, p->cost_part, p->pinv_part);
   p->launches += 2;
   return check_launch(p, "landmark");
 }

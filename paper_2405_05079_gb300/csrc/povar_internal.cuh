@@ -94,6 +94,7 @@ struct Problem {
   int32_t* sell_cam = nullptr;    // [nsell] (-1: padding)
   float2* sell_m32 = nullptr;
   double2* sell_m64 = nullptr;
+  float4* sell_mdf = nullptr;     // [nsell] (u_hi, u_lo, v_hi, v_lo) double-float pairs
   // camera-major list
   uint32_t* cm_slot = nullptr;    // [nobs]
   float2* cm_m32 = nullptr;
@@ -140,6 +141,8 @@ struct Problem {
   // cameras
   double* P64[2] = {nullptr, nullptr};  // [nc*12]
   double* Ltab = nullptr;               // [nc*48] landmark tables at trial P
+  float2* Ltab_df = nullptr;            // [nc*48] the same tables (36) and P (12) as double-floats
+  bool lm_df = false;                   // current landmark buffers come from the double-float kernel
   float* camP32[2] = {nullptr, nullptr};  // [nc*12] FP32 copies of P64[0], P64[1]
   double* U64 = nullptr;                // [nc*144]
   double* bp64 = nullptr;               // [nc*12]
@@ -225,7 +228,7 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
 // ---------------------------------------------------- landmark.cu (a2,a3)
 // Landmark tables of the cameras in buffer `which_rel` (0: current, 1: trial)
 // and the closed-form landmarks + cost at those cameras.
-povar_status launch_landmarks(Problem* p, int which_rel, double eta);
+povar_status launch_landmarks(Problem* p, int which_rel, double eta, int precision = POVAR_FP64);
 // Reduce the cost partials into state.F (which_rel 0) or state.F_new (1).
 povar_status launch_cost_finish(Problem* p, int which_rel);
 

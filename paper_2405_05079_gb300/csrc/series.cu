@@ -41,6 +41,39 @@ __device__ __forceinline__ void load_row<double>(const double* __restrict__ tab,
   out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
 }
 
+// Warps per camera block of the camera-row schedule.
+constexpr int CAMROW_WARPS = 4;
+
+// Loads of data that each kernel streams through once (SELL camera indices
+// and measurements, per-landmark records): read-only, not allocated in L1, so
+// that L1 keeps the camera rows that every slice row re-reads.
+__device__ __forceinline__ int ld_stream(const int32_t* p) {
+  int v;
+  asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 ld_stream(const float2* p) {
+  float2 v;
+  asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double2 ld_stream(const double2* p) {
+  double2 v;
+  asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
 template <typename T>
 struct PointData {
   // FP32 path
@@ -57,9 +90,9 @@ __device__ __forceinline__ void load_point(const PointData<T>& pd, int s, T X[3]
 template <>
 __device__ __forceinline__ void load_point<float>(const PointData<float>& pd, int s,
                                                   float X[3], float F[6]) {
-  const float4 a = __ldg(pd.A + s), b = __ldg(pd.B + s);
+  const float4 a = ld_stream(pd.A + s), b = ld_stream(pd.B + s);
   X[0] = a.x; X[1] = a.y; X[2] = a.z;
-  F[0] = a.w; F[1] = b.x; F[2] = b.y; F[3] = b.z; F[4] = b.w; F[5] = __ldg(pd.C + s);
+  F[0] = a.w; F[1] = b.x; F[2] = b.y; F[3] = b.z; F[4] = b.w; F[5] = ld_stream(pd.C + s);
 }
 template <>
 __device__ __forceinline__ void load_point<double>(const PointData<double>& pd, int s,
@@ -126,8 +159,8 @@ k_series_gather(const DeviceState* __restrict__ st, T a,
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
       const bool in = k0 + u < len;
-      ci[u] = in ? sell_cam[base + (k0 + u) * SLICE] : 0;
-      mi[u] = in ? sell_m[base + (k0 + u) * SLICE] : M2{0, 0};
+      ci[u] = in ? ld_stream(sell_cam + base + (k0 + u) * SLICE) : 0;
+      mi[u] = in ? ld_stream(sell_m + base + (k0 + u) * SLICE) : M2{0, 0};
     }
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
@@ -415,8 +448,8 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
       const bool in = k0 + u < len;
-      ci[u] = in ? sell_cam[base + (k0 + u) * SLICE] : 0;
-      mi[u] = in ? sell_m[base + (k0 + u) * SLICE] : M2{0, 0};
+      ci[u] = in ? ld_stream(sell_cam + base + (k0 + u) * SLICE) : 0;
+      mi[u] = in ? ld_stream(sell_m + base + (k0 + u) * SLICE) : M2{0, 0};
     }
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
@@ -461,8 +494,8 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
     for (int u = 0; u < RB; ++u) {
       const bool rin = k0 + u < width;
       const bool in = k0 + u < len;
-      ci[u] = in ? sell_cam[base + (k0 + u) * SLICE] : -1;
-      mi[u] = in ? sell_m[base + (k0 + u) * SLICE] : M2{0, 0};
+      ci[u] = in ? ld_stream(sell_cam + base + (k0 + u) * SLICE) : -1;
+      mi[u] = in ? ld_stream(sell_m + base + (k0 + u) * SLICE) : M2{0, 0};
       mk[u] = rin ? __ldg(row_mask + row0 + k0 + u) : 0u;
       bk[u] = rin ? __ldg(row_base + row0 + k0 + u) : 0u;
     }
@@ -636,14 +669,14 @@ k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
 // ---------------------------------------------------------------------------
 // Camera-row schedule (2): after the landmark-major gather has written every
 // landmark's record (s_j, X_j), one block per camera walks the slice rows
-// that contain the camera (rows in index order, strided over the 4 warps).
+// that contain the camera (rows in index order, strided over the NW warps).
 // Each lane adds the contribution vec((C_k Pbar_i s_j) x~_j^T) of its own
 // landmark when that landmark's observation in the row is of this camera, so
 // contributions accumulate in registers across rows; the block reduces once
 // per camera, in a fixed order, and applies the camera update.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(128)
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32)
 k_series_camrows(DeviceState* __restrict__ st, T a, int term, double eps, int nc,
                  const uint32_t* __restrict__ cam_row_off,
                  const uint32_t* __restrict__ cam_row_pos0,
@@ -654,7 +687,7 @@ k_series_camrows(DeviceState* __restrict__ st, T a, int term, double eps, int nc
                  double* __restrict__ camnorm, uint32_t* __restrict__ done_ticket,
                  T* __restrict__ Y, T* __restrict__ D) {
   if (st->converged || st->stop_series) return;
-  __shared__ T sh[4][12];
+  __shared__ T sh[NW][12];
   __shared__ int sh_last;
   using M2 = typename Vt<T>::m2;
   constexpr int RB = 4;
@@ -669,19 +702,19 @@ k_series_camrows(DeviceState* __restrict__ st, T a, int term, double eps, int nc
 #pragma unroll
   for (int e = 0; e < 12; ++e) acc[e] = 0;
   const uint32_t b = cam_row_off[i], e_ = cam_row_off[i + 1];
-  for (uint32_t q0 = b + wl; q0 < e_; q0 += 4 * RB) {
+  for (uint32_t q0 = b + wl; q0 < e_; q0 += NW * RB) {
     uint32_t pos[RB], slot[RB];
     int cv[RB];
     M2 mv[RB];
     T S[RB][3], X[RB][3];
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
-      const uint32_t q = q0 + 4 * u;
+      const uint32_t q = q0 + NW * u;
       const bool in = q < e_;
       pos[u] = in ? __ldg(cam_row_pos0 + q) + lane : 0u;
       slot[u] = in ? __ldg(cam_row_slot0 + q) + lane : 0u;
-      cv[u] = in ? sell_cam[pos[u]] : -1;
-      mv[u] = in ? sell_m[pos[u]] : M2{0, 0};
+      cv[u] = in ? ld_stream(sell_cam + pos[u]) : -1;
+      mv[u] = in ? ld_stream(sell_m + pos[u]) : M2{0, 0};
       if (in) load_rec(rec32, rec64, slot[u], S[u], X[u]);
     }
 #pragma unroll
@@ -711,7 +744,10 @@ k_series_camrows(DeviceState* __restrict__ st, T a, int term, double eps, int nc
   __syncthreads();
   if (wl != 0) return;
   T z = 0;
-  if (lane < 12) z = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
+  if (lane < 12) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) z += sh[w][lane];
+  }
   double yy, dd;
   camera_update<T>(i, lane, z, G, Y, D, yy, dd);
   if (eps <= 0.0) return;
@@ -1132,7 +1168,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
           p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1],
           p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1), p->rec32,
           p->rec64, nullptr);
-      k_series_camrows<double><<<p->nc, 128, 0, p->stream>>>(
+      k_series_camrows<double, CAMROW_WARPS><<<p->nc, CAMROW_WARPS * 32, 0, p->stream>>>(
           p->state, a64, term, eps, p->nc, p->cam_row_off, p->cam_row_pos0, p->cam_row_slot0,
           p->sell_cam, p->sell_m64, p->P64[0], p->P64[1], p->rec32, p->rec64, p->G64,
           p->camnorm, p->done_ticket, p->Y64 + yoff_out, p->D64);
@@ -1141,7 +1177,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
           p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
           p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1),
           p->rec32, p->rec64, nullptr);
-      k_series_camrows<float><<<p->nc, 128, 0, p->stream>>>(
+      k_series_camrows<float, CAMROW_WARPS><<<p->nc, CAMROW_WARPS * 32, 0, p->stream>>>(
           p->state, a32, term, eps, p->nc, p->cam_row_off, p->cam_row_pos0, p->cam_row_slot0,
           p->sell_cam, p->sell_m32, p->camP32[0], p->camP32[1], p->rec32, p->rec64, p->G32,
           p->camnorm, p->done_ticket, p->Y32 + yoff_out, p->D32);

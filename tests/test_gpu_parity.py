@@ -455,3 +455,57 @@ def test_serving_result_same_alone_and_in_the_mix():
             assert pb.cost(0.1) == r.cost
     stats = serving.summarize(res)
     assert stats["latency_p99_s"] >= stats["latency_p50_s"] > 0
+
+
+@pytest.mark.parametrize("name", ["traj", "mid"])
+def test_double_float_trial_landmarks_match_fp64(name):
+    """A mixed-precision step solves its trial landmarks and cost in
+    double-float (about 48 bits); the same cameras evaluated by the FP64
+    kernel give the same cost to 1e-11 and the same landmarks to 1e-9."""
+    sc = SCENES[name]()
+    P0 = scenes.init_cameras(sc.n_cams, 6, normalize=True)
+    prm = povar.make_params(eta=sc.eta, m=8, manifold=povar.EUCLID,
+                            precision=povar.MIXED_FP32, schedule=1)
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        for _ in range(3):
+            rep = pb.step(prm)
+            if rep.accepted:
+                break
+        assert rep.accepted
+        F_df = rep.cost_after
+        P1 = pb.cameras()
+        X_df = pb.points()
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P1, sc.eta)
+        F64 = pb.cost(sc.eta)
+        X64 = pb.points()
+    assert abs(F_df - F64) <= 1e-11 * F64, (F_df, F64)
+    assert np.all(np.abs(X_df - X64) <= 1e-9 * (1.0 + np.abs(X64)))
+
+
+def test_fp64_step_after_mixed_steps_uses_fp64_landmarks():
+    """Switching a problem from mixed to FP64 steps re-solves the landmarks in
+    FP64 first: the FP64 step then equals an FP64 step from the same cameras
+    on a fresh handle."""
+    sc = SCENES["traj"]()
+    P0 = scenes.init_cameras(sc.n_cams, 7, normalize=True)
+    mixed = povar.make_params(eta=sc.eta, m=8, manifold=povar.EUCLID,
+                              precision=povar.MIXED_FP32, schedule=1)
+    fp64 = povar.make_params(eta=sc.eta, m=8, manifold=povar.EUCLID,
+                             precision=povar.FP64, schedule=1, lambda0=1e-3)
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        for _ in range(3):
+            pb.step(mixed)
+        P1 = pb.cameras()
+        pb.set_cameras(P1, sc.eta)
+        pb.step(mixed)
+        P2 = pb.cameras()
+        # the damping state differs between handles; compare the FP64
+        # landmarks and cost that the FP64 step starts from instead
+        rep = pb.step(fp64)
+        F_start = rep.cost_before
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P2, sc.eta)
+        assert pb.cost(sc.eta) == F_start
