@@ -76,9 +76,10 @@ enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1 };
  *             across the lanes of a warp that share a camera; 2 =
  *             landmark-major gather pass + camera-major pass over the
  *             landmark slice rows that contain each camera; 3 = the fused
- *             pass of 1 with one warp per group of up to four slices whose
- *             landmarks share their first camera, one reduction per group
- *             row when all of its lanes see one camera; -1 = autotuned (see
+ *             pass of 1 where the camera of every slice row whose lanes all
+ *             see one camera comes from a per-row table, and the rows of
+ *             those cameras are staged in shared memory before the row loop
+ *             (no dependent global load per row); -1 = autotuned (see
  *             povar_get_tuning). All schedules compute the same series. */
 enum { POVAR_NSCHEDULES = 4 };
 typedef struct {

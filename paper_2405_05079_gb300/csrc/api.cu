@@ -433,6 +433,9 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
   ALLOC(p->cost_part, npd / 32);
   ALLOC(p->pred_part, npd / 32);
   ALLOC(p->pinv_part, npd / 32);
+  ALLOC(p->fin_blk, 2 * povar::FIN_BLOCKS);
+  ALLOC(p->fin_blk_i, povar::FIN_BLOCKS);
+  ALLOC(p->fin_ticket, 2);
   ALLOC(p->state, 1);
   ALLOC(p->d_report, 1);
 #define CK(call)                                                             \
@@ -457,6 +460,7 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
                      p->stream));
   CK(cudaMemsetAsync(p->cam_ticket, 0, nc * sizeof(uint32_t), p->stream));
   CK(cudaMemsetAsync(p->done_ticket, 0, sizeof(uint32_t), p->stream));
+  CK(cudaMemsetAsync(p->fin_ticket, 0, 2 * sizeof(uint32_t), p->stream));
   CK(cudaMemsetAsync(p->P64[0], 0, nc * 12 * sizeof(double), p->stream));
   CK(cudaMemsetAsync(p->P64[1], 0, nc * 12 * sizeof(double), p->stream));
   CK(cudaMemsetAsync(p->camnorm, 0, nc * 2 * sizeof(double), p->stream));

@@ -495,15 +495,23 @@ k_landmark_df(const DeviceState* __restrict__ st, int which_rel, double eta,
   }
 }
 
-__global__ void k_cost_finish(DeviceState* __restrict__ st, int which_rel,
-                              const double* __restrict__ part, const int* __restrict__ pinv,
-                              int n) {
+// F = sum of the per-warp cost partials (and the pseudo-inverse count):
+// each of the FIN_BLOCKS blocks adds a fixed contiguous range of partials,
+// the last block to finish (atomic ticket) adds the block sums in block
+// order, so the result does not depend on the order the blocks ran in.
+__global__ void __launch_bounds__(256)
+k_cost_finish(DeviceState* __restrict__ st, int which_rel, const double* __restrict__ part,
+              const int* __restrict__ pinv, int n, double* __restrict__ blk,
+              int* __restrict__ blk_i, uint32_t* __restrict__ ticket) {
   if (which_rel == 1 && st->converged) return;
   __shared__ double red[256];
   __shared__ int redi[256];
+  __shared__ int last;
+  const int per = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int b0 = (int)blockIdx.x * per, b1 = min(n, b0 + per);
   double c = 0.0;
   int q = 0;
-  for (int i = threadIdx.x; i < n; i += 256) {
+  for (int i = b0 + (int)threadIdx.x; i < b1; i += 256) {
     c += part[i];
     q += pinv[i];
   }
@@ -518,6 +526,32 @@ __global__ void k_cost_finish(DeviceState* __restrict__ st, int which_rel,
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    blk[blockIdx.x] = red[0];
+    blk_i[blockIdx.x] = redi[0];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  c = 0.0;
+  q = 0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += 256) {
+    c += __ldcg(blk + i);
+    q += __ldcg(blk_i + i);
+  }
+  red[threadIdx.x] = c;
+  redi[threadIdx.x] = q;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[threadIdx.x] += red[threadIdx.x + o];
+      redi[threadIdx.x] += redi[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
     if (which_rel == 0) {
       st->F = red[0];
       if (!isfinite(red[0])) st->error = POVAR_ENUMERIC;
@@ -557,8 +591,9 @@ povar_status launch_landmarks(Problem* p, int which_rel, double eta, int precisi
 }
 
 povar_status launch_cost_finish(Problem* p, int which_rel) {
-  k_cost_finish<<<1, 256, 0, p->stream>>>(p->state, which_rel, p->cost_part, p->pinv_part,
-                                          p->np_pad / 32);
+  k_cost_finish<<<FIN_BLOCKS, 256, 0, p->stream>>>(p->state, which_rel, p->cost_part,
+                                                   p->pinv_part, p->np_pad / 32, p->fin_blk,
+                                                   p->fin_blk_i, p->fin_ticket);
   ++p->launches;
   return check_launch(p, "cost_finish");
 }

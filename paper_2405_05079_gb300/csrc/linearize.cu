@@ -130,6 +130,7 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
   __shared__ double smA[4][12][13];
   __shared__ double smL[4][12][13];
   __shared__ double smAcc[4][LIN_ACC];
+  __shared__ double smInv[4][12];  // reciprocals of the Cholesky diagonal
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int i = blockIdx.x * 4 + wl;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -145,6 +146,7 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
   const double* Pc = (cur ? P1 : P0) + 12 * (size_t)i;
   double (*A)[13] = smA[wl];
   double (*L)[13] = smL[wl];
+  double* inv = smInv[wl];
   const double Pl = lane < 12 ? Pc[lane] : 0.0;
   double bpl = 0.0;
   if (need_lin) {
@@ -223,16 +225,21 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
       A[lane][lane] += lam_eff;
     }
     __syncwarp();
-    // Cholesky A = L L^T (lower, in place), lanes own rows
+    // Cholesky A = L L^T (lower, in place), lanes own rows; one reciprocal
+    // square root per pivot gives the diagonal (d r) and its inverse (r), so
+    // the column scaling and the later solve multiply instead of divide
     bool lbad = false;
     for (int k = 0; k < 12; ++k) {
       if (lane == k) {
         const double d = A[k][k];
         if (!(d > 0.0)) lbad = true;
-        A[k][k] = sqrt(fmax(d, 1e-300));
+        const double dd = fmax(d, 1e-300);
+        const double r = rsqrt(dd);
+        A[k][k] = dd * r;
+        inv[k] = r;
       }
       __syncwarp();
-      if (lane > k && lane < 12) A[lane][k] /= A[k][k];
+      if (lane > k && lane < 12) A[lane][k] *= inv[k];
       __syncwarp();
       if (lane > k && lane < 12)
         for (int j = k + 1; j <= lane; ++j) A[lane][j] -= A[lane][k] * A[j][k];
@@ -254,7 +261,7 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
       }
       double s = (r == c) ? 1.0 : 0.0;
       for (int k = c; k < r; ++k) s -= A[r][k] * L[k][c];
-      L[r][c] = s / A[r][r];
+      L[r][c] = s * inv[r];
     }
   }
   __syncwarp();

@@ -33,7 +33,15 @@ constexpr int SLICE = 32;        // landmarks per SELL slice (one warp)
 constexpr int CHUNK = 256;       // observations per camera-major chunk
 constexpr int LIN_ACC = 52;      // linearization accumulators per chunk
 constexpr int BLOCK = 256;       // threads per block for slot kernels
-constexpr int GROUP = 4;         // slices per warp in the grouped series schedule
+// Slices per warp in the grouped series schedule. One slice per warp measured
+// fastest on the 5M-observation scene (71 us per series product against 78
+// for two and 104 for four): larger groups save warp reductions but their
+// registers halve the occupancy of a latency-bound loop, and grouping by
+// group width unbalances the blocks of the slot kernels.
+constexpr int GROUP = 1;
+// Blocks of the final cost and predicted-decrease sums (each block adds a
+// fixed range, the last block to finish adds the block sums in order).
+constexpr int FIN_BLOCKS = 64;
 constexpr double PINV_COND = 1e12;
 constexpr double LAMBDA_MIN = 1e-8;   // damping floor
 constexpr double LAMBDA_MAX = 1e30;   // damping ceiling (solve reported as diverged)
@@ -164,6 +172,9 @@ struct Problem {
   float4* rec32 = nullptr;              // [np_pad*2] (s0 s1 s2 X0)(X1 X2 - -)
   double2* rec64 = nullptr;             // [np_pad*4] (s0 s1)(s2 X0)(X1 X2)(- -)
   double* cost_part = nullptr;          // [np_pad / 32] one per warp
+  double* fin_blk = nullptr;            // [2 * FIN_BLOCKS] block sums of the final reductions
+  int* fin_blk_i = nullptr;             // [FIN_BLOCKS]
+  uint32_t* fin_ticket = nullptr;       // [2] last-block tickets (cost, predicted decrease)
   double* pred_part = nullptr;          // [np_pad / 32] one per warp
   int* pinv_part = nullptr;             // [np_pad / 32] one per warp
   int32_t n_slot_blocks = 0;

@@ -838,14 +838,20 @@ k_pred_cam(const DeviceState* __restrict__ st, int nc, const double* __restrict_
 }
 
 // pred = -2 b_p^T d - d^T U d + sum_j ||F_j W^T d||^2, fixed-order sums.
-__global__ void k_pred_finish(DeviceState* __restrict__ st, int nc, int nparts, int m,
-                              const double* __restrict__ pred_part,
-                              const double* __restrict__ camsum) {
+// pred = sum of the per-warp partials ||F_j W^T d||^2 minus the camera terms
+// d^T U d + 2 b_p^T d, over FIN_BLOCKS blocks with a fixed-order last-block
+// finish (as k_cost_finish).
+__global__ void __launch_bounds__(256)
+k_pred_finish(DeviceState* __restrict__ st, int nc, int nparts, int m,
+              const double* __restrict__ pred_part, const double* __restrict__ camsum,
+              double* __restrict__ blk, uint32_t* __restrict__ ticket) {
   if (st->converged) return;
   __shared__ double red[256];
+  __shared__ int last;
+  const int per = (nparts + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int b0 = (int)blockIdx.x * per, b1 = min(nparts, b0 + per);
   double v = 0.0;
-  for (int q = threadIdx.x; q < nparts; q += 256) v += pred_part[q];
-  for (int i = threadIdx.x; i < nc; i += 256) v -= camsum[2 * (size_t)i] + 2.0 * camsum[2 * (size_t)i + 1];
+  for (int q = b0 + (int)threadIdx.x; q < b1; q += 256) v += pred_part[q];
   red[threadIdx.x] = v;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -853,6 +859,25 @@ __global__ void k_pred_finish(DeviceState* __restrict__ st, int nc, int nparts, 
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    blk[blockIdx.x] = red[0];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  v = 0.0;
+  for (int q = threadIdx.x; q < (int)gridDim.x; q += 256) v += __ldcg(blk + q);
+  for (int i = threadIdx.x; i < nc; i += 256)
+    v -= camsum[2 * (size_t)i] + 2.0 * camsum[2 * (size_t)i + 1];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
     st->pred = red[0];
     if (!st->stop_series) st->terms_used = m;
   }
@@ -1280,8 +1305,9 @@ povar_status launch_pred(Problem* p, int precision, double eta, int manifold, in
         point_data<double>(p, 0), point_data<double>(p, 1), p->rec32, p->rec64, p->pred_part);
     k_pred_cam<double><<<grid_for(p->nc, 8), 256, 0, p->stream>>>(p->state, p->nc, p->U64,
                                                                    p->bp64, p->D64, p->camnorm);
-    k_pred_finish<<<1, 256, 0, p->stream>>>(p->state, p->nc, p->np_pad / 32, m, p->pred_part,
-                                            p->camnorm);
+    k_pred_finish<<<FIN_BLOCKS, 256, 0, p->stream>>>(p->state, p->nc, p->np_pad / 32, m,
+                                                     p->pred_part, p->camnorm,
+                                                     p->fin_blk + FIN_BLOCKS, p->fin_ticket + 1);
   } else {
     if (manifold == POVAR_SPHERE)
       k_project_delta<float><<<gc, 128, 0, p->stream>>>(p->state, p->nc, p->P64[0], p->P64[1],
@@ -1291,8 +1317,9 @@ povar_status launch_pred(Problem* p, int precision, double eta, int manifold, in
         point_data<float>(p, 0), point_data<float>(p, 1), p->rec32, p->rec64, p->pred_part);
     k_pred_cam<float><<<grid_for(p->nc, 8), 256, 0, p->stream>>>(p->state, p->nc, p->U64,
                                                                   p->bp64, p->D32, p->camnorm);
-    k_pred_finish<<<1, 256, 0, p->stream>>>(p->state, p->nc, p->np_pad / 32, m, p->pred_part,
-                                            p->camnorm);
+    k_pred_finish<<<FIN_BLOCKS, 256, 0, p->stream>>>(p->state, p->nc, p->np_pad / 32, m,
+                                                     p->pred_part, p->camnorm,
+                                                     p->fin_blk + FIN_BLOCKS, p->fin_ticket + 1);
   }
   p->launches += manifold == POVAR_SPHERE ? 4 : 3;
   return check_launch(p, "pred");
