@@ -371,7 +371,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         "phases_ms_per_lm_step": {k: round(v / steps_timed, 4) for k, v in phases.items()},
         "lm_iterations_per_solve": iters_total / max(len(results), 1),
         "series_terms_per_step": round(terms_per_step, 3),
-        "series_schedule": {"chosen": sched, "tuned_ms_two_terms": [round(x, 4) for x in tune_ms]},
+        "series_schedule": {"chosen": sched, "tuned_ms_per_term": [round(x, 4) for x in tune_ms]},
         "reached_target": bool(reached),
         "final_cost": final_cost,
         "per_solve_ms": [round(x, 3) for x in per_solve],

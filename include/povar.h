@@ -212,11 +212,12 @@ povar_status povar_get_profile(povar_problem* p, double* ms_out, int64_t* steps_
                                int64_t* products_out, int32_t reset);
 
 /* Series-schedule autotuner. The first povar_solve with params->schedule
- * = -1 times two series terms of every schedule (0 .. POVAR_NSCHEDULES-1)
- * on the live state with CUDA events and keeps the fastest for that
- * precision; later solves and povar_step with schedule -1 use it.
- * povar_get_tuning returns the chosen schedule (-1 before tuning) and the
- * measured times in milliseconds (ms_out[POVAR_NSCHEDULES], may be NULL). */
+ * = -1 times every schedule (0 .. POVAR_NSCHEDULES-1) on the live state
+ * with CUDA events (one warm-up term, then three timed terms, two rounds)
+ * and keeps the fastest for that precision; later solves and povar_step
+ * with schedule -1 use it. povar_get_tuning returns the chosen schedule (-1
+ * before tuning) and the measured milliseconds per series term
+ * (ms_out[POVAR_NSCHEDULES], may be NULL). */
 povar_status povar_get_tuning(povar_problem* p, int32_t precision, int32_t* schedule_out,
                               float* ms_out);
 

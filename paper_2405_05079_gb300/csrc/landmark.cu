@@ -200,7 +200,7 @@ __device__ __forceinline__ PinvOut pinv_solve(Sym3 Vs, Vec3 hs) {
 }
 
 __global__ void __launch_bounds__(BLOCK)
-k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
+k_landmark(DeviceState* __restrict__ st, int which_rel, double eta,
            const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
            const int32_t* __restrict__ sell_cam, const double2* __restrict__ sell_m,
            const double* __restrict__ Ltab, const double* __restrict__ P0,
@@ -209,6 +209,7 @@ k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
   if (which_rel == 1 && st->converged) return;
   const int t = which_rel ? 1 - st->cur : st->cur;
   const int s = blockIdx.x * BLOCK + threadIdx.x;
+  if (s == 0) st->x_df[t] = 0;
   double cost = 0.0;
   int npinv = 0;
   if (s < np) {
@@ -335,7 +336,7 @@ k_landmark(const DeviceState* __restrict__ st, int which_rel, double eta,
 // by the FP32 kernels and the cost partials; the FP64 factor F64 is not
 // written (an FP64 step re-solves the landmarks with k_landmark first).
 __global__ void __launch_bounds__(BLOCK)
-k_landmark_df(const DeviceState* __restrict__ st, int which_rel, double eta,
+k_landmark_df(DeviceState* __restrict__ st, int which_rel, df64 a, df64 eta,
               const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
               const int32_t* __restrict__ sell_cam, const float4* __restrict__ sell_mdf,
               const float2* __restrict__ Ldf, int np, SlotBufs bufs,
@@ -343,7 +344,8 @@ k_landmark_df(const DeviceState* __restrict__ st, int which_rel, double eta,
   if (which_rel == 1 && st->converged) return;
   const int t = which_rel ? 1 - st->cur : st->cur;
   const int s = blockIdx.x * BLOCK + threadIdx.x;
-  double cost = 0.0;
+  if (s == 0) st->x_df[t] = 1;
+  df64 cost = {0.f, 0.f};
   int npinv = 0;
   if (s < np) {
     const uint32_t len = slot_len[s];
@@ -425,14 +427,16 @@ k_landmark_df(const DeviceState* __restrict__ st, int which_rel, double eta,
       X[1] = df_neg(df_add(df_mul(f11, z1), df_mul(f21, z2)));
       X[2] = df_neg(df_mul(f22, z2));
       F[0] = f00.hi; F[1] = f10.hi; F[2] = f11.hi; F[3] = f20.hi; F[4] = f21.hi; F[5] = f22.hi;
-      for (int c = 0; c < 3; ++c) X64v[c] = df_to_double(X[c]);
     } else {
       for (int c = 0; c < 3; ++c) X[c] = df_from_double(X64v[c]);
       for (int e = 0; e < 6; ++e) F[e] = (float)F64v[e];
     }
     npinv = deficient ? 1 : 0;
-    double* Xo = bufs.X[t] + 3 * (size_t)s;
-    Xo[0] = X64v[0]; Xo[1] = X64v[1]; Xo[2] = X64v[2];
+    // X as double-float pairs in the FP64 buffer (same 24 bytes; x_df[t] = 1)
+    float2* Xo = reinterpret_cast<float2*>(bufs.X[t] + 3 * (size_t)s);
+    Xo[0] = make_float2(X[0].hi, X[0].lo);
+    Xo[1] = make_float2(X[1].hi, X[1].lo);
+    Xo[2] = make_float2(X[2].hi, X[2].lo);
     bufs.A[t][s] = make_float4(X[0].hi, X[1].hi, X[2].hi, F[0]);
     bufs.B[t][s] = make_float4(F[1], F[2], F[3], F[4]);
     bufs.C[t][s] = F[5];
@@ -476,7 +480,7 @@ k_landmark_df(const DeviceState* __restrict__ st, int which_rel, double eta,
       df_acc_mul(e2, b0, b0);
       df_acc_mul(e2, b1, b1);
     }
-    cost = (1.0 - eta) * df_to_double(df_norm(e1)) + eta * df_to_double(df_norm(e2));
+    cost = df_add(df_mul(a, df_norm(e1)), df_mul(eta, df_norm(e2)));
   } else {
     double* Xo = bufs.X[t] + 3 * (size_t)s;
     Xo[0] = Xo[1] = Xo[2] = 0.0;
@@ -484,13 +488,16 @@ k_landmark_df(const DeviceState* __restrict__ st, int which_rel, double eta,
     bufs.B[t][s] = make_float4(0.f, 0.f, 0.f, 0.f);
     bufs.C[t][s] = 0.f;
   }
+  // warp sum in double-float, one FP64 partial per warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    cost += __shfl_xor_sync(0xffffffffu, cost, o);
+    const df64 other = {__shfl_xor_sync(0xffffffffu, cost.hi, o),
+                        __shfl_xor_sync(0xffffffffu, cost.lo, o)};
+    cost = df_add(cost, other);
     npinv += __shfl_xor_sync(0xffffffffu, npinv, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    cost_part[s / 32] = cost;
+    cost_part[s / 32] = df_to_double(cost);
     pinv_part[s / 32] = npinv;
   }
 }
@@ -564,6 +571,12 @@ k_cost_finish(DeviceState* __restrict__ st, int which_rel, const double* __restr
 
 }  // namespace
 
+// double-float pair of a host double (kernel argument)
+static df64 df_host(double x) {
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+
 povar_status launch_landmarks(Problem* p, int which_rel, double eta, int precision) {
   k_ltab<<<grid_for(p->nc, 128), 128, 0, p->stream>>>(p->state, which_rel, eta, p->P64[0],
                                                       p->P64[1], p->nc, p->Ltab, p->Ltab_df,
@@ -580,7 +593,7 @@ povar_status launch_landmarks(Problem* p, int which_rel, double eta, int precisi
   // evaluation (and every FP64 step) in FP64
   if (which_rel == 1 && precision == POVAR_MIXED_FP32)
     k_landmark_df<<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
-        p->state, which_rel, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_mdf,
+        p->state, which_rel, df_host(1.0 - eta), df_host(eta), p->slot_len, p->sell_off, p->sell_cam, p->sell_mdf,
         p->Ltab_df, p->np, b, p->cost_part, p->pinv_part);
   else
     k_landmark<<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(

@@ -70,6 +70,7 @@ struct DeviceState {
   int n_pinv;        // landmarks solved by pseudo-inverse at the last solve
   int n_regularized; // camera blocks whose damping had to be raised (cumulative)
   long long products; // series products M y computed by all steps (never reset)
+  int x_df[2];        // landmark buffer t holds X as double-float pairs (1) or FP64 (0)
 };
 
 // Host-side handle.

@@ -587,6 +587,68 @@ template <> struct Rec12<double> {
   }
 };
 
+// Threshold rule of the series (stop after term k when ||x_k|| <= eps
+// ||delta_k||): every camera block stores the two squared norms of its
+// camera; the block that arrives last on the ticket adds all cameras'
+// norms with all of its NW warps in a fixed order (thread t takes cameras
+// t, t + 32 NW, ...; the warps are combined in index order) and sets the
+// stop flag. Thread 0 of the block holds the camera's norms on entry.
+template <int NW>
+__device__ __forceinline__ void stop_check(DeviceState* __restrict__ st, int term, double eps,
+                                           int nc, int i, double yy, double dd,
+                                           double* __restrict__ camnorm,
+                                           uint32_t* __restrict__ done_ticket, int* sh_last,
+                                           double (*shn)[2]) {
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    camnorm[2 * (size_t)i] = yy;
+    camnorm[2 * (size_t)i + 1] = dd;
+    __threadfence();
+    *sh_last = atomicAdd(done_ticket, 1u) == (unsigned)(nc - 1);
+  }
+  __syncthreads();
+  if (!*sh_last) return;
+  __threadfence();
+  double sy = 0.0, sd = 0.0;
+  for (int c0 = (int)threadIdx.x; c0 < nc; c0 += 4 * NW * 32) {
+    double vy[4], vd[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u * NW * 32;
+      vy[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c) : 0.0;
+      vd[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c + 1) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      sy += vy[u];
+      sd += vd[u];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    sd += __shfl_xor_sync(0xffffffffu, sd, o);
+  }
+  if (lane == 0) {
+    shn[wl][0] = sy;
+    shn[wl][1] = sd;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sy = 0.0;
+    sd = 0.0;
+    for (int w = 0; w < NW; ++w) {
+      sy += shn[w][0];
+      sd += shn[w][1];
+    }
+    *done_ticket = 0;
+    if (sy <= eps * eps * sd) {
+      st->stop_series = 1;
+      st->terms_used = term + 1;
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128)
 k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
@@ -594,12 +656,19 @@ k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
                const T* __restrict__ part, const T* __restrict__ G, double* __restrict__ camnorm,
                uint32_t* __restrict__ done_ticket, T* __restrict__ Y, T* __restrict__ D) {
   // one block of 4 warps per camera: each warp adds a strided quarter of the
-  // camera's partials, the four warp sums are combined in a fixed order
+  // camera's partials, the four warp sums are combined in a fixed order;
+  // warp 0 loads the camera's row of G and of delta before the partials
+  // arrive, so the update waits on no further load
   if (st->converged || st->stop_series) return;
   __shared__ T sh[4][12];
   __shared__ int sh_last;
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int i = blockIdx.x;
+  T g[12], dprev = 0;
+  if (wl == 0) {
+    Row12<T>::load(G + 144 * (size_t)i + 12 * (lane < 12 ? lane : 0), g);
+    if (lane < 12) dprev = D[12 * (size_t)i + lane];
+  }
   T acc[12];
 #pragma unroll
   for (int e = 0; e < 12; ++e) acc[e] = 0;
@@ -611,59 +680,45 @@ k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
     Rec12<T>::add(part + (size_t)i1 * 12, acc);
   }
   if (q < e_) Rec12<T>::add(part + (size_t)__ldg(cam_part_idx + q) * 12, acc);
-#pragma unroll
-  for (int e = 0; e < 12; ++e) {
-    T v = acc[e];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    acc[e] = v;
+  {
+    T r[3];
+    int vb;
+    warp_reduce12<T>(acc, lane, r, vb);
+    if ((lane & 7) == 0) {
+      sh[wl][vb] = r[0];
+      sh[wl][vb + 1] = r[1];
+      sh[wl][vb + 2] = r[2];
+    }
   }
-  if (lane == 0)
-#pragma unroll
-    for (int e = 0; e < 12; ++e) sh[wl][e] = acc[e];
   __syncthreads();
-  if (wl != 0) return;
-  T z = 0;
-  if (lane < 12) z = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
-  double yy, dd;
-  camera_update<T>(i, lane, z, G, Y, D, yy, dd);
+  constexpr int NWARPS = 4;
+  __shared__ double shn[NWARPS][2];
+  double yy = 0.0, dd = 0.0;
+  if (wl == 0) {
+    T z = 0;
+    if (lane < 12) z = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
+    // x_i = G_i z_i, delta_i += x_i, Y_i = x_i
+    T x = 0;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) x += g[c] * __shfl_sync(0xffffffffu, z, c);
+    T y2 = 0, d2 = 0;
+    if (lane < 12) {
+      const T d = dprev + x;
+      D[12 * (size_t)i + lane] = d;
+      Y[12 * (size_t)i + lane] = x;
+      y2 = x * x;
+      d2 = d * d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    }
+    yy = (double)y2;
+    dd = (double)d2;
+  }
   if (eps <= 0.0) return;
-  if (lane == 0) {
-    camnorm[2 * (size_t)i] = yy;
-    camnorm[2 * (size_t)i + 1] = dd;
-    __threadfence();
-    sh_last = atomicAdd(done_ticket, 1u) == (unsigned)(nc - 1);
-  }
-  __syncwarp();
-  if (!sh_last) return;
-  __threadfence();
-  double sy = 0.0, sd = 0.0;
-  for (int c0 = 0; c0 < nc; c0 += 32 * 8) {
-    double vy[8], vd[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int c = c0 + u * 32 + lane;
-      vy[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c) : 0.0;
-      vd[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c + 1) : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      sy += vy[u];
-      sd += vd[u];
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sy += __shfl_xor_sync(0xffffffffu, sy, o);
-    sd += __shfl_xor_sync(0xffffffffu, sd, o);
-  }
-  if (lane == 0) {
-    *done_ticket = 0;
-    if (sy <= eps * eps * sd) {
-      st->stop_series = 1;
-      st->terms_used = term + 1;
-    }
-  }
+  stop_check<NWARPS>(st, term, eps, nc, i, yy, dd, camnorm, done_ticket, &sh_last, shn);
 }
 
 // ---------------------------------------------------------------------------
@@ -742,51 +797,19 @@ k_series_camrows(DeviceState* __restrict__ st, T a, int term, double eps, int nc
     sh[wl][vb + 2] = r[2];
   }
   __syncthreads();
-  if (wl != 0) return;
-  T z = 0;
-  if (lane < 12) {
+  constexpr int NWARPS = NW;
+  __shared__ double shn[NWARPS][2];
+  double yy = 0.0, dd = 0.0;
+  if (wl == 0) {
+    T z = 0;
+    if (lane < 12) {
 #pragma unroll
-    for (int w = 0; w < NW; ++w) z += sh[w][lane];
+      for (int w = 0; w < NW; ++w) z += sh[w][lane];
+    }
+    camera_update<T>(i, lane, z, G, Y, D, yy, dd);
   }
-  double yy, dd;
-  camera_update<T>(i, lane, z, G, Y, D, yy, dd);
   if (eps <= 0.0) return;
-  if (lane == 0) {
-    camnorm[2 * (size_t)i] = yy;
-    camnorm[2 * (size_t)i + 1] = dd;
-    __threadfence();
-    sh_last = atomicAdd(done_ticket, 1u) == (unsigned)(nc - 1);
-  }
-  __syncwarp();
-  if (!sh_last) return;
-  __threadfence();
-  double sy = 0.0, sd = 0.0;
-  for (int c0 = 0; c0 < nc; c0 += 32 * 8) {
-    double vy[8], vd[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int c = c0 + u * 32 + lane;
-      vy[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c) : 0.0;
-      vd[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c + 1) : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      sy += vy[u];
-      sd += vd[u];
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sy += __shfl_xor_sync(0xffffffffu, sy, o);
-    sd += __shfl_xor_sync(0xffffffffu, sd, o);
-  }
-  if (lane == 0) {
-    *done_ticket = 0;
-    if (sy <= eps * eps * sd) {
-      st->stop_series = 1;
-      st->terms_used = term + 1;
-    }
-  }
+  stop_check<NWARPS>(st, term, eps, nc, i, yy, dd, camnorm, done_ticket, &sh_last, shn);
 }
 
 // delta <- Pi delta on the sphere (removes rounding drift out of the tangent

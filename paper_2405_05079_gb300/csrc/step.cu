@@ -154,9 +154,15 @@ __global__ void k_gather_points(const DeviceState* __restrict__ st,
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= np) return;
   const double* X = (st->cur ? X1 : X0) + 3 * (size_t)pt_slot[j];
-  out[3 * (size_t)j] = X[0];
-  out[3 * (size_t)j + 1] = X[1];
-  out[3 * (size_t)j + 2] = X[2];
+  if (st->x_df[st->cur]) {
+    // double-float pairs (written by the mixed-precision landmark kernel)
+    const float2* Xf = reinterpret_cast<const float2*>(X);
+    for (int c = 0; c < 3; ++c) out[3 * (size_t)j + c] = (double)Xf[c].x + (double)Xf[c].y;
+  } else {
+    out[3 * (size_t)j] = X[0];
+    out[3 * (size_t)j + 1] = X[1];
+    out[3 * (size_t)j + 2] = X[2];
+  }
 }
 
 }  // namespace
