@@ -30,14 +30,15 @@
 namespace povar {
 
 constexpr int SLICE = 32;        // landmarks per SELL slice (one warp)
-constexpr int CHUNK = 256;       // observations per camera-major chunk
+constexpr int CHUNK = 512;       // observations per camera-major chunk
 constexpr int LIN_ACC = 52;      // linearization accumulators per chunk
 constexpr int BLOCK = 256;       // threads per block for slot kernels
-// Slices per warp in the grouped series schedule. One slice per warp measured
-// fastest on the 5M-observation scene (71 us per series product against 78
-// for two and 104 for four): larger groups save warp reductions but their
-// registers halve the occupancy of a latency-bound loop, and grouping by
-// group width unbalances the blocks of the slot kernels.
+// Slices per group of the schedule-3 row table (its kernel takes one slice
+// per warp). Groups of two and four slices per warp were measured slower on
+// the 5M-observation scene (78 and 104 us per series product against 71):
+// they save warp reductions, but their registers halve the occupancy of a
+// latency-bound loop, and ordering by group width unbalances the blocks of
+// the slot kernels.
 constexpr int GROUP = 1;
 // Blocks of the final cost and predicted-decrease sums (each block adds a
 // fixed range, the last block to finish adds the block sums in order).

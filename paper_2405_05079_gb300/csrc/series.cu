@@ -417,6 +417,104 @@ __device__ __forceinline__ void warp_reduce12(const T v[12], int lane, T r[3], i
   vbase = (hiA ? 6 : 0) + (hiB ? 3 : 0);
 }
 
+// t += Pbar^T C (Y x~) for one observation (W^T-gather)
+template <typename T>
+__device__ __forceinline__ void gather_obs(const T Y0[4], const T Y1[4], const T Y2[4],
+                                           const T P0[4], const T P1[4], const T P2[4], T a,
+                                           T mu, T mv, const T X[3], T t[3]) {
+  const T e0 = Y0[0] * X[0] + Y0[1] * X[1] + Y0[2] * X[2] + Y0[3];
+  const T e1 = Y1[0] * X[0] + Y1[1] * X[1] + Y1[2] * X[2] + Y1[3];
+  const T e2 = Y2[0] * X[0] + Y2[1] * X[1] + Y2[2] * X[2] + Y2[3];
+  const T au = a * mu, av = a * mv;
+  const T aw = au * mu + av * mv;
+  const T c0 = e0 - au * e2;
+  const T c1 = e1 - av * e2;
+  const T c2 = aw * e2 - au * e0 - av * e1;
+  t[0] += P0[0] * c0 + P1[0] * c1 + P2[0] * c2;
+  t[1] += P0[1] * c0 + P1[1] * c1 + P2[1] * c2;
+  t[2] += P0[2] * c0 + P1[2] * c1 + P2[2] * c2;
+}
+
+// v += vec((C Pbar s) x~^T) for one observation (W-scatter)
+template <typename T>
+__device__ __forceinline__ void scatter_obs(const T P0[4], const T P1[4], const T P2[4], T a,
+                                            T mu, T mv, const T S[3], const T X[3], T v[12]) {
+  const T w0 = P0[0] * S[0] + P0[1] * S[1] + P0[2] * S[2];
+  const T w1 = P1[0] * S[0] + P1[1] * S[1] + P1[2] * S[2];
+  const T w2 = P2[0] * S[0] + P2[1] * S[1] + P2[2] * S[2];
+  const T au = a * mu, av = a * mv;
+  const T aw = au * mu + av * mv;
+  const T q0 = w0 - au * w2;
+  const T q1 = w1 - av * w2;
+  const T q2 = aw * w2 - au * w0 - av * w1;
+  v[0] += q0 * X[0]; v[1] += q0 * X[1]; v[2] += q0 * X[2]; v[3] += q0;
+  v[4] += q1 * X[0]; v[5] += q1 * X[1]; v[6] += q1 * X[2]; v[7] += q1;
+  v[8] += q2 * X[0]; v[9] += q2 * X[1]; v[10] += q2 * X[2]; v[11] += q2;
+}
+
+// Segmented sum of v over the runs of equal camera that start at the set
+// bits of mask; the run starting at a valid lane stores its sum as the next
+// partial from pbase (valid run starts in lane order).
+template <typename T>
+__device__ __forceinline__ void store_runs(T v[12], uint32_t mask, bool valid, uint32_t pbase,
+                                           int lane, T* __restrict__ part) {
+  const uint32_t nb = lane < 31 ? (mask >> (lane + 1)) : 0u;
+  bool ok[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int o = 1 << q;
+    ok[q] = (lane + o < 32) && ((nb & ((1u << o) - 1u)) == 0u);
+  }
+#pragma unroll
+  for (int e = 0; e < 12; ++e) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const T other = __shfl_down_sync(0xffffffffu, v[e], 1 << q);
+      if (ok[q]) v[e] += other;
+    }
+  }
+  const uint32_t starts = mask & __ballot_sync(0xffffffffu, valid);
+  if ((starts >> lane) & 1u) {
+    T* out = part + ((size_t)pbase + __popc(starts & ((1u << lane) - 1u))) * 12;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) out[e] = v[e];
+  }
+}
+
+// Reduction of two rows of 12 values across the warp (transposed butterfly):
+// lanes with (lane & 3) == 0 end with three totals of row `row_b`, entries
+// vbase .. vbase + 2.
+template <typename T>
+__device__ __forceinline__ void warp_reduce24(const T vA[12], const T vB[12], int lane, T r[3],
+                                              int& row_b, int& vbase) {
+  // xor 16: keep one row, send the other
+  const bool hiA = lane & 16, hiB = lane & 8, hiC = lane & 4;
+  T r12[12];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    const T send = hiA ? vA[j] : vB[j];
+    const T keep = hiA ? vB[j] : vA[j];
+    r12[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  T r6[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const T send = hiB ? r12[j] : r12[j + 6];
+    const T keep = hiB ? r12[j + 6] : r12[j];
+    r6[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const T send = hiC ? r6[j] : r6[j + 3];
+    const T keep = hiC ? r6[j + 3] : r6[j];
+    r[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    r[j] += __shfl_xor_sync(0xffffffffu, r[j], 2);
+    r[j] += __shfl_xor_sync(0xffffffffu, r[j], 1);
+  }
+  row_b = hiA ? 1 : 0;
+  vbase = (hiB ? 6 : 0) + (hiC ? 3 : 0);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(BLOCK)
 k_series_fused(const DeviceState* __restrict__ st, T a,
@@ -500,7 +598,37 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
       bk[u] = rin ? __ldg(row_base + row0 + k0 + u) : 0u;
     }
 #pragma unroll
-    for (int u = 0; u < RB; ++u) {
+    for (int up = 0; up < RB; up += 2) {
+    if (k0 + up >= width) break;
+    // two consecutive uniform rows are reduced across the warp together
+    if (k0 + up + 1 < width && mk[up] == 0u && mk[up + 1] == 0u) {
+      T vA[12], vB[12];
+#pragma unroll
+      for (int e = 0; e < 12; ++e) vA[e] = vB[e] = 0;
+      const T Sv[3] = {S0, S1, S2};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = ci[up + h];
+        if (i >= 0) {
+          T P0[4], P1[4], P2[4];
+          load_row<T>(camP, i, 0, P0);
+          load_row<T>(camP, i, 1, P1);
+          load_row<T>(camP, i, 2, P2);
+          scatter_obs<T>(P0, P1, P2, a, (T)mi[up + h].x, (T)mi[up + h].y, Sv, X, h ? vB : vA);
+        }
+      }
+      T r[3];
+      int rowb, vb;
+      warp_reduce24<T>(vA, vB, lane, r, rowb, vb);
+      if ((lane & 3) == 0) {
+        T* out = part + (size_t)(rowb ? bk[up + 1] : bk[up]) * 12 + vb;
+        out[0] = r[0]; out[1] = r[1]; out[2] = r[2];
+      }
+      continue;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+    const int u = up + h;
     if (k0 + u >= width) break;
     const int i = ci[u];
     const auto m = mi[u];
@@ -513,17 +641,8 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
       load_row<T>(camP, i, 0, P0);
       load_row<T>(camP, i, 1, P1);
       load_row<T>(camP, i, 2, P2);
-      const T w0 = P0[0] * S0 + P0[1] * S1 + P0[2] * S2;
-      const T w1 = P1[0] * S0 + P1[1] * S1 + P1[2] * S2;
-      const T w2 = P2[0] * S0 + P2[1] * S1 + P2[2] * S2;
-      const T au = a * (T)m.x, av = a * (T)m.y;
-      const T aw = au * (T)m.x + av * (T)m.y;
-      const T q0 = w0 - au * w2;
-      const T q1 = w1 - av * w2;
-      const T q2 = aw * w2 - au * w0 - av * w1;
-      v[0] = q0 * X[0]; v[1] = q0 * X[1]; v[2] = q0 * X[2]; v[3] = q0;
-      v[4] = q1 * X[0]; v[5] = q1 * X[1]; v[6] = q1 * X[2]; v[7] = q1;
-      v[8] = q2 * X[0]; v[9] = q2 * X[1]; v[10] = q2 * X[2]; v[11] = q2;
+      const T Sv[3] = {S0, S1, S2};
+      scatter_obs<T>(P0, P1, P2, a, (T)m.x, (T)m.y, Sv, X, v);
     }
     if (mask == 0u) {
       T r[3];
@@ -534,28 +653,8 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
         out[0] = r[0]; out[1] = r[1]; out[2] = r[2];
       }
     } else {
-      const uint32_t nb = lane < 31 ? (mask >> (lane + 1)) : 0u;
-      bool ok[5];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        const int o = 1 << q;
-        ok[q] = (lane + o < 32) && ((nb & ((1u << o) - 1u)) == 0u);
-      }
-#pragma unroll
-      for (int e = 0; e < 12; ++e) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          const T other = __shfl_down_sync(0xffffffffu, v[e], 1 << q);
-          if (ok[q]) v[e] += other;
-        }
-      }
-      const uint32_t valid = __ballot_sync(0xffffffffu, i >= 0);
-      const uint32_t starts = mask & valid;
-      if ((starts >> lane) & 1u) {
-        T* out = part + ((size_t)pbase + __popc(starts & lt_mask)) * 12;
-#pragma unroll
-        for (int e = 0; e < 12; ++e) out[e] = v[e];
-      }
+      store_runs<T>(v, mask, i >= 0, pbase, lane, part);
+    }
     }
     }
   }
@@ -907,80 +1006,11 @@ k_pred_finish(DeviceState* __restrict__ st, int nc, int nparts, int m,
 }
 
 // ---------------------------------------------------------------------------
-// Grouped schedule (3). One warp handles a group of up to GROUP slices whose
-// landmarks share their smallest camera, lane l holding landmark l of every
-// slice of the group. Row t of the group is row t of each of its slices; in
-// a "uniform" group row every valid lane of every slice observes the same
-// camera (known from the table, so its rows are loaded once, before any
-// observation data), and the camera contributions of all the group's
-// landmarks are summed in registers and reduced across the warp once,
-// into one partial. Other group rows are handled slice row by slice row
-// exactly as in the fused schedule.
+// Schedule 3 (row table). The host groups slices (GROUP per warp, see
+// povar_internal.cuh) and gives every group row whose valid lanes all see
+// one camera that camera and its partial; other rows keep the run
+// description of the fused schedule. Helpers shared with its kernel below.
 // ---------------------------------------------------------------------------
-// t += Pbar^T C (Y x~) for one observation (W^T-gather)
-template <typename T>
-__device__ __forceinline__ void gather_obs(const T Y0[4], const T Y1[4], const T Y2[4],
-                                           const T P0[4], const T P1[4], const T P2[4], T a,
-                                           T mu, T mv, const T X[3], T t[3]) {
-  const T e0 = Y0[0] * X[0] + Y0[1] * X[1] + Y0[2] * X[2] + Y0[3];
-  const T e1 = Y1[0] * X[0] + Y1[1] * X[1] + Y1[2] * X[2] + Y1[3];
-  const T e2 = Y2[0] * X[0] + Y2[1] * X[1] + Y2[2] * X[2] + Y2[3];
-  const T au = a * mu, av = a * mv;
-  const T aw = au * mu + av * mv;
-  const T c0 = e0 - au * e2;
-  const T c1 = e1 - av * e2;
-  const T c2 = aw * e2 - au * e0 - av * e1;
-  t[0] += P0[0] * c0 + P1[0] * c1 + P2[0] * c2;
-  t[1] += P0[1] * c0 + P1[1] * c1 + P2[1] * c2;
-  t[2] += P0[2] * c0 + P1[2] * c1 + P2[2] * c2;
-}
-
-// v += vec((C Pbar s) x~^T) for one observation (W-scatter)
-template <typename T>
-__device__ __forceinline__ void scatter_obs(const T P0[4], const T P1[4], const T P2[4], T a,
-                                            T mu, T mv, const T S[3], const T X[3], T v[12]) {
-  const T w0 = P0[0] * S[0] + P0[1] * S[1] + P0[2] * S[2];
-  const T w1 = P1[0] * S[0] + P1[1] * S[1] + P1[2] * S[2];
-  const T w2 = P2[0] * S[0] + P2[1] * S[1] + P2[2] * S[2];
-  const T au = a * mu, av = a * mv;
-  const T aw = au * mu + av * mv;
-  const T q0 = w0 - au * w2;
-  const T q1 = w1 - av * w2;
-  const T q2 = aw * w2 - au * w0 - av * w1;
-  v[0] += q0 * X[0]; v[1] += q0 * X[1]; v[2] += q0 * X[2]; v[3] += q0;
-  v[4] += q1 * X[0]; v[5] += q1 * X[1]; v[6] += q1 * X[2]; v[7] += q1;
-  v[8] += q2 * X[0]; v[9] += q2 * X[1]; v[10] += q2 * X[2]; v[11] += q2;
-}
-
-// Segmented sum of v over the runs of equal camera that start at the set
-// bits of mask; the run starting at a valid lane stores its sum as the next
-// partial from pbase (valid run starts in lane order).
-template <typename T>
-__device__ __forceinline__ void store_runs(T v[12], uint32_t mask, bool valid, uint32_t pbase,
-                                           int lane, T* __restrict__ part) {
-  const uint32_t nb = lane < 31 ? (mask >> (lane + 1)) : 0u;
-  bool ok[5];
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    const int o = 1 << q;
-    ok[q] = (lane + o < 32) && ((nb & ((1u << o) - 1u)) == 0u);
-  }
-#pragma unroll
-  for (int e = 0; e < 12; ++e) {
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      const T other = __shfl_down_sync(0xffffffffu, v[e], 1 << q);
-      if (ok[q]) v[e] += other;
-    }
-  }
-  const uint32_t starts = mask & __ballot_sync(0xffffffffu, valid);
-  if ((starts >> lane) & 1u) {
-    T* out = part + ((size_t)pbase + __popc(starts & ((1u << lane) - 1u))) * 12;
-#pragma unroll
-    for (int e = 0; e < 12; ++e) out[e] = v[e];
-  }
-}
-
 // Per warp, 32 group rows at a time: the rows' cameras are read with one
 // coalesced load (lane r holds the camera of row r0 + r) and the rows Y_i, P_i
 // of every uniform row's camera are staged in shared memory by the lanes in
@@ -1018,18 +1048,29 @@ __device__ __forceinline__ void stage_rows(T (*dst)[24], const int32_t* __restri
   __syncwarp();
 }
 
+static_assert(GROUP == 1, "k_series_rows takes one slice per group");
+
+// Row-pair schedule (3) with one slice per warp: the per-row camera table
+// of the grouped layout (GROUP = 1) gives every uniform slice row its camera
+// without a dependent load, the rows of those cameras are staged in shared
+// memory 32 rows at a time, the measurements of RB rows are loaded together,
+// and in pass 2 two consecutive uniform rows are reduced across the warp
+// together (27 shuffles for the pair instead of 18 per row). The row loops
+// run over the slice width for all lanes (a lane past its track length
+// contributes nothing), so every shuffle is executed by the whole warp.
+// Rows that are not uniform take the per-lane camera and run path of the
+// fused schedule.
 template <typename T>
-__global__ void __launch_bounds__(BLOCK, 2)
-k_series_grouped(const DeviceState* __restrict__ st, T a,
-                 const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
-                 const int32_t* __restrict__ sell_cam,
-                 const typename Vt<T>::m2* __restrict__ sell_m, const T* __restrict__ camPa,
-                 const T* __restrict__ camPb, const T* __restrict__ vec, PointData<T> pd0,
-                 PointData<T> pd1, const uint32_t* __restrict__ grp_slice0,
-                 const uint32_t* __restrict__ grp_row0, int ngroups,
-                 const int32_t* __restrict__ grow_cam, const uint32_t* __restrict__ grow_base,
-                 const uint32_t* __restrict__ srow_mask, const uint32_t* __restrict__ srow_base,
-                 T* __restrict__ part) {
+__global__ void __launch_bounds__(BLOCK)
+k_series_rows(const DeviceState* __restrict__ st, T a, const uint32_t* __restrict__ slot_len,
+              const uint32_t* __restrict__ sell_off, const int32_t* __restrict__ sell_cam,
+              const typename Vt<T>::m2* __restrict__ sell_m, const T* __restrict__ camPa,
+              const T* __restrict__ camPb, const T* __restrict__ vec, PointData<T> pd0,
+              PointData<T> pd1, const uint32_t* __restrict__ grp_slice0,
+              const uint32_t* __restrict__ grp_row0, int ngroups,
+              const int32_t* __restrict__ grow_cam, const uint32_t* __restrict__ grow_base,
+              const uint32_t* __restrict__ srow_mask, const uint32_t* __restrict__ srow_base,
+              T* __restrict__ part) {
   __shared__ __align__(16) GroupStage<T> stage;
   if (st->converged || st->stop_series) return;
   const int wl = (int)(threadIdx.x >> 5);
@@ -1037,154 +1078,177 @@ k_series_grouped(const DeviceState* __restrict__ st, T a,
   if (g >= ngroups) return;  // whole warp (no block-level barrier below)
   const int lane = threadIdx.x & 31;
   using M2 = typename Vt<T>::m2;
+  constexpr int RB = 4;
   T (*sm)[24] = stage.cam[wl];
   const PointData<T>& pd = st->cur ? pd1 : pd0;
   const T* __restrict__ camP = st->cur ? camPb : camPa;
-  const uint32_t s0 = grp_slice0[g];
-  const int ns = (int)(grp_slice0[g + 1] - s0);
+  const uint32_t s = grp_slice0[g];  // one slice per group
   const uint32_t r0 = grp_row0[g], W = grp_row0[g + 1] - r0;
-  uint32_t sb[GROUP], wid[GROUP], len[GROUP];
-  T X[GROUP][3], t[GROUP][3];
-#pragma unroll
-  for (int k = 0; k < GROUP; ++k) {
-    sb[k] = 0;
-    wid[k] = 0;
-    len[k] = 0;
-    X[k][0] = X[k][1] = X[k][2] = 0;
-    t[k][0] = t[k][1] = t[k][2] = 0;
-    if (k < ns) {
-      const uint32_t s = s0 + (uint32_t)k;
-      sb[k] = sell_off[s];
-      wid[k] = (sell_off[s + 1] - sb[k]) / SLICE;
-      len[k] = slot_len[s * SLICE + lane];
-      T Fk[6];
-      load_point<T>(pd, (int)(s * SLICE) + lane, X[k], Fk);
-    }
+  const uint32_t sb = sell_off[s];
+  const uint32_t len = slot_len[s * SLICE + lane];
+  const uint32_t base = sb + (uint32_t)lane;
+  T X[3];
+  {
+    T F0[6];
+    load_point<T>(pd, (int)(s * SLICE) + lane, X, F0);
   }
-  // pass 1: t_j = sum over the landmark's observations of Pbar^T C (Y x~_j)
-  M2 mn[GROUP];
-#pragma unroll
-  for (int k = 0; k < GROUP; ++k) mn[k] = 0u < len[k] ? sell_m[sb[k] + lane] : M2{0, 0};
+  T t[3] = {0, 0, 0};
   int gc = -1;
-  for (uint32_t r = 0; r < W; ++r) {
-    const uint32_t rl = r & (SLICE - 1);
-    if (rl == 0) stage_rows<T>(sm, grow_cam, r0 + r, min(W - r, (uint32_t)SLICE), vec, camP, true,
-                               lane, gc);
-    const int c = __shfl_sync(0xffffffffu, gc, (int)rl);
-    M2 m[GROUP];
+  // pass 1: t_j = sum over the landmark's observations of Pbar^T C (Y x~_j)
+  for (uint32_t c0 = 0; c0 < W; c0 += SLICE) {
+    const uint32_t nr = min(W - c0, (uint32_t)SLICE);
+    stage_rows<T>(sm, grow_cam, r0 + c0, nr, vec, camP, true, lane, gc);
+    for (uint32_t k0 = 0; k0 < nr; k0 += RB) {
+      M2 m[RB];
 #pragma unroll
-    for (int k = 0; k < GROUP; ++k) {
-      m[k] = mn[k];
-      mn[k] = r + 1 < len[k] ? sell_m[sb[k] + lane + (r + 1) * SLICE] : M2{0, 0};
-    }
-    if (c >= 0) {
-      const T* q = sm[rl];
-      T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        Y0[e] = q[e]; Y1[e] = q[4 + e]; Y2[e] = q[8 + e];
-        P0[e] = q[12 + e]; P1[e] = q[16 + e]; P2[e] = q[20 + e];
+      for (int u = 0; u < RB; ++u) {
+        const uint32_t r = c0 + k0 + u;
+        m[u] = (k0 + u < nr && r < len) ? ld_stream(sell_m + base + r * SLICE) : M2{0, 0};
       }
 #pragma unroll
-      for (int k = 0; k < GROUP; ++k)
-        if (r < len[k]) gather_obs<T>(Y0, Y1, Y2, P0, P1, P2, a, (T)m[k].x, (T)m[k].y, X[k], t[k]);
-    } else {
+      for (int u = 0; u < RB; ++u) {
+        if (k0 + u >= nr) break;  // warp-uniform
+        const uint32_t r = c0 + k0 + u;
+        const int c = __shfl_sync(0xffffffffu, gc, (int)(k0 + u));
+        if (c >= 0) {
+          if (r < len) {
+            const T* q = sm[k0 + u];
+            T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
 #pragma unroll
-      for (int k = 0; k < GROUP; ++k) {
-        if (r >= len[k]) continue;
-        const int i = sell_cam[sb[k] + lane + r * SLICE];
-        T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
-        load_row<T>(vec, i, 0, Y0);
-        load_row<T>(vec, i, 1, Y1);
-        load_row<T>(vec, i, 2, Y2);
-        load_row<T>(camP, i, 0, P0);
-        load_row<T>(camP, i, 1, P1);
-        load_row<T>(camP, i, 2, P2);
-        gather_obs<T>(Y0, Y1, Y2, P0, P1, P2, a, (T)m[k].x, (T)m[k].y, X[k], t[k]);
+            for (int e = 0; e < 4; ++e) {
+              Y0[e] = q[e]; Y1[e] = q[4 + e]; Y2[e] = q[8 + e];
+              P0[e] = q[12 + e]; P1[e] = q[16 + e]; P2[e] = q[20 + e];
+            }
+            gather_obs<T>(Y0, Y1, Y2, P0, P1, P2, a, (T)m[u].x, (T)m[u].y, X, t);
+          }
+        } else if (r < len) {
+          const int i = ld_stream(sell_cam + base + r * SLICE);
+          T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
+          load_row<T>(vec, i, 0, Y0);
+          load_row<T>(vec, i, 1, Y1);
+          load_row<T>(vec, i, 2, Y2);
+          load_row<T>(camP, i, 0, P0);
+          load_row<T>(camP, i, 1, P1);
+          load_row<T>(camP, i, 2, P2);
+          gather_obs<T>(Y0, Y1, Y2, P0, P1, P2, a, (T)m[u].x, (T)m[u].y, X, t);
+        }
       }
     }
   }
   // s_j = V_j^-1 t_j = F^T (F t_j)
-  T S[GROUP][3];
-#pragma unroll
-  for (int k = 0; k < GROUP; ++k) {
-    T Xk[3], F[6] = {0, 0, 0, 0, 0, 0};
-    if (k < ns) load_point<T>(pd, (int)((s0 + (uint32_t)k) * SLICE) + lane, Xk, F);
-    const T z0 = F[0] * t[k][0];
-    const T z1 = F[1] * t[k][0] + F[2] * t[k][1];
-    const T z2 = F[3] * t[k][0] + F[4] * t[k][1] + F[5] * t[k][2];
-    S[k][0] = F[0] * z0 + F[1] * z1 + F[3] * z2;
-    S[k][1] = F[2] * z1 + F[4] * z2;
-    S[k][2] = F[5] * z2;
+  T S[3];
+  {
+    T Xk[3], F[6];
+    load_point<T>(pd, (int)(s * SLICE) + lane, Xk, F);
+    const T z0 = F[0] * t[0];
+    const T z1 = F[1] * t[0] + F[2] * t[1];
+    const T z2 = F[3] * t[0] + F[4] * t[1] + F[5] * t[2];
+    S[0] = F[0] * z0 + F[1] * z1 + F[3] * z2;
+    S[1] = F[2] * z1 + F[4] * z2;
+    S[2] = F[5] * z2;
   }
   // pass 2: camera contributions vec((C Pbar s_j) x~_j^T); the staged rows of
-  // the first 32 group rows are still in place when W <= 32
+  // the first 32 rows are still in place when W <= 32
+  for (uint32_t c0 = 0; c0 < W; c0 += SLICE) {
+    const uint32_t nr = min(W - c0, (uint32_t)SLICE);
+    if (W > (uint32_t)SLICE)
+      stage_rows<T>(sm, grow_cam, r0 + c0, nr, vec, camP, false, lane, gc);
+    for (uint32_t k4 = 0; k4 < nr; k4 += 4) {
+      // the measurements of up to four rows are loaded together
+      M2 m4[4];
 #pragma unroll
-  for (int k = 0; k < GROUP; ++k) mn[k] = 0u < len[k] ? sell_m[sb[k] + lane] : M2{0, 0};
-  for (uint32_t r = 0; r < W; ++r) {
-    const uint32_t rl = r & (SLICE - 1);
-    if (rl == 0 && W > (uint32_t)SLICE)
-      stage_rows<T>(sm, grow_cam, r0 + r, min(W - r, (uint32_t)SLICE), vec, camP, false, lane,
-                    gc);
-    const int c = __shfl_sync(0xffffffffu, gc, (int)rl);
-    M2 m[GROUP];
-#pragma unroll
-    for (int k = 0; k < GROUP; ++k) {
-      m[k] = mn[k];
-      mn[k] = r + 1 < len[k] ? sell_m[sb[k] + lane + (r + 1) * SLICE] : M2{0, 0};
-    }
-    if (c >= 0) {
-      const T* q = sm[rl];
-      T P0[4], P1[4], P2[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        P0[e] = q[12 + e]; P1[e] = q[16 + e]; P2[e] = q[20 + e];
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t r = c0 + k4 + u;
+        m4[u] = (k4 + u < nr && r < len) ? ld_stream(sell_m + base + r * SLICE) : M2{0, 0};
       }
-      T v[12];
 #pragma unroll
-      for (int e = 0; e < 12; ++e) v[e] = 0;
+      for (int pr = 0; pr < 2; ++pr) {
+      const uint32_t k0 = k4 + 2 * pr;
+      if (k0 >= nr) break;  // warp-uniform
+      const bool two = k0 + 1 < nr;
+      const uint32_t rA = c0 + k0, rB = rA + 1;
+      const int cA = __shfl_sync(0xffffffffu, gc, (int)k0);
+      const int cB = __shfl_sync(0xffffffffu, gc, two ? (int)k0 + 1 : (int)k0);
+      const M2 mA = m4[2 * pr], mB = m4[2 * pr + 1];
+      if (two && cA >= 0 && cB >= 0) {
+        T vA[12], vB[12];
 #pragma unroll
-      for (int k = 0; k < GROUP; ++k)
-        if (r < len[k]) scatter_obs<T>(P0, P1, P2, a, (T)m[k].x, (T)m[k].y, S[k], X[k], v);
-      T red[3];
-      int vb;
-      warp_reduce12<T>(v, lane, red, vb);
-      if ((lane & 7) == 0) {
-        T* out = part + (size_t)__ldg(grow_base + r0 + r) * 12 + vb;
-        out[0] = red[0];
-        out[1] = red[1];
-        out[2] = red[2];
+        for (int e = 0; e < 12; ++e) vA[e] = vB[e] = 0;
+        if (rA < len) {
+          const T* q = sm[k0];
+          const T P0[4] = {q[12], q[13], q[14], q[15]}, P1[4] = {q[16], q[17], q[18], q[19]},
+                  P2[4] = {q[20], q[21], q[22], q[23]};
+          scatter_obs<T>(P0, P1, P2, a, (T)mA.x, (T)mA.y, S, X, vA);
+        }
+        if (rB < len) {
+          const T* q = sm[k0 + 1];
+          const T P0[4] = {q[12], q[13], q[14], q[15]}, P1[4] = {q[16], q[17], q[18], q[19]},
+                  P2[4] = {q[20], q[21], q[22], q[23]};
+          scatter_obs<T>(P0, P1, P2, a, (T)mB.x, (T)mB.y, S, X, vB);
+        }
+        T red[3];
+        int rowb, vb;
+        warp_reduce24<T>(vA, vB, lane, red, rowb, vb);
+        if ((lane & 3) == 0) {
+          T* out = part + (size_t)__ldg(grow_base + r0 + (rowb ? rB : rA)) * 12 + vb;
+          out[0] = red[0];
+          out[1] = red[1];
+          out[2] = red[2];
+        }
+        continue;
       }
-    } else {
+      // rows one at a time (an odd last row or a row that is not uniform)
 #pragma unroll
-      for (int k = 0; k < GROUP; ++k) {
-        if (r >= wid[k]) continue;  // warp-uniform
-        const uint32_t row = sb[k] / SLICE + r;
-        const uint32_t mask = __ldg(srow_mask + row), pbase = __ldg(srow_base + row);
-        const int i = r < len[k] ? sell_cam[sb[k] + lane + r * SLICE] : -1;
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !two) break;  // warp-uniform
+        const uint32_t r = h ? rB : rA;
+        const int c = h ? cB : cA;
+        const M2 mr = h ? mB : mA;
         T v[12];
 #pragma unroll
         for (int e = 0; e < 12; ++e) v[e] = 0;
-        if (i >= 0) {
-          T P0[4], P1[4], P2[4];
-          load_row<T>(camP, i, 0, P0);
-          load_row<T>(camP, i, 1, P1);
-          load_row<T>(camP, i, 2, P2);
-          scatter_obs<T>(P0, P1, P2, a, (T)m[k].x, (T)m[k].y, S[k], X[k], v);
-        }
-        if (mask == 0u) {
+        if (c >= 0) {
+          if (r < len) {
+            const T* q = sm[k0 + h];
+            const T P0[4] = {q[12], q[13], q[14], q[15]}, P1[4] = {q[16], q[17], q[18], q[19]},
+                    P2[4] = {q[20], q[21], q[22], q[23]};
+            scatter_obs<T>(P0, P1, P2, a, (T)mr.x, (T)mr.y, S, X, v);
+          }
           T red[3];
           int vb;
           warp_reduce12<T>(v, lane, red, vb);
           if ((lane & 7) == 0) {
-            T* out = part + (size_t)pbase * 12 + vb;
+            T* out = part + (size_t)__ldg(grow_base + r0 + r) * 12 + vb;
             out[0] = red[0];
             out[1] = red[1];
             out[2] = red[2];
           }
         } else {
-          store_runs<T>(v, mask, i >= 0, pbase, lane, part);
+          const uint32_t row = sb / SLICE + r;
+          const uint32_t mask = __ldg(srow_mask + row), pbase = __ldg(srow_base + row);
+          const int i = r < len ? ld_stream(sell_cam + base + r * SLICE) : -1;
+          if (i >= 0) {
+            T P0[4], P1[4], P2[4];
+            load_row<T>(camP, i, 0, P0);
+            load_row<T>(camP, i, 1, P1);
+            load_row<T>(camP, i, 2, P2);
+            scatter_obs<T>(P0, P1, P2, a, (T)mr.x, (T)mr.y, S, X, v);
+          }
+          if (mask == 0u) {
+            T red[3];
+            int vb;
+            warp_reduce12<T>(v, lane, red, vb);
+            if ((lane & 7) == 0) {
+              T* out = part + (size_t)pbase * 12 + vb;
+              out[0] = red[0];
+              out[1] = red[1];
+              out[2] = red[2];
+            }
+          } else {
+            store_runs<T>(v, mask, i >= 0, pbase, lane, part);
+          }
         }
+      }
       }
     }
   }
@@ -1237,7 +1301,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
     const unsigned gg = (unsigned)((p->ngroups + BLOCK / SLICE - 1) / (BLOCK / SLICE));
     if (precision == POVAR_FP64) {
       if (gg > 0)
-        k_series_grouped<double><<<gg, BLOCK, 0, p->stream>>>(
+        k_series_rows<double><<<gg, BLOCK, 0, p->stream>>>(
             p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0],
             p->P64[1], p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1),
             p->grp_slice0, p->grp_row0, p->ngroups, p->grow_cam, p->grow_base, p->srow_mask,
@@ -1248,7 +1312,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
           p->Y64 + yoff_out, p->D64);
     } else {
       if (gg > 0)
-        k_series_grouped<float><<<gg, BLOCK, 0, p->stream>>>(
+        k_series_rows<float><<<gg, BLOCK, 0, p->stream>>>(
             p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
             p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1),
             p->grp_slice0, p->grp_row0, p->ngroups, p->grow_cam, p->grow_base, p->srow_mask,
