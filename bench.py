@@ -184,6 +184,18 @@ def ncu_traffic(kernel_file: str, key: str):
     return int(m.group(1)) if m else None
 
 
+# ----------------------------------------------------------------- ranks
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (the timed region of a replica
+    run ends when the slowest rank ends); device is where the process group
+    reduces (a GPU under NCCL, the CPU under gloo)."""
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------- CPU oracle sample
 
 def cpu_oracle_sample(scene, g: dict, target: float, steps: int = 2) -> dict:
@@ -274,9 +286,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     per_solve = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
     phases, nsteps, nproducts = pb.profile(reset=True, products=True)
     sched, tune_ms = pb.tuning(prec)
     if args.schedule >= 0:
