@@ -509,3 +509,56 @@ def test_fp64_step_after_mixed_steps_uses_fp64_landmarks():
     with povar.Problem.from_scene(sc) as pb:
         pb.set_cameras(P2, sc.eta)
         assert pb.cost(sc.eta) == F_start
+
+
+def test_large_scene_fp64_trajectory_matches_oracle():
+    """Full size (1,800 cameras, 1,000,000 landmarks, ~5,000,000
+    observations): the FP64 path follows the oracle's stored trajectory from
+    the same random cameras (cost after each of the first 12 iterations, to
+    1e-9), and sampled landmarks at the GPU's cameras equal the oracle's
+    closed form (Eq. update_landmark) computed one by one on the CPU."""
+    import json
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", "converged_large.json")) as f:
+        g = json.load(f)
+    sc = scenes.scene_by_name("large", g["scene_seed"])
+    P0 = scenes.init_cameras(sc.n_cams, g["init_seed"], normalize=True)
+    prm = povar.make_params(eta=g["eta"], lambda0=g["lambda0"], m=g["m"],
+                            series_eps=g["series_eps"], manifold=povar.EUCLID,
+                            precision=povar.FP64, schedule=1)
+    trace = g["series"]["trace"]
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        for it in range(12):
+            rep = pb.step(prm)
+            F = rep.cost_after if rep.accepted else rep.cost_before
+            assert abs(F - trace[it][0]) <= 1e-9 * trace[it][0], (it, F, trace[it][0])
+        P = pb.cameras()
+        X = pb.points()
+    rng = np.random.default_rng(3)
+    keep = np.sort(rng.choice(sc.n_points, size=2000, replace=False))
+    sub = sc.subset_points(keep)
+    Xo = O.landmarks(P, sub.cam_idx, sub.pt_idx, sub.meas, sc.eta, sub.n_points)
+    assert np.all(np.abs(X[keep] - Xo) <= 1e-9 * (1.0 + np.abs(Xo)))
+
+
+def test_large_scene_mixed_reaches_oracle_target():
+    """Full size, mixed precision (FP32 series, double-float trial landmarks):
+    from the oracle's random start the solve reaches the oracle's 50-iteration
+    cost within 1e-5 relative in at most 60 iterations."""
+    import json
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", "converged_large.json")) as f:
+        g = json.load(f)
+    sc = scenes.scene_by_name("large", g["scene_seed"])
+    P0 = scenes.init_cameras(sc.n_cams, g["init_seed"], normalize=True)
+    prm = povar.make_params(eta=g["eta"], lambda0=g["lambda0"], m=g["m"],
+                            series_eps=g["series_eps"], manifold=povar.EUCLID,
+                            precision=povar.MIXED_FP32, schedule=-1)
+    target = g["series"]["F"] * (1.0 + 1e-5)
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        rep, iters = pb.solve(prm, max_iters=60, ftol=0.0, target_cost=target)
+        assert pb.cost(sc.eta) <= target, (pb.cost(sc.eta), target, iters)
