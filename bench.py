@@ -52,6 +52,7 @@ SERIES_KERNELS = {
     0: "series product (k_series_gather + k_series_scatter)",
     1: "series product (k_series_fused + k_series_apply)",
     2: "series product (k_series_gather + k_series_camrows)",
+    3: "series product (k_series_rows + k_series_apply)",
 }
 
 

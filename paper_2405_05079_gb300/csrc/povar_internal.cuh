@@ -147,7 +147,7 @@ struct Problem {
   void* part3 = nullptr;                // [npart3 * 12] float or double
   int schedule_default = 1;         // chosen at creation from the run statistics
   int tuned_schedule[2] = {-1, -1}; // autotuned series schedule per precision (-1: not yet)
-  float tune_ms[2][POVAR_NSCHEDULES] = {};  // measured ms of two series terms per schedule
+  float tune_ms[2][POVAR_NSCHEDULES] = {};  // measured ms per series term, per schedule
   // cameras
   double* P64[2] = {nullptr, nullptr};  // [nc*12]
   double* Ltab = nullptr;               // [nc*48] landmark tables at trial P
