@@ -60,6 +60,12 @@ def workload_scene(name: str):
     return scenes.scene_by_name(name, 0)
 
 
+def golden_name(args) -> str:
+    """Reference trajectory of the workload: the series at m = args.m terms
+    when given (mid scene), else the scene's default series length."""
+    return f"{args.workload}_m{args.m}" if getattr(args, "m", None) else args.workload
+
+
 def load_golden(name: str) -> dict:
     path = os.path.join(ROOT, "tests", "golden", f"converged_{name}.json")
     with open(path) as f:
@@ -247,7 +253,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     sc = workload_scene(args.workload)
-    g = load_golden(args.workload)
+    g = load_golden(golden_name(args))
     Fstar = g["series"]["F"]
     target = Fstar * (1.0 + REL_TARGET)
     P0 = scenes.init_cameras(sc.n_cams, g["init_seed"], normalize=True)
@@ -547,7 +553,7 @@ def run_reference(args, rank: int) -> dict | None:
     if rank != 0:
         return None
     sc = workload_scene(args.workload)
-    g = load_golden(args.workload)
+    g = load_golden(golden_name(args))
     target = g["series"]["F"] * (1.0 + REL_TARGET)
     vals = []
     last = None
@@ -579,6 +585,8 @@ def main(argv=None):
     ap.add_argument("--rate", type=float, default=40.0, help="serving: arrivals per second")
     ap.add_argument("--precision", default="mixed", choices=("mixed", "fp64"))
     ap.add_argument("--max-iters", type=int, default=200)
+    ap.add_argument("--m", type=int, default=None,
+                    help="series terms (mid scene: 5, 10 or 20, against the oracle run at that m)")
     ap.add_argument("--schedule", type=int, default=-1,
                     help="series schedule (-1: autotuned; a profiler distorts the tuning "
                          "timings, so profiled runs pin the schedule the plain run chose)")

@@ -12,7 +12,10 @@ oracle step (its dense S does not fit); small scenes also record the exact
 (dense Cholesky) mode from the same start. No value here comes from the
 CUDA path.
 
-    python tests/golden/make_golden.py [tiny] [mid] [large]
+"mid_m<k>" runs the mid scene with the series at m = k terms for the paper's
+50 iterations (no decrease rule), for the comparison of series lengths.
+
+    python tests/golden/make_golden.py [tiny] [mid] [large] [mid_m5] [mid_m10] [mid_m20]
 """
 import json
 import os
@@ -34,16 +37,19 @@ MAX_ITERS = {"tiny": 300, "mid": 3000, "large": 50}
 
 
 def run(name):
-    sc = scenes.scene_by_name(name, 0)
+    scene, m, ftol, max_iters = name, SETTINGS["m"], FTOL.get(name), MAX_ITERS.get(name)
+    if name.startswith("mid_m"):
+        scene, m, ftol, max_iters = "mid", int(name[len("mid_m"):]), 0.0, 50
+    sc = scenes.scene_by_name(scene, 0)
     P0 = scenes.init_cameras(sc.n_cams, 1, normalize=True)
-    cls = O.MatrixFreeProblem if name == "large" else O.Problem
+    cls = O.MatrixFreeProblem if scene == "large" else O.Problem
     pr = cls(sc.n_cams, sc.n_points, sc.cam_idx, sc.pt_idx, sc.meas)
-    out = {"scene": name, "scene_seed": 0, "init_seed": 1, "eta": sc.eta,
-           "ftol": FTOL[name], **SETTINGS,
+    out = {"scene": scene, "scene_seed": 0, "init_seed": 1, "eta": sc.eta,
+           "ftol": ftol, **SETTINGS, "m": m,
            "source": "tests/golden/make_golden.py (oracle/povar_oracle.py only)"}
-    solvers = ("series",) if name == "large" else ("series", "exact")
+    solvers = ("series",) if scene == "large" or name != scene else ("series", "exact")
     for solver in solvers:
-        prm = O.Params(eta=sc.eta, m=SETTINGS["m"], series_eps=SETTINGS["series_eps"],
+        prm = O.Params(eta=sc.eta, m=m, series_eps=SETTINGS["series_eps"],
                        manifold=O.EUCLID, solver=solver, lambda0=SETTINGS["lambda0"])
         t = time.time()
         trace = []
@@ -52,10 +58,10 @@ def run(name):
             trace.append([rep.cost_after if rep.accepted else rep.cost_before,
                           round(time.time() - t, 2), int(rep.terms_used)])
             print(name, solver, len(trace), trace[-1], flush=True)
-        st, reps = pr.solve(P0, prm, max_iters=MAX_ITERS[name], ftol=FTOL[name], callback=cb)
+        st, reps = pr.solve(P0, prm, max_iters=max_iters, ftol=ftol, callback=cb)
         out[solver] = {"F": st.F, "iterations": len(reps), "F0": reps[0].cost_before,
                        "seconds": time.time() - t, "trace": trace}
-        if solver == "series" and name != "large":
+        if solver == "series" and scene != "large":
             out[solver]["P"] = st.P.tolist()
         print(name, solver, len(reps), st.F, f"{time.time() - t:.1f}s", flush=True)
     with open(os.path.join(HERE, f"converged_{name}.json"), "w") as f:
