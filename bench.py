@@ -266,7 +266,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
 
     def one_solve():
         pb.set_cameras_device(dP0.data_ptr(), g["eta"])
-        rep, iters = pb.solve(params, max_iters=args.max_iters, ftol=0.0, target_cost=target)
+        rep, iters = pb.solve(params, max_iters=args.max_iters, ftol=0.0, target_cost=target,
+                              allow_stall=True)
         return rep, iters
 
     for _ in range(args.warmup):
@@ -310,7 +311,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             t0 = time.perf_counter()
             with povar.Problem.from_scene(sc, stream=stream.cuda_stream) as q:
                 q.set_cameras(P0, g["eta"])
-                q.solve(params, max_iters=args.max_iters, ftol=0.0, target_cost=target)
+                q.solve(params, max_iters=args.max_iters, ftol=0.0, target_cost=target,
+                        allow_stall=True)
                 Pout = q.cameras()
                 Fout = q.cost(g["eta"])
             times.append(time.perf_counter() - t0)

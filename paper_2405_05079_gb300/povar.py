@@ -229,11 +229,18 @@ class Problem:
         self._check(lib().povar_step(self._h, C.byref(params), C.byref(rep)))
         return rep
 
-    def solve(self, params: Params, max_iters=50, ftol=1e-6, target_cost=0.0):
+    def solve(self, params: Params, max_iters=50, ftol=1e-6, target_cost=0.0,
+              allow_stall=False):
+        """povar_solve. With allow_stall, a solve that ends with
+        POVAR_ENOTCONVERGED (the damping diverged: no step could lower the
+        cost any more) returns its report instead of raising; the cameras and
+        cost stay at the last accepted iterate."""
         rep = StepReport()
         it = C.c_int32()
-        self._check(lib().povar_solve(self._h, C.byref(params), max_iters, ftol, target_cost,
-                                      C.byref(rep), C.byref(it)))
+        st = lib().povar_solve(self._h, C.byref(params), max_iters, ftol, target_cost,
+                               C.byref(rep), C.byref(it))
+        if not (allow_stall and st == 6):
+            self._check(st)
         return rep, it.value
 
     def orders(self):
