@@ -46,3 +46,23 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(povar, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not found"):
         povar.lib()
+
+
+def test_create_rejects_empty_and_oversized_inputs_before_touching_the_device():
+    """n_obs = 0 and n_obs >= 2^31 (32-bit observation indices) are rejected by
+    the argument checks, before any CUDA call: this runs without a GPU."""
+    import ctypes as C
+    import numpy as np
+    from paper_2405_05079_gb300 import povar
+    L = povar.lib()
+    cam = np.zeros(4, np.int32)
+    pt = np.zeros(4, np.int32)
+    meas = np.zeros((4, 2))
+    h = C.c_void_p()
+    args = (cam.ctypes.data_as(C.POINTER(C.c_int32)), pt.ctypes.data_as(C.POINTER(C.c_int32)),
+            meas.ctypes.data_as(C.POINTER(C.c_double)), None, C.byref(h))
+    assert L.povar_create(1, 1, 0, *args) == 1          # empty observation set
+    assert L.povar_create(1, 1, 1 << 31, *args) == 1    # beyond 32-bit observation indices
+    assert L.povar_create(0, 1, 4, *args) == 1          # no camera
+    assert L.povar_create(1, 0, 4, *args) == 1          # no landmark
+    assert not h.value
