@@ -53,7 +53,12 @@ SERIES_KERNELS = {
     1: "series product (k_series_fused + k_series_apply)",
     2: "series product (k_series_gather + k_series_camrows)",
     3: "series product (k_series_rows + k_series_apply)",
+    4: "series product (k_series_fused on stored blocks + k_series_apply; per-step "
+       "k_build_blocks included)",
 }
+# bytes of one stored block G_k per observation, by precision name
+BLOCK_BYTES = {"fp64": 72, "mixed": 36, "bf16": 18}
+PRECISIONS = ("mixed", "fp64", "bf16")
 
 
 def workload_scene(name: str):
@@ -155,11 +160,20 @@ def measured_peaks() -> dict:
         return {}
 
 
-def series_bytes_per_term(n_obs: int, n_points: int) -> int:
+def series_bytes_per_term(n_obs: int, n_points: int, block_bytes: int = 0) -> int:
     """Algorithmic bytes of one series term in FP32: per observation a 4-byte
-    camera index and an 8-byte measurement; per landmark X (12 B), the
-    factor of V^-1 (24 B) and a 4-byte offset."""
-    return 12 * n_obs + 40 * n_points
+    camera index and an 8-byte measurement (or, in the stored schedule, the
+    camera index and the stored block G_k of block_bytes); per landmark X
+    (12 B), the factor of V^-1 (24 B) and a 4-byte offset."""
+    per_obs = 4 + block_bytes if block_bytes else 12
+    return per_obs * n_obs + 40 * n_points
+
+
+def block_build_bytes(n_obs: int, block_bytes: int) -> int:
+    """Algorithmic bytes of the per-step build of the stored blocks: per
+    observation the camera index and the FP32 measurement read, the block
+    written."""
+    return (4 + 8 + block_bytes) * n_obs
 
 
 def landmark_df_ops_per_launch(n_obs: int, n_points: int) -> int:
@@ -258,7 +272,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     target = Fstar * (1.0 + REL_TARGET)
     P0 = scenes.init_cameras(sc.n_cams, g["init_seed"], normalize=True)
     stream = torch.cuda.current_stream(dev)
-    prec = povar.FP64 if args.precision == "fp64" else povar.MIXED_FP32
+    prec = {"fp64": povar.FP64, "mixed": povar.MIXED_FP32,
+            "bf16": povar.MIXED_BF16}[args.precision]
     params = solver_params(povar, g, prec, args.schedule)
     pb = povar.Problem.from_scene(sc, stream=stream.cuda_stream)
     dP0 = torch.tensor(P0, dtype=torch.float64, device=dev)
@@ -296,7 +311,10 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     if dist is not None:
         total_ms = max_over_ranks(total_ms, dist, dev)
     phases, nsteps, nproducts = pb.profile(reset=True, products=True)
-    sched, tune_ms = pb.tuning(prec)
+    if prec == povar.MIXED_BF16:
+        sched, tune_ms = 4, []       # one schedule, not tuned
+    else:
+        sched, tune_ms = pb.tuning(prec)
     if args.schedule >= 0:
         sched = args.schedule
     clocks = clk.summary()
@@ -338,9 +356,13 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     # the step graph return at once and their time stays in the phase)
     products = max(nproducts, 1)
     terms_per_step = 1.0 + nproducts / steps_timed
-    bytes_term = series_bytes_per_term(sc.n_obs, sc.n_points)
-    series_gbs = bytes_term * products / (ms_series * 1e-3) / 1e9
-    if prec == povar.MIXED_FP32:
+    blk = BLOCK_BYTES[args.precision] if sched == 4 else 0
+    bytes_term = series_bytes_per_term(sc.n_obs, sc.n_points, blk)
+    # the series phase of a stored-schedule step also holds its block build
+    series_bytes = bytes_term * products + (block_build_bytes(sc.n_obs, blk) * steps_timed
+                                            if blk else 0)
+    series_gbs = series_bytes / (ms_series * 1e-3) / 1e9
+    if prec != povar.FP64:
         # double-float on the FP32 pipes: lane operations against the FP32 issue peak
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         lm_rate = (landmark_df_ops_per_launch(sc.n_obs, sc.n_points) * steps_timed
@@ -356,7 +378,9 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         lm_src = "nominal FP64 of the recipe (1.25 TFLOP/s)"
     roof_series = {"bound": "hbm", "achieved": round(series_gbs, 1), "peak": hbm,
                    "unit": "GB/s", "frac": round(series_gbs / hbm, 4),
-                   "traffic": ncu_traffic("series.cu", f"series_product_s{sched}"),
+                   "traffic": ncu_traffic("series.cu", f"series_product_s{sched}"
+                                          + ("_bf16" if prec == povar.MIXED_BF16 else "")),
+                   "algorithmic_bytes_per_product": bytes_term,
                    "kernel": SERIES_KERNELS.get(sched, "series term"),
                    "schedule": sched,
                    "us_per_product": round(ms_series * 1e3 / products, 2),
@@ -364,7 +388,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
                    "frac_of_8TBs": round(series_gbs / 8000.0, 4)}
     roof_lm = {"bound": "alu", "achieved": round(lm_rate, 1), "peak": round(lm_peak, 1),
                "unit": lm_unit, "frac": round(lm_rate / lm_peak, 4),
-               "traffic": ncu_traffic("landmark.cu", "landmark_df" if prec == povar.MIXED_FP32
+               "traffic": ncu_traffic("landmark.cu", "landmark_df" if prec != povar.FP64
                                       else "landmark"),
                "kernel": lm_kernel, "peak_source": lm_src}
     dominant = roof_series if ms_series >= phases["landmarks"] else roof_lm
@@ -374,7 +398,8 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         "metric": METRIC, "value": round(secs, 5), "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if prec == povar.MIXED_FP32 else "f64", "data": "synthetic",
+        "dtype": {povar.FP64: "f64", povar.MIXED_FP32: "f32+f64",
+                  povar.MIXED_BF16: "bf16-stored+f32+f64"}[prec], "data": "synthetic",
         "config": {"workload": (f"{args.workload}: {sc.n_cams} cams, {sc.n_points} landmarks, "
                                 f"{sc.n_obs} obs, {WORKLOAD_KIND[args.workload]}"),
                    "precision": args.precision, "manifold": "euclid (first stage, Sec. 3.2)",
@@ -585,7 +610,7 @@ def main(argv=None):
                     choices=("large", "mid", "tiny", "batched", "serving"))
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=40.0, help="serving: arrivals per second")
-    ap.add_argument("--precision", default="mixed", choices=("mixed", "fp64"))
+    ap.add_argument("--precision", default="mixed", choices=PRECISIONS)
     ap.add_argument("--max-iters", type=int, default=200)
     ap.add_argument("--m", type=int, default=None,
                     help="series terms (mid scene: 5, 10 or 20, against the oracle run at that m)")

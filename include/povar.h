@@ -50,7 +50,7 @@ typedef enum {
 } povar_status;
 
 enum { POVAR_EUCLID = 0, POVAR_SPHERE = 1 };
-enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1 };
+enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1, POVAR_MIXED_BF16 = 2 };
 
 /* Solver parameters (Sec. 5.2 of the paper gives eta = 0.1, lambda0 = 1e-4,
  * series order 20 with threshold 0.01).
@@ -70,6 +70,13 @@ enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1 };
  *  precision  POVAR_FP64: every kernel in FP64.
  *             POVAR_MIXED_FP32: series and linearization in FP32; landmark
  *             elimination, 12x12 inverses, cost and gain ratio in FP64.
+ *             POVAR_MIXED_BF16: POVAR_MIXED_FP32 whose series terms read the
+ *             stored blocks of schedule 4 in bfloat16 (18 bytes per
+ *             observation) and accumulate in FP32: the blocks are rounded,
+ *             so its steps differ from the FP32 ones by about the bfloat16
+ *             rounding (2^-9 relative per block entry). It always runs
+ *             schedule 4; params->schedule must be -1 or 4. The predicted
+ *             decrease is computed in FP32 from the unrounded factors.
  *  schedule   series schedule: 0 = landmark-major gather pass + camera-major
  *             scatter pass over observation chunks; 1 = one fused
  *             landmark-major pass whose camera contributions are reduced
@@ -79,9 +86,16 @@ enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1 };
  *             pass of 1 where the camera of every slice row whose lanes all
  *             see one camera comes from a per-row table, and the rows of
  *             those cameras are staged in shared memory before the row loop
- *             (no dependent global load per row); -1 = autotuned (see
- *             povar_get_tuning). All schedules compute the same series. */
-enum { POVAR_NSCHEDULES = 4 };
+ *             (no dependent global load per row); 4 = the fused pass of 1
+ *             reading, per observation, the stored 3x3 block
+ *             G_k = B_k^T B_k Pbar_i (B_k^T times the landmark Jacobian block
+ *             of Eq. pose; Pbar_i the left 3x3 of camera i), written once
+ *             per step at the current cameras (72 / 36 bytes per SELL entry
+ *             in FP64 / FP32, allocated at first use) instead of the camera
+ *             rows and the measurement; -1 = autotuned (see
+ *             povar_get_tuning). All schedules compute the same series (up
+ *             to rounding order). */
+enum { POVAR_NSCHEDULES = 5 };
 typedef struct {
   double eta;
   double lambda0;
@@ -214,10 +228,13 @@ povar_status povar_get_profile(povar_problem* p, double* ms_out, int64_t* steps_
 /* Series-schedule autotuner. The first povar_solve with params->schedule
  * = -1 times every schedule (0 .. POVAR_NSCHEDULES-1) on the live state
  * with CUDA events (one warm-up term, then three timed terms, two rounds)
- * and keeps the fastest for that precision; later solves and povar_step
- * with schedule -1 use it. povar_get_tuning returns the chosen schedule (-1
+ * and keeps the fastest for that precision; the per-step build of the
+ * stored blocks of schedule 4 is timed too and charged to that schedule
+ * spread over the m - 1 terms of a step. Later solves and povar_step with
+ * schedule -1 use it. povar_get_tuning returns the chosen schedule (-1
  * before tuning) and the measured milliseconds per series term
- * (ms_out[POVAR_NSCHEDULES], may be NULL). */
+ * (ms_out[POVAR_NSCHEDULES], may be NULL) for POVAR_FP64 or
+ * POVAR_MIXED_FP32 (POVAR_MIXED_BF16 is not tuned: POVAR_EINVAL). */
 povar_status povar_get_tuning(povar_problem* p, int32_t precision, int32_t* schedule_out,
                               float* ms_out);
 

@@ -65,11 +65,23 @@ povar_status check_params(Problem* p, const povar_params* q) {
   if (q->lambda_l != 0.0) return fail(p, POVAR_EINVAL, "lambda_l must be 0 (undamped V_0)");
   if (q->manifold != POVAR_EUCLID && q->manifold != POVAR_SPHERE)
     return fail(p, POVAR_EINVAL, "unknown manifold");
-  if (q->precision != POVAR_FP64 && q->precision != POVAR_MIXED_FP32)
+  if (q->precision != POVAR_FP64 && q->precision != POVAR_MIXED_FP32 &&
+      q->precision != POVAR_MIXED_BF16)
     return fail(p, POVAR_EINVAL, "unknown precision");
   if (q->schedule < -1 || q->schedule >= POVAR_NSCHEDULES)
     return fail(p, POVAR_EINVAL, "unknown schedule");
+  if (q->precision == POVAR_MIXED_BF16 && q->schedule != -1 && q->schedule != 4)
+    return fail(p, POVAR_EINVAL, "POVAR_MIXED_BF16 runs schedule 4 only");
   return POVAR_OK;
+}
+
+// Series schedule of a step: the explicit one, else the tuned one for the
+// precision, else the default chosen at creation; POVAR_MIXED_BF16 always
+// runs the stored schedule.
+int resolve_schedule(const Problem* p, const povar_params* q) {
+  if (q->precision == POVAR_MIXED_BF16) return 4;
+  const int tuned = p->tuned_schedule[q->precision == POVAR_FP64 ? 0 : 1];
+  return q->schedule >= 0 ? q->schedule : (tuned >= 0 ? tuned : p->schedule_default);
 }
 
 // Landmarks + cost at the current cameras for eta (no damping reset).
@@ -131,7 +143,10 @@ povar_status prepare_step(Problem* p, const povar_params* q) {
   // re-solved in FP64 at the current cameras
   if (q->precision == POVAR_FP64 && p->lm_df && (s = refresh_landmarks(p, q->eta)) != POVAR_OK)
     return s;
-  if (q->precision == POVAR_MIXED_FP32) p->lm_df = true;
+  if (q->precision != POVAR_FP64) p->lm_df = true;
+  // stored blocks are allocated here, outside any graph capture
+  if (resolve_schedule(p, q) == 4 && (s = ensure_blocks(p, block_kind(q->precision))) != POVAR_OK)
+    return s;
   return POVAR_OK;
 }
 
@@ -141,8 +156,7 @@ povar_status enqueue_step_kernels(Problem* p, const povar_params* q, std::vector
                                   const cudaEvent_t* fixed = nullptr) {
   povar_status s;
   const int prec = q->precision;
-  const int tuned = p->tuned_schedule[q->precision == POVAR_FP64 ? 0 : 1];
-  const int sched = q->schedule >= 0 ? q->schedule : (tuned >= 0 ? tuned : p->schedule_default);
+  const int sched = resolve_schedule(p, q);
   int nmark = 0;
   // phase boundary: a pooled event (eager profiling) or a fixed event node
   // (profiling inside the step graph)
@@ -159,6 +173,7 @@ povar_status enqueue_step_kernels(Problem* p, const povar_params* q, std::vector
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_camera_prepare(p, prec, q->manifold, q->eta)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
+  if (sched == 4 && q->m > 1 && (s = launch_build_blocks(p, prec, q->eta)) != POVAR_OK) return s;
   for (int k = 1; k < q->m; ++k)
     if ((s = launch_series_term(p, prec, q->eta, k, q->series_eps, sched)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
@@ -205,10 +220,14 @@ void sample_graph_profile(Problem* p, bool last_step_worked) {
 // Series-schedule autotuner: on the live state of the first step, run every
 // schedule for one untimed term (caches and instruction caches warm) and then
 // three timed terms, in two rounds over the schedules, and keep the schedule
-// with the smallest time per term for this precision. The damped blocks are
-// re-prepared afterwards, so the solve continues from exactly the state it
-// would have had without tuning.
+// with the smallest time per term for this precision. The stored schedule
+// (4) also pays its per-step block build, timed before its terms and spread
+// over the m - 1 terms of a step. The damped blocks are re-prepared
+// afterwards, so the solve continues from exactly the state it would have
+// had without tuning. POVAR_MIXED_BF16 has a single schedule and is not
+// tuned.
 povar_status autotune_schedule(Problem* p, const povar_params* q) {
+  if (q->precision == POVAR_MIXED_BF16) return POVAR_OK;
   const int prec = q->precision == POVAR_FP64 ? 0 : 1;
   if (p->tuned_schedule[prec] >= 0) return POVAR_OK;
   povar_status s;
@@ -221,6 +240,16 @@ povar_status autotune_schedule(Problem* p, const povar_params* q) {
   for (int sched = 0; sched < POVAR_NSCHEDULES; ++sched) p->tune_ms[prec][sched] = 1e30f;
   for (int round = 0; round < 2 && s == POVAR_OK; ++round) {
     for (int sched = 0; sched < POVAR_NSCHEDULES; ++sched) {
+      float build_ms = 0.f;
+      if (sched == 4) {
+        if ((s = ensure_blocks(p, block_kind(q->precision))) != POVAR_OK) break;
+        POVAR_CUDA(cudaEventRecord(ev[2], p->stream));
+        if ((s = launch_build_blocks(p, q->precision, q->eta)) != POVAR_OK) break;
+        POVAR_CUDA(cudaEventRecord(ev[3], p->stream));
+        POVAR_CUDA(cudaEventSynchronize(ev[3]));
+        POVAR_CUDA(cudaEventElapsedTime(&build_ms, ev[2], ev[3]));
+        build_ms /= (float)std::max(1, q->m - 1);
+      }
       if ((s = launch_camera_prepare(p, q->precision, q->manifold, q->eta)) != POVAR_OK) break;
       if ((s = launch_series_term(p, q->precision, q->eta, 1, 0.0, sched)) != POVAR_OK) break;
       POVAR_CUDA(cudaEventRecord(ev[0], p->stream));
@@ -231,7 +260,7 @@ povar_status autotune_schedule(Problem* p, const povar_params* q) {
       POVAR_CUDA(cudaEventSynchronize(ev[1]));
       float ms = 0.f;
       POVAR_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
-      ms /= 3.f;
+      ms = ms / 3.f + build_ms;
       if (ms < p->tune_ms[prec][sched]) p->tune_ms[prec][sched] = ms;
     }
   }
@@ -253,8 +282,7 @@ bool same_params(const povar_params& a, const povar_params& b) {
 
 // Graph of one step on p->gstream (captured once per parameter set).
 povar_status step_graph(Problem* p, const povar_params* q) {
-  const int tuned = p->tuned_schedule[q->precision == POVAR_FP64 ? 0 : 1];
-  const int sched = q->schedule >= 0 ? q->schedule : (tuned >= 0 ? tuned : p->schedule_default);
+  const int sched = resolve_schedule(p, q);
   if (p->gexec && same_params(p->gkey, *q) && p->gkey_sched == sched &&
       p->g_profiled == p->profiling)
     return POVAR_OK;
@@ -341,6 +369,9 @@ int64_t povar_estimate_bytes(int32_t n_cams, int32_t n_points, int64_t n_obs) {
   b += no * 8 + (nc + 1) * 4;
   // grouped schedule: group tables, group rows, slice-row runs, partials
   b += 2 * (npd / 32 + 1) * 4 + (nsell / 32) * 16 + no * (12 * 8 + 4) + (nc + 1) * 4;
+  // stored-block schedule: FP64, FP32 and BF16 blocks (each allocated at
+  // its first use)
+  b += nsell * (72 + 36 + 18);
   return b + (1 << 20);
 }
 

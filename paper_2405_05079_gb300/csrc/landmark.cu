@@ -591,7 +591,7 @@ povar_status launch_landmarks(Problem* p, int which_rel, double eta, int precisi
   }
   // trial landmarks of a mixed-precision step in double-float; every other
   // evaluation (and every FP64 step) in FP64
-  if (which_rel == 1 && precision == POVAR_MIXED_FP32)
+  if (which_rel == 1 && precision != POVAR_FP64)
     k_landmark_df<<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
         p->state, which_rel, df_host(1.0 - eta), df_host(eta), p->slot_len, p->sell_off, p->sell_cam, p->sell_mdf,
         p->Ltab_df, p->np, b, p->cost_part, p->pinv_part);

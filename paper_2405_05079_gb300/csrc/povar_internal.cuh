@@ -47,6 +47,17 @@ constexpr double PINV_COND = 1e12;
 constexpr double LAMBDA_MIN = 1e-8;   // damping floor
 constexpr double LAMBDA_MAX = 1e30;   // damping ceiling (solve reported as diverged)
 
+// Stored observation blocks G_k = C_k Pbar_i (3x3, row-major g[3r + q]) of
+// the stored series schedule, one per SELL entry e (E = max(nsell, 1)
+// entries per plane), in planes so that the loads of a slice row coalesce:
+//   FP64 (72 B): p[0..3] double2 (g0 g1)(g2 g3)(g4 g5)(g6 g7), p[4] double g8
+//   FP32 (36 B): p[0], p[1] float4 (g0..g3)(g4..g7), p[2] float g8
+//   BF16 (18 B): p[0] 8 x bf16 (g0..g7, g[2k] in the low half of word k),
+//                p[1] bf16 g8
+struct BlockPlanes {
+  void* p[5];
+};
+
 // Device-resident LM / VarPro controller state (one per problem).
 struct DeviceState {
   double F;          // cost at the current iterate
@@ -145,6 +156,9 @@ struct Problem {
   uint32_t* cam_part3_off = nullptr;    // [nc + 1]
   uint32_t* cam_part3_idx = nullptr;    // [npart3]
   void* part3 = nullptr;                // [npart3 * 12] float or double
+  // stored series blocks per kind (0 FP64, 1 FP32, 2 BF16), allocated at
+  // first use and rebuilt by every step that runs the stored schedule
+  void* blk[3] = {nullptr, nullptr, nullptr};
   int schedule_default = 1;         // chosen at creation from the run statistics
   int tuned_schedule[2] = {-1, -1}; // autotuned series schedule per precision (-1: not yet)
   float tune_ms[2][POVAR_NSCHEDULES] = {};  // measured ms per series term, per schedule
@@ -251,10 +265,18 @@ povar_status launch_camera_prepare(Problem* p, int precision, int manifold,
                                    double eta);
 
 // ---------------------------------------------------- series.cu (a7,a8)
-// schedule 0: point gather + camera-major scatter; 1: fused runs
+// schedule 0: point gather + camera-major scatter; 1: fused runs; 2: camera
+// rows; 3: row table; 4 (and every POVAR_MIXED_BF16 term): stored blocks
 povar_status launch_series_term(Problem* p, int precision, double eta,
                                 int term, double eps, int schedule);
 povar_status launch_pred(Problem* p, int precision, double eta, int manifold, int m);
+// Stored schedule (4) and the BF16 precision: block kind of a precision,
+// allocation (before any capture), plane pointers, and the per-step build of
+// G_k at the current cameras.
+int block_kind(int precision);
+povar_status ensure_blocks(Problem* p, int kind);
+BlockPlanes block_planes(const Problem* p, int kind);
+povar_status launch_build_blocks(Problem* p, int precision, double eta);
 
 // ---------------------------------------------------- step.cu (a9,a10)
 povar_status launch_update(Problem* p, int precision, int manifold);

@@ -17,6 +17,11 @@
 //     with one more gather pass at d and FP64 reductions.
 #include "povar_internal.cuh"
 
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <type_traits>
+
 namespace povar {
 namespace {
 
@@ -73,6 +78,80 @@ __device__ __forceinline__ float ld_stream(const float* p) {
   asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
   return v;
 }
+__device__ __forceinline__ double ld_stream(const double* p) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned short ld_stream(const unsigned short* p) {
+  unsigned short v;
+  asm("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return v;
+}
+
+// Stored observation blocks G_k = C_k Pbar_i (row-major 3x3, g[3r + q]),
+// one per SELL entry, in planes of BlockPlanes (layout in
+// povar_internal.cuh). Blk<TS> loads them as T and stores them from T.
+struct Bf16 {};   // storage tag: bfloat16, round to nearest even
+template <typename TS> struct Blk;
+template <> struct Blk<float> {
+  static __device__ __forceinline__ void load(const BlockPlanes& b, size_t e, float g[9]) {
+    const float4 x = ld_stream(static_cast<const float4*>(b.p[0]) + e);
+    const float4 y = ld_stream(static_cast<const float4*>(b.p[1]) + e);
+    g[0] = x.x; g[1] = x.y; g[2] = x.z; g[3] = x.w;
+    g[4] = y.x; g[5] = y.y; g[6] = y.z; g[7] = y.w;
+    g[8] = ld_stream(static_cast<const float*>(b.p[2]) + e);
+  }
+  static __device__ __forceinline__ void store(const BlockPlanes& b, size_t e, const float g[9]) {
+    static_cast<float4*>(b.p[0])[e] = make_float4(g[0], g[1], g[2], g[3]);
+    static_cast<float4*>(b.p[1])[e] = make_float4(g[4], g[5], g[6], g[7]);
+    static_cast<float*>(b.p[2])[e] = g[8];
+  }
+};
+template <> struct Blk<double> {
+  static __device__ __forceinline__ void load(const BlockPlanes& b, size_t e, double g[9]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double2 x = ld_stream(static_cast<const double2*>(b.p[k]) + e);
+      g[2 * k] = x.x;
+      g[2 * k + 1] = x.y;
+    }
+    g[8] = ld_stream(static_cast<const double*>(b.p[4]) + e);
+  }
+  static __device__ __forceinline__ void store(const BlockPlanes& b, size_t e, const double g[9]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      static_cast<double2*>(b.p[k])[e] = make_double2(g[2 * k], g[2 * k + 1]);
+    static_cast<double*>(b.p[4])[e] = g[8];
+  }
+};
+// A bfloat16 is the upper half of an FP32 word: widening is a shift.
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+template <> struct Blk<Bf16> {
+  static __device__ __forceinline__ void load(const BlockPlanes& b, size_t e, float g[9]) {
+    const uint4 x = ld_stream(static_cast<const uint4*>(b.p[0]) + e);
+    g[0] = bf16_lo(x.x); g[1] = bf16_hi(x.x); g[2] = bf16_lo(x.y); g[3] = bf16_hi(x.y);
+    g[4] = bf16_lo(x.z); g[5] = bf16_hi(x.z); g[6] = bf16_lo(x.w); g[7] = bf16_hi(x.w);
+    g[8] = bf16_lo((uint32_t)ld_stream(static_cast<const unsigned short*>(b.p[1]) + e));
+  }
+  static __device__ __forceinline__ void store(const BlockPlanes& b, size_t e, const float g[9]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[k] = bf16_bits(g[2 * k]) | (bf16_bits(g[2 * k + 1]) << 16);
+    static_cast<uint4*>(b.p[0])[e] = make_uint4(w[0], w[1], w[2], w[3]);
+    static_cast<unsigned short*>(b.p[1])[e] = (unsigned short)bf16_bits(g[8]);
+  }
+};
 
 template <typename T>
 struct PointData {
@@ -452,6 +531,17 @@ __device__ __forceinline__ void scatter_obs(const T P0[4], const T P1[4], const 
   v[8] += q2 * X[0]; v[9] += q2 * X[1]; v[10] += q2 * X[2]; v[11] += q2;
 }
 
+// v += vec((G s) x~^T) for one observation with its stored block G = C Pbar
+template <typename T>
+__device__ __forceinline__ void stored_obs(const T g[9], const T S[3], const T X[3], T v[12]) {
+  const T q0 = g[0] * S[0] + g[1] * S[1] + g[2] * S[2];
+  const T q1 = g[3] * S[0] + g[4] * S[1] + g[5] * S[2];
+  const T q2 = g[6] * S[0] + g[7] * S[1] + g[8] * S[2];
+  v[0] += q0 * X[0]; v[1] += q0 * X[1]; v[2] += q0 * X[2]; v[3] += q0;
+  v[4] += q1 * X[0]; v[5] += q1 * X[1]; v[6] += q1 * X[2]; v[7] += q1;
+  v[8] += q2 * X[0]; v[9] += q2 * X[1]; v[10] += q2 * X[2]; v[11] += q2;
+}
+
 // Segmented sum of v over the runs of equal camera that start at the set
 // bits of mask; the run starting at a valid lane stores its sum as the next
 // partial from pbase (valid run starts in lane order).
@@ -515,7 +605,46 @@ __device__ __forceinline__ void warp_reduce24(const T vA[12], const T vB[12], in
   vbase = (hiB ? 6 : 0) + (hiC ? 3 : 0);
 }
 
-template <typename T>
+// Stored schedule: the blocks G_k = C_k Pbar_i of every SELL entry at the
+// current cameras (zero for padding entries), written once per step before
+// the series terms, which then read G_k instead of the camera's Pbar and the
+// measurement: t_j += G_k^T (Y_i x~_j) and z_i += vec((G_k s_j) x~_j^T).
+template <typename T, typename TS>
+__global__ void __launch_bounds__(256)
+k_build_blocks(const DeviceState* __restrict__ st, T a, int64_t nsell,
+               const int32_t* __restrict__ sell_cam,
+               const typename Vt<T>::m2* __restrict__ sell_m, const T* __restrict__ camPa,
+               const T* __restrict__ camPb, BlockPlanes bp) {
+  if (st->converged) return;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nsell) return;
+  const int i = ld_stream(sell_cam + e);
+  T g[9];
+  if (i < 0) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = 0;
+  } else {
+    const T* __restrict__ camP = st->cur ? camPb : camPa;
+    T P0[4], P1[4], P2[4];
+    load_row<T>(camP, i, 0, P0);
+    load_row<T>(camP, i, 1, P1);
+    load_row<T>(camP, i, 2, P2);
+    const auto m = ld_stream(sell_m + e);
+    const T au = a * (T)m.x, av = a * (T)m.y;
+    const T aw = au * (T)m.x + av * (T)m.y;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      g[q] = P0[q] - au * P2[q];
+      g[3 + q] = P1[q] - av * P2[q];
+      g[6 + q] = aw * P2[q] - au * P0[q] - av * P1[q];
+    }
+  }
+  Blk<TS>::store(bp, (size_t)e, g);
+}
+
+// TS = void: factored (schedule 1); otherwise the stored blocks of storage TS
+// (schedule 4 / the BF16 precision). Both write the same run partials.
+template <typename T, typename TS>
 __global__ void __launch_bounds__(BLOCK)
 k_series_fused(const DeviceState* __restrict__ st, T a,
                const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
@@ -523,7 +652,9 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
                const typename Vt<T>::m2* __restrict__ sell_m, const T* __restrict__ camPa,
                const T* __restrict__ camPb, const T* __restrict__ vec, PointData<T> pd0,
                PointData<T> pd1, const uint32_t* __restrict__ row_mask,
-               const uint32_t* __restrict__ row_base, T* __restrict__ part) {
+               const uint32_t* __restrict__ row_base, T* __restrict__ part, BlockPlanes bp) {
+  constexpr bool STORED = !std::is_void<TS>::value;
+  using BS = typename std::conditional<STORED, TS, float>::type;
   if (st->converged || st->stop_series) return;
   const int s = blockIdx.x * BLOCK + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -547,12 +678,30 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
     for (int u = 0; u < RB; ++u) {
       const bool in = k0 + u < len;
       ci[u] = in ? ld_stream(sell_cam + base + (k0 + u) * SLICE) : 0;
-      mi[u] = in ? ld_stream(sell_m + base + (k0 + u) * SLICE) : M2{0, 0};
+      if constexpr (STORED)
+        mi[u] = M2{0, 0};   // unused
+      else
+        mi[u] = in ? ld_stream(sell_m + base + (k0 + u) * SLICE) : M2{0, 0};
     }
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
       if (k0 + u >= len) break;
       const int i = ci[u];
+      if constexpr (STORED) {
+        T g[9];
+        Blk<BS>::load(bp, base + (size_t)(k0 + u) * SLICE, g);
+        T Y0[4], Y1[4], Y2[4];
+        load_row<T>(vec, i, 0, Y0);
+        load_row<T>(vec, i, 1, Y1);
+        load_row<T>(vec, i, 2, Y2);
+        const T e0 = Y0[0] * X[0] + Y0[1] * X[1] + Y0[2] * X[2] + Y0[3];
+        const T e1 = Y1[0] * X[0] + Y1[1] * X[1] + Y1[2] * X[2] + Y1[3];
+        const T e2 = Y2[0] * X[0] + Y2[1] * X[1] + Y2[2] * X[2] + Y2[3];
+        t0 += g[0] * e0 + g[3] * e1 + g[6] * e2;
+        t1 += g[1] * e0 + g[4] * e1 + g[7] * e2;
+        t2 += g[2] * e0 + g[5] * e1 + g[8] * e2;
+        continue;
+      }
       const auto m = mi[u];
       T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
       load_row<T>(vec, i, 0, Y0);
@@ -592,8 +741,13 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
     for (int u = 0; u < RB; ++u) {
       const bool rin = k0 + u < width;
       const bool in = k0 + u < len;
-      ci[u] = in ? ld_stream(sell_cam + base + (k0 + u) * SLICE) : -1;
-      mi[u] = in ? ld_stream(sell_m + base + (k0 + u) * SLICE) : M2{0, 0};
+      if constexpr (STORED) {
+        ci[u] = in ? 0 : -1;   // only validity is needed
+        mi[u] = M2{0, 0};
+      } else {
+        ci[u] = in ? ld_stream(sell_cam + base + (k0 + u) * SLICE) : -1;
+        mi[u] = in ? ld_stream(sell_m + base + (k0 + u) * SLICE) : M2{0, 0};
+      }
       mk[u] = rin ? __ldg(row_mask + row0 + k0 + u) : 0u;
       bk[u] = rin ? __ldg(row_base + row0 + k0 + u) : 0u;
     }
@@ -610,11 +764,17 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
       for (int h = 0; h < 2; ++h) {
         const int i = ci[up + h];
         if (i >= 0) {
-          T P0[4], P1[4], P2[4];
-          load_row<T>(camP, i, 0, P0);
-          load_row<T>(camP, i, 1, P1);
-          load_row<T>(camP, i, 2, P2);
-          scatter_obs<T>(P0, P1, P2, a, (T)mi[up + h].x, (T)mi[up + h].y, Sv, X, h ? vB : vA);
+          if constexpr (STORED) {
+            T g[9];
+            Blk<BS>::load(bp, base + (size_t)(k0 + up + h) * SLICE, g);
+            stored_obs<T>(g, Sv, X, h ? vB : vA);
+          } else {
+            T P0[4], P1[4], P2[4];
+            load_row<T>(camP, i, 0, P0);
+            load_row<T>(camP, i, 1, P1);
+            load_row<T>(camP, i, 2, P2);
+            scatter_obs<T>(P0, P1, P2, a, (T)mi[up + h].x, (T)mi[up + h].y, Sv, X, h ? vB : vA);
+          }
         }
       }
       T r[3];
@@ -637,12 +797,18 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
 #pragma unroll
     for (int e = 0; e < 12; ++e) v[e] = 0;
     if (i >= 0) {
-      T P0[4], P1[4], P2[4];
-      load_row<T>(camP, i, 0, P0);
-      load_row<T>(camP, i, 1, P1);
-      load_row<T>(camP, i, 2, P2);
       const T Sv[3] = {S0, S1, S2};
-      scatter_obs<T>(P0, P1, P2, a, (T)m.x, (T)m.y, Sv, X, v);
+      if constexpr (STORED) {
+        T g[9];
+        Blk<BS>::load(bp, base + (size_t)(k0 + u) * SLICE, g);
+        stored_obs<T>(g, Sv, X, v);
+      } else {
+        T P0[4], P1[4], P2[4];
+        load_row<T>(camP, i, 0, P0);
+        load_row<T>(camP, i, 1, P1);
+        load_row<T>(camP, i, 2, P2);
+        scatter_obs<T>(P0, P1, P2, a, (T)m.x, (T)m.y, Sv, X, v);
+      }
     }
     if (mask == 0u) {
       T r[3];
@@ -1274,6 +1440,38 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
   // the series vector is double-buffered by term parity
   const size_t yoff_in = ((term - 1) & 1) * (size_t)p->nc * 12;
   const size_t yoff_out = (term & 1) * (size_t)p->nc * 12;
+  if (schedule == 4 || precision == POVAR_MIXED_BF16) {
+    const unsigned ga = (unsigned)p->nc;
+    const BlockPlanes bp = block_planes(p, block_kind(precision));
+    if (!bp.p[0]) return fail(p, POVAR_EINVAL, "stored blocks were not allocated");
+    if (precision == POVAR_FP64) {
+      k_series_fused<double, double><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+          p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0],
+          p->P64[1], p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1),
+          p->row_mask, p->row_base, static_cast<double*>(p->part_run), bp);
+      k_series_apply<double><<<ga, 128, 0, p->stream>>>(
+          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
+          static_cast<const double*>(p->part_run), p->G64, p->camnorm, p->done_ticket,
+          p->Y64 + yoff_out, p->D64);
+    } else {
+      if (precision == POVAR_MIXED_BF16)
+        k_series_fused<float, Bf16><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+            p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
+            p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1),
+            p->row_mask, p->row_base, static_cast<float*>(p->part_run), bp);
+      else
+        k_series_fused<float, float><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+            p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
+            p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1),
+            p->row_mask, p->row_base, static_cast<float*>(p->part_run), bp);
+      k_series_apply<float><<<ga, 128, 0, p->stream>>>(
+          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
+          static_cast<const float*>(p->part_run), p->G32, p->camnorm, p->done_ticket,
+          p->Y32 + yoff_out, p->D32);
+    }
+    p->launches += 2;
+    return check_launch(p, "series_term (stored blocks)");
+  }
   if (schedule == 2) {
     if (precision == POVAR_FP64) {
       k_series_gather<double, false><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
@@ -1328,19 +1526,19 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
   if (schedule == 1) {
     const unsigned ga = (unsigned)p->nc;
     if (precision == POVAR_FP64) {
-      k_series_fused<double><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+      k_series_fused<double, void><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
           p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0],
           p->P64[1], p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1), p->row_mask,
-          p->row_base, static_cast<double*>(p->part_run));
+          p->row_base, static_cast<double*>(p->part_run), BlockPlanes{});
       k_series_apply<double><<<ga, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
           static_cast<const double*>(p->part_run), p->G64, p->camnorm, p->done_ticket, p->Y64 + yoff_out,
           p->D64);
     } else {
-      k_series_fused<float><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+      k_series_fused<float, void><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
           p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
           p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1), p->row_mask,
-          p->row_base, static_cast<float*>(p->part_run));
+          p->row_base, static_cast<float*>(p->part_run), BlockPlanes{});
       k_series_apply<float><<<ga, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
           static_cast<const float*>(p->part_run), p->G32, p->camnorm, p->done_ticket, p->Y32 + yoff_out,
@@ -1377,6 +1575,58 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
     ++p->launches;
   }
   return check_launch(p, "series_term");
+}
+
+int block_kind(int precision) {
+  return precision == POVAR_FP64 ? 0 : precision == POVAR_MIXED_BF16 ? 2 : 1;
+}
+
+// Bytes of one SELL entry's stored block, per kind (FP64, FP32, BF16).
+static const int64_t kBlockBytes[3] = {72, 36, 18};
+
+povar_status ensure_blocks(Problem* p, int kind) {
+  if (p->blk[kind]) return POVAR_OK;
+  const int64_t E = std::max<int64_t>(p->nsell, 1);
+  return dev_alloc_bytes(p, &p->blk[kind], (size_t)(E * kBlockBytes[kind]), "stored blocks");
+}
+
+BlockPlanes block_planes(const Problem* p, int kind) {
+  BlockPlanes b{};
+  char* base = static_cast<char*>(p->blk[kind]);
+  if (!base) return b;
+  const size_t E = (size_t)std::max<int64_t>(p->nsell, 1);
+  if (kind == 0) {
+    for (int k = 0; k < 4; ++k) b.p[k] = base + 16 * E * k;
+    b.p[4] = base + 64 * E;
+  } else if (kind == 1) {
+    b.p[0] = base;
+    b.p[1] = base + 16 * E;
+    b.p[2] = base + 32 * E;
+  } else {
+    b.p[0] = base;
+    b.p[1] = base + 16 * E;
+  }
+  return b;
+}
+
+povar_status launch_build_blocks(Problem* p, int precision, double eta) {
+  const double a64 = 1.0 - eta;
+  const float a32 = (float)a64;
+  const BlockPlanes bp = block_planes(p, block_kind(precision));
+  if (!bp.p[0]) return fail(p, POVAR_EINVAL, "stored blocks were not allocated");
+  const unsigned g = grid_for(p->nsell, 256);
+  if (g == 0) return POVAR_OK;
+  if (precision == POVAR_FP64)
+    k_build_blocks<double, double><<<g, 256, 0, p->stream>>>(
+        p->state, a64, p->nsell, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1], bp);
+  else if (precision == POVAR_MIXED_BF16)
+    k_build_blocks<float, Bf16><<<g, 256, 0, p->stream>>>(
+        p->state, a32, p->nsell, p->sell_cam, p->sell_m32, p->camP32[0], p->camP32[1], bp);
+  else
+    k_build_blocks<float, float><<<g, 256, 0, p->stream>>>(
+        p->state, a32, p->nsell, p->sell_cam, p->sell_m32, p->camP32[0], p->camP32[1], bp);
+  ++p->launches;
+  return check_launch(p, "build_blocks");
 }
 
 povar_status launch_pred(Problem* p, int precision, double eta, int manifold, int m) {

@@ -6,7 +6,10 @@ Tolerances:
   step delta, trial cameras, predicted decrease);
 * mixed FP32 path: per step 1e-4 relative on the step (FP32 series), and the
   converged cost within 1e-5 relative of the oracle's converged cost with
-  normalized cameras within 1e-4.
+  normalized cameras within 1e-4;
+* bfloat16-stored blocks (POVAR_MIXED_BF16): per step m 2^-8 relative on the
+  step (the rounding of the blocks carried through m series terms), and the
+  same converged-cost bounds as the FP32 path.
 """
 import numpy as np
 import pytest
@@ -231,6 +234,36 @@ def test_one_step_mixed_close_to_oracle(scene, manifold, schedule):
     assert abs(rep.cost_after - orep.cost_after) <= 1e-4 * orep.cost_after
 
 
+@pytest.mark.parametrize("manifold", [O.SPHERE, O.EUCLID])
+def test_one_step_bf16_blocks_close_to_oracle(scene, manifold):
+    """POVAR_MIXED_BF16: the series reads the blocks G_k rounded to bfloat16
+    (relative error <= 2^-9 per entry). Each product M y uses G_k in both of
+    its passes, so M is perturbed by <= ~2^-8 relative, and the k-th term
+    M^k x_0 by <= ~k 2^-8; the step, a sum of m terms dominated by the first
+    ones, is bounded here by m 2^-8. The cost before the step is FP64 and
+    agrees to 1e-10."""
+    P0 = scenes.init_cameras(scene.n_cams, 4, normalize=True)
+    orc = oracle_for(scene)
+    op = O.Params(eta=scene.eta, m=scene.m, manifold=manifold)
+    _, orep = orc.step(orc.init_state(P0, op), op)
+    with povar.Problem.from_scene(scene) as pb:
+        pb.set_cameras(P0, scene.eta)
+        rep = pb.step(povar.make_params(eta=scene.eta, m=scene.m, manifold=manifold,
+                                        precision=povar.MIXED_BF16))
+        _, _, d = pb.last_step()
+    assert rel(d, orep.delta) <= scene.m * 2.0 ** -8
+    assert abs(rep.cost_before - orep.cost_before) <= 1e-10 * orep.cost_before
+
+
+def test_bf16_precision_accepts_only_the_stored_schedule():
+    sc = SCENES["tiny"]()
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(scenes.init_cameras(sc.n_cams, 1, normalize=True), sc.eta)
+        with pytest.raises(povar.PovarError):
+            pb.step(povar.make_params(eta=sc.eta, m=5, precision=povar.MIXED_BF16, schedule=1))
+        pb.step(povar.make_params(eta=sc.eta, m=5, precision=povar.MIXED_BF16, schedule=4))
+
+
 def _golden(name):
     import json
     import os
@@ -257,7 +290,7 @@ def _affine_aligned_error(P, Pref):
 
 
 def test_solve_reaches_oracle_converged_cost_tiny():
-    """Both GPU precisions, run to convergence from the oracle's start with the
+    """Every GPU precision (FP64, FP32 series, bfloat16-stored blocks), run to convergence from the oracle's start with the
     paper's settings, reach the oracle's converged cost
     (tests/golden/converged_tiny.json, written from the oracle only) within
     1e-5 relative, with gauge-aligned unit-normalized cameras within 1e-4."""
@@ -266,7 +299,7 @@ def test_solve_reaches_oracle_converged_cost_tiny():
     P0 = scenes.init_cameras(sc.n_cams, g["init_seed"], normalize=True)
     Fstar = g["series"]["F"]
     Pref = np.array(g["series"]["P"])
-    for prec in (povar.FP64, povar.MIXED_FP32):
+    for prec in (povar.FP64, povar.MIXED_FP32, povar.MIXED_BF16):
         with povar.Problem.from_scene(sc) as pb:
             pb.set_cameras(P0, sc.eta)
             pb.solve(_golden_params(g, prec), max_iters=g["series"]["iterations"] + 50,
@@ -356,15 +389,17 @@ def test_schedules_agree_bitwise_in_fp64_up_to_rounding():
         assert rel(out[k], out[0]) <= 1e-12, k
 
 
-@pytest.mark.parametrize("precision", [povar.FP64, povar.MIXED_FP32])
-def test_graph_solve_equals_eager_steps(precision):
+@pytest.mark.parametrize("precision,schedule",
+                         [(povar.FP64, 1), (povar.MIXED_FP32, 1), (povar.FP64, 4),
+                          (povar.MIXED_FP32, 4), (povar.MIXED_BF16, 4)])
+def test_graph_solve_equals_eager_steps(precision, schedule):
     """povar_solve runs every step as one captured CUDA graph; the kernels and
     reduction orders are the same as the eager povar_step path, so the
     iterates agree bit for bit."""
     sc = SCENES["traj"]()
     P0 = scenes.init_cameras(sc.n_cams, 2, normalize=True)
     prm = povar.make_params(eta=sc.eta, m=9, series_eps=0.01, manifold=povar.EUCLID,
-                            precision=precision, schedule=1)
+                            precision=precision, schedule=schedule)
     with povar.Problem.from_scene(sc) as a, povar.Problem.from_scene(sc) as b:
         a.set_cameras(P0, sc.eta)
         b.set_cameras(P0, sc.eta)
