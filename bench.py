@@ -533,11 +533,17 @@ def run_serving(args) -> dict:
             for k, s in enumerate(scs)]
     mixed = family_params(povar, povar.MIXED_FP32)
     fp64 = family_params(povar, povar.FP64)
+    m_table = None
+    if args.m_table:
+        with open(args.m_table) as f:
+            m_table = json.load(f)
     # warm-up: library load, first graph captures, allocator
     warm = [serving.Request(rid=k, arrival=0.0, scene=r.scene, P0=r.P0)
             for k, r in enumerate(reqs[:4])]
-    serving.Server(mixed, budget_bytes=40 << 30, slots=8, max_iters=50, ftol=1e-6).run(warm)
-    srv = serving.Server(mixed, budget_bytes=40 << 30, slots=8, max_iters=50, ftol=1e-6)
+    serving.Server(mixed, budget_bytes=40 << 30, slots=8, max_iters=50, ftol=1e-6,
+                   m_table=m_table).run(warm)
+    srv = serving.Server(mixed, budget_bytes=40 << 30, slots=8, max_iters=50, ftol=1e-6,
+                         m_table=m_table)
     t0 = time.perf_counter()
     res = srv.run(reqs)
     wall = time.perf_counter() - t0
@@ -558,6 +564,8 @@ def run_serving(args) -> dict:
                                 f"{sum(s.n_obs for s in scs)} obs), 100 points per camera, "
                                 f"mean track 5, Poisson arrivals at {args.rate}/s"),
                    "budget_bytes": 40 << 30, "slots": 8,
+                   "series_terms": (f"per size class from {args.m_table}" if m_table
+                                    else "m = 21 (Sec. 5.2)"),
                    "stop": "rel. decrease < 1e-6 or 50 iterations (Sec. 5.2)"},
         "latency_p50_s": round(st["latency_p50_s"], 4),
         "latency_p99_s": round(st["latency_p99_s"], 4),
@@ -611,6 +619,9 @@ def main(argv=None):
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=40.0, help="serving: arrivals per second")
     ap.add_argument("--precision", default="mixed", choices=PRECISIONS)
+    ap.add_argument("--m-table", default=None,
+                    help="serving workload: series lengths per size class from a table of "
+                         "the series-length autotuner (paper_2405_05079_gb300/autotune.py)")
     ap.add_argument("--max-iters", type=int, default=200)
     ap.add_argument("--m", type=int, default=None,
                     help="series terms (mid scene: 5, 10 or 20, against the oracle run at that m)")

@@ -102,8 +102,8 @@ def profiles(traces: dict, taus=TAUS, alphas=ALPHAS) -> dict:
 # ------------------------------------------------------------------ GPU runs
 
 def default_solvers(povar):
-    """Solver variants of the family: (name, precision, series terms m,
-    camera parametrization)."""
+    """Solver variants of the family: (name, precision, series terms m (or a
+    function of the scene giving m), camera parametrization)."""
     return [("mixed m=21", povar.MIXED_FP32, 21, povar.EUCLID),
             ("fp64 m=21", povar.FP64, 21, povar.EUCLID),
             ("mixed m=11", povar.MIXED_FP32, 11, povar.EUCLID),
@@ -134,8 +134,10 @@ def time_to_targets(problems, solvers, eta: float, taus=TAUS, max_iters: int = 5
     for k, sc in enumerate(problems):
         P0 = scenes.init_cameras(sc.n_cams, seed + k, normalize=True)
         with povar.Problem.from_scene(sc) as pb:
-            prms = {name: povar.make_params(eta=eta, lambda0=1e-4, m=m, series_eps=0.01,
-                                            manifold=man, precision=prec)
+            # m is a number of terms, or a function of the scene (a tuned policy)
+            prms = {name: povar.make_params(eta=eta, lambda0=1e-4,
+                                            m=int(m(sc) if callable(m) else m),
+                                            series_eps=0.01, manifold=man, precision=prec)
                     for name, prec, m, man in solvers}
             final = {}
             for name in prms:

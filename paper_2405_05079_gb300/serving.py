@@ -64,11 +64,15 @@ class Server:
     """Admission by device-memory budget, one stream and one worker per slot."""
 
     def __init__(self, params, budget_bytes: int, slots: int = 8, max_iters: int = 50,
-                 ftol: float = 1e-6):
+                 ftol: float = 1e-6, m_table: dict | None = None):
+        """m_table: a series-length table of the autotuner (autotune.py); when
+        given, each request runs with the m of its size class instead of
+        params.m."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the serving loop needs a CUDA device")
         self.params = params
+        self.m_table = m_table
         self.budget = int(budget_bytes)
         self.slots = int(slots)
         self.max_iters = int(max_iters)
@@ -78,6 +82,16 @@ class Server:
         self._lock = threading.Lock()
         self._used = 0
 
+    def params_for(self, scene):
+        """Solver parameters of a request: params, with the tuned m of the
+        scene's size class when the server has an m table."""
+        if self.m_table is None:
+            return self.params
+        from .autotune import m_for
+        q = povar.Params.from_buffer_copy(self.params)
+        q.m = m_for(self.m_table, scene.n_obs)
+        return q
+
     def _solve(self, req: Request, slot: int, t0: float, admitted: float, reserved: int):
         stream = self.streams[slot].cuda_stream
         sc = req.scene
@@ -85,8 +99,8 @@ class Server:
             with povar.Problem.from_scene(sc, stream=stream) as pb:
                 actual = pb.device_bytes
                 pb.set_cameras(req.P0, self.params.eta)
-                _, iters = pb.solve(self.params, max_iters=self.max_iters, ftol=self.ftol,
-                                    target_cost=req.target_cost)
+                _, iters = pb.solve(self.params_for(sc), max_iters=self.max_iters,
+                                    ftol=self.ftol, target_cost=req.target_cost)
                 cost = pb.cost(self.params.eta)
                 cams = pb.cameras()
         finally:

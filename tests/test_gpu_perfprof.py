@@ -38,3 +38,19 @@ def test_time_to_targets_on_small_family():
     for tau, rows in prof.items():
         assert sum(r[0] for r in rows.values()) >= 100.0 - 1e-9
         assert all(np.all(np.diff(r) >= 0) for r in rows.values())
+
+
+def test_series_length_tuner_on_small_family():
+    """The tuner's table holds a candidate m for every size class it saw,
+    chosen by the profile of the measured times; the tuned policy then runs
+    through the same harness."""
+    from paper_2405_05079_gb300 import autotune as at
+    fam = scenes.family_scenes("batched", 4, seed=5)
+    tab = at.tune(fam, eta=0.1, tau=0.003, candidates=(6, 21), max_iters=20, seed=5)
+    assert tab["rows"] and all(r["m"] in (6, 21) for r in tab["rows"])
+    assert sum(r["problems"] for r in tab["rows"]) == len(fam)
+    for r in tab["rows"]:
+        assert max(r["reached"].values()) >= 1
+    ev = at.evaluate(tab, fam[:2], eta=0.1, tau=0.003, fixed_m=21, max_iters=20, seed=5)
+    assert set(ev["rho"]) == {"m=21", "tuned"}
+    assert sum(r[0] for r in ev["rho"].values()) >= 100.0 - 1e-9
