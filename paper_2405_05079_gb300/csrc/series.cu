@@ -542,6 +542,91 @@ __device__ __forceinline__ void stored_obs(const T g[9], const T S[3], const T X
   v[8] += q2 * X[0]; v[9] += q2 * X[1]; v[10] += q2 * X[2]; v[11] += q2;
 }
 
+// q = C Pbar s for one observation: its W-scatter contribution is vec(q x~^T)
+template <typename T>
+__device__ __forceinline__ void scatter_q(const T P0[4], const T P1[4], const T P2[4], T a,
+                                          T mu, T mv, const T S[3], T q[3]) {
+  const T w0 = P0[0] * S[0] + P0[1] * S[1] + P0[2] * S[2];
+  const T w1 = P1[0] * S[0] + P1[1] * S[1] + P1[2] * S[2];
+  const T w2 = P2[0] * S[0] + P2[1] * S[1] + P2[2] * S[2];
+  const T au = a * mu, av = a * mv;
+  const T aw = au * mu + av * mv;
+  q[0] = w0 - au * w2;
+  q[1] = w1 - av * w2;
+  q[2] = aw * w2 - au * w0 - av * w1;
+}
+
+// q = G s for one observation with its stored block G = C Pbar
+template <typename T>
+__device__ __forceinline__ void stored_q(const T g[9], const T S[3], T q[3]) {
+  q[0] = g[0] * S[0] + g[1] * S[1] + g[2] * S[2];
+  q[1] = g[3] * S[0] + g[4] * S[1] + g[5] * S[2];
+  q[2] = g[6] * S[0] + g[7] * S[1] + g[8] * S[2];
+}
+
+// The columns of x~ = (X, 1) in the order in which reduce_rows halves them on
+// this lane: lane bit 8 puts the pair {2, 3} first, lane bit 4 swaps within
+// each pair, so that every halving stage keeps its first half. cfin is the
+// column the lane holds at the end.
+template <typename T>
+__device__ __forceinline__ void stage_columns(const T X[3], int lane, T xp[4], int& cfin) {
+  const bool hB = lane & 8, hC = lane & 4;
+  const T one = 1;
+  const T lo0 = hC ? X[1] : X[0], lo1 = hC ? X[0] : X[1];
+  const T hi0 = hC ? one : X[2], hi1 = hC ? X[2] : one;
+  xp[0] = hB ? hi0 : lo0;
+  xp[1] = hB ? hi1 : lo1;
+  xp[2] = hB ? lo0 : hi0;
+  xp[3] = hB ? lo1 : hi1;
+  cfin = (hB ? 2 : 0) + (hC ? 1 : 0);
+}
+
+// Sums over the 32 lanes of vec(q x~^T) for two consecutive warp-uniform
+// slice rows (row A from every lane's qa, row B from qb); a single uniform
+// row keeps warp_reduce12, whose cost this does not beat with an empty row B. Lanes with bit 16 own row B: in the
+// first stage each lane keeps its row's q and sends the other row's q (3
+// values instead of 12 products), and adds the partner's outer product with
+// the partner's columns xq. The 12 sums are held column-major (3c + r) in the
+// lane's stage order xp, so the stages over lane bits 8 and 4 keep the first
+// half with no select; bits 2 and 1 finish the sums. Lanes with (lane & 3) ==
+// 0 store entries cfin, 4 + cfin, 8 + cfin of their row's partial (outA /
+// outB; a null pointer skips the row).
+template <typename T>
+__device__ __forceinline__ void reduce_rows(const T qa[3], const T qb[3], const T xp[4],
+                                            const T xq[4], int lane, int cfin, T* outA,
+                                            T* outB) {
+  const bool hA = lane & 16;
+  T qk[3], qo[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const T keep = hA ? qb[r] : qa[r];
+    const T send = hA ? qa[r] : qb[r];
+    qk[r] = keep;
+    qo[r] = __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  T r12[12];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) r12[3 * c + r] = qk[r] * xp[c] + qo[r] * xq[c];
+  T r6[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) r6[j] = r12[j] + __shfl_xor_sync(0xffffffffu, r12[6 + j], 8);
+  T r3[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    r3[j] = r6[j] + __shfl_xor_sync(0xffffffffu, r6[3 + j], 4);
+    r3[j] += __shfl_xor_sync(0xffffffffu, r3[j], 2);
+    r3[j] += __shfl_xor_sync(0xffffffffu, r3[j], 1);
+  }
+  T* out = hA ? outB : outA;
+  if ((lane & 3) == 0 && out) {
+    out[cfin] = r3[0];
+    out[4 + cfin] = r3[1];
+    out[8 + cfin] = r3[2];
+  }
+}
+
 // Segmented sum of v over the runs of equal camera that start at the set
 // bits of mask; the run starting at a valid lane stores its sum as the next
 // partial from pbase (valid run starts in lane order).
@@ -730,7 +815,6 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
   const T S1 = F[2] * z1 + F[4] * z2;
   const T S2 = F[5] * z2;
   const uint32_t row0 = sbeg / SLICE;
-  const uint32_t lt_mask = (1u << lane) - 1u;
   // pass 2 in chunks of RB slice rows: the rows' camera indices,
   // measurements and run metadata are loaded together
   for (uint32_t k0 = 0; k0 < width; k0 += RB) {
@@ -756,9 +840,7 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
     if (k0 + up >= width) break;
     // two consecutive uniform rows are reduced across the warp together
     if (k0 + up + 1 < width && mk[up] == 0u && mk[up + 1] == 0u) {
-      T vA[12], vB[12];
-#pragma unroll
-      for (int e = 0; e < 12; ++e) vA[e] = vB[e] = 0;
+      T qA[3] = {0, 0, 0}, qB[3] = {0, 0, 0};
       const T Sv[3] = {S0, S1, S2};
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -767,23 +849,23 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
           if constexpr (STORED) {
             T g[9];
             Blk<BS>::load(bp, base + (size_t)(k0 + up + h) * SLICE, g);
-            stored_obs<T>(g, Sv, X, h ? vB : vA);
+            stored_q<T>(g, Sv, h ? qB : qA);
           } else {
             T P0[4], P1[4], P2[4];
             load_row<T>(camP, i, 0, P0);
             load_row<T>(camP, i, 1, P1);
             load_row<T>(camP, i, 2, P2);
-            scatter_obs<T>(P0, P1, P2, a, (T)mi[up + h].x, (T)mi[up + h].y, Sv, X, h ? vB : vA);
+            scatter_q<T>(P0, P1, P2, a, (T)mi[up + h].x, (T)mi[up + h].y, Sv, h ? qB : qA);
           }
         }
       }
-      T r[3];
-      int rowb, vb;
-      warp_reduce24<T>(vA, vB, lane, r, rowb, vb);
-      if ((lane & 3) == 0) {
-        T* out = part + (size_t)(rowb ? bk[up + 1] : bk[up]) * 12 + vb;
-        out[0] = r[0]; out[1] = r[1]; out[2] = r[2];
-      }
+      T xp[4], xq[4];
+      int cfin;
+      stage_columns<T>(X, lane, xp, cfin);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) xq[c] = __shfl_xor_sync(0xffffffffu, xp[c], 16);
+      reduce_rows<T>(qA, qB, xp, xq, lane, cfin, part + (size_t)bk[up] * 12,
+                     part + (size_t)bk[up + 1] * 12);
       continue;
     }
 #pragma unroll
