@@ -405,11 +405,6 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
   if (n_cams < 1 || n_points < 1 || n_obs < 1 || n_obs >= (int64_t)1 << 31 || !cam_idx ||
       !pt_idx || !meas)
     return POVAR_EINVAL;
-  for (int64_t k = 0; k < n_obs; ++k) {
-    if (cam_idx[k] < 0 || cam_idx[k] >= n_cams || pt_idx[k] < 0 || pt_idx[k] >= n_points)
-      return POVAR_EINVAL;
-    if (!std::isfinite(meas[2 * k]) || !std::isfinite(meas[2 * k + 1])) return POVAR_EINVAL;
-  }
   povar_problem* pp = new (std::nothrow) povar_problem();
   if (!pp) return POVAR_ENOMEM;
   Problem* p = &pp->impl;

@@ -246,6 +246,175 @@ __global__ void k_to_u32(const int32_t* __restrict__ src, uint32_t* __restrict__
   if (i < n) dst[i] = (uint32_t)src[i];
 }
 
+// Input check before any index is used: every camera and landmark index in
+// range and every measurement finite; flag bit 0 set otherwise.
+__global__ void k_validate(const int32_t* __restrict__ cam, const int32_t* __restrict__ pt,
+                           const double* __restrict__ meas, int64_t n, int nc, int np,
+                           uint32_t* __restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (i < n) {
+    const int32_t c = cam[i], j = pt[i];
+    bad = c < 0 || c >= nc || j < 0 || j >= np || !isfinite(meas[2 * i]) ||
+          !isfinite(meas[2 * i + 1]);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+// Longest track (stats[0]) and whether some landmark has no observation
+// (stats[1] = 1).
+__global__ void k_len_stats(const uint32_t* __restrict__ len, int np,
+                            uint32_t* __restrict__ stats) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t l = j < np ? len[j] : 1u;
+  const uint32_t mx = __reduce_max_sync(0xffffffffu, l);
+  const bool empty = __any_sync(0xffffffffu, j < np && l == 0u);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(stats, mx);
+    if (empty) atomicOr(stats + 1, 1u);
+  }
+}
+
+// Slice order (every slice is its own group, GROUP = 1): full slice sl of
+// the sorted landmark order gets the key maxlen - (its longest track), so a
+// stable ascending sort puts the widest slices first and keeps the sorted
+// order among equal widths.
+__global__ void k_full_slice_keys(const uint32_t* __restrict__ order,
+                                  const uint32_t* __restrict__ len, int nfull, uint32_t maxlen,
+                                  uint32_t* __restrict__ wkey, uint32_t* __restrict__ wval) {
+  const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= nfull) return;
+  uint32_t w = 0;
+  for (int l = 0; l < SLICE; ++l) w = max(w, len[order[(size_t)sl * SLICE + l]]);
+  wkey[sl] = maxlen - w;
+  wval[sl] = (uint32_t)sl;
+}
+
+// Slot q: the full slices in the width order sl_order, then the remaining
+// landmarks of the sorted order (the last partial slice), then padding.
+__global__ void k_slot_fill(const uint32_t* __restrict__ order,
+                            const uint32_t* __restrict__ sl_order,
+                            const uint32_t* __restrict__ len, int np, int np_pad, int nfull,
+                            uint32_t* __restrict__ slot_pt, uint32_t* __restrict__ slot_len,
+                            uint32_t* __restrict__ pt_slot) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= np_pad) return;
+  uint32_t j = 0xffffffffu;
+  const int sl = q / SLICE;
+  if (sl < nfull) j = order[(size_t)sl_order[sl] * SLICE + (q % SLICE)];
+  else if (q < np) j = order[q];
+  slot_pt[q] = j;
+  slot_len[q] = j == 0xffffffffu ? 0u : len[j];
+  if (j != 0xffffffffu) pt_slot[j] = (uint32_t)q;
+}
+
+// Run table of the fused schedule, one warp per slice row (the row's 32
+// camera indices, -1 for padding). A row whose valid lanes all see one
+// camera is uniform: mask 0, its camera in rcam, one partial. Otherwise bit l
+// of the mask marks a lane whose camera differs from lane l - 1's (bit 0
+// always), rcam = -1, and every marked lane with a valid camera opens a
+// partial. nvis counts the row's distinct valid cameras (its camera-row
+// visits).
+__global__ void k_row_runs(const int32_t* __restrict__ cam, int64_t nrows,
+                           uint32_t* __restrict__ mask, int32_t* __restrict__ rcam,
+                           uint32_t* __restrict__ npart, uint32_t* __restrict__ nvis) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nrows) return;  // the whole warp
+  const int32_t c = cam[row * SLICE + lane];
+  const bool valid = c >= 0;
+  const uint32_t vb = __ballot_sync(0xffffffffu, valid);
+  const int32_t c0 = __shfl_sync(0xffffffffu, c, vb ? __ffs(vb) - 1 : 0);
+  const bool uniform = vb != 0u && __ballot_sync(0xffffffffu, valid && c != c0) == 0u;
+  const int32_t prev = __shfl_up_sync(0xffffffffu, c, 1);
+  const uint32_t start = __ballot_sync(0xffffffffu, lane == 0 || c != prev);
+  const uint32_t same = __match_any_sync(0xffffffffu, c);
+  const uint32_t firsts = __ballot_sync(0xffffffffu, valid && __ffs(same) - 1 == lane);
+  if (lane == 0) {
+    mask[row] = uniform ? 0u : start;
+    rcam[row] = uniform ? c0 : -1;
+    npart[row] = uniform ? 1u : (uint32_t)__popc(start & vb);
+    nvis[row] = (uint32_t)__popc(firsts);
+  }
+}
+
+// Cameras of the partials (pcam, in partial order) and the camera-row visits
+// (vcam, vrow: the row's distinct valid cameras in lane order), at the
+// row offsets pbase and vbase.
+__global__ void k_row_fill(const int32_t* __restrict__ cam, int64_t nrows,
+                           const uint32_t* __restrict__ mask, const int32_t* __restrict__ rcam,
+                           const uint32_t* __restrict__ pbase, const uint32_t* __restrict__ vbase,
+                           uint32_t* __restrict__ pcam, uint32_t* __restrict__ vcam,
+                           uint32_t* __restrict__ vrow) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nrows) return;  // the whole warp
+  const int32_t c = cam[row * SLICE + lane];
+  const bool valid = c >= 0;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t vb = __ballot_sync(0xffffffffu, valid);
+  const uint32_t m = mask[row];
+  if (m == 0u) {
+    if (lane == 0) pcam[pbase[row]] = (uint32_t)rcam[row];
+  } else {
+    const uint32_t sv = m & vb;
+    if ((sv >> lane) & 1u) pcam[pbase[row] + __popc(sv & lt)] = (uint32_t)c;
+  }
+  const uint32_t same = __match_any_sync(0xffffffffu, c);
+  const uint32_t firsts = __ballot_sync(0xffffffffu, valid && __ffs(same) - 1 == lane);
+  if ((firsts >> lane) & 1u) {
+    const uint32_t q = vbase[row] + __popc(firsts & lt);
+    vcam[q] = (uint32_t)c;
+    vrow[q] = (uint32_t)row;
+  }
+}
+
+// Slice of every slice row.
+__global__ void k_row_slice(const uint32_t* __restrict__ sell_off, int nslices,
+                            uint32_t* __restrict__ row_slice) {
+  const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= nslices) return;
+  for (uint32_t r = sell_off[sl] / SLICE; r < sell_off[sl + 1] / SLICE; ++r) row_slice[r] = sl;
+}
+
+// Camera-row lists: visit q of the camera-sorted order is the row vrow[v]
+// (v = vidx[q]), given as the SELL position of the row and the slot of its
+// lane 0.
+__global__ void k_visit_fill(const uint32_t* __restrict__ vidx, const uint32_t* __restrict__ vrow,
+                             const uint32_t* __restrict__ row_slice, int64_t nvis,
+                             uint32_t* __restrict__ pos0, uint32_t* __restrict__ slot0) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nvis) return;
+  const uint32_t row = vrow[vidx[q]];
+  pos0[q] = row * SLICE;
+  slot0[q] = row_slice[row] * SLICE;
+}
+
+// Tables of the grouped schedule with one slice per group: group g is slice
+// g, its rows are the slice rows, and the partial space is the fused one.
+__global__ void k_group_tables(int64_t nrows, const uint32_t* __restrict__ mask,
+                               const int32_t* __restrict__ rcam,
+                               const uint32_t* __restrict__ pbase,
+                               int32_t* __restrict__ grow_cam, uint32_t* __restrict__ grow_base,
+                               uint32_t* __restrict__ srow_mask,
+                               uint32_t* __restrict__ srow_base) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const bool u = rcam[r] >= 0;
+  grow_cam[r] = rcam[r];
+  grow_base[r] = u ? pbase[r] : 0u;
+  srow_mask[r] = u ? 0u : mask[r];
+  srow_base[r] = u ? 0u : pbase[r];
+}
+
+__global__ void k_group_rows(const uint32_t* __restrict__ sell_off, int nslices,
+                             uint32_t* __restrict__ grp_slice0, uint32_t* __restrict__ grp_row0) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g > nslices) return;
+  grp_slice0[g] = (uint32_t)g;
+  grp_row0[g] = sell_off[g] / SLICE;
+}
+
 int bits_for(uint64_t maxval) {
   int b = 0;
   while (b < 32 && (maxval >> b) != 0) ++b;
@@ -333,11 +502,24 @@ povar_status radix_sort(Problem* p, Scratch& sc, uint32_t** k, uint32_t** v, int
 povar_status build_runs(Problem* p);
 
 povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt) {
+  (void)h_cam;
   (void)h_pt;
   Scratch sc;
   const int64_t n = p->nobs;
   const unsigned gb = grid_for(n, 256);
   povar_status s;
+
+  // ---- indices in range and measurements finite, before any index is used
+  {
+    uint32_t* flag = sc.get<uint32_t>(1);
+    if (!flag) return fail(p, POVAR_ENOMEM, "validation scratch");
+    POVAR_CUDA(cudaMemsetAsync(flag, 0, sizeof(uint32_t), p->stream));
+    k_validate<<<gb, 256, 0, p->stream>>>(p->d_cam, p->d_pt, p->d_meas, n, p->nc, p->np, flag);
+    ++p->launches;
+    uint32_t h_flag = 0;
+    POVAR_COPY(&h_flag, flag, 1, cudaMemcpyDeviceToHost);
+    if (h_flag) return fail(p, POVAR_EINVAL, "index out of range or non-finite measurement");
+  }
 
   // ---- point-major and camera-major stable orders
   for (int which = 0; which < 2; ++which) {
@@ -385,16 +567,16 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
   k_point_stats<<<gp, 256, 0, p->stream>>>(p->off_pt, p->perm_pt, p->d_cam, p->np, len,
                                            mincam);
   ++p->launches;
-  std::vector<uint32_t> h_off(p->np + 1);
-  POVAR_CUDA(cudaMemcpyAsync(h_off.data(), p->off_pt, (p->np + 1) * sizeof(uint32_t),
-                             cudaMemcpyDeviceToHost, p->stream));
-  POVAR_CUDA(cudaStreamSynchronize(p->stream));
-  uint32_t maxlen = 0;
-  for (int j = 0; j < p->np; ++j) {
-    const uint32_t l = h_off[j + 1] - h_off[j];
-    if (l == 0) return fail(p, POVAR_EINVAL, "landmark without observations");
-    maxlen = std::max(maxlen, l);
-  }
+  // longest track, and every landmark must be observed
+  uint32_t* stats = sc.get<uint32_t>(2);
+  if (!stats) return fail(p, POVAR_ENOMEM, "slot scratch");
+  POVAR_CUDA(cudaMemsetAsync(stats, 0, 2 * sizeof(uint32_t), p->stream));
+  k_len_stats<<<gp, 256, 0, p->stream>>>(len, p->np, stats);
+  ++p->launches;
+  uint32_t h_stats[2] = {0, 0};
+  POVAR_COPY(h_stats, stats, 2, cudaMemcpyDeviceToHost);
+  if (h_stats[1]) return fail(p, POVAR_EINVAL, "landmark without observations");
+  const uint32_t maxlen = h_stats[0];
   const int len_bits = bits_for(maxlen);
   const int cam_bits = bits_for((uint64_t)(p->nc - 1));
   const int use_cam = (len_bits + cam_bits <= 32) ? 1 : 0;
@@ -406,56 +588,29 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
     if ((s = radix_sort(p, sc, &kk, &vv, p->np, use_cam ? len_bits + cam_bits : len_bits)) !=
         POVAR_OK)
       return s;
-    // Full slices of the sorted order are grouped: up to GROUP consecutive
-    // slices whose first landmarks share the smallest camera (their rows
-    // then tend to see the same camera, row by row). Groups are ordered by
-    // width (longest track first, stable) so that the warps of a block get
-    // similar work; the last partial slice and the pads stay at the end,
-    // one group each.
-    std::vector<uint32_t> order(p->np), h_len(p->np), h_min(p->np);
-    POVAR_COPY(order.data(), vv, p->np, cudaMemcpyDeviceToHost);
-    POVAR_COPY(h_len.data(), len, p->np, cudaMemcpyDeviceToHost);
-    POVAR_COPY(h_min.data(), mincam, p->np, cudaMemcpyDeviceToHost);
+    // Full slices of the sorted order are ordered by width (longest track
+    // first, stable) so that the warps of a block get similar work; the last
+    // partial slice and the pads stay at the end. Every slice is its own
+    // group (GROUP = 1).
+    static_assert(GROUP == 1, "the slot order and the run tables take one slice per group");
     const int nfull = p->np / SLICE;
-    std::vector<uint32_t> width(nfull, 0);
-    for (int sl = 0; sl < nfull; ++sl)
-      for (int l = 0; l < SLICE; ++l) width[sl] = std::max(width[sl], h_len[order[sl * SLICE + l]]);
-    std::vector<std::pair<int, int>> groups;  // [first, last) sorted slices
-    for (int sl = 0; sl < nfull;) {
-      int e = sl + 1;
-      while (e < nfull && e - sl < GROUP && h_min[order[e * SLICE]] == h_min[order[sl * SLICE]]) ++e;
-      groups.emplace_back(sl, e);
-      sl = e;
+    const uint32_t* sl_order = nullptr;
+    if (nfull > 0) {
+      uint32_t* wkey = sc.get<uint32_t>(nfull);
+      uint32_t* wval = sc.get<uint32_t>(nfull);
+      if (!wkey || !wval) return fail(p, POVAR_ENOMEM, "slice scratch");
+      k_full_slice_keys<<<grid_for(nfull, 256), 256, 0, p->stream>>>(vv, len, nfull, maxlen,
+                                                                     wkey, wval);
+      ++p->launches;
+      uint32_t *wk = wkey, *wv = wval;
+      if ((s = radix_sort(p, sc, &wk, &wv, nfull, bits_for(maxlen))) != POVAR_OK) return s;
+      sl_order = wv;
     }
-    std::vector<uint32_t> gwidth(groups.size(), 0);
-    for (size_t g = 0; g < groups.size(); ++g)
-      for (int sl = groups[g].first; sl < groups[g].second; ++sl)
-        gwidth[g] = std::max(gwidth[g], width[sl]);
-    std::vector<int> g_order(groups.size());
-    for (size_t g = 0; g < groups.size(); ++g) g_order[g] = (int)g;
-    std::stable_sort(g_order.begin(), g_order.end(),
-                     [&](int x, int y) { return gwidth[x] > gwidth[y]; });
-    std::vector<int> sl_order;
-    sl_order.reserve(nfull);
-    p->h_grp_slice0.assign(1, 0u);
-    for (int g : g_order) {
-      for (int sl = groups[g].first; sl < groups[g].second; ++sl) sl_order.push_back(sl);
-      p->h_grp_slice0.push_back((uint32_t)sl_order.size());
-    }
-    for (int sl = nfull; sl < p->nslices; ++sl) p->h_grp_slice0.push_back((uint32_t)sl + 1);
-    p->ngroups = (int32_t)p->h_grp_slice0.size() - 1;
-    std::vector<uint32_t> slot_pt(p->np_pad, 0xffffffffu), slot_len(p->np_pad, 0),
-        pt_slot(p->np);
-    for (int sl = 0; sl < nfull; ++sl)
-      for (int l = 0; l < SLICE; ++l) slot_pt[sl * SLICE + l] = order[sl_order[sl] * SLICE + l];
-    for (int q = nfull * SLICE; q < p->np; ++q) slot_pt[q] = order[q];
-    for (int q = 0; q < p->np; ++q) {
-      slot_len[q] = h_len[slot_pt[q]];
-      pt_slot[slot_pt[q]] = (uint32_t)q;
-    }
-    POVAR_COPY(p->slot_pt, slot_pt.data(), p->np_pad, cudaMemcpyHostToDevice);
-    POVAR_COPY(p->slot_len, slot_len.data(), p->np_pad, cudaMemcpyHostToDevice);
-    POVAR_COPY(p->pt_slot, pt_slot.data(), (size_t)p->np, cudaMemcpyHostToDevice);
+    k_slot_fill<<<grid_for(p->np_pad, 256), 256, 0, p->stream>>>(
+        vv, sl_order, len, p->np, p->np_pad, nfull, p->slot_pt, p->slot_len, p->pt_slot);
+    ++p->launches;
+    if ((s = check_launch(p, "slot order")) != POVAR_OK) return s;
+    p->ngroups = p->nslices;
   }
   // ---- SELL offsets
   uint32_t* w = sc.get<uint32_t>(p->nslices + 1);
@@ -530,213 +685,112 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
 // row; otherwise bit l is set when lane l starts a run (bit 0 always set).
 // row_base is the index of the row's first partial. The partials of camera
 // i are listed, in increasing index, at cam_part_idx[cam_part_off[i] ..).
-povar_status build_group_runs(Problem* p, const std::vector<int32_t>& cam,
-                              const std::vector<uint32_t>& off);
-
+// The same pass lists, per camera, the slice rows that contain it (camera-row
+// schedule), and the grouped schedule's tables follow from the runs (one
+// slice per group). Everything is built on the device: per-row counts (one
+// warp per row), exclusive scans, per-row fills, and stable radix sorts by
+// camera for the per-camera lists.
 povar_status build_runs(Problem* p) {
   povar_status s;
+  Scratch sc;
   const int64_t nrows = p->nsell / SLICE;
-  std::vector<int32_t> cam(p->nsell);
-  std::vector<uint32_t> off(p->nslices + 1);
-  POVAR_COPY(cam.data(), p->sell_cam, p->nsell, cudaMemcpyDeviceToHost);
-  POVAR_COPY(off.data(), p->sell_off, (p->nslices + 1), cudaMemcpyDeviceToHost);
-  std::vector<uint32_t> mask(std::max<int64_t>(nrows, 1)), base(std::max<int64_t>(nrows, 1));
-  std::vector<int32_t> pcam;
-  pcam.reserve(nrows + nrows / 4);
-  for (int64_t row = 0; row < nrows; ++row) {
-    const int32_t* c = cam.data() + row * SLICE;
-    int32_t c0 = -1;
-    bool uniform = true;
-    for (int l = 0; l < SLICE; ++l) {
-      if (c[l] < 0) continue;
-      if (c0 < 0) c0 = c[l];
-      else if (c[l] != c0) uniform = false;
-    }
-    base[row] = (uint32_t)pcam.size();
-    if (uniform && c0 >= 0) {
-      mask[row] = 0;
-      pcam.push_back(c0);
-      continue;
-    }
-    uint32_t m = 0;
-    for (int l = 0; l < SLICE; ++l) {
-      if (l == 0 || c[l] != c[l - 1]) {
-        m |= 1u << l;
-        if (c[l] >= 0) pcam.push_back(c[l]);
-      }
-    }
-    mask[row] = m;
-  }
-  // camera-row lists: every distinct valid camera of every slice row
-  std::vector<uint32_t> voff(p->nc + 1, 0);
-  std::vector<std::pair<uint32_t, uint32_t>> vis;  // (camera, row) in row order
-  {
-    std::vector<uint32_t> row_slice(std::max<int64_t>(nrows, 1), 0);
-    for (int sl = 0; sl < p->nslices; ++sl)
-      for (uint32_t r = off[sl] / SLICE; r < off[sl + 1] / SLICE; ++r) row_slice[r] = sl;
-    vis.reserve(nrows + nrows / 4);
-    int32_t seen[SLICE];
-    for (int64_t row = 0; row < nrows; ++row) {
-      const int32_t* c = cam.data() + row * SLICE;
-      int nseen = 0;
-      for (int l = 0; l < SLICE; ++l) {
-        if (c[l] < 0) continue;
-        bool dup = false;
-        for (int q = 0; q < nseen; ++q) dup |= seen[q] == c[l];
-        if (!dup) {
-          seen[nseen++] = c[l];
-          vis.emplace_back((uint32_t)c[l], (uint32_t)row);
-        }
-      }
-    }
-    for (const auto& v : vis) ++voff[v.first + 1];
-    for (int c = 0; c < p->nc; ++c) voff[c + 1] += voff[c];
-    std::vector<uint32_t> cursor(voff.begin(), voff.end() - 1);
-    std::vector<uint32_t> pos0(std::max<size_t>(vis.size(), 1)), slot0(std::max<size_t>(vis.size(), 1));
-    for (const auto& v : vis) {
-      const uint32_t q = cursor[v.first]++;
-      pos0[q] = v.second * SLICE;
-      slot0[q] = row_slice[v.second] * SLICE;
-    }
-    p->nvisits = (int64_t)vis.size();
-    if ((s = dev_alloc(p, &p->cam_row_off, voff.size(), "cam_row_off")) ||
-        (s = dev_alloc(p, &p->cam_row_pos0, pos0.size(), "cam_row_pos0")) ||
-        (s = dev_alloc(p, &p->cam_row_slot0, slot0.size(), "cam_row_slot0")))
-      return s;
-    POVAR_COPY(p->cam_row_off, voff.data(), voff.size(), cudaMemcpyHostToDevice);
-    POVAR_COPY(p->cam_row_pos0, pos0.data(), pos0.size(), cudaMemcpyHostToDevice);
-    POVAR_COPY(p->cam_row_slot0, slot0.data(), slot0.size(), cudaMemcpyHostToDevice);
-  }
-  const int64_t npart = (int64_t)pcam.size();
-  std::vector<uint32_t> poff(p->nc + 1, 0), pidx(std::max<int64_t>(npart, 1));
-  for (int32_t c : pcam) ++poff[c + 1];
-  for (int c = 0; c < p->nc; ++c) poff[c + 1] += poff[c];
-  {
-    std::vector<uint32_t> cursor(poff.begin(), poff.end() - 1);
-    for (int64_t q = 0; q < npart; ++q) pidx[cursor[pcam[q]]++] = (uint32_t)q;
-  }
+  const unsigned gw = grid_for(nrows * SLICE, 256);   // one warp per row
+  const unsigned gr = grid_for(nrows, 256);
+  int32_t* rcam = sc.get<int32_t>(nrows);
+  uint32_t* nvis = sc.get<uint32_t>(nrows + 1);
+  uint32_t* row_slice = sc.get<uint32_t>(nrows);
+  if (!rcam || !nvis || !row_slice) return fail(p, POVAR_ENOMEM, "run scratch");
+  if ((s = dev_alloc(p, &p->row_mask, std::max<int64_t>(nrows, 1), "row_mask")) ||
+      (s = dev_alloc(p, &p->row_base, nrows + 1, "row_base")))
+    return s;
+  POVAR_CUDA(cudaMemsetAsync(p->row_base, 0, (nrows + 1) * sizeof(uint32_t), p->stream));
+  POVAR_CUDA(cudaMemsetAsync(nvis, 0, (nrows + 1) * sizeof(uint32_t), p->stream));
+  k_row_runs<<<gw, 256, 0, p->stream>>>(p->sell_cam, nrows, p->row_mask, rcam, p->row_base,
+                                        nvis);
+  ++p->launches;
+  if ((s = check_launch(p, "row runs")) != POVAR_OK) return s;
+  // counts -> offsets; the last entries hold the totals
+  if ((s = scan_exclusive(p, sc, p->row_base, nrows + 1)) != POVAR_OK) return s;
+  if ((s = scan_exclusive(p, sc, nvis, nrows + 1)) != POVAR_OK) return s;
+  uint32_t npart = 0, nvisit = 0;
+  POVAR_COPY(&npart, p->row_base + nrows, 1, cudaMemcpyDeviceToHost);
+  POVAR_COPY(&nvisit, nvis + nrows, 1, cudaMemcpyDeviceToHost);
+  if (npart == 0 || nvisit == 0) return fail(p, POVAR_EINVAL, "no observation in the layout");
+  uint32_t* pcam = sc.get<uint32_t>(npart);
+  uint32_t* pval = sc.get<uint32_t>(npart);
+  uint32_t* vcam = sc.get<uint32_t>(nvisit);
+  uint32_t* vrow = sc.get<uint32_t>(nvisit);
+  uint32_t* vval = sc.get<uint32_t>(nvisit);
+  if (!pcam || !pval || !vcam || !vrow || !vval) return fail(p, POVAR_ENOMEM, "run scratch");
+  k_row_fill<<<gw, 256, 0, p->stream>>>(p->sell_cam, nrows, p->row_mask, rcam, p->row_base, nvis,
+                                        pcam, vcam, vrow);
+  k_row_slice<<<grid_for(p->nslices, 256), 256, 0, p->stream>>>(p->sell_off, p->nslices,
+                                                                row_slice);
+  k_iota<<<grid_for(npart, 256), 256, 0, p->stream>>>(pval, npart);
+  k_iota<<<grid_for(nvisit, 256), 256, 0, p->stream>>>(vval, nvisit);
+  p->launches += 4;
+  if ((s = check_launch(p, "row fill")) != POVAR_OK) return s;
+  const int cbits = bits_for((uint64_t)(p->nc - 1));
+
+  // partials of each camera in index order
   p->nrows = nrows;
   p->npart = npart;
+  if ((s = dev_alloc(p, &p->cam_part_off, (size_t)p->nc + 1, "cam_part_off")) ||
+      (s = dev_alloc(p, &p->cam_part_idx, npart, "cam_part_idx")) ||
+      (s = dev_alloc_bytes(p, &p->part_run, (size_t)npart * 12 * sizeof(double), "part_run")))
+    return s;
+  {
+    uint32_t *kk = pcam, *vv = pval;
+    if ((s = radix_sort(p, sc, &kk, &vv, npart, cbits)) != POVAR_OK) return s;
+    POVAR_CUDA(cudaMemcpyAsync(p->cam_part_idx, vv, (size_t)npart * sizeof(uint32_t),
+                               cudaMemcpyDeviceToDevice, p->stream));
+    k_offsets<<<grid_for(npart, 256), 256, 0, p->stream>>>(kk, npart, p->nc, p->cam_part_off);
+    ++p->launches;
+  }
+  std::vector<uint32_t> poff((size_t)p->nc + 1);
+  POVAR_COPY(poff.data(), p->cam_part_off, poff.size(), cudaMemcpyDeviceToHost);
   p->nc_parts = 0;
   for (int c = 0; c < p->nc; ++c) p->nc_parts += poff[c + 1] > poff[c] ? 1 : 0;
-  if ((s = dev_alloc(p, &p->row_mask, mask.size(), "row_mask")) ||
-      (s = dev_alloc(p, &p->row_base, base.size(), "row_base")) ||
-      (s = dev_alloc(p, &p->cam_part_off, poff.size(), "cam_part_off")) ||
-      (s = dev_alloc(p, &p->cam_part_idx, pidx.size(), "cam_part_idx")) ||
-      (s = dev_alloc_bytes(p, &p->part_run, std::max<int64_t>(npart, 1) * 12 * sizeof(double),
-                           "part_run")))
-    return s;
-  POVAR_COPY(p->row_mask, mask.data(), mask.size(), cudaMemcpyHostToDevice);
-  POVAR_COPY(p->row_base, base.data(), base.size(), cudaMemcpyHostToDevice);
-  POVAR_COPY(p->cam_part_off, poff.data(), poff.size(), cudaMemcpyHostToDevice);
-  POVAR_COPY(p->cam_part_idx, pidx.data(), pidx.size(), cudaMemcpyHostToDevice);
-  return build_group_runs(p, cam, off);
-}
 
-// Run structure of the grouped schedule. Group g holds the slices
-// h_grp_slice0[g] .. h_grp_slice0[g+1]-1; its rows t = 0 .. (widest slice)-1
-// are numbered from grp_row0[g]. A group row whose valid lanes (over all of
-// the group's slices that reach row t) all see one camera is "uniform": one
-// partial, at grow_base, camera in grow_cam. For any other group row,
-// grow_cam = -1 and every slice row in it gets the run description of the
-// fused schedule (srow_mask, srow_base) in the grouped partial space. The
-// partials of camera i are listed at cam_part3_idx[cam_part3_off[i] ..).
-povar_status build_group_runs(Problem* p, const std::vector<int32_t>& cam,
-                              const std::vector<uint32_t>& off) {
-  povar_status s;
-  const int ng = p->ngroups;
-  const int64_t nrows = p->nsell / SLICE;
-  std::vector<uint32_t> grow0(ng + 1, 0), gbase, smask(std::max<int64_t>(nrows, 1), 0),
-      sbase(std::max<int64_t>(nrows, 1), 0);
-  std::vector<int32_t> gcam, pcam;
-  for (int g = 0; g < ng; ++g) {
-    const uint32_t s0 = p->h_grp_slice0[g], s1 = p->h_grp_slice0[g + 1];
-    uint32_t W = 0;
-    for (uint32_t sl = s0; sl < s1; ++sl) W = std::max(W, (off[sl + 1] - off[sl]) / SLICE);
-    grow0[g] = (uint32_t)gcam.size();
-    for (uint32_t t = 0; t < W; ++t) {
-      int32_t c0 = -1;
-      bool uniform = true;
-      for (uint32_t sl = s0; sl < s1; ++sl) {
-        if (t >= (off[sl + 1] - off[sl]) / SLICE) continue;
-        const int32_t* c = cam.data() + (size_t)off[sl] + (size_t)t * SLICE;
-        for (int l = 0; l < SLICE; ++l) {
-          if (c[l] < 0) continue;
-          if (c0 < 0) c0 = c[l];
-          else if (c[l] != c0) uniform = false;
-        }
-      }
-      if (uniform && c0 >= 0) {
-        gcam.push_back(c0);
-        gbase.push_back((uint32_t)pcam.size());
-        pcam.push_back(c0);
-        continue;
-      }
-      gcam.push_back(-1);
-      gbase.push_back(0);
-      for (uint32_t sl = s0; sl < s1; ++sl) {
-        if (t >= (off[sl + 1] - off[sl]) / SLICE) continue;
-        const int64_t row = off[sl] / SLICE + t;
-        const int32_t* c = cam.data() + row * SLICE;
-        int32_t r0 = -1;
-        bool ru = true;
-        for (int l = 0; l < SLICE; ++l) {
-          if (c[l] < 0) continue;
-          if (r0 < 0) r0 = c[l];
-          else if (c[l] != r0) ru = false;
-        }
-        sbase[row] = (uint32_t)pcam.size();
-        if (ru && r0 >= 0) {
-          smask[row] = 0;
-          pcam.push_back(r0);
-          continue;
-        }
-        uint32_t m = 0;
-        for (int l = 0; l < SLICE; ++l) {
-          if (l == 0 || c[l] != c[l - 1]) {
-            m |= 1u << l;
-            if (c[l] >= 0) pcam.push_back(c[l]);
-          }
-        }
-        smask[row] = m;
-      }
-    }
-  }
-  grow0[ng] = (uint32_t)gcam.size();
-  const int64_t npart = (int64_t)pcam.size();
-  std::vector<uint32_t> poff(p->nc + 1, 0), pidx(std::max<int64_t>(npart, 1));
-  for (int32_t c : pcam) ++poff[c + 1];
-  for (int c = 0; c < p->nc; ++c) poff[c + 1] += poff[c];
-  {
-    std::vector<uint32_t> cursor(poff.begin(), poff.end() - 1);
-    for (int64_t q = 0; q < npart; ++q) pidx[cursor[pcam[q]]++] = (uint32_t)q;
-  }
-  p->ngrows = (int64_t)gcam.size();
-  p->npart3 = npart;
-  if (gcam.empty()) {
-    gcam.push_back(-1);
-    gbase.push_back(0);
-  }
-  if ((s = dev_alloc(p, &p->grp_slice0, p->h_grp_slice0.size(), "grp_slice0")) ||
-      (s = dev_alloc(p, &p->grp_row0, grow0.size(), "grp_row0")) ||
-      (s = dev_alloc(p, &p->grow_cam, gcam.size(), "grow_cam")) ||
-      (s = dev_alloc(p, &p->grow_base, gbase.size(), "grow_base")) ||
-      (s = dev_alloc(p, &p->srow_mask, smask.size(), "srow_mask")) ||
-      (s = dev_alloc(p, &p->srow_base, sbase.size(), "srow_base")) ||
-      (s = dev_alloc(p, &p->cam_part3_off, poff.size(), "cam_part3_off")) ||
-      (s = dev_alloc(p, &p->cam_part3_idx, pidx.size(), "cam_part3_idx")) ||
-      (s = dev_alloc_bytes(p, &p->part3, std::max<int64_t>(npart, 1) * 12 * sizeof(double),
-                           "part3")))
+  // camera-row lists: every distinct valid camera of every slice row, per
+  // camera in row order
+  p->nvisits = nvisit;
+  if ((s = dev_alloc(p, &p->cam_row_off, (size_t)p->nc + 1, "cam_row_off")) ||
+      (s = dev_alloc(p, &p->cam_row_pos0, nvisit, "cam_row_pos0")) ||
+      (s = dev_alloc(p, &p->cam_row_slot0, nvisit, "cam_row_slot0")))
     return s;
-  POVAR_COPY(p->grp_slice0, p->h_grp_slice0.data(), p->h_grp_slice0.size(),
-             cudaMemcpyHostToDevice);
-  POVAR_COPY(p->grp_row0, grow0.data(), grow0.size(), cudaMemcpyHostToDevice);
-  POVAR_COPY(p->grow_cam, gcam.data(), gcam.size(), cudaMemcpyHostToDevice);
-  POVAR_COPY(p->grow_base, gbase.data(), gbase.size(), cudaMemcpyHostToDevice);
-  POVAR_COPY(p->srow_mask, smask.data(), smask.size(), cudaMemcpyHostToDevice);
-  POVAR_COPY(p->srow_base, sbase.data(), sbase.size(), cudaMemcpyHostToDevice);
-  POVAR_COPY(p->cam_part3_off, poff.data(), poff.size(), cudaMemcpyHostToDevice);
-  POVAR_COPY(p->cam_part3_idx, pidx.data(), pidx.size(), cudaMemcpyHostToDevice);
+  {
+    uint32_t *kk = vcam, *vv = vval;
+    if ((s = radix_sort(p, sc, &kk, &vv, nvisit, cbits)) != POVAR_OK) return s;
+    k_visit_fill<<<grid_for(nvisit, 256), 256, 0, p->stream>>>(vv, vrow, row_slice, nvisit,
+                                                               p->cam_row_pos0,
+                                                               p->cam_row_slot0);
+    k_offsets<<<grid_for(nvisit, 256), 256, 0, p->stream>>>(kk, nvisit, p->nc, p->cam_row_off);
+    p->launches += 2;
+  }
+
+  // grouped schedule (one slice per group): the fused runs in the group
+  // layout; its partial lists are the fused ones
+  p->ngrows = nrows;
+  p->npart3 = npart;
+  if ((s = dev_alloc(p, &p->grp_slice0, (size_t)p->ngroups + 1, "grp_slice0")) ||
+      (s = dev_alloc(p, &p->grp_row0, (size_t)p->ngroups + 1, "grp_row0")) ||
+      (s = dev_alloc(p, &p->grow_cam, std::max<int64_t>(nrows, 1), "grow_cam")) ||
+      (s = dev_alloc(p, &p->grow_base, std::max<int64_t>(nrows, 1), "grow_base")) ||
+      (s = dev_alloc(p, &p->srow_mask, std::max<int64_t>(nrows, 1), "srow_mask")) ||
+      (s = dev_alloc(p, &p->srow_base, std::max<int64_t>(nrows, 1), "srow_base")))
+    return s;
+  k_group_tables<<<gr, 256, 0, p->stream>>>(nrows, p->row_mask, rcam, p->row_base, p->grow_cam,
+                                            p->grow_base, p->srow_mask, p->srow_base);
+  k_group_rows<<<grid_for((int64_t)p->ngroups + 1, 256), 256, 0, p->stream>>>(
+      p->sell_off, p->ngroups, p->grp_slice0, p->grp_row0);
+  p->launches += 2;
+  p->cam_part3_off = p->cam_part_off;
+  p->cam_part3_idx = p->cam_part_idx;
+  p->part3 = p->part_run;   // schedules 1 and 3 never run at the same time
+  if ((s = check_launch(p, "run tables")) != POVAR_OK) return s;
+  // the scratch is freed on return: wait for the kernels that read it
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
   return POVAR_OK;
 }
 

@@ -146,13 +146,14 @@ struct Problem {
   // single partial; other group rows fall back to per-slice-row runs
   int32_t ngroups = 0;
   int64_t ngrows = 0, npart3 = 0;
-  std::vector<uint32_t> h_grp_slice0;   // [ngroups + 1] (host)
   uint32_t* grp_slice0 = nullptr;       // [ngroups + 1] first slice of each group
   uint32_t* grp_row0 = nullptr;         // [ngroups + 1] first group row of each group
   int32_t* grow_cam = nullptr;          // [ngrows] camera of a group-uniform row, else -1
   uint32_t* grow_base = nullptr;        // [ngrows] partial of a group-uniform row
   uint32_t* srow_mask = nullptr;        // [nrows] runs of slice rows in non-uniform group rows
   uint32_t* srow_base = nullptr;        // [nrows]
+  // with one slice per group (GROUP = 1) the grouped partials are the
+  // fused ones: these alias cam_part_off, cam_part_idx and part_run
   uint32_t* cam_part3_off = nullptr;    // [nc + 1]
   uint32_t* cam_part3_idx = nullptr;    // [npart3]
   void* part3 = nullptr;                // [npart3 * 12] float or double
