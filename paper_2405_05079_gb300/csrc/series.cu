@@ -729,8 +729,11 @@ k_build_blocks(const DeviceState* __restrict__ st, T a, int64_t nsell,
 
 // TS = void: factored (schedule 1); otherwise the stored blocks of storage TS
 // (schedule 4 / the BF16 precision). Both write the same run partials.
+// Blocks per SM: four in FP32 (64 registers; the pass-1 chunk kept for pass
+// 2 would otherwise raise it to 80 and cut the occupancy by a quarter), two
+// in FP64.
 template <typename T, typename TS>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? 4 : 2)
 k_series_fused(const DeviceState* __restrict__ st, T a,
                const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
                const int32_t* __restrict__ sell_cam,
@@ -756,9 +759,10 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
   // measurements are loaded together so that RB rows are in flight per warp
   using M2 = typename Vt<T>::m2;
   constexpr int RB = 4;
+  // the chunk loaded last stays in ci / mi: it is the first chunk of pass 2
+  int ci[RB] = {0, 0, 0, 0};
+  M2 mi[RB] = {M2{0, 0}, M2{0, 0}, M2{0, 0}, M2{0, 0}};
   for (uint32_t k0 = 0; k0 < len; k0 += RB) {
-    int ci[RB];
-    M2 mi[RB];
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
       const bool in = k0 + u < len;
@@ -815,11 +819,16 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
   const T S1 = F[2] * z1 + F[4] * z2;
   const T S2 = F[5] * z2;
   const uint32_t row0 = sbeg / SLICE;
-  // pass 2 in chunks of RB slice rows: the rows' camera indices,
-  // measurements and run metadata are loaded together
-  for (uint32_t k0 = 0; k0 < width; k0 += RB) {
-    int ci[RB];
-    M2 mi[RB];
+  // pass 2 in chunks of RB slice rows, last chunk first: the rows' camera
+  // indices, measurements and run metadata are loaded together, except (FP32)
+  // for the last chunk, whose indices and measurements pass 1 loaded last (a
+  // lane whose track reaches that chunk loaded it; every other lane has no
+  // observation there); in FP64 the registers are scarcer than the reload.
+  // Each row writes its own partial slots, so the order of the rows does not
+  // change any result.
+  const uint32_t klast = width > 0 ? (width - 1) / RB * RB : 0;
+  for (int64_t kr = width > 0 ? (int64_t)klast : -1; kr >= 0; kr -= RB) {
+    const uint32_t k0 = (uint32_t)kr;
     uint32_t mk[RB], bk[RB];
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
@@ -828,6 +837,11 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
       if constexpr (STORED) {
         ci[u] = in ? 0 : -1;   // only validity is needed
         mi[u] = M2{0, 0};
+      } else if (sizeof(T) == 4 && k0 == klast) {
+        if (!in) {
+          ci[u] = -1;
+          mi[u] = M2{0, 0};
+        }
       } else {
         ci[u] = in ? ld_stream(sell_cam + base + (k0 + u) * SLICE) : -1;
         mi[u] = in ? ld_stream(sell_m + base + (k0 + u) * SLICE) : M2{0, 0};
