@@ -135,9 +135,14 @@ typedef struct {
  *  meas[2*n_obs]     normalized measurement (u, v) of each observation.
  *  cuda_stream       cudaStream_t to issue work on (NULL = default stream).
  * Every landmark must be observed at least once (else POVAR_EINVAL); a
- * camera without observations is allowed (its step is zero).
- * Builds the camera-major and point-major observation orders on the device
- * (stable integer sorts, bit-exact) and allocates all device state.
+ * camera without observations is allowed (its step is zero). Sizes are
+ * checked on the host before anything is allocated; indices out of range and
+ * non-finite measurements are found by a device check right after the copy
+ * of the arrays, before any index is used (POVAR_EINVAL, nothing is kept).
+ * Builds the camera-major and point-major observation orders, the landmark
+ * layout and the run tables of the series on the device (stable integer
+ * sorts, bit-exact) and allocates all device state. The arrays are only read
+ * during the call.
  * Cameras start at zero: call povar_set_cameras or povar_init_random. */
 povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs,
                           const int32_t* cam_idx, const int32_t* pt_idx,
