@@ -459,9 +459,16 @@ def run_batched(args) -> dict:
     stream = torch.cuda.current_stream(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
+    m_table = None
+    if args.m_table:
+        with open(args.m_table) as f:
+            m_table = json.load(f)
     with povar.Batch(scs, stream=stream.cuda_stream) as b:
         for name, prec in (("mixed", povar.MIXED_FP32), ("fp64", povar.FP64)):
             prm = family_params(povar, prec)
+            if m_table is not None and prec == povar.MIXED_FP32:
+                from paper_2405_05079_gb300.autotune import params_with_m
+                prm = [params_with_m(m_table, prm, int(n)) for n in b.n_obs]
             times = []
             for k in range(args.warmup + args.steps):
                 b.set_cameras(P0s, 0.1)
@@ -503,7 +510,8 @@ def run_batched(args) -> dict:
                                 f"({sum(s.n_cams for s in scs)} total), 50 points per camera, "
                                 f"mean track 4 ({sum(s.n_obs for s in scs)} obs total)"),
                    "stop": "rel. decrease < 1e-6 or 50 iterations (Sec. 5.2)",
-                   "series": "m = 21, threshold 0.01, autotuned schedule per problem"},
+                   "series": ("mixed: m per size class from " + args.m_table if m_table
+                              else "m = 21") + ", threshold 0.01, autotuned schedule per problem"},
         "fp64_batch_solves_per_s": round(len(scs) / (out["fp64"]["ms"] / 1e3), 2),
         "mixed_one_after_another_solves_per_s": round(len(scs) / (alone_ms / 1e3), 2),
         "iterations_mixed": {"mean": float(np.mean(out["mixed"]["iters"])),
@@ -620,8 +628,9 @@ def main(argv=None):
     ap.add_argument("--rate", type=float, default=40.0, help="serving: arrivals per second")
     ap.add_argument("--precision", default="mixed", choices=PRECISIONS)
     ap.add_argument("--m-table", default=None,
-                    help="serving workload: series lengths per size class from a table of "
-                         "the series-length autotuner (paper_2405_05079_gb300/autotune.py)")
+                    help="batched / serving workloads: series lengths per size class from a "
+                         "table of the series-length autotuner "
+                         "(paper_2405_05079_gb300/autotune.py)")
     ap.add_argument("--max-iters", type=int, default=200)
     ap.add_argument("--m", type=int, default=None,
                     help="series terms (mid scene: 5, 10 or 20, against the oracle run at that m)")

@@ -281,6 +281,13 @@ povar_status povar_batch_cost(povar_batch* b, double eta, double* costs_out);
 povar_status povar_batch_solve(povar_batch* b, const povar_params* params, int32_t max_iters,
                                double ftol, const double* target_costs,
                                povar_step_report* reports, int32_t* iters_out);
+/* povar_batch_solve with one parameter set per problem: params[k] for
+ * problem k (n_problems entries; e.g. a series length m per problem size from
+ * a tuning table). Each problem's result equals solving it alone with
+ * params[k]. */
+povar_status povar_batch_solve_each(povar_batch* b, const povar_params* params,
+                                    int32_t max_iters, double ftol, const double* target_costs,
+                                    povar_step_report* reports, int32_t* iters_out);
 
 /* ---- allocation-free cost evaluation ----
  * No counterpart in the paper: a library utility. It evaluates the same

@@ -10,8 +10,8 @@ problems (observation count) it keeps the m whose performance profile over
 the class is best, i.e. the largest mean of rho(m, alpha) over the profile's
 alphas (the area under the profile: fastest to the threshold on most
 problems, and reaching it at all on the rest). Ties keep the larger m. The
-result is a JSON table; `m_for` looks a problem up in it, and the serving
-loop uses it per request.
+result is a JSON table; `m_for` looks a problem up in it; the serving loop
+applies it per request and a batch per problem (povar_batch_solve_each).
 
     python -m paper_2405_05079_gb300.autotune --family serving --problems 24 \\
         --eta 0.1 --tau 0.001 --out m_table.json
@@ -80,6 +80,14 @@ def m_for(table: dict, n_obs: int) -> int:
         raise ValueError("empty m table")
     best = min(rows, key=lambda r: (abs(r["class"] - c), -r["class"]))
     return int(best["m"])
+
+
+def params_with_m(table: dict, params, n_obs: int):
+    """A copy of params whose series length is the table's m for n_obs."""
+    from . import povar
+    q = povar.Params.from_buffer_copy(params)
+    q.m = m_for(table, n_obs)
+    return q
 
 
 def tune(problems, eta: float, tau: float = 0.001, candidates=CANDIDATES,

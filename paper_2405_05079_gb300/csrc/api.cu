@@ -788,7 +788,7 @@ struct povar_batch {
   cudaStream_t stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  povar_params key{};
+  std::vector<povar_params> keys;       // parameters of each problem in the graph
   bool built = false;
   std::string err;
 };
@@ -869,17 +869,22 @@ povar_status povar_batch_cost(povar_batch* b, double eta, double* costs_out) {
   return POVAR_OK;
 }
 
-povar_status povar_batch_solve(povar_batch* b, const povar_params* params, int32_t max_iters,
-                               double ftol, const double* target_costs,
-                               povar_step_report* reports, int32_t* iters_out) {
-  if (!b) return POVAR_EINVAL;
+// Batch solve with the parameters of problem k at params[k * each] (each = 0:
+// one parameter set for all).
+static povar_status batch_solve(povar_batch* b, const povar_params* params_base, size_t each,
+                                int32_t max_iters, double ftol, const double* target_costs,
+                                povar_step_report* reports, int32_t* iters_out) {
+  if (!b || !params_base) return POVAR_EINVAL;
   if (max_iters < 1) return batch_fail(b, POVAR_EINVAL, "max_iters must be >= 1");
   povar_status s;
   const size_t n = b->probs.size();
   std::vector<int> it0(n);
-  bool rebuild = !b->built || !povar::same_params(b->key, *params);
+  bool rebuild = !b->built || b->keys.size() != n;
+  for (size_t k = 0; k < n && !rebuild; ++k)
+    rebuild = !povar::same_params(b->keys[k], params_base[k * each]);
   for (size_t k = 0; k < n; ++k) {
     Problem* p = &b->probs[k]->impl;
+    const povar_params* params = params_base + k * each;
     if ((s = povar::check_params(p, params)) != POVAR_OK) return batch_fail(b, s, p->err);
     if ((s = povar::sync_state(p)) != POVAR_OK) return batch_fail(b, s, p->err);
     it0[k] = p->h_state->iteration;
@@ -909,7 +914,8 @@ povar_status povar_batch_solve(povar_batch* b, const povar_params* params, int32
       b->built = false;
       return batch_fail(b, POVAR_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
     }
-    b->key = *params;
+    b->keys.assign(n, povar_params{});
+    for (size_t k = 0; k < n; ++k) b->keys[k] = params_base[k * each];
     b->built = true;
   }
   const int check_every = 4;
@@ -944,6 +950,18 @@ povar_status povar_batch_solve(povar_batch* b, const povar_params* params, int32
     if (p->h_state->error && worst == POVAR_OK) worst = (povar_status)p->h_state->error;
   }
   return worst == POVAR_OK ? POVAR_OK : batch_fail(b, worst, "a problem reported a device error");
+}
+
+povar_status povar_batch_solve(povar_batch* b, const povar_params* params, int32_t max_iters,
+                               double ftol, const double* target_costs,
+                               povar_step_report* reports, int32_t* iters_out) {
+  return batch_solve(b, params, 0, max_iters, ftol, target_costs, reports, iters_out);
+}
+
+povar_status povar_batch_solve_each(povar_batch* b, const povar_params* params,
+                                    int32_t max_iters, double ftol, const double* target_costs,
+                                    povar_step_report* reports, int32_t* iters_out) {
+  return batch_solve(b, params, 1, max_iters, ftol, target_costs, reports, iters_out);
 }
 
 }  // extern "C"

@@ -101,10 +101,12 @@ def lib() -> C.CDLL:
     L.povar_batch_cost.argtypes = [vp, C.c_double, dp]
     L.povar_batch_solve.argtypes = [vp, C.POINTER(Params), i32, C.c_double, dp,
                                     C.POINTER(StepReport), C.POINTER(C.c_int32)]
+    L.povar_batch_solve_each.argtypes = [vp, C.POINTER(Params), i32, C.c_double, dp,
+                                         C.POINTER(StepReport), C.POINTER(C.c_int32)]
     L.povar_cost_noalloc.argtypes = [i32, i32, i64, vp, vp, vp, vp, C.c_double, vp, vp, vp]
     L.povar_cost_noalloc.restype = C.c_int
     for name in ("povar_batch_create", "povar_batch_set_cameras", "povar_batch_get_cameras",
-                 "povar_batch_cost", "povar_batch_solve"):
+                 "povar_batch_cost", "povar_batch_solve", "povar_batch_solve_each"):
         getattr(L, name).restype = C.c_int
     for name in ("povar_create", "povar_set_cameras", "povar_init_random", "povar_get_cameras",
                  "povar_get_points", "povar_cost", "povar_step", "povar_solve",
@@ -289,6 +291,7 @@ class Batch:
         pt = np.ascontiguousarray(np.concatenate([s.pt_idx for s in scenes_list]), np.int32)
         m = np.ascontiguousarray(np.concatenate([s.meas for s in scenes_list]), np.float64)
         self.n_cams = nc
+        self.n_obs = nob
         self.cam0 = np.concatenate([[0], np.cumsum(nc)])
         h = C.c_void_p()
         st = L.povar_batch_create(self.n, _ptr(nc, C.c_int32), _ptr(npnt, C.c_int32),
@@ -336,12 +339,20 @@ class Batch:
         return out
 
     def solve(self, params, max_iters=50, ftol=1e-6, target_costs=None):
+        """povar_batch_solve; params is one Params for every problem, or a
+        sequence of n Params (povar_batch_solve_each)."""
         reps = (StepReport * self.n)()
         its = np.zeros(self.n, np.int32)
         tc = None if target_costs is None else np.ascontiguousarray(target_costs, np.float64)
-        self._check(lib().povar_batch_solve(self._h, C.byref(params), max_iters, ftol,
-                                            None if tc is None else _ptr(tc, C.c_double), reps,
-                                            _ptr(its, C.c_int32)))
+        tcp = None if tc is None else _ptr(tc, C.c_double)
+        if isinstance(params, Params):
+            st = lib().povar_batch_solve(self._h, C.byref(params), max_iters, ftol, tcp, reps,
+                                         _ptr(its, C.c_int32))
+        else:
+            arr = (Params * self.n)(*params)
+            st = lib().povar_batch_solve_each(self._h, arr, max_iters, ftol, tcp, reps,
+                                              _ptr(its, C.c_int32))
+        self._check(st)
         return list(reps), its
 
 

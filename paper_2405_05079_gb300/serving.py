@@ -87,10 +87,8 @@ class Server:
         scene's size class when the server has an m table."""
         if self.m_table is None:
             return self.params
-        from .autotune import m_for
-        q = povar.Params.from_buffer_copy(self.params)
-        q.m = m_for(self.m_table, scene.n_obs)
-        return q
+        from .autotune import params_with_m
+        return params_with_m(self.m_table, self.params, scene.n_obs)
 
     def _solve(self, req: Request, slot: int, t0: float, admitted: float, reserved: int):
         stream = self.streams[slot].cuda_stream

@@ -455,6 +455,38 @@ def test_batch_solve_equals_each_problem_alone():
                 assert pb.cost(0.1) == Fb[k]
 
 
+def test_batch_with_parameters_per_problem_equals_each_alone():
+    """povar_batch_solve_each: every problem with its own series length (as
+    from a tuning table) gives the result of solving it alone with those
+    parameters, bit for bit."""
+    scs = [SCENES["tiny"](), SCENES["traj"](), scenes.ring_scene(7, 300, 9, eta=0.1)]
+    P0s = [scenes.init_cameras(s.n_cams, 20 + k, normalize=True) for k, s in enumerate(scs)]
+    prms = [povar.make_params(eta=0.1, m=m, series_eps=0.01, manifold=povar.EUCLID,
+                              precision=povar.MIXED_FP32, schedule=1) for m in (6, 21, 11)]
+    with povar.Batch(scs) as b:
+        b.set_cameras(P0s, 0.1)
+        _, its = b.solve(prms, max_iters=10, ftol=1e-9)
+        Pb = b.cameras()
+        Fb = b.costs(0.1)
+        # a second solve with other lengths rebuilds the batch graph
+        b.set_cameras(P0s, 0.1)
+        prms2 = [povar.make_params(eta=0.1, m=m, series_eps=0.01, manifold=povar.EUCLID,
+                                   precision=povar.MIXED_FP32, schedule=1) for m in (21, 6, 6)]
+        _, its2 = b.solve(prms2, max_iters=10, ftol=1e-9)
+        Pb2 = b.cameras()
+    for k, sc in enumerate(scs):
+        for prm, it_b, P_b in ((prms[k], its[k], Pb[k]), (prms2[k], its2[k], Pb2[k])):
+            with povar.Problem.from_scene(sc) as pb:
+                pb.set_cameras(P0s[k], 0.1)
+                _, it = pb.solve(prm, max_iters=10, ftol=1e-9)
+                assert it == it_b
+                assert np.array_equal(pb.cameras(), P_b)
+        with povar.Problem.from_scene(sc) as pb:
+            pb.set_cameras(P0s[k], 0.1)
+            pb.solve(prms[k], max_iters=10, ftol=1e-9)
+            assert pb.cost(0.1) == Fb[k]
+
+
 def test_footprint_estimate_bounds_actual():
     for sc in (SCENES["tiny"](), SCENES["traj"](), SCENES["mid"]()):
         with povar.Problem.from_scene(sc) as pb:
