@@ -196,6 +196,21 @@ povar_status povar_solve(povar_problem* p, const povar_params* params,
 
 /* ---- diagnostics (inspection of intermediate results for testing) ---- */
 
+/* Landmark layout and run tables built by povar_create (the SELL-32 layout
+ * of the series and landmark kernels). sizes[6] receives np_pad (slots),
+ * n_slices, n_sell (slice entries), n_rows (slice rows), n_part (run
+ * partials), n_visits (camera-row visits); call with NULL arrays to get them.
+ * slot_pt[np_pad]: landmark of each slot (0xffffffff for padding);
+ * sell_off[n_slices + 1]: first entry of each slice; sell_cam[n_sell]: camera
+ * of each entry (-1 for padding); row_mask[n_rows] / row_base[n_rows]: runs of
+ * each slice row (0 = all valid lanes see one camera) and its first partial;
+ * cam_part_off[n_cams + 1] / cam_part_idx[n_part]: partials of each camera in
+ * increasing index. Any array may be NULL; arrays are host memory. */
+povar_status povar_get_layout(povar_problem* p, int64_t* sizes, uint32_t* slot_pt,
+                              uint32_t* sell_off, int32_t* sell_cam, uint32_t* row_mask,
+                              uint32_t* row_base, uint32_t* cam_part_off,
+                              uint32_t* cam_part_idx);
+
 /* Observation orders built by povar_create: perm_pt[n_obs] lists the
  * observation ids sorted by (landmark, id), off_pt[n_points + 1] the segment
  * starts; perm_cam / off_cam the same by (camera, id). Any pointer may be

@@ -754,6 +754,38 @@ povar_status povar_get_orders(povar_problem* pp, uint32_t* perm_pt, uint32_t* of
   return POVAR_OK;
 }
 
+povar_status povar_get_layout(povar_problem* pp, int64_t* sizes, uint32_t* slot_pt,
+                              uint32_t* sell_off, int32_t* sell_cam, uint32_t* row_mask,
+                              uint32_t* row_base, uint32_t* cam_part_off,
+                              uint32_t* cam_part_idx) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  if (sizes) {
+    sizes[0] = p->np_pad;
+    sizes[1] = p->nslices;
+    sizes[2] = p->nsell;
+    sizes[3] = p->nrows;
+    sizes[4] = p->npart;
+    sizes[5] = p->nvisits;
+  }
+  auto get = [&](void* dst, const void* src, size_t bytes) -> povar_status {
+    if (dst && bytes)
+      POVAR_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, p->stream));
+    return POVAR_OK;
+  };
+  povar_status s;
+  if ((s = get(slot_pt, p->slot_pt, (size_t)p->np_pad * 4)) != POVAR_OK ||
+      (s = get(sell_off, p->sell_off, ((size_t)p->nslices + 1) * 4)) != POVAR_OK ||
+      (s = get(sell_cam, p->sell_cam, (size_t)p->nsell * 4)) != POVAR_OK ||
+      (s = get(row_mask, p->row_mask, (size_t)p->nrows * 4)) != POVAR_OK ||
+      (s = get(row_base, p->row_base, (size_t)p->nrows * 4)) != POVAR_OK ||
+      (s = get(cam_part_off, p->cam_part_off, ((size_t)p->nc + 1) * 4)) != POVAR_OK ||
+      (s = get(cam_part_idx, p->cam_part_idx, (size_t)p->npart * 4)) != POVAR_OK)
+    return s;
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  return POVAR_OK;
+}
+
 povar_status povar_get_last_step(povar_problem* pp, double* U_out, double* bp_out,
                                  double* delta_out) {
   if (!pp) return POVAR_EINVAL;

@@ -76,6 +76,8 @@ def lib() -> C.CDLL:
                               C.POINTER(StepReport), C.POINTER(C.c_int32)]
     u32p = C.POINTER(C.c_uint32)
     L.povar_get_orders.argtypes = [vp, u32p, u32p, u32p, u32p]
+    L.povar_get_layout.argtypes = [vp, C.POINTER(C.c_int64), u32p, u32p,
+                                   C.POINTER(C.c_int32), u32p, u32p, u32p, u32p]
     L.povar_get_last_step.argtypes = [vp, dp, dp, dp]
     L.povar_set_profiling.argtypes = [vp, i32]
     L.povar_get_profile.argtypes = [vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), i32]
@@ -110,7 +112,8 @@ def lib() -> C.CDLL:
         getattr(L, name).restype = C.c_int
     for name in ("povar_create", "povar_set_cameras", "povar_init_random", "povar_get_cameras",
                  "povar_get_points", "povar_cost", "povar_step", "povar_solve",
-                 "povar_get_orders", "povar_get_last_step", "povar_set_profiling",
+                 "povar_get_orders", "povar_get_layout", "povar_get_last_step",
+                 "povar_set_profiling",
                  "povar_get_profile", "povar_get_tuning"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -254,6 +257,27 @@ class Problem:
         self._check(lib().povar_get_orders(self._h, _ptr(pp, C.c_uint32), _ptr(op, C.c_uint32),
                                            _ptr(pc, C.c_uint32), _ptr(oc, C.c_uint32)))
         return pp, op, pc, oc
+
+    def layout(self) -> dict:
+        """povar_get_layout: the SELL-32 landmark layout and the run tables."""
+        L = lib()
+        sz = np.zeros(6, np.int64)
+        u32 = C.c_uint32
+        self._check(L.povar_get_layout(self._h, _ptr(sz, C.c_int64), None, None, None, None,
+                                       None, None, None))
+        np_pad, nsl, nsell, nrows, npart, nvis = (int(x) for x in sz)
+        out = {"slot_pt": np.empty(np_pad, np.uint32), "sell_off": np.empty(nsl + 1, np.uint32),
+               "sell_cam": np.empty(nsell, np.int32), "row_mask": np.empty(nrows, np.uint32),
+               "row_base": np.empty(nrows, np.uint32),
+               "cam_part_off": np.empty(self.n_cams + 1, np.uint32),
+               "cam_part_idx": np.empty(npart, np.uint32)}
+        self._check(L.povar_get_layout(
+            self._h, _ptr(sz, C.c_int64), _ptr(out["slot_pt"], u32), _ptr(out["sell_off"], u32),
+            _ptr(out["sell_cam"], C.c_int32), _ptr(out["row_mask"], u32),
+            _ptr(out["row_base"], u32), _ptr(out["cam_part_off"], u32),
+            _ptr(out["cam_part_idx"], u32)))
+        out["n_visits"] = nvis
+        return out
 
     def last_step(self):
         U = np.empty((self.n_cams, 12, 12))
