@@ -41,50 +41,51 @@ struct SlotBufs {
 // Ltab layout (48 doubles per camera):
 //  [0,6) R, [6,12) E1, [12,18) E2, [18,24) Fm   (symmetric 3x3: 00 01 02 11 12 22)
 //  [24,27) h0, [27,30) hu, [30,33) hv, [33,36) hw, [36,48) unused
-__global__ void k_ltab(const DeviceState* __restrict__ st, int which_rel, double eta,
-                       const double* __restrict__ P0, const double* __restrict__ P1, int nc,
-                       double* __restrict__ Ltab, float2* __restrict__ Ldf,
-                       float* __restrict__ C0, float* __restrict__ C1) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// 64 threads per camera: thread e < 36 computes table entry e, threads
+// 36 <= e < 48 copy P[e - 36] into the double-float block, threads e < 12
+// also write the FP32 copy of P; consecutive threads write consecutive
+// entries, so the stores of a warp coalesce.
+__global__ void __launch_bounds__(256)
+k_ltab(const DeviceState* __restrict__ st, int which_rel, double eta,
+       const double* __restrict__ P0, const double* __restrict__ P1, int nc,
+       double* __restrict__ Ltab, float2* __restrict__ Ldf, float* __restrict__ C0,
+       float* __restrict__ C1) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(g >> 6), e = (int)(g & 63);
   if (i >= nc) return;
   if (which_rel == 1 && st->converged) return;
   const int t = which_rel ? 1 - st->cur : st->cur;
   const double* P = (t ? P1 : P0) + 12 * (size_t)i;
-  float* Pf = (t ? C1 : C0) + 12 * (size_t)i;  // FP32 copy used by the FP32 kernels
-  for (int c = 0; c < 12; ++c) Pf[c] = (float)P[c];
+  if (e < 12) ((t ? C1 : C0) + 12 * (size_t)i)[e] = (float)P[e];  // for the FP32 kernels
+  if (e >= 48) return;
   const double a = 1.0 - eta;
-  double p0[3], p1[3], p2[3];
-  for (int c = 0; c < 3; ++c) {
-    p0[c] = P[c];
-    p1[c] = P[4 + c];
-    p2[c] = P[8 + c];
+  double v;
+  if (e < 24) {
+    // symmetric 3x3 entry (x, y) of block R, E1, E2 or Fm
+    const int k = e % 6, blk = e / 6;
+    const int x = k < 3 ? 0 : (k < 5 ? 1 : 2);
+    const int y = k < 3 ? k : (k < 5 ? k - 2 : 2);
+    const double p0x = P[x], p0y = P[y], p1x = P[4 + x], p1y = P[4 + y];
+    const double p2x = P[8 + x], p2y = P[8 + y];
+    if (blk == 0) v = p0x * p0y + p1x * p1y;
+    else if (blk == 1) v = -a * (p0x * p2y + p2x * p0y);
+    else if (blk == 2) v = -a * (p1x * p2y + p2x * p1y);
+    else v = a * p2x * p2y;
+  } else if (e < 36) {
+    const int c = (e - 24) % 3, blk = (e - 24) / 3;
+    const double q0 = P[3], q1 = P[7], q2 = P[11];
+    const double p0 = P[c], p1 = P[4 + c], p2 = P[8 + c];
+    if (blk == 0) v = q0 * p0 + q1 * p1;
+    else if (blk == 1) v = (-a * q2 - eta) * p0 - a * q0 * p2;
+    else if (blk == 2) v = (-a * q2 - eta) * p1 - a * q1 * p2;
+    else v = a * q2 * p2;
+  } else {
+    v = P[e - 36];
   }
-  const double q0 = P[3], q1 = P[7], q2 = P[11];
-  double* T = Ltab + 48 * (size_t)i;
-  const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-  for (int e = 0; e < 6; ++e) {
-    const int x = ia[e], y = ib[e];
-    T[e] = p0[x] * p0[y] + p1[x] * p1[y];
-    T[6 + e] = -a * (p0[x] * p2[y] + p2[x] * p0[y]);
-    T[12 + e] = -a * (p1[x] * p2[y] + p2[x] * p1[y]);
-    T[18 + e] = a * p2[x] * p2[y];
-  }
-  for (int c = 0; c < 3; ++c) {
-    T[24 + c] = q0 * p0[c] + q1 * p1[c];
-    T[27 + c] = (-a * q2 - eta) * p0[c] - a * q0 * p2[c];
-    T[30 + c] = (-a * q2 - eta) * p1[c] - a * q1 * p2[c];
-    T[33 + c] = a * q2 * p2[c];
-  }
+  if (e < 36) Ltab[48 * (size_t)i + e] = v;
   // double-float copy: the 36 table entries, then P itself (12)
-  float2* D = Ldf + 48 * (size_t)i;
-  for (int e = 0; e < 36; ++e) {
-    const float hi = (float)T[e];
-    D[e] = make_float2(hi, (float)(T[e] - (double)hi));
-  }
-  for (int e = 0; e < 12; ++e) {
-    const float hi = (float)P[e];
-    D[36 + e] = make_float2(hi, (float)(P[e] - (double)hi));
-  }
+  const float hi = (float)v;
+  Ldf[48 * (size_t)i + e] = make_float2(hi, (float)(v - (double)hi));
 }
 
 // Symmetric 3x3 packed as (00 01 02 11 12 22).
@@ -578,7 +579,8 @@ static df64 df_host(double x) {
 }
 
 povar_status launch_landmarks(Problem* p, int which_rel, double eta, int precision) {
-  k_ltab<<<grid_for(p->nc, 128), 128, 0, p->stream>>>(p->state, which_rel, eta, p->P64[0],
+  k_ltab<<<grid_for((int64_t)p->nc * 64, 256), 256, 0, p->stream>>>(p->state, which_rel, eta,
+                                                                      p->P64[0],
                                                       p->P64[1], p->nc, p->Ltab, p->Ltab_df,
                                                       p->camP32[0], p->camP32[1]);
   SlotBufs b;
