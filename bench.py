@@ -548,9 +548,9 @@ def run_serving(args) -> dict:
     # warm-up: library load, first graph captures, allocator
     warm = [serving.Request(rid=k, arrival=0.0, scene=r.scene, P0=r.P0)
             for k, r in enumerate(reqs[:4])]
-    serving.Server(mixed, budget_bytes=40 << 30, slots=8, max_iters=50, ftol=1e-6,
+    serving.Server(mixed, budget_bytes=40 << 30, slots=args.slots, max_iters=50, ftol=1e-6,
                    m_table=m_table).run(warm)
-    srv = serving.Server(mixed, budget_bytes=40 << 30, slots=8, max_iters=50, ftol=1e-6,
+    srv = serving.Server(mixed, budget_bytes=40 << 30, slots=args.slots, max_iters=50, ftol=1e-6,
                          m_table=m_table)
     t0 = time.perf_counter()
     res = srv.run(reqs)
@@ -571,7 +571,7 @@ def run_serving(args) -> dict:
                                 f"({sum(s.n_cams for s in scs)} total, "
                                 f"{sum(s.n_obs for s in scs)} obs), 100 points per camera, "
                                 f"mean track 5, Poisson arrivals at {args.rate}/s"),
-                   "budget_bytes": 40 << 30, "slots": 8,
+                   "budget_bytes": 40 << 30, "slots": args.slots,
                    "series_terms": (f"per size class from {args.m_table}" if m_table
                                     else "m = 21 (Sec. 5.2)"),
                    "stop": "rel. decrease < 1e-6 or 50 iterations (Sec. 5.2)"},
@@ -625,7 +625,11 @@ def main(argv=None):
     ap.add_argument("--workload", default="large",
                     choices=("large", "mid", "tiny", "batched", "serving"))
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
-    ap.add_argument("--rate", type=float, default=40.0, help="serving: arrivals per second")
+    ap.add_argument("--rate", type=float, default=200.0,
+                    help="serving: arrivals per second (above the server's capacity, so that "
+                         "served solves/s measures the capacity)")
+    ap.add_argument("--slots", type=int, default=8,
+                    help="serving: problems on the GPU at the same time")
     ap.add_argument("--precision", default="mixed", choices=PRECISIONS)
     ap.add_argument("--m-table", default=None,
                     help="batched / serving workloads: series lengths per size class from a "

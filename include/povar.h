@@ -260,9 +260,13 @@ povar_status povar_get_tuning(povar_problem* p, int32_t precision, int32_t* sche
 
 /* Device memory held by a handle (bytes), and an upper-bound estimate of
  * it from the problem sizes alone, for admission control before
- * povar_create. */
+ * povar_create. Handles take their device memory from a memory pool that the
+ * library keeps per device; memory of destroyed handles stays in that pool
+ * for later handles until povar_release_cached_memory returns it to the
+ * device. */
 int64_t povar_device_bytes(const povar_problem* p);
 int64_t povar_estimate_bytes(int32_t n_cams, int32_t n_points, int64_t n_obs);
+void povar_release_cached_memory(void);
 
 /* Number of kernel launches this handle has issued so far. */
 int64_t povar_launch_count(const povar_problem* p);

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 struct povar_problem {
@@ -29,9 +30,52 @@ povar_status check_launch(Problem* p, const char* what) {
   return POVAR_OK;
 }
 
+// Device memory comes from the stream-ordered allocator, on the problem's
+// stream, out of a memory pool the library owns per device: cudaMalloc /
+// cudaFree may synchronize the whole device, which would serialize every
+// problem solved concurrently with the one being created or destroyed (the
+// serving loop creates and destroys one per request). The pool keeps freed
+// memory for the next problems (no release threshold);
+// povar_release_cached_memory returns it to the device.
+namespace {
+std::mutex g_pool_mu;
+std::vector<std::pair<int, cudaMemPool_t>> g_pools;
+}  // namespace
+
+cudaError_t library_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (const auto& dp : g_pools)
+    if (dp.first == dev) {
+      *out = dp.second;
+      return cudaSuccess;
+    }
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool;
+  if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+  uint64_t keep = UINT64_MAX;
+  if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess)
+    return e;
+  g_pools.emplace_back(dev, pool);
+  *out = pool;
+  return cudaSuccess;
+}
+
+void release_cached_memory() {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (const auto& dp : g_pools) cudaMemPoolTrimTo(dp.second, 0);
+}
+
 povar_status dev_alloc_bytes(Problem* p, void** ptr, size_t bytes, const char* what) {
   void* q = nullptr;
-  const cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 1);
+  cudaMemPool_t pool;
+  cudaError_t e = library_pool(&pool);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&q, bytes > 0 ? bytes : 1, pool, p->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(p, POVAR_ENOMEM, std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
@@ -43,6 +87,41 @@ povar_status dev_alloc_bytes(Problem* p, void** ptr, size_t bytes, const char* w
 }
 
 namespace {
+
+// Page-locked host slots for the per-problem mirrors of the device state and
+// step report (copied to asynchronously, read after a stream sync). They are
+// carved from chunks that are never freed and handed out under a mutex, so
+// creating or destroying a problem calls neither cudaMallocHost nor
+// cudaFreeHost, which may synchronize the device.
+constexpr size_t kPinHalf = 512;              // one mirror per half slot
+constexpr size_t kPinSlot = 2 * kPinHalf;
+constexpr size_t kPinChunkSlots = 256;
+static_assert(sizeof(DeviceState) <= kPinHalf && sizeof(povar_step_report) <= kPinHalf,
+              "host mirror slots too small");
+std::mutex g_pin_mu;
+std::vector<char*> g_pin_free;
+
+char* pinned_slot_get() {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (g_pin_free.empty()) {
+    char* c = nullptr;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&c), kPinSlot * kPinChunkSlots,
+                      cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (size_t k = 0; k < kPinChunkSlots; ++k) g_pin_free.push_back(c + k * kPinSlot);
+  }
+  char* q = g_pin_free.back();
+  g_pin_free.pop_back();
+  return q;
+}
+
+void pinned_slot_put(char* q) {
+  if (!q) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(q);
+}
 
 void collect_profile(Problem* p);
 
@@ -375,22 +454,23 @@ int64_t povar_estimate_bytes(int32_t n_cams, int32_t n_points, int64_t n_obs) {
   return b + (1 << 20);
 }
 
+void povar_release_cached_memory(void) { povar::release_cached_memory(); }
+
 void povar_destroy(povar_problem* pp) {
   if (!pp) return;
   Problem* p = &pp->impl;
-  if (p->stream) cudaStreamSynchronize(p->stream);
-  for (void* q : p->allocs) cudaFree(q);
-  if (p->h_state) cudaFreeHost(p->h_state);
-  if (p->h_report) cudaFreeHost(p->h_report);
+  // work of the graph stream is joined back to the problem's stream by every
+  // solve; wait for both, then return the memory in stream order
+  if (p->gstream) cudaStreamSynchronize(p->gstream);
+  cudaStreamSynchronize(p->stream);
+  for (void* q : p->allocs) cudaFreeAsync(q, p->stream);
+  povar::pinned_slot_put(reinterpret_cast<char*>(p->h_state));
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->graph) cudaGraphDestroy(p->graph);
-  if (p->gstream) {
-    cudaStreamSynchronize(p->gstream);
-    cudaStreamDestroy(p->gstream);
-  }
+  if (p->gstream) cudaStreamDestroy(p->gstream);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   for (int ph = 0; ph <= POVAR_NPHASES; ++ph)
     if (p->gprof[ph]) cudaEventDestroy(p->gprof[ph]);
@@ -481,8 +561,17 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
       return POVAR_ECUDA;                                                    \
     }                                                                        \
   } while (0)
-  CK(cudaMallocHost(&p->h_state, sizeof(povar::DeviceState)));
-  CK(cudaMallocHost(&p->h_report, sizeof(povar_step_report)));
+  // page-locked host mirrors of the device state and report, from the slot
+  // pool (no pinned allocation per problem)
+  {
+    char* slot = povar::pinned_slot_get();
+    if (!slot) {
+      povar_destroy(pp);
+      return POVAR_ENOMEM;
+    }
+    p->h_state = new (slot) povar::DeviceState();
+    p->h_report = new (slot + povar::kPinHalf) povar_step_report();
+  }
   CK(cudaEventCreate(&p->ev0));
   CK(cudaEventCreate(&p->ev1));
   CK(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));

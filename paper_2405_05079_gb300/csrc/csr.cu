@@ -438,16 +438,26 @@ povar_status copy_sync(Problem* p, T* dst, const T* src, size_t count, cudaMemcp
     if (cs_ != POVAR_OK) return cs_;                                         \
   } while (0)
 
-// Scratch buffer list freed at the end of build_orders.
+// Scratch buffers of the set-up, from the stream-ordered allocator on the
+// problem's stream and returned in stream order when the scope ends (after
+// every kernel enqueued before that point).
 struct Scratch {
+  cudaStream_t stream;
   std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t s) : stream(s) {}
   ~Scratch() {
-    for (void* q : ptrs) cudaFree(q);
+    for (void* q : ptrs) cudaFreeAsync(q, stream);
   }
   template <class T>
   T* get(size_t count) {
     void* q = nullptr;
-    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    cudaMemPool_t pool;
+    if (library_pool(&pool) != cudaSuccess ||
+        cudaMallocFromPoolAsync(&q, std::max<size_t>(count, 1) * sizeof(T), pool, stream) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
     ptrs.push_back(q);
     return static_cast<T*>(q);
   }
@@ -504,7 +514,7 @@ povar_status build_runs(Problem* p);
 povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt) {
   (void)h_cam;
   (void)h_pt;
-  Scratch sc;
+  Scratch sc(p->stream);
   const int64_t n = p->nobs;
   const unsigned gb = grid_for(n, 256);
   povar_status s;
@@ -692,7 +702,7 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
 // camera for the per-camera lists.
 povar_status build_runs(Problem* p) {
   povar_status s;
-  Scratch sc;
+  Scratch sc(p->stream);
   const int64_t nrows = p->nsell / SLICE;
   const unsigned gw = grid_for(nrows * SLICE, 256);   // one warp per row
   const unsigned gr = grid_for(nrows, 256);
@@ -788,10 +798,7 @@ povar_status build_runs(Problem* p) {
   p->cam_part3_off = p->cam_part_off;
   p->cam_part3_idx = p->cam_part_idx;
   p->part3 = p->part_run;   // schedules 1 and 3 never run at the same time
-  if ((s = check_launch(p, "run tables")) != POVAR_OK) return s;
-  // the scratch is freed on return: wait for the kernels that read it
-  POVAR_CUDA(cudaStreamSynchronize(p->stream));
-  return POVAR_OK;
+  return check_launch(p, "run tables");
 }
 
 }  // namespace povar

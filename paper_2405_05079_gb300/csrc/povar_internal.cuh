@@ -197,7 +197,7 @@ struct Problem {
   int32_t n_slot_blocks = 0;
   // controller
   DeviceState* state = nullptr;
-  DeviceState* h_state = nullptr;       // pinned mirror
+  DeviceState* h_state = nullptr;       // host mirror (read after a stream synchronization)
   povar_step_report* d_report = nullptr;
   povar_step_report* h_report = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -239,7 +239,10 @@ struct Problem {
 povar_status fail(Problem* p, povar_status s, const std::string& msg);
 povar_status check_launch(Problem* p, const char* what);
 
-// cudaMalloc tracked by the handle (freed by povar_destroy).
+// Device allocation tracked by the handle (freed by povar_destroy): stream
+// ordered on the problem's stream, from the library's memory pool of the
+// current device (library_pool).
+cudaError_t library_pool(cudaMemPool_t* out);
 povar_status dev_alloc_bytes(Problem* p, void** ptr, size_t bytes, const char* what);
 template <class T>
 inline povar_status dev_alloc(Problem* p, T** ptr, size_t count, const char* what) {

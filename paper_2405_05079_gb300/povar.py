@@ -105,6 +105,8 @@ def lib() -> C.CDLL:
                                     C.POINTER(StepReport), C.POINTER(C.c_int32)]
     L.povar_batch_solve_each.argtypes = [vp, C.POINTER(Params), i32, C.c_double, dp,
                                          C.POINTER(StepReport), C.POINTER(C.c_int32)]
+    L.povar_release_cached_memory.argtypes = []
+    L.povar_release_cached_memory.restype = None
     L.povar_cost_noalloc.argtypes = [i32, i32, i64, vp, vp, vp, vp, C.c_double, vp, vp, vp]
     L.povar_cost_noalloc.restype = C.c_int
     for name in ("povar_batch_create", "povar_batch_set_cameras", "povar_batch_get_cameras",
@@ -410,6 +412,12 @@ def cost_noalloc(n_cams: int, n_points: int, n_obs: int, P: int, off_pt: int, ca
                          f"of {NOALLOC_MAX_POINTS} landmarks")
     if st != 0:
         raise PovarError(st, "povar_cost_noalloc failed")
+
+
+def release_cached_memory() -> None:
+    """povar_release_cached_memory: give the device memory that destroyed
+    problems left in the library's pool back to the device."""
+    lib().povar_release_cached_memory()
 
 
 def version() -> str:
