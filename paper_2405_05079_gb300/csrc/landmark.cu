@@ -336,7 +336,9 @@ k_landmark(DeviceState* __restrict__ st, int which_rel, double eta,
 // pseudo-inverse path of k_landmark. Writes X (FP64), the FP32 copies used
 // by the FP32 kernels and the cost partials; the FP64 factor F64 is not
 // written (an FP64 step re-solves the landmarks with k_landmark first).
-__global__ void __launch_bounds__(BLOCK)
+// The kernel is bound by FP32 issue; capping it at 64 registers (4 blocks
+// per SM, a few spilled values) hides more latency than the spills cost.
+__global__ void __launch_bounds__(BLOCK, 4)
 k_landmark_df(DeviceState* __restrict__ st, int which_rel, df64 a, df64 eta,
               const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
               const int32_t* __restrict__ sell_cam, const float4* __restrict__ sell_mdf,
