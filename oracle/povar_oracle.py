@@ -23,10 +23,10 @@ Initialization-Free Large-Scale Bundle Adjustment", ECCV 2024):
   Cholesky or by the truncated power series of Proposition 1 / the PoVar
   series x(m) (Sec. 4.2);
 * one damped VarPro step: pose update, closed-form landmark re-solve at the new
-  cameras (Sec. 4.2, "the landmark update is derived following closed-form"),
+  cameras (Sec. 4.2: the landmarks are eliminated in closed form),
   gain ratio, accept/reject and damping update.
 
-Readings where the paper is silent or garbled (each also listed in the design doc):
+Readings where the paper is silent or garbled:
 
 * Sign of the right-hand side of Eq. pose_update: the paper's series x(m)
   carries a leading minus, so the step solves S dx = -(b_p - W V^-1 b_l).
