@@ -126,6 +126,21 @@ def _ptr(a: np.ndarray, ctype):
     return a.ctypes.data_as(C.POINTER(ctype))
 
 
+def _obs_arrays(cam_idx, pt_idx, meas, n_obs=None):
+    """Contiguous int32 / int32 / float64 (n_obs x 2) copies of one problem's
+    observation arrays; ValueError when their lengths disagree (the library
+    reads n_obs entries of each)."""
+    cam = np.ascontiguousarray(cam_idx, dtype=np.int32).reshape(-1)
+    pt = np.ascontiguousarray(pt_idx, dtype=np.int32).reshape(-1)
+    m = np.ascontiguousarray(meas, dtype=np.float64)
+    n = cam.shape[0] if n_obs is None else int(n_obs)
+    if cam.shape[0] != n or pt.shape[0] != n or m.size != 2 * n:
+        raise ValueError(f"observation arrays disagree: {n} observations, cam_idx "
+                         f"{cam.shape[0]}, pt_idx {pt.shape[0]}, meas {m.size} values "
+                         f"(2 per observation)")
+    return cam, pt, m.reshape(n, 2)
+
+
 def make_params(eta=0.1, lambda0=1e-4, m=10, series_eps=0.0, manifold=SPHERE,
                 precision=MIXED_FP32, schedule=-1) -> Params:
     return Params(eta=eta, lambda0=lambda0, series_eps=series_eps, lambda_l=0.0, m=m,
@@ -149,9 +164,7 @@ class Problem:
     def __init__(self, n_cams: int, n_points: int, cam_idx, pt_idx, meas, stream=None):
         L = lib()
         self.n_cams, self.n_points = int(n_cams), int(n_points)
-        cam = np.ascontiguousarray(cam_idx, dtype=np.int32)
-        pt = np.ascontiguousarray(pt_idx, dtype=np.int32)
-        m = np.ascontiguousarray(meas, dtype=np.float64).reshape(-1, 2)
+        cam, pt, m = _obs_arrays(cam_idx, pt_idx, meas)
         self.n_obs = int(cam.shape[0])
         h = C.c_void_p()
         st = L.povar_create(self.n_cams, self.n_points, self.n_obs, _ptr(cam, C.c_int32),
@@ -313,9 +326,10 @@ class Batch:
         nc = np.array([s.n_cams for s in scenes_list], np.int32)
         npnt = np.array([s.n_points for s in scenes_list], np.int32)
         nob = np.array([s.n_obs for s in scenes_list], np.int64)
-        cam = np.ascontiguousarray(np.concatenate([s.cam_idx for s in scenes_list]), np.int32)
-        pt = np.ascontiguousarray(np.concatenate([s.pt_idx for s in scenes_list]), np.int32)
-        m = np.ascontiguousarray(np.concatenate([s.meas for s in scenes_list]), np.float64)
+        arrs = [_obs_arrays(s.cam_idx, s.pt_idx, s.meas, s.n_obs) for s in scenes_list]
+        cam = np.ascontiguousarray(np.concatenate([a[0] for a in arrs]))
+        pt = np.ascontiguousarray(np.concatenate([a[1] for a in arrs]))
+        m = np.ascontiguousarray(np.concatenate([a[2] for a in arrs]))
         self.n_cams = nc
         self.n_obs = nob
         self.cam0 = np.concatenate([[0], np.cumsum(nc)])
@@ -350,8 +364,11 @@ class Batch:
         self.close()
 
     def set_cameras(self, P_list, eta):
-        P = np.ascontiguousarray(np.concatenate([np.asarray(p).reshape(-1, 12) for p in P_list]),
-                                 np.float64)
+        Ps = [np.asarray(p).reshape(-1, 12) for p in P_list]
+        if len(Ps) != self.n or any(q.shape[0] != int(c) for q, c in zip(Ps, self.n_cams)):
+            raise ValueError(f"expected {self.n} camera arrays of {list(map(int, self.n_cams))} "
+                             f"cameras, got {[q.shape[0] for q in Ps]}")
+        P = np.ascontiguousarray(np.concatenate(Ps), np.float64)
         self._check(lib().povar_batch_set_cameras(self._h, _ptr(P, C.c_double), eta))
 
     def cameras(self):

@@ -93,3 +93,4 @@ def test_request_over_budget_is_rejected():
     srv, _ = host_server(povar.estimate_bytes(s.n_cams, s.n_points, s.n_obs) - 1, slots=2)
     with pytest.raises(ValueError):
         srv.run([serving.Request(rid=0, arrival=0.0, scene=s, P0=None)])
+
