@@ -78,7 +78,7 @@ povar_status dev_alloc_bytes(Problem* p, void** ptr, size_t bytes, const char* w
   if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&q, bytes > 0 ? bytes : 1, pool, p->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(p, POVAR_ENOMEM, std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
+    return fail(p, POVAR_ENOMEM, std::string("device allocation ") + what + ": " + cudaGetErrorString(e));
   }
   p->allocs.push_back(q);
   p->device_bytes += (int64_t)(bytes > 0 ? bytes : 1);

@@ -1271,7 +1271,7 @@ k_pred_finish(DeviceState* __restrict__ st, int nc, int nparts, int m,
 }
 
 // ---------------------------------------------------------------------------
-// Schedule 3 (row table). The host groups slices (GROUP per warp, see
+// Schedule 3 (row table). Creation groups slices (GROUP per warp, see
 // povar_internal.cuh) and gives every group row whose valid lanes all see
 // one camera that camera and its partial; other rows keep the run
 // description of the fused schedule. Helpers shared with its kernel below.
