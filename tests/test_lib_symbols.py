@@ -66,3 +66,54 @@ def test_create_rejects_empty_and_oversized_inputs_before_touching_the_device():
     assert L.povar_create(0, 1, 4, *args) == 1          # no camera
     assert L.povar_create(1, 0, 4, *args) == 1          # no landmark
     assert not h.value
+
+
+def test_create_rejects_invalid_arguments_on_the_host(libpath):
+    """povar_create / povar_batch_create check sizes and pointers before any
+    CUDA call (POVAR_EINVAL = 1, *out left NULL); povar_destroy(NULL) is a no-op."""
+    C = ctypes
+    lib = C.CDLL(libpath)
+    for f in (lib.povar_create, lib.povar_batch_create):
+        f.restype = C.c_int
+    lib.povar_create.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.povar_batch_create.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.POINTER(C.c_void_p)]
+    lib.povar_destroy.argtypes = [C.c_void_p]
+    cam = (C.c_int32 * 2)(0, 0)
+    pt = (C.c_int32 * 2)(0, 0)
+    meas = (C.c_double * 4)(0.0, 0.0, 0.1, 0.1)
+    p = lambda a: C.cast(a, C.c_void_p)
+    out = C.c_void_p(12345)
+    cases = [(0, 1, 2, p(cam), p(pt), p(meas)),          # no cameras
+             (1, 0, 2, p(cam), p(pt), p(meas)),          # no landmarks
+             (1, 1, 0, p(cam), p(pt), p(meas)),          # no observations
+             (1, 1, 1 << 31, p(cam), p(pt), p(meas)),    # observation count beyond int32
+             (1, 1, 2, None, p(pt), p(meas)),
+             (1, 1, 2, p(cam), None, p(meas)),
+             (1, 1, 2, p(cam), p(pt), None)]
+    for n_c, n_p, n_o, a, b, m in cases:
+        out.value = 12345
+        assert lib.povar_create(n_c, n_p, n_o, a, b, m, None, C.byref(out)) == 1
+        assert out.value is None
+    assert lib.povar_create(1, 1, 2, p(cam), p(pt), p(meas), None, None) == 1
+    nc, npt, nob = (C.c_int32 * 1)(1), (C.c_int32 * 1)(1), (C.c_int64 * 1)(2)
+    out.value = 12345
+    assert lib.povar_batch_create(0, p(nc), p(npt), p(nob), p(cam), p(pt), p(meas), None,
+                                  C.byref(out)) == 1
+    assert out.value is None
+    assert lib.povar_batch_create(1, None, p(npt), p(nob), p(cam), p(pt), p(meas), None,
+                                  C.byref(out)) == 1
+    lib.povar_destroy(None)
+
+
+def test_estimate_bytes_grows_with_each_size(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.povar_estimate_bytes.restype = ctypes.c_int64
+    lib.povar_estimate_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]
+    base = lib.povar_estimate_bytes(100, 10_000, 50_000)
+    assert base > 50_000 * 12 + 10_000 * 40
+    assert lib.povar_estimate_bytes(200, 10_000, 50_000) > base
+    assert lib.povar_estimate_bytes(100, 20_000, 50_000) > base
+    assert lib.povar_estimate_bytes(100, 10_000, 100_000) > base
