@@ -59,8 +59,10 @@ cudaError_t library_pool(cudaMemPool_t* out) {
   cudaMemPool_t pool;
   if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
   uint64_t keep = UINT64_MAX;
-  if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess)
+  if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+    cudaMemPoolDestroy(pool);
     return e;
+  }
   g_pools.emplace_back(dev, pool);
   *out = pool;
   return cudaSuccess;
