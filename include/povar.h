@@ -309,11 +309,12 @@ povar_status povar_batch_solve_each(povar_batch* b, const povar_params* params,
                                     povar_step_report* reports, int32_t* iters_out);
 
 /* ---- allocation-free cost evaluation ----
- * No counterpart in the paper: a library utility. It evaluates the same
- * quantity as povar_set_cameras + povar_cost + povar_get_points (the pOSE
- * cost of Eq. ba_first_stage with every landmark eliminated in closed form
- * by Eq. update_landmark, pseudo-inverse for rank-deficient V_j, all in
- * FP64) without a problem handle and without allocating any memory.
+ * No counterpart in the paper: a library utility. It returns the pOSE cost
+ * at the given cameras with every landmark eliminated in closed form (each
+ * landmark is the least-squares point of its observations for those cameras,
+ * a pseudo-inverse where its 3x3 normal block is rank-deficient), all in
+ * FP64: the same value as povar_set_cameras + povar_cost + povar_get_points,
+ * but without a problem handle and without allocating any memory.
  *
  * Who needs it: callers that must not allocate at the point of the call.
  * cudaMalloc and cudaFree synchronize the device, so a latency-critical loop
@@ -327,27 +328,34 @@ povar_status povar_batch_solve_each(povar_batch* b, const povar_params* params,
  * which bounds the problem size.
  *
  * Inputs (all DEVICE pointers, caller-owned, only read): P = n_cams x 12
- * row-major FP64 cameras; the observations in landmark-major order:
- * off_pt[n_points + 1] (u32, observations of landmark j are
- * off_pt[j] .. off_pt[j+1]-1), cam[n_obs] (i32 camera index) and
+ * row-major FP64 cameras, 16-byte aligned; the observations in
+ * landmark-major order: off_pt[n_points + 1] (u32, observations of landmark
+ * j are off_pt[j] .. off_pt[j+1]-1), cam[n_obs] (i32 camera index) and
  * meas[n_obs x 2] (FP64 normalized coordinates, 16-byte aligned). Outputs
- * (DEVICE pointers, caller-owned): cost_out[1] receives the cost; X_out
- * (n_points x 3 FP64, may be NULL) receives the landmarks. Work is enqueued
- * on cuda_stream (NULL = legacy default stream) and nothing is
+ * (DEVICE pointers, caller-owned, 8-byte aligned): cost_out[1] receives the
+ * cost; X_out (n_points x 3 FP64, may be NULL) receives the landmarks. Work
+ * is enqueued on cuda_stream (NULL = legacy default stream) and nothing is
  * synchronized: the outputs are ready when the stream reaches this point.
  *
  * Errors: POVAR_EINVAL for a NULL pointer, a size < 1, eta outside [0, 1],
- * or n_points > POVAR_NOALLOC_MAX_POINTS (the fixed working array would be
- * too small); nothing is launched then. POVAR_ECUDA if the set-up or a
- * launch fails. Index errors are detected on the device without a host
- * round trip: a camera index outside [0, n_cams) or an offset table that is
- * decreasing or points past n_obs makes *cost_out NaN (the offending
- * observations are skipped, never read out of bounds).
+ * n_points > POVAR_NOALLOC_MAX_POINTS (the fixed working array would be too
+ * small), or a pointer that is not aligned as stated above (P and meas to 16
+ * bytes, off_pt and cam to 4, cost_out and X_out to 8); these checks make no
+ * CUDA call and nothing is launched. POVAR_ECUDA, with nothing launched, if
+ * a CUDA error from earlier work is already pending on the calling thread
+ * (it is left pending for its owner); POVAR_ECUDA also if the set-up or a
+ * launch of this call fails. Index errors are detected on the device
+ * without a host round trip: a camera index outside [0, n_cams) or an
+ * offset table that is decreasing or points past n_obs makes *cost_out NaN
+ * (the offending observations are skipped, never read out of bounds).
  *
  * Set-up and concurrency: the first call on each device (with that device
  * current) looks up the device address of the library's working array
  * (cudaGetSymbolAddress, which also loads the library's device code if it
- * is not yet loaded); make that first call before any stream capture.
+ * is not yet loaded); make that first call before any stream capture. The
+ * address is kept for the life of the process: after cudaDeviceReset on a
+ * device this entry point must not be called on that device again (the kept
+ * address belonged to the destroyed context).
  * All calls on one device share the same working array, so calls whose
  * executions overlap in time (on different streams or from different host
  * threads without ordering between them) race and may return a wrong cost;

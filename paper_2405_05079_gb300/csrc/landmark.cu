@@ -812,13 +812,26 @@ extern "C" povar_status povar_cost_noalloc(int32_t n_cams, int32_t n_points, int
                                            const int32_t* cam, const double* meas, double eta,
                                            double* X_out, double* cost_out, void* cuda_stream) {
   using namespace povar;
+  // argument checks first: they make no CUDA call
   if (!P || !off_pt || !cam || !meas || !cost_out) return POVAR_EINVAL;
   if (n_cams < 1 || n_points < 1 || n_obs < 1) return POVAR_EINVAL;
   if (n_points > POVAR_NOALLOC_MAX_POINTS) return POVAR_EINVAL;
   if (!(eta >= 0.0 && eta <= 1.0)) return POVAR_EINVAL;
+  // the kernel reads P and meas as 16-byte pairs and the other arrays as
+  // their own element type: a misaligned pointer is refused here instead of
+  // faulting on the device
+  const auto misaligned = [](const void* q, uintptr_t align) {
+    return (reinterpret_cast<uintptr_t>(q) & (align - 1)) != 0;
+  };
+  if (misaligned(P, 16) || misaligned(meas, 16) || misaligned(off_pt, 4) ||
+      misaligned(cam, 4) || misaligned(cost_out, 8) || (X_out && misaligned(X_out, 8)))
+    return POVAR_EINVAL;
+  // an error left pending by earlier, unrelated work belongs to its owner:
+  // report it without consuming it, and launch nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return POVAR_ECUDA;
   double* part = nullptr;
   if (na_scratch(&part) != cudaSuccess) {
-    cudaGetLastError();
+    cudaGetLastError();   // the error of this call's own look-up
     return POVAR_ECUDA;
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -826,6 +839,7 @@ extern "C" povar_status povar_cost_noalloc(int32_t n_cams, int32_t n_points, int
   k_landmark_csr<<<nb, NA_BLOCK, 0, s>>>(P, n_cams, off_pt, cam,
                                          reinterpret_cast<const double2*>(meas), n_obs, n_points,
                                          eta, X_out, part);
+  if (cudaGetLastError() != cudaSuccess) return POVAR_ECUDA;
   k_noalloc_sum<<<1, 256, 0, s>>>(part, nb, cost_out);
   if (cudaGetLastError() != cudaSuccess) return POVAR_ECUDA;
   return POVAR_OK;

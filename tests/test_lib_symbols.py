@@ -117,3 +117,36 @@ def test_estimate_bytes_grows_with_each_size(libpath):
     assert lib.povar_estimate_bytes(200, 10_000, 50_000) > base
     assert lib.povar_estimate_bytes(100, 20_000, 50_000) > base
     assert lib.povar_estimate_bytes(100, 10_000, 100_000) > base
+
+
+def test_binding_noalloc_limit_equals_the_header():
+    """The binding's copy of POVAR_NOALLOC_MAX_POINTS is the header's value."""
+    from paper_2405_05079_gb300 import povar
+    text = open(os.path.join(ROOT, "include", "povar.h")).read()
+    m = re.search(r"POVAR_NOALLOC_MAX_POINTS\s*=\s*(\d+)", text)
+    assert m and int(m.group(1)) == povar.NOALLOC_MAX_POINTS
+
+
+def test_noalloc_rejects_misaligned_pointers_before_any_cuda_call(libpath):
+    """povar_cost_noalloc checks the alignment of every device pointer on the
+    host (P and meas 16 bytes, off_pt and cam 4, cost_out and X_out 8) and
+    returns POVAR_EINVAL (1) before any CUDA call, so a misaligned caller
+    pointer never reaches the device. The addresses below are never
+    dereferenced: this runs without a GPU."""
+    C = ctypes
+    lib = C.CDLL(libpath)
+    f = lib.povar_cost_noalloc
+    f.restype = C.c_int
+    f.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                  C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
+    base = 1 << 20
+    good = dict(P=base, off=base + 0x1000, cam=base + 0x2000, meas=base + 0x3000,
+                X=base + 0x4000, F=base + 0x5000)
+
+    def call(**kw):
+        a = {**good, **kw}
+        return f(2, 3, 6, a["P"], a["off"], a["cam"], a["meas"], 0.1, a["X"], a["F"], None)
+
+    for bad in (dict(P=base + 8), dict(meas=base + 0x3008), dict(off=base + 0x1002),
+                dict(cam=base + 0x2001), dict(F=base + 0x5004), dict(X=base + 0x4004)):
+        assert call(**bad) == 1, bad
