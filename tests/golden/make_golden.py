@@ -15,7 +15,16 @@ CUDA path.
 "mid_m<k>" runs the mid scene with the series at m = k terms for the paper's
 50 iterations (no decrease rule), for the comparison of series lengths.
 
+Every series run also stores its final cameras "P" and the damping state
+("lambda", "nu"), so that a later run can resume the oracle exactly.
+"large_more" resumes the large scene from the state stored in
+converged_large.json and continues until the paper's stop rule (Sec. 5.2:
+an accepted step with relative decrease below 1e-6) or 400 more iterations,
+so that the cost after the 50-iteration budget can be compared with the
+cost at the stop rule.
+
     python tests/golden/make_golden.py [tiny] [mid] [large] [mid_m5] [mid_m10] [mid_m20]
+                                       [large_more]
 """
 import json
 import os
@@ -61,13 +70,48 @@ def run(name):
         st, reps = pr.solve(P0, prm, max_iters=max_iters, ftol=ftol, callback=cb)
         out[solver] = {"F": st.F, "iterations": len(reps), "F0": reps[0].cost_before,
                        "seconds": time.time() - t, "trace": trace}
-        if solver == "series" and scene != "large":
+        if solver == "series":
             out[solver]["P"] = st.P.tolist()
+            out[solver]["lambda"] = st.lam
+            out[solver]["nu"] = st.nu
         print(name, solver, len(reps), st.F, f"{time.time() - t:.1f}s", flush=True)
     with open(os.path.join(HERE, f"converged_{name}.json"), "w") as f:
         json.dump(out, f, indent=1)
 
 
+def run_more(max_more=400, ftol=1e-6):
+    """Resume the large scene from its stored 50-iteration state."""
+    with open(os.path.join(HERE, "converged_large.json")) as f:
+        base = json.load(f)
+    sc = scenes.scene_by_name("large", 0)
+    pr = O.MatrixFreeProblem(sc.n_cams, sc.n_points, sc.cam_idx, sc.pt_idx, sc.meas)
+    prm = O.Params(eta=sc.eta, m=base["m"], series_eps=base["series_eps"], manifold=O.EUCLID,
+                   solver="series", lambda0=base["lambda0"])
+    b = base["series"]
+    P = np.asarray(b["P"], dtype=np.float64)
+    X = pr.landmarks(P, sc.eta)
+    st = O.State(P=P, X=X, F=pr.cost(P, X, sc.eta), lam=b["lambda"], nu=b["nu"],
+                 iteration=b["iterations"])
+    t = time.time()
+    trace = []
+    for _ in range(max_more):
+        st, rep = pr.step(st, prm)
+        trace.append([rep.cost_after if rep.accepted else rep.cost_before,
+                      round(time.time() - t, 2), int(rep.terms_used)])
+        print("large_more", st.iteration, trace[-1], flush=True)
+        if rep.accepted and (rep.cost_before - rep.cost_after) < ftol * rep.cost_before:
+            break
+        if st.lam > O.LAMBDA_MAX:
+            break
+    out = {"scene": "large", "resumed_from": "converged_large.json", "start_iteration":
+           b["iterations"], "F_start": b["F"], "ftol": ftol, "F": st.F,
+           "iterations": st.iteration, "stopped_by_rule": len(trace) < max_more,
+           "seconds": time.time() - t, "trace": trace, "lambda": st.lam, "nu": st.nu,
+           "source": "tests/golden/make_golden.py (oracle/povar_oracle.py only)"}
+    with open(os.path.join(HERE, "converged_large_more.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
 if __name__ == "__main__":
     for n in (sys.argv[1:] or ["tiny", "mid"]):
-        run(n)
+        run_more() if n == "large_more" else run(n)

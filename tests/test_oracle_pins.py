@@ -91,6 +91,55 @@ def test_landmarks_match_bruteforce_lstsq(tiny):
     assert np.all(np.abs(X - Xb) <= 1e-8 * np.maximum(scale, 1.0))
 
 
+def test_pseudo_inverse_branch_gives_minimum_norm_landmarks(tiny):
+    """At eta = 0 an observation constrains its landmark only through the two
+    rows of the projective error (B_k has rank 2), so a landmark seen once
+    has a singular V_j (footnote of Sec. 4.2: pseudo-inverse). The minimum-norm
+    least-squares solution of its stacked 4k x 3 system -- what the library
+    least-squares solver returns -- is V_j^+ (-h_j), so the pseudo-inverse
+    branch must reproduce landmark_bruteforce exactly where V_j is singular,
+    and the ordinary inverse must reproduce it where it is not."""
+    pr0, P, _, _ = _state(tiny)
+    keep = np.ones(len(pr0.pt_idx), bool)
+    single = np.arange(0, pr0.n_points, 3)            # every third landmark: one view
+    for j in single:
+        ks = np.nonzero(pr0.pt_idx == j)[0]
+        keep[ks[1:]] = False
+    cam, pt, meas = pr0.cam_idx[keep], pr0.pt_idx[keep], pr0.meas[keep]
+    assert np.all(np.bincount(pt, minlength=pr0.n_points)[single] == 1)
+    X, V, n_pinv = O.landmarks(P, cam, pt, meas, 0.0, pr0.n_points, return_V=True)
+    assert n_pinv == len(single)                       # exactly the single-view landmarks
+    Xb = O.landmark_bruteforce(P, cam, pt, meas, 0.0, pr0.n_points)
+    scale = np.maximum(np.abs(Xb).max(axis=1, keepdims=True), 1.0)
+    assert np.all(np.abs(X - Xb) <= 1e-8 * scale)
+    # the single-view solutions are minimum-norm: orthogonal to the null space of V_j
+    for j in single[:20]:
+        w, E = np.linalg.eigh(V[j])
+        assert abs(E[:, 0] @ X[j]) <= 1e-8 * max(1.0, np.linalg.norm(X[j]))
+    # and solve the consistent 2x3 projective system exactly (zero residual)
+    F_single = O.cost(P, X, cam, pt, meas, 0.0)
+    sel = np.isin(pt, single)
+    r = O.pose_residuals(P, X, cam[sel], pt[sel], meas[sel], 0.0)
+    assert np.abs(r).max() <= 1e-9 * max(1.0, F_single)
+
+
+def test_sym_inverse_batch_picks_the_branch_by_condition():
+    """Blocks with a known spectrum: a well-conditioned block gets its
+    inverse, a block with a zero eigenvalue and one with cond = 1e14 get the
+    pseudo-inverse E diag(1/w or 0) E^T, written out from the construction."""
+    rng = np.random.default_rng(4)
+    E, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    spectra = [np.array([3.0, 2.0, 0.5]), np.array([3.0, 2.0, 0.0]),
+               np.array([3.0, 2.0, 3e-14])]
+    V = np.stack([E @ np.diag(w) @ E.T for w in spectra])
+    inv, n_pinv = O.sym_inverse_batch(V)
+    assert n_pinv == 2
+    for k, w in enumerate(spectra):
+        keep = w > w.max() / O.PINV_COND
+        d = np.where(keep, 1.0 / np.where(keep, w, 1.0), 0.0)
+        assert np.allclose(inv[k], E @ np.diag(d) @ E.T, rtol=1e-9, atol=1e-9)
+
+
 def test_landmark_first_order_optimality(tiny):
     """b_l = J_l^T r = 0 at X*(P) (first-order optimality of Eq. update_landmark)."""
     pr, P, X, eta = _state(tiny)
@@ -237,6 +286,36 @@ def test_series_converges_with_proposition1_bound(micro, manifold):
         errs.append(err)
     assert all(b <= a * (1 + 1e-12) for a, b in zip(errs, errs[1:]))
     assert errs[-1] < 1e-3 * enorm(exact) or rho > 0.9
+
+
+def test_exact_step_falls_back_to_floored_eigen_solve():
+    """When rounding leaves S numerically indefinite, exact_step solves with
+    every eigenvalue floored at lambda (S >= lambda I holds in exact
+    arithmetic). S is built from a known orthonormal E and spectrum w with a
+    negative entry, so Cholesky fails; the expected step
+    E diag(1 / max(w, lambda)) E^T g is written from the construction."""
+    rng = np.random.default_rng(5)
+    n = 12
+    E, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    w = np.geomspace(10.0, 1e-3, n)
+    w[-1] = -0.02                     # indefinite: Cholesky must fail
+    w[-2] = 0.004                     # below lambda: floored too
+    lam = 0.01
+    S = E @ np.diag(w) @ E.T
+    S = 0.5 * (S + S.T)
+    g = rng.normal(size=n)
+    with pytest.raises(np.linalg.LinAlgError):
+        sla.cho_factor(S, lower=True)
+    rs = O.ReducedSystem(Ut=None, Wt=None, Vinv=None, S=S, g=g, Q=None, lam=lam)
+    d = O.exact_step(rs)
+    expect = E @ ((E.T @ g) / np.maximum(w, lam))
+    assert np.allclose(d, expect, rtol=1e-10, atol=1e-12 * np.linalg.norm(expect))
+    # an SPD S takes the Cholesky branch: the plain solve
+    S_pd = E @ np.diag(np.abs(w) + lam) @ E.T
+    rs_pd = O.ReducedSystem(Ut=None, Wt=None, Vinv=None, S=0.5 * (S_pd + S_pd.T), g=g, Q=None,
+                            lam=lam)
+    expect_pd = E @ ((E.T @ g) / (np.abs(w) + lam))
+    assert np.allclose(O.exact_step(rs_pd), expect_pd, rtol=1e-9, atol=1e-12)
 
 
 def test_series_first_term_and_large_damping(micro):
