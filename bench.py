@@ -5,11 +5,16 @@ One timed step is one full first-stage solve of the large synthetic scene
 (1,800 cameras on a trajectory, 1,000,000 landmarks, ~5,000,000 observations,
 0.5 px noise, 1% outliers; a stand-in for BAL venice-1672) from the random
 camera initialization of the paper's experiments until the pOSE cost is
-within 1e-5 relative of F*, the FP64 CPU oracle's converged cost from the same
-start (tests/golden/converged_large.json). Solver settings follow Sec. 5.2 of
-the paper: eta = 0.1, lambda0 = 1e-4, series order 20 (m = 21 terms) with
-threshold 0.01; mixed precision (FP32 series / linearization, FP64 landmark
-elimination, 12x12 inverses, cost and gain ratio).
+within 1e-5 relative of F*, the FP64 CPU oracle's cost after the paper's
+iteration budget of 50 LM iterations (Sec. 5.2) from the same start
+(tests/golden/converged_large.json). F* is NOT a converged cost: at the 50th
+iteration the oracle's cost still falls by about 0.2% per iteration. Solver
+settings follow Sec. 5.2 of the paper: eta = 0.1, lambda0 = 1e-4, series
+order 20 (m = 21 terms) with threshold 0.01; mixed precision (FP32 series /
+linearization, FP64 12x12 inverses, cost and gain ratio, landmark
+elimination in FP64 at given cameras and in double-float for the trial
+cameras of a step). The same line reports the plain FP64 GPU path's time to
+the same target and the mixed result's error against the FP64 result.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -82,6 +87,32 @@ def oracle_iters_to_target(g: dict, target: float) -> int:
         if F <= target:
             return i + 1
     return len(g["series"]["trace"])
+
+
+def aligned_camera_error(P, Pref) -> float:
+    """Largest entry difference of the unit-normalized cameras after the
+    least-squares affine gauge transform P_i -> P_i H (the pOSE cost is
+    invariant under P -> P H, X~ -> H^-1 X~ with H = [[A, t], [0, 1]])."""
+    A = np.asarray(P, dtype=np.float64).reshape(-1, 4)
+    B = np.asarray(Pref, dtype=np.float64).reshape(-1, 4)
+    H = np.linalg.lstsq(A, B, rcond=None)[0]
+    Q = (A @ H).reshape(-1, 12)
+    Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    R = B.reshape(-1, 12) / np.linalg.norm(B.reshape(-1, 12), axis=1, keepdims=True)
+    return float(np.abs(Q - R).max())
+
+
+def oracle_stop_rule_reference(workload: str) -> dict | None:
+    """The oracle resumed from its 50-iteration state to the Sec. 5.2 stop
+    rule (tests/golden/converged_large_more.json), when that file exists."""
+    if workload != "large":
+        return None
+    try:
+        g = load_golden("large_more")
+    except OSError:
+        return None
+    return {"F": g["F"], "iterations": g["iterations"], "stopped_by_rule": g["stopped_by_rule"],
+            "ftol": g["ftol"]}
 
 
 def solver_params(povar, g: dict, precision: int, schedule: int = -1):
@@ -301,7 +332,7 @@ def run_ours(args, rank: int, world: int) -> dict | None:
             rep, iters = one_solve()
             ev[k + 1].record(stream)
             results.append((rep.cost_after if rep.accepted else rep.cost_before, iters,
-                            rep.terms_used))
+                            rep.terms_used, rep.fp64_fallback_at))
         torch.cuda.synchronize(dev)
     if dist is not None:
         dist.barrier()
@@ -319,6 +350,36 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         sched = args.schedule
     clocks = clk.summary()
     final_cost = pb.cost(g["eta"])
+    final_P = pb.cameras()
+
+    # ---- the plain FP64 GPU path to the same target (outside the timed
+    # region): one untimed solve (schedule tuning, graph capture), one timed
+    fp64_path = err_vs_fp64 = None
+    if rank == 0 and prec != povar.FP64 and not args.no_fp64_arm:
+        p64 = solver_params(povar, g, povar.FP64, -1)
+        ev64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for k in range(2):
+            pb.set_cameras_device(dP0.data_ptr(), g["eta"])
+            torch.cuda.synchronize(dev)
+            ev64[0].record(stream)
+            rep64, it64 = pb.solve(p64, max_iters=args.max_iters, ftol=0.0, target_cost=target,
+                                   allow_stall=True)
+            ev64[1].record(stream)
+            torch.cuda.synchronize(dev)
+        F64 = pb.cost(g["eta"])
+        P64 = pb.cameras()
+        fp64_path = {"value": round(ev64[0].elapsed_time(ev64[1]) / 1e3, 5), "unit": "s",
+                     "lm_iterations": int(it64), "final_cost": F64,
+                     "reached_target": bool(F64 <= target),
+                     "schedule": pb.tuning(povar.FP64)[0],
+                     "note": "same workload, target and timing as `value`, precision FP64 "
+                             "throughout (one untimed solve first)"}
+        err_vs_fp64 = {"final_cost_rel": abs(final_cost - F64) / F64,
+                       "aligned_cameras_max_abs": aligned_camera_error(final_P, P64),
+                       "note": "mixed result of the timed solves against the FP64 result, each "
+                               "at the first iterate with cost <= target (the two stop at "
+                               "different iterates of a still-decreasing cost, so the "
+                               "difference includes up to one LM iteration of progress)"}
 
     # ---- e2e: the user's call sequence with host buffers
     e2e = None
@@ -404,7 +465,15 @@ def run_ours(args, rank: int, world: int) -> dict | None:
                                 f"{sc.n_obs} obs, {WORKLOAD_KIND[args.workload]}"),
                    "precision": args.precision, "manifold": "euclid (first stage, Sec. 3.2)",
                    "eta": g["eta"], "m": g["m"], "series_eps": g["series_eps"],
-                   "lambda0": g["lambda0"], "target_cost": target, "F_star_oracle": Fstar,
+                   "lambda0": g["lambda0"], "target_cost": target,
+                   "F_star_oracle_after_50_iterations": Fstar,
+                   "F_star_reading": ("the FP64 CPU oracle's cost after the paper's budget of 50 "
+                                      "LM iterations (Sec. 5.2) from the same start; not "
+                                      "converged"),
+                   "oracle_at_stop_rule": oracle_stop_rule_reference(args.workload),
+                   "trial_landmarks": ("double-float (FP32 pairs, ~48-bit significand) for the "
+                                       "trial cameras of a mixed step; FP64 at given cameras"
+                                       if prec != povar.FP64 else "FP64"),
                    "l2": (f"no flush: the problem's resident state ({pb.device_bytes / 1e9:.2f} "
                           f"GB) is larger than the 129 MB L2 and a timed step (one whole "
                           f"solve) streams all of it every LM iteration"),
@@ -418,6 +487,9 @@ def run_ours(args, rank: int, world: int) -> dict | None:
         "series_schedule": {"chosen": sched, "tuned_ms_per_term": [round(x, 4) for x in tune_ms]},
         "reached_target": bool(reached),
         "final_cost": final_cost,
+        "fp64_fallback_at": [int(r[3]) for r in results],
+        "fp64_path": fp64_path,
+        "err_vs_fp64": err_vs_fp64,
         "per_solve_ms": [round(x, 3) for x in per_solve],
         "solves_per_s_all_ranks": round(world * args.steps / (total_ms / 1e3), 3),
         "gpu_launches": int(launches),
@@ -643,6 +715,8 @@ def main(argv=None):
                          "timings, so profiled runs pin the schedule the plain run chose)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-arm", action="store_true",
+                    help="skip the FP64 GPU path's time to the same target")
     args = ap.parse_args(argv)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

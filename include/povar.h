@@ -124,7 +124,11 @@ typedef struct {
   int32_t iteration;
   int32_t converged;
   float ms;                  /* device time of the step (0 if not measured) */
-  float reserved[3];
+  int32_t precision;         /* precision the step ran in (POVAR_FP64 after the
+                                mixed-precision safeguard of povar_solve) */
+  int32_t fp64_fallback_at;  /* povar_solve: iteration at which the safeguard
+                                switched to FP64 (0: it did not) */
+  float reserved[1];
 } povar_step_report;
 
 /* Create a problem from the observation set Omega (Sec. 3):
@@ -189,7 +193,18 @@ povar_status povar_step(povar_problem* p, const povar_params* params,
  * ftol, the cost reaches target_cost (if > 0), or max_iters steps ran.
  * last (may be NULL) receives the report of the last step, iters_out (may
  * be NULL) the number of steps taken. Steps are issued without a host
- * round-trip in between; the stream is synchronized every few steps. */
+ * round-trip in between; the stream is synchronized every few steps.
+ *
+ * Mixed-precision safeguard (POVAR_MIXED_FP32 / POVAR_MIXED_BF16; not in
+ * the paper): when POVAR_FALLBACK_REJECTIONS consecutive mixed steps are
+ * rejected, the remaining steps of this solve run in POVAR_FP64 (same
+ * schedule rule, landmarks re-solved in FP64 first). FP32 series and
+ * linearizations cannot resolve the reduced camera system where it is a
+ * strong cancellation of much larger terms (e.g. landmarks drifting towards
+ * infinity at a small pOSE weight); there every damping is rejected and a
+ * pure mixed solve would stall. last->fp64_fallback_at reports the iteration
+ * at which it switched. povar_step and the batch solves never switch. */
+enum { POVAR_FALLBACK_REJECTIONS = 10 };
 povar_status povar_solve(povar_problem* p, const povar_params* params,
                          int32_t max_iters, double ftol, double target_cost,
                          povar_step_report* last, int32_t* iters_out);

@@ -265,7 +265,7 @@ povar_status enqueue_step_kernels(Problem* p, const povar_params* q, std::vector
   if ((s = launch_landmarks(p, 1, q->eta, prec)) != POVAR_OK) return s;
   if ((s = launch_cost_finish(p, 1)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
-  if ((s = launch_controller(p)) != POVAR_OK) return s;
+  if ((s = launch_controller(p, prec)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   p->last_precision = prec;
   return POVAR_OK;
@@ -404,6 +404,69 @@ povar_status step_graph(Problem* p, const povar_params* q) {
 void fill_report(Problem* p, povar_step_report* r, float ms) {
   *r = *p->h_report;
   r->ms = ms;
+}
+
+// Up to max_iters steps with parameters q (launch_begin done by the caller),
+// synchronizing the state every few steps and stopping at the device's
+// convergence flag; on return p->h_state is current.
+povar_status solve_loop(Problem* p, const povar_params* q, int max_iters) {
+  povar_status s;
+  const int check_every = 4;
+  if (p->use_graphs) {
+    // one graph launch per step on the library stream, joined to the
+    // caller's stream with events before and after
+    if ((s = prepare_step(p, q)) != POVAR_OK) return s;
+    if (q->schedule < 0 && (s = autotune_schedule(p, q)) != POVAR_OK) return s;
+    if ((s = step_graph(p, q)) != POVAR_OK) return s;
+    POVAR_CUDA(cudaEventRecord(p->ev_join, p->stream));
+    POVAR_CUDA(cudaStreamWaitEvent(p->gstream, p->ev_join, 0));
+    cudaStream_t user = p->stream;
+    p->stream = p->gstream;
+    // the phase events hold the last launched step: it is sampled when it
+    // did work, i.e. when every launch since the last sample advanced the
+    // iteration count (launches after convergence return at once)
+    int since = 0, iter_mark = p->h_state->iteration;
+    auto sample = [&]() -> povar_status {
+      if ((s = sync_state(p)) != POVAR_OK) return s;
+      sample_graph_profile(p, since > 0 && p->h_state->iteration - iter_mark == since);
+      iter_mark = p->h_state->iteration;
+      since = 0;
+      return POVAR_OK;
+    };
+    for (int it = 0; it < max_iters; ++it) {
+      const cudaError_t e = cudaGraphLaunch(p->gexec, p->gstream);
+      if (e != cudaSuccess) {
+        p->stream = user;
+        return fail(p, POVAR_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+      }
+      p->launches += p->g_launches;
+      ++since;
+      if ((it + 1) % check_every == 0 && it + 1 < max_iters) {
+        if (sample() != POVAR_OK) {
+          p->stream = user;
+          return s;
+        }
+        if (p->h_state->converged) break;
+      }
+    }
+    if (since > 0 && sample() != POVAR_OK) {
+      p->stream = user;
+      return s;
+    }
+    POVAR_CUDA(cudaEventRecord(p->ev_join, p->gstream));
+    p->stream = user;
+    POVAR_CUDA(cudaStreamWaitEvent(p->stream, p->ev_join, 0));
+  } else {
+    for (int it = 0; it < max_iters; ++it) {
+      if ((s = enqueue_step(p, q)) != POVAR_OK) return s;
+      if ((it + 1) % check_every == 0 && it + 1 < max_iters) {
+        if ((s = sync_state(p)) != POVAR_OK) return s;
+        if (p->h_state->converged) break;
+      }
+    }
+    if ((s = sync_state(p)) != POVAR_OK) return s;
+  }
+  return POVAR_OK;
 }
 
 }  // namespace
@@ -717,61 +780,24 @@ povar_status povar_solve(povar_problem* pp, const povar_params* params, int32_t 
   if (max_iters < 1) return povar::fail(p, POVAR_EINVAL, "max_iters must be >= 1");
   if ((s = povar::sync_state(p)) != POVAR_OK) return s;
   const int it0 = p->h_state->iteration;
-  if ((s = povar::launch_begin(p, ftol, target_cost, max_iters)) != POVAR_OK) return s;
+  povar_params q = *params;
+  const bool mixed = q.precision != POVAR_FP64;
+  if ((s = povar::launch_begin(p, ftol, target_cost, max_iters,
+                               mixed ? POVAR_FALLBACK_REJECTIONS : 0)) != POVAR_OK)
+    return s;
   POVAR_CUDA(cudaEventRecord(p->ev0, p->stream));
-  const int check_every = 4;
-  if (p->use_graphs) {
-    // one graph launch per step on the library stream, joined to the
-    // caller's stream with events before and after
-    if ((s = povar::prepare_step(p, params)) != POVAR_OK) return s;
-    if (params->schedule < 0 && (s = povar::autotune_schedule(p, params)) != POVAR_OK) return s;
-    if ((s = povar::step_graph(p, params)) != POVAR_OK) return s;
-    POVAR_CUDA(cudaEventRecord(p->ev_join, p->stream));
-    POVAR_CUDA(cudaStreamWaitEvent(p->gstream, p->ev_join, 0));
-    cudaStream_t user = p->stream;
-    p->stream = p->gstream;
-    // the phase events hold the last launched step: it is sampled when it
-    // did work, i.e. when every launch since the last sample advanced the
-    // iteration count (launches after convergence return at once)
-    int since = 0, iter_mark = it0;
-    auto sample = [&]() -> povar_status {
-      if ((s = povar::sync_state(p)) != POVAR_OK) return s;
-      povar::sample_graph_profile(p, since > 0 && p->h_state->iteration - iter_mark == since);
-      iter_mark = p->h_state->iteration;
-      since = 0;
-      return POVAR_OK;
-    };
-    for (int it = 0; it < max_iters; ++it) {
-      const cudaError_t e = cudaGraphLaunch(p->gexec, p->gstream);
-      if (e != cudaSuccess) {
-        p->stream = user;
-        return povar::fail(p, POVAR_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
-      }
-      p->launches += p->g_launches;
-      ++since;
-      if ((it + 1) % check_every == 0 && it + 1 < max_iters) {
-        if (sample() != POVAR_OK) {
-          p->stream = user;
-          return s;
-        }
-        if (p->h_state->converged) break;
-      }
-    }
-    if (since > 0 && sample() != POVAR_OK) {
-      p->stream = user;
+  int fallback_at = 0;
+  for (;;) {
+    const int budget = it0 + max_iters - p->h_state->iteration;
+    if ((s = povar::solve_loop(p, &q, budget)) != POVAR_OK) return s;
+    // the mixed-precision safeguard stopped the solve: continue in FP64
+    if (!p->h_state->fallback || q.precision == POVAR_FP64) break;
+    fallback_at = p->h_state->iteration;
+    q.precision = POVAR_FP64;
+    if (it0 + max_iters - fallback_at <= 0) break;
+    if ((s = povar::launch_begin(p, ftol, target_cost, it0 + max_iters - fallback_at, 0)) !=
+        POVAR_OK)
       return s;
-    }
-    POVAR_CUDA(cudaEventRecord(p->ev_join, p->gstream));
-    p->stream = user;
-    POVAR_CUDA(cudaStreamWaitEvent(p->stream, p->ev_join, 0));
-  } else {
-    for (int it = 0; it < max_iters; ++it) {
-      if ((s = povar::enqueue_step(p, params)) != POVAR_OK) return s;
-      if ((it + 1) % check_every == 0 && it + 1 < max_iters) {
-        if ((s = povar::sync_state(p)) != POVAR_OK) return s;
-        if (p->h_state->converged) break;
-      }
-    }
   }
   POVAR_CUDA(cudaEventRecord(p->ev1, p->stream));
   POVAR_CUDA(cudaMemcpyAsync(p->h_report, p->d_report, sizeof(povar_step_report),
@@ -779,7 +805,10 @@ povar_status povar_solve(povar_problem* pp, const povar_params* params, int32_t 
   if ((s = povar::sync_state(p)) != POVAR_OK) return s;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, p->ev0, p->ev1);
-  if (last) povar::fill_report(p, last, ms);
+  if (last) {
+    povar::fill_report(p, last, ms);
+    last->fp64_fallback_at = fallback_at > 0 ? fallback_at - it0 : 0;
+  }
   if (iters_out) *iters_out = p->h_state->iteration - it0;
   if (p->h_state->error)
     return povar::fail(p, (povar_status)p->h_state->error, "device reported an error");

@@ -83,6 +83,9 @@ struct DeviceState {
   int n_regularized; // camera blocks whose damping had to be raised (cumulative)
   long long products; // series products M y computed by all steps (never reset)
   int x_df[2];        // landmark buffer t holds X as double-float pairs (1) or FP64 (0)
+  int rej_run;        // consecutive rejected steps
+  int fallback_after; // mixed-precision safeguard: rejections that trigger it (0: off)
+  int fallback;       // set with `converged` when the safeguard triggered
 };
 
 // Host-side handle.
@@ -284,9 +287,10 @@ povar_status launch_build_blocks(Problem* p, int precision, double eta);
 
 // ---------------------------------------------------- step.cu (a9,a10)
 povar_status launch_update(Problem* p, int precision, int manifold);
-povar_status launch_controller(Problem* p);
+povar_status launch_controller(Problem* p, int precision);
 povar_status launch_init_state(Problem* p, double lambda0, int reset_lm, int reset_all);
-povar_status launch_begin(Problem* p, double ftol, double target, int max_iters);
+povar_status launch_begin(Problem* p, double ftol, double target, int max_iters,
+                          int fallback_after = 0);
 povar_status launch_random_cameras(Problem* p, uint64_t seed, int normalize);
 povar_status launch_gather_points(Problem* p, double* d_out);
 

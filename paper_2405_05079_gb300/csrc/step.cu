@@ -6,6 +6,12 @@
 //     the damping rule is Madsen-Nielsen: on accept lambda *= max(1/3,
 //     1 - (2 rho - 1)^3), nu = 2; on reject lambda *= nu, nu *= 2; lambda is
 //     kept >= LAMBDA_MIN and a damping above LAMBDA_MAX stops the solve).
+//     Mixed-precision safeguard (not in the paper): when fallback_after > 0
+//     and that many mixed-precision steps in a row were rejected, the
+//     controller stops the solve with `fallback` set, and the host continues
+//     it in FP64 (FP32 cannot resolve the reduced camera system when it is a
+//     strong cancellation of much larger terms, e.g. landmarks drifting
+//     towards infinity at a small pOSE weight).
 // Also: state initialization, device random cameras (Philox4x32-10 of
 //     Salmon et al., SC'11, with the Box-Muller transform) and the landmark
 //     gather back to the caller's numbering.
@@ -33,7 +39,8 @@ __global__ void k_update(const DeviceState* __restrict__ st, int manifold, int n
   for (int e = 0; e < 12; ++e) Pn[e] = q[e] * f;
 }
 
-__global__ void k_controller(DeviceState* __restrict__ st, povar_step_report* __restrict__ rep) {
+__global__ void k_controller(DeviceState* __restrict__ st, povar_step_report* __restrict__ rep,
+                             int precision) {
   if (st->converged) return;
   const double F = st->F, Fn = st->F_new, pred = st->pred;
   const double rho = pred > 0.0 ? (F - Fn) / pred : 0.0;
@@ -45,6 +52,7 @@ __global__ void k_controller(DeviceState* __restrict__ st, povar_step_report* __
   rep->lambda_used = st->lam_used;
   rep->accepted = accepted ? 1 : 0;
   rep->terms_used = st->terms_used;
+  rep->precision = precision;
   st->products += st->terms_used > 1 ? st->terms_used - 1 : 0;
   st->rho = rho;
   st->accepted = accepted ? 1 : 0;
@@ -58,12 +66,18 @@ __global__ void k_controller(DeviceState* __restrict__ st, povar_step_report* __
     st->cur = 1 - st->cur;
     st->F = Fn;
     st->need_lin = 1;
+    st->rej_run = 0;
     if (st->ftol > 0.0 && (F - Fn) < st->ftol * F) conv = 1;
     if (st->target > 0.0 && Fn <= st->target) conv = 1;
   } else {
     st->lam = st->lam * st->nu;
     st->nu = 2.0 * st->nu;
     st->need_lin = 0;
+    st->rej_run += 1;
+    if (precision != POVAR_FP64 && st->fallback_after > 0 && st->rej_run >= st->fallback_after) {
+      st->fallback = 1;
+      conv = 1;
+    }
   }
   if (st->max_iters > 0 && st->iteration >= st->max_iters) conv = 1;
   if (!(st->lam < LAMBDA_MAX)) {
@@ -91,16 +105,22 @@ __global__ void k_init_state(DeviceState* __restrict__ st, double lambda0, int r
     st->F_new = 0.0;
     st->pred = 0.0;
     st->rho = 0.0;
+    st->fallback_after = 0;
+    st->fallback = 0;
   }
   st->need_lin = 1;
   if (reset_lm) {
     st->lam = lambda0;
     st->nu = 2.0;
+    st->rej_run = 0;
   }
 }
 
-__global__ void k_begin(DeviceState* __restrict__ st, double ftol, double target, int max_iters) {
+__global__ void k_begin(DeviceState* __restrict__ st, double ftol, double target, int max_iters,
+                        int fallback_after) {
   st->converged = 0;
+  st->fallback = 0;
+  st->fallback_after = fallback_after;
   st->ftol = ftol;
   st->target = target;
   st->max_iters = max_iters > 0 ? st->iteration + max_iters : 0;
@@ -179,8 +199,8 @@ povar_status launch_update(Problem* p, int precision, int manifold) {
   return check_launch(p, "update");
 }
 
-povar_status launch_controller(Problem* p) {
-  k_controller<<<1, 1, 0, p->stream>>>(p->state, p->d_report);
+povar_status launch_controller(Problem* p, int precision) {
+  k_controller<<<1, 1, 0, p->stream>>>(p->state, p->d_report, precision);
   ++p->launches;
   return check_launch(p, "controller");
 }
@@ -191,8 +211,9 @@ povar_status launch_init_state(Problem* p, double lambda0, int reset_lm, int res
   return check_launch(p, "init_state");
 }
 
-povar_status launch_begin(Problem* p, double ftol, double target, int max_iters) {
-  k_begin<<<1, 1, 0, p->stream>>>(p->state, ftol, target, max_iters);
+povar_status launch_begin(Problem* p, double ftol, double target, int max_iters,
+                          int fallback_after) {
+  k_begin<<<1, 1, 0, p->stream>>>(p->state, ftol, target, max_iters, fallback_after);
   ++p->launches;
   return check_launch(p, "begin");
 }

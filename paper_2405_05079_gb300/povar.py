@@ -40,7 +40,8 @@ class StepReport(C.Structure):
     _fields_ = [("cost_before", C.c_double), ("cost_after", C.c_double), ("pred", C.c_double),
                 ("rho", C.c_double), ("lambda_used", C.c_double), ("lambda_next", C.c_double),
                 ("accepted", C.c_int32), ("terms_used", C.c_int32), ("iteration", C.c_int32),
-                ("converged", C.c_int32), ("ms", C.c_float), ("reserved", C.c_float * 3)]
+                ("converged", C.c_int32), ("ms", C.c_float), ("precision", C.c_int32),
+                ("fp64_fallback_at", C.c_int32), ("reserved", C.c_float * 1)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

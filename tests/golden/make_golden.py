@@ -23,8 +23,16 @@ an accepted step with relative decrease below 1e-6) or 400 more iterations,
 so that the cost after the 50-iteration budget can be compared with the
 cost at the stop rule.
 
+"midnear_m<k>" is the end-state reference of the mid scene: from the mid
+scene's standard start the exact (dense Cholesky) damped solve converges to
+a local minimum (relative decrease below 1e-12); every camera entry of that
+minimum is perturbed by 1e-3 times the mean absolute entry (seeded normal
+noise), and from there the series solve with m = k terms runs until its
+relative decrease is below 1e-12 (at most 400 iterations). The file stores
+the perturbed start, the final cost and cameras.
+
     python tests/golden/make_golden.py [tiny] [mid] [large] [mid_m5] [mid_m10] [mid_m20]
-                                       [large_more]
+                                       [large_more] [midnear_m5] [midnear_m10] [midnear_m20]
 """
 import json
 import os
@@ -112,6 +120,39 @@ def run_more(max_more=400, ftol=1e-6):
         json.dump(out, f, indent=1)
 
 
+def run_near(m):
+    """End-state reference of the mid scene at m series terms (see above)."""
+    sc = scenes.scene_by_name("mid", 0)
+    P0 = scenes.init_cameras(sc.n_cams, 1, normalize=True)
+    pr = O.Problem(sc.n_cams, sc.n_points, sc.cam_idx, sc.pt_idx, sc.meas)
+    ex = O.Params(eta=sc.eta, m=m, series_eps=SETTINGS["series_eps"], manifold=O.EUCLID,
+                  solver="exact", lambda0=SETTINGS["lambda0"])
+    st_ex, reps_ex = pr.solve(P0, ex, max_iters=200, ftol=1e-12)
+    rng = np.random.default_rng(7)
+    Pstart = st_ex.P + 1e-3 * np.abs(st_ex.P).mean() * rng.normal(size=st_ex.P.shape)
+    prm = O.Params(eta=sc.eta, m=m, series_eps=SETTINGS["series_eps"], manifold=O.EUCLID,
+                   solver="series", lambda0=SETTINGS["lambda0"])
+    t = time.time()
+    st, reps = pr.solve(Pstart, prm, max_iters=400, ftol=1e-12)
+    out = {"scene": "mid", "scene_seed": 0, "init_seed": 1, "eta": sc.eta, "m": m,
+           "series_eps": SETTINGS["series_eps"], "lambda0": SETTINGS["lambda0"],
+           "manifold": "euclid", "ftol": 1e-12, "perturbation": 1e-3, "perturbation_seed": 7,
+           "exact_minimum": {"F": st_ex.F, "iterations": len(reps_ex)},
+           "P_start": Pstart.tolist(), "F_start": reps[0].cost_before,
+           "series": {"F": st.F, "iterations": len(reps), "P": st.P.tolist(),
+                      "stopped_by_rule": len(reps) < 400, "seconds": time.time() - t,
+                      "trace": [r.cost_after if r.accepted else r.cost_before for r in reps]},
+           "source": "tests/golden/make_golden.py (oracle/povar_oracle.py only)"}
+    print(f"midnear_m{m}", st_ex.F, len(reps_ex), st.F, len(reps), flush=True)
+    with open(os.path.join(HERE, f"converged_midnear_m{m}.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
 if __name__ == "__main__":
     for n in (sys.argv[1:] or ["tiny", "mid"]):
-        run_more() if n == "large_more" else run(n)
+        if n == "large_more":
+            run_more()
+        elif n.startswith("midnear_m"):
+            run_near(int(n[len("midnear_m"):]))
+        else:
+            run(n)

@@ -26,6 +26,16 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def per_camera_rel(a, b):
+    """Largest relative difference of a single camera's 12-vector (a global
+    norm ratio can hide a few wrong cameras)."""
+    a = np.asarray(a, dtype=np.float64).reshape(-1, 12)
+    b = np.asarray(b, dtype=np.float64).reshape(-1, 12)
+    nb = np.linalg.norm(b, axis=1)
+    scale = np.maximum(nb, 1e-12 * max(nb.max(), 1e-300))
+    return float((np.linalg.norm(a - b, axis=1) / scale).max())
+
+
 def oracle_for(sc):
     return O.Problem(sc.n_cams, sc.n_points, sc.cam_idx, sc.pt_idx, sc.meas)
 
@@ -156,6 +166,7 @@ def test_one_step_fp64_matches_oracle(scene, manifold, schedule):
     assert rel(U, ne.U) <= 1e-10
     assert rel(bp, ne.b_p.reshape(-1, 12)) <= 1e-10
     assert rel(d, orep.delta) <= 1e-10
+    assert per_camera_rel(d, orep.delta) <= 1e-9
     assert abs(rep.cost_before - orep.cost_before) <= 1e-10 * orep.cost_before
     assert abs(rep.cost_after - orep.cost_after) <= 1e-10 * orep.cost_after
     assert abs(rep.pred - orep.pred) <= 1e-9 * abs(orep.pred)
@@ -229,9 +240,13 @@ def test_one_step_mixed_close_to_oracle(scene, manifold, schedule):
         rep = pb.step(povar.make_params(eta=scene.eta, m=scene.m, manifold=manifold,
                                         precision=povar.MIXED_FP32, schedule=schedule))
         _, _, d = pb.last_step()
-    assert rel(d, orep.delta) <= 1e-3
+    # the FP32 series term k carries ~k 2^-24 relative rounding times the
+    # amplification of the camera blocks; measured on GB300 at most 3.4e-6
+    # overall and 2.3e-5 for a single camera over these scenes and schedules
+    assert rel(d, orep.delta) <= 1e-4
+    assert per_camera_rel(d, orep.delta) <= 1e-4
     assert abs(rep.cost_before - orep.cost_before) <= 1e-10 * orep.cost_before
-    assert abs(rep.cost_after - orep.cost_after) <= 1e-4 * orep.cost_after
+    assert abs(rep.cost_after - orep.cost_after) <= 1e-5 * orep.cost_after
 
 
 @pytest.mark.parametrize("manifold", [O.SPHERE, O.EUCLID])
@@ -310,19 +325,50 @@ def test_solve_reaches_oracle_converged_cost_tiny():
         assert _affine_aligned_error(P, Pref) <= 1e-4, prec
 
 
+@pytest.mark.parametrize("m", [5, 10, 20])
+@pytest.mark.parametrize("precision", [povar.FP64, povar.MIXED_FP32])
+def test_end_state_mid_from_near_minimum(m, precision):
+    """Mid scene (50 cameras, 8,000 landmarks, eta = 0.01), series of m
+    terms: from the oracle's perturbed local minimum
+    (tests/golden/converged_midnear_m<m>.json, oracle only) the GPU solve
+    runs to the same stop rule (relative decrease below 1e-12) and reaches
+    the oracle's final cost within 1e-5 relative, with gauge-aligned,
+    unit-normalized cameras within 1e-4 entry by entry. The mixed solve gets
+    there without the FP64 safeguard."""
+    g = _golden(f"midnear_m{m}")
+    sc = scenes.scene_by_name("mid", g["scene_seed"])
+    Pstart = np.array(g["P_start"])
+    Fstar = g["series"]["F"]
+    Pref = np.array(g["series"]["P"])
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(Pstart, sc.eta)
+        assert abs(pb.cost(sc.eta) - g["F_start"]) <= 1e-10 * g["F_start"]
+        prm = povar.make_params(eta=g["eta"], m=m, series_eps=g["series_eps"],
+                                lambda0=g["lambda0"], manifold=povar.EUCLID, precision=precision)
+        rep, iters = pb.solve(prm, max_iters=400, ftol=g["ftol"])
+        F = pb.cost(sc.eta)
+        P = pb.cameras()
+    assert rep.fp64_fallback_at == 0
+    assert abs(F - Fstar) <= 1e-5 * Fstar, (F, Fstar, iters)
+    assert _affine_aligned_error(P, Pref) <= 1e-4
+
+
 def test_solve_trajectory_matches_oracle_mid():
     """Mid scene (eta = 0.01): the per-iteration costs of the oracle's trace
     (tests/golden/converged_mid.json) are reproduced by the FP64 GPU path to
-    1e-9 relative over the first 12 iterations (later, while the damped
-    iteration stalls on this ill-conditioned scene, rounding differences
-    grow; single steps stay at 1e-10), and by the mixed path to 1e-4 over
-    the first 3 (FP32 steps on this ill-conditioned scene then follow their
-    own trajectory)."""
+    1e-9 relative over the first 15 iterations and by the mixed path to 1e-4
+    over the first 5. Later the traces separate although every single step
+    still agrees (test_steps_along_the_mid_trajectory_match_the_oracle): on
+    this scene a third of the landmarks drift towards infinity (|X| ~ 1e6 by
+    iteration 40, cond V_j ~ 1e10), and the damped iteration amplifies
+    differences at the rounding level (1e-16 in FP64, 1e-7 in FP32) until
+    the two trajectories differ (measured on GB300: FP64 within 1e-9 up to
+    iteration 17, 1e-3 at 40; mixed within 2e-5 up to 5, 3e-3 at 19)."""
     g = _golden("mid")
     sc = scenes.scene_by_name("mid", g["scene_seed"])
     P0 = scenes.init_cameras(sc.n_cams, g["init_seed"], normalize=True)
     trace = [t[0] for t in g["series"]["trace"]]
-    for prec, n, tol in ((povar.FP64, 12, 1e-9), (povar.MIXED_FP32, 3, 1e-4)):
+    for prec, n, tol in ((povar.FP64, 15, 1e-9), (povar.MIXED_FP32, 5, 1e-4)):
         with povar.Problem.from_scene(sc) as pb:
             pb.set_cameras(P0, sc.eta)
             prm = _golden_params(g, prec)
@@ -330,6 +376,68 @@ def test_solve_trajectory_matches_oracle_mid():
                 rep = pb.step(prm)
                 F = rep.cost_after if rep.accepted else rep.cost_before
                 assert abs(F - trace[k]) <= tol * trace[k], (prec, k, F, trace[k])
+
+
+@pytest.mark.parametrize("precision,n,tol", [(povar.FP64, 30, 1e-9), (povar.MIXED_FP32, 15, 1e-3)])
+def test_steps_along_the_mid_trajectory_match_the_oracle(precision, n, tol):
+    """Every step of the GPU's own mid-scene trajectory equals the oracle's
+    step from the same state (cameras, closed-form landmarks, damping): the
+    step delta and the trial cost, accept / reject, terms used. FP64: 1e-9
+    (measured at most 3e-10 over 40 steps, the largest where |X| ~ 1e7).
+    Mixed: the FP32 series error is amplified by the camera blocks of
+    landmarks near infinity (measured 2e-6 at the start, up to 6e-4 once
+    |X| ~ 1e4..1e6), so 1e-3; the trial cost stays within 1e-5."""
+    g = _golden("mid")
+    sc = scenes.scene_by_name("mid", g["scene_seed"])
+    P0 = scenes.init_cameras(sc.n_cams, g["init_seed"], normalize=True)
+    orc = oracle_for(sc)
+    op = O.Params(eta=sc.eta, m=g["m"], series_eps=g["series_eps"], manifold=O.EUCLID,
+                  lambda0=g["lambda0"])
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        prm = _golden_params(g, precision)
+        for k in range(n):
+            P = pb.cameras()
+            rep = pb.step(prm)
+            _, _, d = pb.last_step()
+            X = orc.landmarks(P, sc.eta)
+            st = O.State(P=P, X=X, F=orc.cost(P, X, sc.eta), lam=rep.lambda_used)
+            _, orep = orc.step(st, op)
+            assert rel(d, orep.delta) <= tol, (k, rel(d, orep.delta))
+            assert abs(rep.cost_after - orep.cost_after) <= min(tol, 1e-5) * orep.cost_after, k
+            assert abs(rep.cost_before - orep.cost_before) <= 1e-10 * orep.cost_before, k
+            assert rep.accepted == int(orep.accepted), k
+            assert rep.terms_used == orep.terms_used, k
+
+
+def test_mixed_safeguard_reaches_the_mid_m5_target():
+    """Mid scene, m = 5: a pure mixed-precision run (povar_step, which never
+    switches) wanders with the oracle into the region where landmarks drift
+    towards infinity, where FP32 no longer resolves the reduced camera system
+    and it stops improving; povar_solve's safeguard switches to FP64 after
+    POVAR_FALLBACK_REJECTIONS rejected mixed steps in a row and reaches the
+    oracle's 50-iteration cost (tests/golden/converged_mid_m5.json) within
+    1e-5."""
+    g = _golden("mid_m5")
+    sc = scenes.scene_by_name("mid", g["scene_seed"])
+    P0 = scenes.init_cameras(sc.n_cams, g["init_seed"], normalize=True)
+    target = g["series"]["F"] * (1.0 + 1e-5)
+    prm = _golden_params(g, povar.MIXED_FP32)
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        rep, iters = pb.solve(prm, max_iters=300, ftol=0.0, target_cost=target)
+        assert rep.fp64_fallback_at > 0 and rep.precision == povar.FP64
+        assert pb.cost(sc.eta) <= target, (pb.cost(sc.eta), target, iters)
+    with povar.Problem.from_scene(sc) as pb:
+        pb.set_cameras(P0, sc.eta)
+        best = np.inf
+        for _ in range(200):
+            try:
+                rep = pb.step(prm)
+            except povar.PovarError:      # damping diverged
+                break
+            best = min(best, rep.cost_after if rep.accepted else rep.cost_before)
+        assert best > target
 
 
 # ---------------------------------------------------------------- init_random
