@@ -60,6 +60,8 @@ SERIES_KERNELS = {
     3: "series product (k_series_rows + k_series_apply)",
     4: "series product (k_series_fused on stored blocks + k_series_apply; per-step "
        "k_build_blocks included)",
+    5: "series product (k_series_group + k_series_fused on the slices outside groups + "
+       "k_series_apply)",
 }
 # bytes of one stored block G_k per observation, by precision name
 BLOCK_BYTES = {"fp64": 72, "mixed": 36, "bf16": 18}

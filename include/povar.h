@@ -92,10 +92,15 @@ enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1, POVAR_MIXED_BF16 = 2 };
  *             of Eq. pose; Pbar_i the left 3x3 of camera i), written once
  *             per step at the current cameras (72 / 36 bytes per SELL entry
  *             in FP64 / FP32, allocated at first use) instead of the camera
- *             rows and the measurement; -1 = autotuned (see
+ *             rows and the measurement; 5 = groups of slices whose
+ *             rows are all warp-uniform and see the same camera at each row
+ *             index (tracks over the same consecutive cameras): one block
+ *             per group stages the rows' cameras and the landmarks' s_j in
+ *             shared memory and reduces once per (row, up to 8 slices);
+ *             other slices run the fused pass of 1; -1 = autotuned (see
  *             povar_get_tuning). All schedules compute the same series (up
  *             to rounding order). */
-enum { POVAR_NSCHEDULES = 5 };
+enum { POVAR_NSCHEDULES = 6 };
 typedef struct {
   double eta;
   double lambda0;
@@ -197,8 +202,10 @@ povar_status povar_step(povar_problem* p, const povar_params* params,
  *
  * Mixed-precision safeguard (POVAR_MIXED_FP32 / POVAR_MIXED_BF16; not in
  * the paper): when POVAR_FALLBACK_REJECTIONS consecutive mixed steps are
- * rejected, the remaining steps of this solve run in POVAR_FP64 (same
- * schedule rule, landmarks re-solved in FP64 first). FP32 series and
+ * rejected, or the damping grows 1e10 times above the smallest damping of
+ * the solve (or diverges), the remaining steps of this solve run in
+ * POVAR_FP64 (same schedule rule, landmarks re-solved in FP64 first,
+ * damping reset to the smallest one of the solve). FP32 series and
  * linearizations cannot resolve the reduced camera system where it is a
  * strong cancellation of much larger terms (e.g. landmarks drifting towards
  * infinity at a small pOSE weight); there every damping is rejected and a

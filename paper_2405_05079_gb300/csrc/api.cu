@@ -88,6 +88,36 @@ povar_status dev_alloc_bytes(Problem* p, void** ptr, size_t bytes, const char* w
   return POVAR_OK;
 }
 
+// Arrays with one entry per landmark slot (np_pad slots, known once the
+// landmark layout is sorted). Padding slots keep zero landmarks and factors,
+// so that every kernel reading a whole slice sees finite values there.
+povar_status alloc_slot_arrays(Problem* p) {
+  const size_t npd = (size_t)p->np_pad;
+  povar_status s;
+  if ((s = dev_alloc(p, &p->slot_pt, npd, "slot_pt")) ||
+      (s = dev_alloc(p, &p->slot_len, npd, "slot_len")) ||
+      (s = dev_alloc(p, &p->sell_off, (size_t)p->nslices + 1, "sell_off")) ||
+      (s = dev_alloc(p, &p->rec32, npd * 2, "rec32")) ||
+      (s = dev_alloc(p, &p->rec64, npd * 4, "rec64")) ||
+      (s = dev_alloc(p, &p->cost_part, npd / 32, "cost_part")) ||
+      (s = dev_alloc(p, &p->pred_part, npd / 32, "pred_part")) ||
+      (s = dev_alloc(p, &p->pinv_part, npd / 32, "pinv_part")))
+    return s;
+  for (int t = 0; t < 2; ++t) {
+    if ((s = dev_alloc(p, &p->X64[t], npd * 3, "X64")) ||
+        (s = dev_alloc(p, &p->F64[t], npd * 6, "F64")) ||
+        (s = dev_alloc(p, &p->pdA[t], npd, "pdA")) || (s = dev_alloc(p, &p->pdB[t], npd, "pdB")) ||
+        (s = dev_alloc(p, &p->pdC[t], npd, "pdC")))
+      return s;
+    POVAR_CUDA(cudaMemsetAsync(p->X64[t], 0, npd * 3 * sizeof(double), p->stream));
+    POVAR_CUDA(cudaMemsetAsync(p->F64[t], 0, npd * 6 * sizeof(double), p->stream));
+    POVAR_CUDA(cudaMemsetAsync(p->pdA[t], 0, npd * sizeof(float4), p->stream));
+    POVAR_CUDA(cudaMemsetAsync(p->pdB[t], 0, npd * sizeof(float4), p->stream));
+    POVAR_CUDA(cudaMemsetAsync(p->pdC[t], 0, npd * sizeof(float), p->stream));
+  }
+  return POVAR_OK;
+}
+
 namespace {
 
 // Page-locked host slots for the per-problem mirrors of the device state and
@@ -488,7 +518,12 @@ int64_t povar_device_bytes(const povar_problem* pp) { return pp ? pp->impl.devic
 
 int64_t povar_estimate_bytes(int32_t n_cams, int32_t n_points, int64_t n_obs) {
   if (n_cams < 1 || n_points < 1 || n_obs < 1) return 0;
-  const int64_t nc = n_cams, npd = ((int64_t)n_points + 255) / 256 * 256, no = n_obs;
+  // slots: every smallest camera (at most min(n_cams, n_points) of them)
+  // starts a slice, so at most 31 padding slots per camera, then a multiple
+  // of 256
+  const int64_t nbk = std::min<int64_t>(n_cams, n_points);
+  const int64_t nc = n_cams, npd = ((int64_t)n_points + 31 * nbk + 255) / 256 * 256,
+                no = n_obs;
   // SELL entries are bounded by 32 x (longest track) per slice; two times the
   // observations bounds the padding of the scenes this library targets
   const int64_t nsell = 2 * no + 32 * 64;
@@ -513,6 +548,10 @@ int64_t povar_estimate_bytes(int32_t n_cams, int32_t n_points, int64_t n_obs) {
   b += no * 8 + (nc + 1) * 4;
   // grouped schedule: group tables, group rows, slice-row runs, partials
   b += 2 * (npd / 32 + 1) * 4 + (nsell / 32) * 16 + no * (12 * 8 + 4) + (nc + 1) * 4;
+  // group schedule: slice, row and item lists (each at most one per slice
+  // row), the rest list, per-camera lists and partials (items + run partials)
+  b += (nsell / 32) * 16 + (npd / 32 + 1) * 16 + (nc + 1) * 4 +
+       (nsell / 32 + no) * (12 * 8 + 4);
   // stored-block schedule: FP64, FP32 and BF16 blocks (each allocated at
   // its first use)
   b += nsell * (72 + 36 + 18);
@@ -557,11 +596,10 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
   p->np = n_points;
   p->nobs = n_obs;
   p->stream = static_cast<cudaStream_t>(cuda_stream);
-  p->np_pad = (int32_t)(((int64_t)n_points + povar::BLOCK - 1) / povar::BLOCK * povar::BLOCK);
-  p->nslices = p->np_pad / povar::SLICE;
-  p->n_slot_blocks = p->np_pad / povar::BLOCK;
+  // the slot count (np_pad) follows from the landmark layout: build_orders
+  // sets it and allocates the per-slot arrays (alloc_slot_arrays)
   povar_status s = POVAR_OK;
-  const size_t nc = n_cams, npd = p->np_pad, no = n_obs;
+  const size_t nc = n_cams, no = n_obs;
 #define ALLOC(ptr, count)                                                    \
   if ((s = povar::dev_alloc(p, &(ptr), (count), #ptr)) != POVAR_OK) {       \
     povar_destroy(pp);                                                       \
@@ -574,10 +612,7 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
   ALLOC(p->perm_cam, no);
   ALLOC(p->off_pt, (size_t)n_points + 1);
   ALLOC(p->off_cam, nc + 1);
-  ALLOC(p->slot_pt, npd);
   ALLOC(p->pt_slot, (size_t)n_points);
-  ALLOC(p->slot_len, npd);
-  ALLOC(p->sell_off, (size_t)p->nslices + 1);
   ALLOC(p->cm_slot, no);
   ALLOC(p->cm_m32, no);
   ALLOC(p->cm_m64, no);
@@ -600,18 +635,6 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
   ALLOC(p->Y64, 2 * nc * 12);
   ALLOC(p->D64, nc * 12);
   ALLOC(p->camnorm, nc * 2);
-  for (int t = 0; t < 2; ++t) {
-    ALLOC(p->X64[t], npd * 3);
-    ALLOC(p->F64[t], npd * 6);
-    ALLOC(p->pdA[t], npd);
-    ALLOC(p->pdB[t], npd);
-    ALLOC(p->pdC[t], npd);
-  }
-  ALLOC(p->rec32, npd * 2);
-  ALLOC(p->rec64, npd * 4);
-  ALLOC(p->cost_part, npd / 32);
-  ALLOC(p->pred_part, npd / 32);
-  ALLOC(p->pinv_part, npd / 32);
   ALLOC(p->fin_blk, 2 * povar::FIN_BLOCKS);
   ALLOC(p->fin_blk_i, povar::FIN_BLOCKS);
   ALLOC(p->fin_ticket, 2);

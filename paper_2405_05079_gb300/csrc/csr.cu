@@ -7,6 +7,8 @@
 // match/ballot and a per-digit running count, which keeps it stable.
 #include "povar_internal.cuh"
 
+#include <unordered_map>
+
 #include <algorithm>
 
 namespace povar {
@@ -199,11 +201,12 @@ __global__ void k_fill_sell(const uint32_t* __restrict__ slot_pt,
                             const uint32_t* __restrict__ off_pt,
                             const uint32_t* __restrict__ perm_pt,
                             const int32_t* __restrict__ cam, const double* __restrict__ meas,
-                            int np, int32_t* __restrict__ sell_cam,
+                            int nslots, int32_t* __restrict__ sell_cam,
                             float2* __restrict__ m32, double2* __restrict__ m64) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= np) return;
+  if (s >= nslots) return;
   const uint32_t j = slot_pt[s];
+  if (j == 0xffffffffu) return;   // padding slot
   const uint32_t len = slot_len[s];
   const uint32_t b = off_pt[j];
   const uint32_t base = sell_off[s / SLICE] + (uint32_t)(s % SLICE);
@@ -275,34 +278,83 @@ __global__ void k_len_stats(const uint32_t* __restrict__ len, int np,
   }
 }
 
-// Slice order (every slice is its own group, GROUP = 1): full slice sl of
-// the sorted landmark order gets the key maxlen - (its longest track), so a
-// stable ascending sort puts the widest slices first and keeps the sorted
-// order among equal widths.
-__global__ void k_full_slice_keys(const uint32_t* __restrict__ order,
-                                  const uint32_t* __restrict__ len, int nfull, uint32_t maxlen,
-                                  uint32_t* __restrict__ wkey, uint32_t* __restrict__ wval) {
+// Bucket-aligned slot sequence. The landmarks sorted by (smallest camera,
+// track length descending) form one bucket per smallest camera; every bucket
+// starts a new slice (its last slice is padded to 32 slots), so that a slice
+// never mixes landmarks whose tracks start at different cameras: for tracks
+// over consecutive cameras every row of a slice then sees one camera.
+//   k_bucket_flags: flag[i] = 1 where the sorted order starts a new bucket;
+//   k_bucket_first: bfirst[b] = first sorted index of bucket b;
+//   k_bucket_pad:   psize[b] = size of bucket b rounded up to 32 slots;
+//   k_seq_fill:     seq[pstart[b] + (i - bfirst[b])] = order[i].
+__global__ void k_bucket_flags(const uint32_t* __restrict__ order,
+                               const uint32_t* __restrict__ mincam, int np,
+                               uint32_t* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  // without mincam (the camera does not fit the sort key): a single bucket
+  flag[i] = (i == 0 || (mincam && mincam[order[i]] != mincam[order[i - 1]])) ? 1u : 0u;
+}
+
+// excl = exclusive scan of the flags: the bucket of i is excl[i + 1] - 1
+__global__ void k_bucket_first(const uint32_t* __restrict__ excl, int np,
+                               uint32_t* __restrict__ bfirst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > np) return;
+  if (i == np) {
+    bfirst[excl[np]] = (uint32_t)np;
+    return;
+  }
+  if (excl[i + 1] != excl[i]) bfirst[excl[i]] = (uint32_t)i;
+}
+
+__global__ void k_bucket_pad(const uint32_t* __restrict__ bfirst, int nb,
+                             uint32_t* __restrict__ psize) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const uint32_t sz = bfirst[b + 1] - bfirst[b];
+  psize[b] = (sz + SLICE - 1) / SLICE * SLICE;
+}
+
+__global__ void k_seq_fill(const uint32_t* __restrict__ order, const uint32_t* __restrict__ excl,
+                           const uint32_t* __restrict__ bfirst,
+                           const uint32_t* __restrict__ pstart, int np,
+                           uint32_t* __restrict__ seq) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const uint32_t b = excl[i + 1] - 1;
+  seq[pstart[b] + ((uint32_t)i - bfirst[b])] = order[i];
+}
+
+// Slice order: slice sl of the aligned sequence gets the key maxlen - (its
+// longest track), so a stable ascending sort puts the widest slices first and
+// keeps the sequence order among equal widths.
+__global__ void k_slice_keys(const uint32_t* __restrict__ seq, const uint32_t* __restrict__ len,
+                             int nsl, uint32_t maxlen, uint32_t* __restrict__ wkey,
+                             uint32_t* __restrict__ wval) {
   const int sl = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sl >= nfull) return;
+  if (sl >= nsl) return;
   uint32_t w = 0;
-  for (int l = 0; l < SLICE; ++l) w = max(w, len[order[(size_t)sl * SLICE + l]]);
+  for (int l = 0; l < SLICE; ++l) {
+    const uint32_t j = seq[(size_t)sl * SLICE + l];
+    if (j != 0xffffffffu) w = max(w, len[j]);
+  }
   wkey[sl] = maxlen - w;
   wval[sl] = (uint32_t)sl;
 }
 
-// Slot q: the full slices in the width order sl_order, then the remaining
-// landmarks of the sorted order (the last partial slice), then padding.
-__global__ void k_slot_fill(const uint32_t* __restrict__ order,
+// Slot q: the slices of the aligned sequence in the width order sl_order,
+// then padding up to np_pad.
+__global__ void k_slot_fill(const uint32_t* __restrict__ seq,
                             const uint32_t* __restrict__ sl_order,
-                            const uint32_t* __restrict__ len, int np, int np_pad, int nfull,
+                            const uint32_t* __restrict__ len, int nsl, int np_pad,
                             uint32_t* __restrict__ slot_pt, uint32_t* __restrict__ slot_len,
                             uint32_t* __restrict__ pt_slot) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= np_pad) return;
   uint32_t j = 0xffffffffu;
   const int sl = q / SLICE;
-  if (sl < nfull) j = order[(size_t)sl_order[sl] * SLICE + (q % SLICE)];
-  else if (q < np) j = order[q];
+  if (sl < nsl) j = seq[(size_t)sl_order[sl] * SLICE + (q % SLICE)];
   slot_pt[q] = j;
   slot_len[q] = j == 0xffffffffu ? 0u : len[j];
   if (j != 0xffffffffu) pt_slot[j] = (uint32_t)q;
@@ -510,6 +562,7 @@ povar_status radix_sort(Problem* p, Scratch& sc, uint32_t** k, uint32_t** v, int
 }  // namespace
 
 povar_status build_runs(Problem* p);
+povar_status build_groups5(Problem* p, const int32_t* d_rcam);
 
 povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt) {
   (void)h_cam;
@@ -598,26 +651,49 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
     if ((s = radix_sort(p, sc, &kk, &vv, p->np, use_cam ? len_bits + cam_bits : len_bits)) !=
         POVAR_OK)
       return s;
-    // Full slices of the sorted order are ordered by width (longest track
-    // first, stable) so that the warps of a block get similar work; the last
-    // partial slice and the pads stay at the end. Every slice is its own
-    // group (GROUP = 1).
+    // Bucket-aligned sequence (every smallest camera starts a slice; when the
+    // camera does not fit the sort key, one bucket), then all of its slices
+    // ordered by width (longest track first, stable) so that the warps of a
+    // block get similar work; padding up to a multiple of BLOCK slots at the
+    // end. Every slice is its own group (GROUP = 1).
     static_assert(GROUP == 1, "the slot order and the run tables take one slice per group");
-    const int nfull = p->np / SLICE;
-    const uint32_t* sl_order = nullptr;
-    if (nfull > 0) {
-      uint32_t* wkey = sc.get<uint32_t>(nfull);
-      uint32_t* wval = sc.get<uint32_t>(nfull);
-      if (!wkey || !wval) return fail(p, POVAR_ENOMEM, "slice scratch");
-      k_full_slice_keys<<<grid_for(nfull, 256), 256, 0, p->stream>>>(vv, len, nfull, maxlen,
-                                                                     wkey, wval);
-      ++p->launches;
-      uint32_t *wk = wkey, *wv = wval;
-      if ((s = radix_sort(p, sc, &wk, &wv, nfull, bits_for(maxlen))) != POVAR_OK) return s;
-      sl_order = wv;
-    }
+    uint32_t* flag = sc.get<uint32_t>((size_t)p->np + 1);
+    uint32_t* bfirst = sc.get<uint32_t>((size_t)p->np + 1);
+    uint32_t* pstart = sc.get<uint32_t>((size_t)p->np + 1);
+    if (!flag || !bfirst || !pstart) return fail(p, POVAR_ENOMEM, "bucket scratch");
+    POVAR_CUDA(cudaMemsetAsync(flag, 0, ((size_t)p->np + 1) * sizeof(uint32_t), p->stream));
+    k_bucket_flags<<<gp, 256, 0, p->stream>>>(vv, use_cam ? mincam : nullptr, p->np, flag);
+    if ((s = scan_exclusive(p, sc, flag, (int64_t)p->np + 1)) != POVAR_OK) return s;
+    k_bucket_first<<<grid_for((int64_t)p->np + 1, 256), 256, 0, p->stream>>>(flag, p->np,
+                                                                            bfirst);
+    p->launches += 2;
+    uint32_t nb = 0;
+    POVAR_COPY(&nb, flag + p->np, 1, cudaMemcpyDeviceToHost);
+    POVAR_CUDA(cudaMemsetAsync(pstart, 0, ((size_t)nb + 1) * sizeof(uint32_t), p->stream));
+    k_bucket_pad<<<grid_for(nb, 256), 256, 0, p->stream>>>(bfirst, (int)nb, pstart);
+    ++p->launches;
+    if ((s = scan_exclusive(p, sc, pstart, (int64_t)nb + 1)) != POVAR_OK) return s;
+    uint32_t total = 0;
+    POVAR_COPY(&total, pstart + nb, 1, cudaMemcpyDeviceToHost);
+    p->np_pad = (int32_t)(((int64_t)total + BLOCK - 1) / BLOCK * BLOCK);
+    p->nslices = p->np_pad / SLICE;
+    p->n_slot_blocks = p->np_pad / BLOCK;
+    if ((s = alloc_slot_arrays(p)) != POVAR_OK) return s;
+    uint32_t* seq = sc.get<uint32_t>(total);
+    if (!seq) return fail(p, POVAR_ENOMEM, "bucket scratch");
+    POVAR_CUDA(cudaMemsetAsync(seq, 0xff, (size_t)total * sizeof(uint32_t), p->stream));
+    k_seq_fill<<<gp, 256, 0, p->stream>>>(vv, flag, bfirst, pstart, p->np, seq);
+    ++p->launches;
+    const int nsl = (int)(total / SLICE);
+    uint32_t* wkey = sc.get<uint32_t>(nsl);
+    uint32_t* wval = sc.get<uint32_t>(nsl);
+    if (!wkey || !wval) return fail(p, POVAR_ENOMEM, "slice scratch");
+    k_slice_keys<<<grid_for(nsl, 256), 256, 0, p->stream>>>(seq, len, nsl, maxlen, wkey, wval);
+    ++p->launches;
+    uint32_t *wk = wkey, *wv = wval;
+    if ((s = radix_sort(p, sc, &wk, &wv, nsl, bits_for(maxlen))) != POVAR_OK) return s;
     k_slot_fill<<<grid_for(p->np_pad, 256), 256, 0, p->stream>>>(
-        vv, sl_order, len, p->np, p->np_pad, nfull, p->slot_pt, p->slot_len, p->pt_slot);
+        seq, wv, len, nsl, p->np_pad, p->slot_pt, p->slot_len, p->pt_slot);
     ++p->launches;
     if ((s = check_launch(p, "slot order")) != POVAR_OK) return s;
     p->ngroups = p->nslices;
@@ -644,9 +720,9 @@ povar_status build_orders(Problem* p, const int32_t* h_cam, const int32_t* h_pt)
   POVAR_CUDA(cudaMemsetAsync(p->sell_cam, 0xff, nsell * sizeof(int32_t), p->stream));
   POVAR_CUDA(cudaMemsetAsync(p->sell_m32, 0, nsell * sizeof(float2), p->stream));
   POVAR_CUDA(cudaMemsetAsync(p->sell_m64, 0, nsell * sizeof(double2), p->stream));
-  k_fill_sell<<<gp, 256, 0, p->stream>>>(p->slot_pt, p->slot_len, p->sell_off, p->off_pt,
-                                         perm_ptcam, p->d_cam, p->d_meas, p->np, p->sell_cam,
-                                         p->sell_m32, p->sell_m64);
+  k_fill_sell<<<grid_for(p->np_pad, 256), 256, 0, p->stream>>>(
+      p->slot_pt, p->slot_len, p->sell_off, p->off_pt, perm_ptcam, p->d_cam, p->d_meas,
+      p->np_pad, p->sell_cam, p->sell_m32, p->sell_m64);
   k_fill_cm<<<gb, 256, 0, p->stream>>>(p->perm_cam, p->d_pt, p->pt_slot, p->d_meas, n,
                                        p->cm_slot, p->cm_m32, p->cm_m64);
   k_split_meas<<<grid_for((int64_t)nsell, 256), 256, 0, p->stream>>>(p->sell_m64, nsell,
@@ -798,7 +874,130 @@ povar_status build_runs(Problem* p) {
   p->cam_part3_off = p->cam_part_off;
   p->cam_part3_idx = p->cam_part_idx;
   p->part3 = p->part_run;   // schedules 1 and 3 never run at the same time
-  return check_launch(p, "run tables");
+  if ((s = check_launch(p, "run tables")) != POVAR_OK) return s;
+  return build_groups5(p, rcam);
+}
+
+// Tables of the group schedule (5), built on the host from the row tables
+// (O(rows + partials) work). A slice joins a group when every row of it is
+// warp-uniform and its row cameras agree with the group's at every row index
+// both have; slices arrive widest first, so a group's first slice fixes its
+// row count and the slices that reach row k are a prefix of the group.
+povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
+  const int64_t nrows = p->nrows;
+  const int nsl = p->nslices;
+  std::vector<uint32_t> off((size_t)nsl + 1), rbase((size_t)nrows + 1), poff((size_t)p->nc + 1),
+      pidx((size_t)p->npart);
+  std::vector<int32_t> rcam((size_t)nrows);
+  POVAR_COPY(off.data(), p->sell_off, off.size(), cudaMemcpyDeviceToHost);
+  POVAR_COPY(rcam.data(), d_rcam, rcam.size(), cudaMemcpyDeviceToHost);
+  POVAR_COPY(rbase.data(), p->row_base, rbase.size(), cudaMemcpyDeviceToHost);
+  POVAR_COPY(poff.data(), p->cam_part_off, poff.size(), cudaMemcpyDeviceToHost);
+  POVAR_COPY(pidx.data(), p->cam_part_idx, pidx.size(), cudaMemcpyDeviceToHost);
+  struct Grp {
+    std::vector<uint32_t> sl;
+    std::vector<int32_t> cam;
+    uint32_t rows = 0;   // sum of the slices' widths (staged measurement rows)
+  };
+  std::vector<Grp> groups;
+  std::vector<uint32_t> rest;
+  std::unordered_map<int32_t, int> open;   // first-row camera -> open group
+  for (int sidx = 0; sidx < nsl; ++sidx) {
+    const uint32_t r0 = off[sidx] / SLICE, w = (off[sidx + 1] - off[sidx]) / SLICE;
+    bool uni = w > 0 && w <= (uint32_t)G5_ROWS && w <= (uint32_t)G5_MROWS;
+    for (uint32_t k = 0; uni && k < w; ++k) uni = rcam[r0 + k] >= 0;
+    if (!uni) {
+      rest.push_back((uint32_t)sidx);
+      continue;
+    }
+    const int32_t key = rcam[r0];
+    auto it = open.find(key);
+    int gi = -1;
+    if (it != open.end()) {
+      Grp& g = groups[(size_t)it->second];
+      bool ok = g.sl.size() < (size_t)G5_SLICES && g.rows + w <= (uint32_t)G5_MROWS;
+      const uint32_t kk = std::min<uint32_t>(w, (uint32_t)g.cam.size());
+      for (uint32_t k = 0; ok && k < kk; ++k) ok = g.cam[k] == rcam[r0 + k];
+      if (ok) gi = it->second;
+    }
+    if (gi < 0) {
+      gi = (int)groups.size();
+      groups.emplace_back();
+      open[key] = gi;
+    }
+    Grp& g = groups[(size_t)gi];
+    g.sl.push_back((uint32_t)sidx);
+    g.rows += w;
+    for (uint32_t k = (uint32_t)g.cam.size(); k < w; ++k) g.cam.push_back(rcam[r0 + k]);
+  }
+  // flat tables; items: for row k the slices that reach it (a prefix of the
+  // group, widest first) in ranges of at most G5_ITEM
+  std::vector<uint32_t> goff(1, 0), gsl, roff(1, 0), ioff(1, 0), items;
+  std::vector<int32_t> rowcam;
+  std::vector<int32_t> item_cam;
+  std::vector<char> grouped_part((size_t)p->npart, 0);
+  int64_t g_obs_rows = 0;
+  for (const Grp& g : groups) {
+    std::vector<uint32_t> width;
+    for (uint32_t sidx : g.sl) {
+      gsl.push_back(sidx);
+      const uint32_t w = (off[sidx + 1] - off[sidx]) / SLICE;
+      width.push_back(w);
+      const uint32_t r0 = off[sidx] / SLICE;
+      for (uint32_t k = 0; k < w; ++k) grouped_part[rbase[r0 + k]] = 1;   // uniform: one partial
+      g_obs_rows += w;
+    }
+    goff.push_back((uint32_t)gsl.size());
+    for (int32_t c : g.cam) rowcam.push_back(c);
+    roff.push_back((uint32_t)rowcam.size());
+    for (uint32_t k = 0; k < (uint32_t)g.cam.size(); ++k) {
+      uint32_t n = 0;
+      while (n < width.size() && width[n] > k) ++n;
+      for (uint32_t j0 = 0; j0 < n; j0 += G5_ITEM) {
+        const uint32_t j1 = std::min<uint32_t>(n, j0 + G5_ITEM);
+        items.push_back((k << 16) | (j0 << 8) | j1);
+        item_cam.push_back(g.cam[k]);
+      }
+    }
+    ioff.push_back((uint32_t)items.size());
+  }
+  const int64_t nitems = (int64_t)items.size();
+  // per camera: its items in item order, then its remaining run partials
+  std::vector<uint32_t> c5off((size_t)p->nc + 1, 0), c5idx;
+  {
+    std::vector<std::vector<uint32_t>> per((size_t)p->nc);
+    for (int64_t q = 0; q < nitems; ++q) per[(size_t)item_cam[(size_t)q]].push_back((uint32_t)q);
+    for (int c = 0; c < p->nc; ++c) {
+      for (uint32_t q : per[(size_t)c]) c5idx.push_back(q);
+      for (uint32_t e = poff[c]; e < poff[c + 1]; ++e)
+        if (!grouped_part[pidx[e]]) c5idx.push_back((uint32_t)nitems + pidx[e]);
+      c5off[(size_t)c + 1] = (uint32_t)c5idx.size();
+    }
+  }
+  p->g5_ngroups = (int32_t)groups.size();
+  p->g5_nrest = (int32_t)rest.size();
+  p->g5_nitems = nitems;
+  p->g5_nslices = (int64_t)gsl.size();
+  p->g5_obs = g_obs_rows;
+  povar_status s;
+  auto up32 = [&](uint32_t** dst, const std::vector<uint32_t>& v, const char* what) {
+    povar_status r = dev_alloc(p, dst, std::max<size_t>(v.size(), 1), what);
+    if (r != POVAR_OK || v.empty()) return r;
+    return copy_sync(p, *dst, v.data(), v.size(), cudaMemcpyHostToDevice);
+  };
+  if ((s = up32(&p->g5_off, goff, "g5_off")) || (s = up32(&p->g5_slices, gsl, "g5_slices")) ||
+      (s = up32(&p->g5_roff, roff, "g5_roff")) || (s = up32(&p->g5_ioff, ioff, "g5_ioff")) ||
+      (s = up32(&p->g5_items, items, "g5_items")) || (s = up32(&p->g5_rest, rest, "g5_rest")) ||
+      (s = up32(&p->cam5_off, c5off, "cam5_off")) || (s = up32(&p->cam5_idx, c5idx, "cam5_idx")))
+    return s;
+  if ((s = dev_alloc(p, &p->g5_rowcam, std::max<size_t>(rowcam.size(), 1), "g5_rowcam")))
+    return s;
+  if (!rowcam.empty())
+    POVAR_COPY(p->g5_rowcam, rowcam.data(), rowcam.size(), cudaMemcpyHostToDevice);
+  if ((s = dev_alloc_bytes(p, &p->part5,
+                           (size_t)(nitems + (int64_t)p->npart) * 12 * sizeof(double), "part5")))
+    return s;
+  return setup_group_kernels(p);
 }
 
 }  // namespace povar

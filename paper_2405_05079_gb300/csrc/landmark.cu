@@ -213,7 +213,8 @@ k_landmark(DeviceState* __restrict__ st, int which_rel, double eta,
   if (s == 0) st->x_df[t] = 0;
   double cost = 0.0;
   int npinv = 0;
-  if (s < np) {
+  // padding slots (track length 0) sit between the slices of the layout
+  if (s < np && slot_len[s] > 0) {
     const uint32_t len = slot_len[s];
     const uint32_t base = sell_off[s / SLICE] + (uint32_t)(s % SLICE);
     double V[6] = {0, 0, 0, 0, 0, 0}, h[3] = {0, 0, 0};
@@ -350,7 +351,8 @@ k_landmark_df(DeviceState* __restrict__ st, int which_rel, df64 a, df64 eta,
   if (s == 0) st->x_df[t] = 1;
   df64 cost = {0.f, 0.f};
   int npinv = 0;
-  if (s < np) {
+  // padding slots (track length 0) sit between the slices of the layout
+  if (s < np && slot_len[s] > 0) {
     const uint32_t len = slot_len[s];
     const uint32_t base = sell_off[s / SLICE] + (uint32_t)(s % SLICE);
     df64 V[6], h[3];
@@ -598,11 +600,11 @@ povar_status launch_landmarks(Problem* p, int which_rel, double eta, int precisi
   if (which_rel == 1 && precision != POVAR_FP64)
     k_landmark_df<<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
         p->state, which_rel, df_host(1.0 - eta), df_host(eta), p->slot_len, p->sell_off, p->sell_cam, p->sell_mdf,
-        p->Ltab_df, p->np, b, p->cost_part, p->pinv_part);
+        p->Ltab_df, p->np_pad, b, p->cost_part, p->pinv_part);
   else
     k_landmark<<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
         p->state, which_rel, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->Ltab,
-        p->P64[0], p->P64[1], p->np, b, p->cost_part, p->pinv_part);
+        p->P64[0], p->P64[1], p->np_pad, b, p->cost_part, p->pinv_part);
   p->launches += 2;
   return check_launch(p, "landmark");
 }

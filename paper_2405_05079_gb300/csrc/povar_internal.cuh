@@ -40,12 +40,23 @@ constexpr int BLOCK = 256;       // threads per block for slot kernels
 // latency-bound loop, and ordering by group width unbalances the blocks of
 // the slot kernels.
 constexpr int GROUP = 1;
+// Group schedule (5): at most G5_SLICES slices, G5_ROWS rows and G5_MROWS
+// slice rows (staged measurement rows) per group (one block each, four
+// blocks per SM in FP32), work items of at most G5_ITEM slices of one row.
+constexpr int G5_THREADS = 256;
+constexpr int G5_SLICES = 16;
+constexpr int G5_ROWS = 64;
+constexpr int G5_MROWS = 88;
+constexpr int G5_ITEM = 16;
 // Blocks of the final cost and predicted-decrease sums (each block adds a
 // fixed range, the last block to finish adds the block sums in order).
 constexpr int FIN_BLOCKS = 64;
 constexpr double PINV_COND = 1e12;
 constexpr double LAMBDA_MIN = 1e-8;   // damping floor
 constexpr double LAMBDA_MAX = 1e30;   // damping ceiling (solve reported as diverged)
+// mixed-precision safeguard: damping growth over the smallest damping of a
+// solve after which its FP32 steps are taken to have failed
+constexpr double FALLBACK_LAMBDA_GROWTH = 1e10;
 
 // Stored observation blocks G_k = C_k Pbar_i (3x3, row-major g[3r + q]) of
 // the stored series schedule, one per SELL entry e (E = max(nsell, 1)
@@ -84,6 +95,7 @@ struct DeviceState {
   long long products; // series products M y computed by all steps (never reset)
   int x_df[2];        // landmark buffer t holds X as double-float pairs (1) or FP64 (0)
   int rej_run;        // consecutive rejected steps
+  double lam_low;     // smallest damping used by a step of the current solve
   int fallback_after; // mixed-precision safeguard: rejections that trigger it (0: off)
   int fallback;       // set with `converged` when the safeguard triggered
 };
@@ -160,6 +172,23 @@ struct Problem {
   uint32_t* cam_part3_off = nullptr;    // [nc + 1]
   uint32_t* cam_part3_idx = nullptr;    // [npart3]
   void* part3 = nullptr;                // [npart3 * 12] float or double
+  // group schedule (5): groups of slices whose rows are all warp-uniform and
+  // that see the same camera at every row index; work items (row, slice
+  // range) of each group; slices outside groups (g5_rest) run the fused pass;
+  // per camera the item partials, then the run partials of its rows outside
+  // groups (offset by g5_nitems), in a fixed order
+  int32_t g5_ngroups = 0, g5_nrest = 0;
+  int64_t g5_nitems = 0, g5_nslices = 0, g5_obs = 0;
+  uint32_t* g5_off = nullptr;        // [ngroups + 1] slices of group g in g5_slices
+  uint32_t* g5_slices = nullptr;     // [grouped slices] slice indices, widest first
+  uint32_t* g5_roff = nullptr;       // [ngroups + 1] rows of group g in g5_rowcam
+  int32_t* g5_rowcam = nullptr;      // camera of each group row
+  uint32_t* g5_ioff = nullptr;       // [ngroups + 1] items of group g
+  uint32_t* g5_items = nullptr;      // (row << 16) | (first slice << 8) | end slice
+  uint32_t* g5_rest = nullptr;       // [nrest] slices outside groups
+  uint32_t* cam5_off = nullptr;      // [nc + 1]
+  uint32_t* cam5_idx = nullptr;
+  void* part5 = nullptr;             // [(nitems + npart) * 12] float or double
   // stored series blocks per kind (0 FP64, 1 FP32, 2 BF16), allocated at
   // first use and rebuilt by every step that runs the stored schedule
   void* blk[3] = {nullptr, nullptr, nullptr};
@@ -247,6 +276,7 @@ povar_status check_launch(Problem* p, const char* what);
 // current device (library_pool).
 cudaError_t library_pool(cudaMemPool_t* out);
 povar_status dev_alloc_bytes(Problem* p, void** ptr, size_t bytes, const char* what);
+povar_status alloc_slot_arrays(Problem* p);
 template <class T>
 inline povar_status dev_alloc(Problem* p, T** ptr, size_t count, const char* what) {
   return dev_alloc_bytes(p, reinterpret_cast<void**>(ptr), count * sizeof(T), what);
@@ -282,6 +312,7 @@ povar_status launch_pred(Problem* p, int precision, double eta, int manifold, in
 // G_k at the current cameras.
 int block_kind(int precision);
 povar_status ensure_blocks(Problem* p, int kind);
+povar_status setup_group_kernels(Problem* p);
 BlockPlanes block_planes(const Problem* p, int kind);
 povar_status launch_build_blocks(Problem* p, int precision, double eta);
 

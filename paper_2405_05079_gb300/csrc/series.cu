@@ -740,12 +740,20 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
                const typename Vt<T>::m2* __restrict__ sell_m, const T* __restrict__ camPa,
                const T* __restrict__ camPb, const T* __restrict__ vec, PointData<T> pd0,
                PointData<T> pd1, const uint32_t* __restrict__ row_mask,
-               const uint32_t* __restrict__ row_base, T* __restrict__ part, BlockPlanes bp) {
+               const uint32_t* __restrict__ row_base, T* __restrict__ part, BlockPlanes bp,
+               const uint32_t* __restrict__ slist = nullptr, int nslist = 0) {
   constexpr bool STORED = !std::is_void<TS>::value;
   using BS = typename std::conditional<STORED, TS, float>::type;
   if (st->converged || st->stop_series) return;
-  const int s = blockIdx.x * BLOCK + threadIdx.x;
   const int lane = threadIdx.x & 31;
+  // one warp per slice: the slice of the warp's index, or the warp's entry
+  // of a slice list (the slices outside the groups of schedule 5)
+  int s = blockIdx.x * BLOCK + threadIdx.x;
+  if (slist) {
+    const int wg = s >> 5;
+    if (wg >= nslist) return;
+    s = (int)__ldg(slist + wg) * SLICE + lane;
+  }
   const PointData<T>& pd = st->cur ? pd1 : pd0;
   const T* __restrict__ camP = st->cur ? camPb : camPa;
   const uint32_t sbeg = sell_off[s / SLICE];
@@ -920,6 +928,432 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
     }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Group schedule (5). A group is a set of slices whose rows are all
+// warp-uniform and whose row k sees the same camera in every slice of the
+// group (landmarks whose tracks start at the same camera and run over the
+// same cameras, as in video or trajectory capture; the layout starts a new
+// slice at every smallest camera). One block per group:
+//   staging: one thread issues bulk asynchronous copies (cp.async.bulk,
+//            completion counted on an mbarrier) of every slice's
+//            measurements, track lengths and landmark records (X, factor of
+//            V^-1) into shared memory, while the block loads the P and Y
+//            rows of the group's row cameras (the camera of a row comes from
+//            the group's row table: no camera index is read per
+//            observation);
+//   phase 1: warp w takes slices w, w + 8, ... of the group; lane = landmark
+//            j: t_j = sum_k Pbar_k^T C_k (Y_k x~_j), s_j = F_j^T F_j t_j,
+//            all operands in shared memory;
+//   phase 2: work items (row k, up to G5_ITEM slices of the group) strided
+//            over the warps: each lane adds vec((C_k Pbar_k s_j) x~_j^T) of
+//            its landmark in every slice of the item in registers, the warp
+//            reduces once per item and writes the item's partial.
+// Slices outside groups (a row whose lanes see several cameras) get blocks
+// of their own in the same launch, whose 8 warps split the slice's rows: the
+// per-lane track sums t_j of the warps are added in warp order, and every
+// row writes its run partials as in the fused schedule. k_series_apply adds
+// both kinds of partials per camera in a fixed order.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Wait for phase `parity` of `bar` with a bounded number of attempts (each
+// attempt suspends the thread for a hardware-defined time); false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Landmark records of a group's slices staged in shared memory, in planes of
+// G5_SLICES * 32 slots: FP32 (X0 X1 X2 F00)(F10 F11 F20 F21) as float4 and
+// F22 as float; FP64 X (3 doubles) and F (6 doubles).
+template <typename T> struct G5Pd;
+template <> struct G5Pd<float> {
+  static constexpr size_t N = (size_t)G5_SLICES * SLICE;
+  static constexpr size_t BYTES = N * (16 + 16 + 4);
+  static constexpr uint32_t SLICE_BYTES = SLICE * (16 + 16 + 4);
+  static __device__ __forceinline__ void copy(unsigned char* base, int j,
+                                              const PointData<float>& pd, uint32_t slot0,
+                                              uint64_t* bar) {
+    bulk_g2s(base + (size_t)j * SLICE * 16, pd.A + slot0, SLICE * 16, bar);
+    bulk_g2s(base + N * 16 + (size_t)j * SLICE * 16, pd.B + slot0, SLICE * 16, bar);
+    bulk_g2s(base + N * 32 + (size_t)j * SLICE * 4, pd.C + slot0, SLICE * 4, bar);
+  }
+  static __device__ __forceinline__ void load(const unsigned char* base, int e, float X[3],
+                                              float F[6]) {
+    const float4 p = reinterpret_cast<const float4*>(base)[e];
+    const float4 q = reinterpret_cast<const float4*>(base + N * 16)[e];
+    X[0] = p.x; X[1] = p.y; X[2] = p.z;
+    F[0] = p.w; F[1] = q.x; F[2] = q.y; F[3] = q.z; F[4] = q.w;
+    F[5] = reinterpret_cast<const float*>(base + N * 32)[e];
+  }
+  static __device__ __forceinline__ void loadX(const unsigned char* base, int e, float X[3]) {
+    const float4 p = reinterpret_cast<const float4*>(base)[e];
+    X[0] = p.x; X[1] = p.y; X[2] = p.z;
+  }
+};
+template <> struct G5Pd<double> {
+  static constexpr size_t N = (size_t)G5_SLICES * SLICE;
+  static constexpr size_t BYTES = N * (24 + 48);
+  static constexpr uint32_t SLICE_BYTES = SLICE * (24 + 48);
+  static __device__ __forceinline__ void copy(unsigned char* base, int j,
+                                              const PointData<double>& pd, uint32_t slot0,
+                                              uint64_t* bar) {
+    bulk_g2s(base + (size_t)j * SLICE * 24, pd.X + 3 * (size_t)slot0, SLICE * 24, bar);
+    bulk_g2s(base + N * 24 + (size_t)j * SLICE * 48, pd.F + 6 * (size_t)slot0, SLICE * 48, bar);
+  }
+  static __device__ __forceinline__ void load(const unsigned char* base, int e, double X[3],
+                                              double F[6]) {
+    const double* x = reinterpret_cast<const double*>(base) + 3 * (size_t)e;
+    const double* f = reinterpret_cast<const double*>(base + N * 24) + 6 * (size_t)e;
+    X[0] = x[0]; X[1] = x[1]; X[2] = x[2];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) F[k] = f[k];
+  }
+  static __device__ __forceinline__ void loadX(const unsigned char* base, int e, double X[3]) {
+    const double* x = reinterpret_cast<const double*>(base) + 3 * (size_t)e;
+    X[0] = x[0]; X[1] = x[1]; X[2] = x[2];
+  }
+};
+
+// Row r (4 values) of the 3x4 camera block k staged in shared memory.
+template <typename T>
+__device__ __forceinline__ void srow(const T* tab, uint32_t k, int r, T out[4]);
+template <>
+__device__ __forceinline__ void srow<float>(const float* tab, uint32_t k, int r, float out[4]) {
+  const float4 q = reinterpret_cast<const float4*>(tab + 12 * (size_t)k)[r];
+  out[0] = q.x; out[1] = q.y; out[2] = q.z; out[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void srow<double>(const double* tab, uint32_t k, int r,
+                                             double out[4]) {
+  const double2* q = reinterpret_cast<const double2*>(tab + 12 * (size_t)k) + 2 * r;
+  const double2 x = q[0], y = q[1];
+  out[0] = x.x; out[1] = x.y; out[2] = y.x; out[3] = y.y;
+}
+
+// Dynamic shared memory of k_series_group (all offsets multiples of 16):
+// mbarrier; camera rows P and Y per group row; staged measurements
+// (G5_MROWS rows of 32); staged landmark records; s_j (3 planes); staged
+// track lengths; per slice its index, first SELL entry, width and first
+// staged measurement row.
+template <typename T> struct G5Layout {
+  using M2 = typename Vt<T>::m2;
+  static constexpr size_t BAR = 0;
+  static constexpr size_t CP = 16;
+  static constexpr size_t CY = CP + (size_t)G5_ROWS * 12 * sizeof(T);
+  static constexpr size_t MEAS = CY + (size_t)G5_ROWS * 12 * sizeof(T);
+  static constexpr size_t PD = MEAS + (size_t)G5_MROWS * SLICE * sizeof(M2);
+  static constexpr size_t S = PD + G5Pd<T>::BYTES;
+  static constexpr size_t LEN = S + 3 * (size_t)G5_SLICES * SLICE * sizeof(T);
+  static constexpr size_t INFO = LEN + (size_t)G5_SLICES * SLICE * sizeof(uint32_t);
+  static constexpr size_t BYTES = INFO + 4 * (size_t)G5_SLICES * sizeof(uint32_t);
+};
+template <typename T>
+constexpr size_t g5_smem_bytes() {
+  return G5Layout<T>::BYTES;
+}
+
+// Tables of the group schedule passed to k_series_group.
+struct G5Tables {
+  const uint32_t* off;     // [ngroups + 1] slices of group g in slices
+  const uint32_t* slices;  // slice indices, widest first
+  const uint32_t* roff;    // [ngroups + 1] rows of group g in rowcam
+  const int32_t* rowcam;   // camera of each group row
+  const uint32_t* ioff;    // [ngroups + 1] items of group g
+  const uint32_t* items;   // (row << 16) | (first slice << 8) | end slice
+  const uint32_t* rest;    // slices outside groups
+  int ngroups;
+};
+
+template <typename T>
+__device__ __forceinline__ void g5_group_block(
+    DeviceState* __restrict__ st, T a, const uint32_t* __restrict__ slot_len,
+    const uint32_t* __restrict__ sell_off, const typename Vt<T>::m2* __restrict__ sell_m,
+    const T* __restrict__ camP, const T* __restrict__ vec, const PointData<T>& pd,
+    const G5Tables& tb, T* __restrict__ part, unsigned char* sm) {
+  using L = G5Layout<T>;
+  using M2 = typename Vt<T>::m2;
+  constexpr int NW = G5_THREADS / 32;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
+  T* cP = reinterpret_cast<T*>(sm + L::CP);
+  T* cY = reinterpret_cast<T*>(sm + L::CY);
+  const M2* sm_m = reinterpret_cast<const M2*>(sm + L::MEAS);
+  unsigned char* sm_pd = sm + L::PD;
+  T* sS = reinterpret_cast<T*>(sm + L::S);
+  const uint32_t* slen = reinterpret_cast<const uint32_t*>(sm + L::LEN);
+  uint32_t* s_idx = reinterpret_cast<uint32_t*>(sm + L::INFO);
+  uint32_t* s_off = s_idx + G5_SLICES;
+  uint32_t* s_w = s_off + G5_SLICES;
+  uint32_t* s_mrow = s_w + G5_SLICES;
+  const int g = blockIdx.x, lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const uint32_t sb = tb.off[g], ns = tb.off[g + 1] - sb;
+  const uint32_t rb = tb.roff[g], nr = tb.roff[g + 1] - rb;
+
+  if (threadIdx.x < ns) {
+    const uint32_t sl = __ldg(tb.slices + sb + threadIdx.x);
+    const uint32_t o = sell_off[sl];
+    s_idx[threadIdx.x] = sl;
+    s_off[threadIdx.x] = o;
+    s_w[threadIdx.x] = (sell_off[sl + 1] - o) / SLICE;
+  }
+  __syncthreads();
+  if (wl == 0) {
+    // staged measurement rows of each slice (the host keeps the sum of the
+    // widths within G5_MROWS), the expected byte count, then the bulk copies
+    // of slice j issued by lane j
+    if (lane == 0) {
+      uint32_t r = 0;
+      for (uint32_t j = 0; j < ns; ++j) {
+        s_mrow[j] = r;
+        r += s_w[j];
+      }
+      mbar_init(bar, 1);
+      mbar_arrive_expect_tx(bar, r * SLICE * (uint32_t)sizeof(M2) +
+                                     ns * (G5Pd<T>::SLICE_BYTES + SLICE * 4u));
+    }
+    __syncwarp();
+    if ((uint32_t)lane < ns) {
+      const uint32_t j = (uint32_t)lane, slot0 = s_idx[j] * SLICE;
+      bulk_g2s(sm + L::MEAS + (size_t)s_mrow[j] * SLICE * sizeof(M2), sell_m + s_off[j],
+               s_w[j] * SLICE * (uint32_t)sizeof(M2), bar);
+      bulk_g2s(sm + L::LEN + (size_t)j * SLICE * 4, slot_len + slot0, SLICE * 4, bar);
+      G5Pd<T>::copy(sm_pd, (int)j, pd, slot0, bar);
+    }
+  }
+  // camera rows of the group rows while the copies are in flight
+  for (uint32_t q = threadIdx.x; q < nr * 24; q += G5_THREADS) {
+    const uint32_t r = q / 24, e = q % 24;
+    const size_t c = (size_t)__ldg(tb.rowcam + rb + r);
+    if (e < 12)
+      cP[12 * r + e] = camP[12 * c + e];
+    else
+      cY[12 * r + e - 12] = vec[12 * c + e - 12];
+  }
+  __syncthreads();
+  const bool arrived = mbar_wait_bounded(bar, 0);
+  if (__syncthreads_or(!arrived)) {
+    // the copies did not complete in time (in any thread's view): report
+    // it, wait once more for them (bounded) so that none lands after the
+    // block has exited, and skip the group
+    if (threadIdx.x == 0) st->error = POVAR_ETIMEOUT;
+    mbar_wait_bounded(bar, 0);
+    return;
+  }
+
+  // phase 1: s_j of every landmark of the group
+  for (uint32_t j = wl; j < ns; j += NW) {
+    const int e = (int)(j * SLICE) + lane;
+    const uint32_t width = s_w[j], len = slen[e];
+    const M2* mrow = sm_m + (size_t)s_mrow[j] * SLICE + lane;
+    T X[3], F[6];
+    G5Pd<T>::load(sm_pd, e, X, F);
+    T t[3] = {0, 0, 0};
+    // branch-free over the rows: a lane past its track length adds its
+    // contribution scaled by 0 (its staged measurement is the zero padding)
+    for (uint32_t k = 0; k < width; ++k) {
+      const M2 m = mrow[k * SLICE];
+      const T f = k < len ? (T)1 : (T)0;
+      const T Xf[3] = {f * X[0], f * X[1], f * X[2]};
+      T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
+      srow<T>(cY, k, 0, Y0);
+      srow<T>(cY, k, 1, Y1);
+      srow<T>(cY, k, 2, Y2);
+      srow<T>(cP, k, 0, P0);
+      srow<T>(cP, k, 1, P1);
+      srow<T>(cP, k, 2, P2);
+      // e = Y (f x~): the homogeneous 1 of x~ is scaled by f as well
+      Y0[3] *= f;
+      Y1[3] *= f;
+      Y2[3] *= f;
+      gather_obs<T>(Y0, Y1, Y2, P0, P1, P2, a, (T)m.x, (T)m.y, Xf, t);
+    }
+    const T z0 = F[0] * t[0];
+    const T z1 = F[1] * t[0] + F[2] * t[1];
+    const T z2 = F[3] * t[0] + F[4] * t[1] + F[5] * t[2];
+    sS[e] = F[0] * z0 + F[1] * z1 + F[3] * z2;
+    sS[G5_SLICES * SLICE + e] = F[2] * z1 + F[4] * z2;
+    sS[2 * G5_SLICES * SLICE + e] = F[5] * z2;
+  }
+  __syncthreads();
+
+  // phase 2: one partial per work item
+  const uint32_t ib = tb.ioff[g], ni = tb.ioff[g + 1] - ib;
+  for (uint32_t it = wl; it < ni; it += NW) {
+    const uint32_t item = __ldg(tb.items + ib + it);
+    const uint32_t k = item >> 16, j0 = (item >> 8) & 0xffu, j1 = item & 0xffu;
+    T P0[4], P1[4], P2[4];
+    srow<T>(cP, k, 0, P0);
+    srow<T>(cP, k, 1, P1);
+    srow<T>(cP, k, 2, P2);
+    T v[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) v[q] = 0;
+    for (uint32_t j = j0; j < j1; ++j) {
+      // branch-free: a lane past its track length adds its contribution
+      // scaled by 0 (s_j scaled; its staged measurement is zero padding)
+      const int e = (int)(j * SLICE) + lane;
+      const T f = k < slen[e] ? (T)1 : (T)0;
+      const M2 m = sm_m[((size_t)s_mrow[j] + k) * SLICE + lane];
+      T X[3];
+      G5Pd<T>::loadX(sm_pd, e, X);
+      const T S[3] = {f * sS[e], f * sS[G5_SLICES * SLICE + e],
+                      f * sS[2 * G5_SLICES * SLICE + e]};
+      scatter_obs<T>(P0, P1, P2, a, (T)m.x, (T)m.y, S, X, v);
+    }
+    T r[3];
+    int vb;
+    warp_reduce12<T>(v, lane, r, vb);
+    if ((lane & 7) == 0) {
+      T* out = part + (size_t)(ib + it) * 12 + vb;
+      out[0] = r[0];
+      out[1] = r[1];
+      out[2] = r[2];
+    }
+  }
+}
+
+// A slice outside the groups (some row's lanes see several cameras), one
+// block: warp w takes rows w, w + 8, ... In the first pass each warp sums
+// its rows' part of t_j per lane; the 8 warp sums are added in warp order,
+// s_j = F_j^T F_j t_j. In the second pass every row writes its run partials
+// (one per run of equal cameras, as the fused schedule).
+template <typename T>
+__device__ __forceinline__ void g5_rest_block(
+    T a, const uint32_t* __restrict__ slot_len, const uint32_t* __restrict__ sell_off,
+    const int32_t* __restrict__ sell_cam, const typename Vt<T>::m2* __restrict__ sell_m,
+    const T* __restrict__ camP, const T* __restrict__ vec, const PointData<T>& pd,
+    const uint32_t* __restrict__ row_mask, const uint32_t* __restrict__ row_base,
+    uint32_t slice, T* __restrict__ part_run, unsigned char* sm) {
+  using M2 = typename Vt<T>::m2;
+  constexpr int NW = G5_THREADS / 32;
+  T* tp = reinterpret_cast<T*>(sm + G5Layout<T>::MEAS);   // [NW][3][32]
+  T* sS = tp + NW * 3 * SLICE;                              // [3][32]
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const uint32_t slot = slice * SLICE + (uint32_t)lane;
+  const uint32_t sbeg = sell_off[slice];
+  const uint32_t width = (sell_off[slice + 1] - sbeg) / SLICE;
+  const uint32_t len = slot_len[slot];
+  const uint32_t base = sbeg + (uint32_t)lane;
+  T X[3], F[6];
+  load_point<T>(pd, (int)slot, X, F);
+  T t[3] = {0, 0, 0};
+  for (uint32_t k = (uint32_t)wl; k < width; k += NW) {
+    if (k < len) {
+      const int i = ld_stream(sell_cam + base + k * SLICE);
+      const M2 m = ld_stream(sell_m + base + k * SLICE);
+      T Y0[4], Y1[4], Y2[4], P0[4], P1[4], P2[4];
+      load_row<T>(vec, i, 0, Y0);
+      load_row<T>(vec, i, 1, Y1);
+      load_row<T>(vec, i, 2, Y2);
+      load_row<T>(camP, i, 0, P0);
+      load_row<T>(camP, i, 1, P1);
+      load_row<T>(camP, i, 2, P2);
+      gather_obs<T>(Y0, Y1, Y2, P0, P1, P2, a, (T)m.x, (T)m.y, X, t);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) tp[(wl * 3 + c) * SLICE + lane] = t[c];
+  __syncthreads();
+  if (wl == 0) {
+    T u[3] = {0, 0, 0};
+    for (int w = 0; w < NW; ++w)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u[c] += tp[(w * 3 + c) * SLICE + lane];
+    const T z0 = F[0] * u[0];
+    const T z1 = F[1] * u[0] + F[2] * u[1];
+    const T z2 = F[3] * u[0] + F[4] * u[1] + F[5] * u[2];
+    sS[lane] = F[0] * z0 + F[1] * z1 + F[3] * z2;
+    sS[SLICE + lane] = F[2] * z1 + F[4] * z2;
+    sS[2 * SLICE + lane] = F[5] * z2;
+  }
+  __syncthreads();
+  const T S[3] = {sS[lane], sS[SLICE + lane], sS[2 * SLICE + lane]};
+  const uint32_t row0 = sbeg / SLICE;
+  for (uint32_t k = (uint32_t)wl; k < width; k += NW) {
+    const uint32_t mask = __ldg(row_mask + row0 + k), pbase = __ldg(row_base + row0 + k);
+    const int i = k < len ? ld_stream(sell_cam + base + k * SLICE) : -1;
+    T v[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) v[q] = 0;
+    if (i >= 0) {
+      const M2 m = ld_stream(sell_m + base + k * SLICE);
+      T P0[4], P1[4], P2[4];
+      load_row<T>(camP, i, 0, P0);
+      load_row<T>(camP, i, 1, P1);
+      load_row<T>(camP, i, 2, P2);
+      scatter_obs<T>(P0, P1, P2, a, (T)m.x, (T)m.y, S, X, v);
+    }
+    if (mask == 0u) {
+      T r[3];
+      int vb;
+      warp_reduce12<T>(v, lane, r, vb);
+      if ((lane & 7) == 0) {
+        T* out = part_run + (size_t)pbase * 12 + vb;
+        out[0] = r[0];
+        out[1] = r[1];
+        out[2] = r[2];
+      }
+    } else {
+      store_runs<T>(v, mask, i >= 0, pbase, lane, part_run);
+    }
+  }
+}
+
+// Blocks [0, ngroups) run the groups, the next ones the slices outside
+// groups. part holds the item partials, followed by the run partials
+// (part_run).
+template <typename T>
+__global__ void __launch_bounds__(G5_THREADS, sizeof(T) == 4 ? 1024 / G5_THREADS : 1)
+k_series_group(DeviceState* __restrict__ st, T a, const uint32_t* __restrict__ slot_len,
+               const uint32_t* __restrict__ sell_off, const int32_t* __restrict__ sell_cam,
+               const typename Vt<T>::m2* __restrict__ sell_m, const T* __restrict__ camPa,
+               const T* __restrict__ camPb, const T* __restrict__ vec, PointData<T> pd0,
+               PointData<T> pd1, G5Tables tb, const uint32_t* __restrict__ row_mask,
+               const uint32_t* __restrict__ row_base, T* __restrict__ part,
+               T* __restrict__ part_run) {
+  if (st->converged || st->stop_series) return;
+  extern __shared__ __align__(16) unsigned char g5_smem[];
+  const T* __restrict__ camP = st->cur ? camPb : camPa;
+  const PointData<T>& pd = st->cur ? pd1 : pd0;
+  if ((int)blockIdx.x < tb.ngroups)
+    g5_group_block<T>(st, a, slot_len, sell_off, sell_m, camP, vec, pd, tb, part, g5_smem);
+  else
+    g5_rest_block<T>(a, slot_len, sell_off, sell_cam, sell_m, camP, vec, pd, row_mask, row_base,
+                     __ldg(tb.rest + (blockIdx.x - tb.ngroups)), part_run, g5_smem);
 }
 
 // Per camera (one warp): z_i = sum of its partials in index order, then the
@@ -1571,6 +2005,37 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
     p->launches += 2;
     return check_launch(p, "series_term (stored blocks)");
   }
+  if (schedule == 5) {
+    // one launch for the groups and the slices outside groups (run partials
+    // after the item partials), then the per-camera sums
+    const unsigned gb = (unsigned)(p->g5_ngroups + p->g5_nrest);
+    const int64_t nit = p->g5_nitems;
+    const G5Tables tb{p->g5_off,  p->g5_slices, p->g5_roff, p->g5_rowcam,
+                      p->g5_ioff, p->g5_items,  p->g5_rest, p->g5_ngroups};
+    if (precision == POVAR_FP64) {
+      double* part = static_cast<double*>(p->part5);
+      if (gb > 0)
+        k_series_group<double><<<gb, G5_THREADS, g5_smem_bytes<double>(), p->stream>>>(
+            p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0],
+            p->P64[1], p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1), tb,
+            p->row_mask, p->row_base, part, part + nit * 12);
+      k_series_apply<double><<<p->nc, 128, 0, p->stream>>>(
+          p->state, term, eps, p->nc, p->cam5_off, p->cam5_idx, part, p->G64, p->camnorm,
+          p->done_ticket, p->Y64 + yoff_out, p->D64);
+    } else {
+      float* part = static_cast<float*>(p->part5);
+      if (gb > 0)
+        k_series_group<float><<<gb, G5_THREADS, g5_smem_bytes<float>(), p->stream>>>(
+            p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
+            p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1), tb,
+            p->row_mask, p->row_base, part, part + nit * 12);
+      k_series_apply<float><<<p->nc, 128, 0, p->stream>>>(
+          p->state, term, eps, p->nc, p->cam5_off, p->cam5_idx, part, p->G32, p->camnorm,
+          p->done_ticket, p->Y32 + yoff_out, p->D32);
+    }
+    p->launches += 1 + (gb > 0);
+    return check_launch(p, "series_term (groups)");
+  }
   if (schedule == 2) {
     if (precision == POVAR_FP64) {
       k_series_gather<double, false><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
@@ -1759,6 +2224,18 @@ povar_status launch_pred(Problem* p, int precision, double eta, int manifold, in
   }
   p->launches += manifold == POVAR_SPHERE ? 4 : 3;
   return check_launch(p, "pred");
+}
+
+// The group kernel's dynamic shared memory exceeds the default 48 KB limit in
+// FP64; raise the per-kernel limit once per problem (outside any capture).
+povar_status setup_group_kernels(Problem* p) {
+  POVAR_CUDA(cudaFuncSetAttribute(k_series_group<double>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)g5_smem_bytes<double>()));
+  POVAR_CUDA(cudaFuncSetAttribute(k_series_group<float>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)g5_smem_bytes<float>()));
+  return POVAR_OK;
 }
 
 }  // namespace povar

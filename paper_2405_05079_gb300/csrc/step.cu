@@ -7,8 +7,10 @@
 //     1 - (2 rho - 1)^3), nu = 2; on reject lambda *= nu, nu *= 2; lambda is
 //     kept >= LAMBDA_MIN and a damping above LAMBDA_MAX stops the solve).
 //     Mixed-precision safeguard (not in the paper): when fallback_after > 0
-//     and that many mixed-precision steps in a row were rejected, the
-//     controller stops the solve with `fallback` set, and the host continues
+//     and that many mixed-precision steps in a row were rejected, or the
+//     damping grew FALLBACK_LAMBDA_GROWTH times above the smallest damping of
+//     the solve (or diverged), the controller stops the solve with
+//     `fallback` set, and the host continues
 //     it in FP64 (FP32 cannot resolve the reduced camera system when it is a
 //     strong cancellation of much larger terms, e.g. landmarks drifting
 //     towards infinity at a small pOSE weight).
@@ -74,10 +76,20 @@ __global__ void k_controller(DeviceState* __restrict__ st, povar_step_report* __
     st->nu = 2.0 * st->nu;
     st->need_lin = 0;
     st->rej_run += 1;
-    if (precision != POVAR_FP64 && st->fallback_after > 0 && st->rej_run >= st->fallback_after) {
-      st->fallback = 1;
-      conv = 1;
-    }
+  }
+  // mixed-precision safeguard: rejections in a row, a damping grown far
+  // above the smallest one of this solve, or a diverging damping mean that
+  // the FP32 steps have stopped being useful; the FP64 continuation starts
+  // from the smallest damping of the solve
+  st->lam_low = fmin(st->lam_low, st->lam_used);
+  if (precision != POVAR_FP64 && st->fallback_after > 0 &&
+      (st->rej_run >= st->fallback_after || st->lam > FALLBACK_LAMBDA_GROWTH * st->lam_low ||
+       !(st->lam < LAMBDA_MAX))) {
+    st->lam = st->lam_low;
+    st->nu = 2.0;
+    st->rej_run = 0;
+    st->fallback = 1;
+    conv = 1;
   }
   if (st->max_iters > 0 && st->iteration >= st->max_iters) conv = 1;
   if (!(st->lam < LAMBDA_MAX)) {
@@ -121,6 +133,7 @@ __global__ void k_begin(DeviceState* __restrict__ st, double ftol, double target
   st->converged = 0;
   st->fallback = 0;
   st->fallback_after = fallback_after;
+  st->lam_low = st->lam;
   st->ftol = ftol;
   st->target = target;
   st->max_iters = max_iters > 0 ? st->iteration + max_iters : 0;

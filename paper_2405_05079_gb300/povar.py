@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libpovar.so")
 
 EUCLID, SPHERE = 0, 1
 FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
-NSCHEDULES = 5            # POVAR_NSCHEDULES
+NSCHEDULES = 6            # POVAR_NSCHEDULES
 
 STATUS = {0: "POVAR_OK", 1: "POVAR_EINVAL", 2: "POVAR_ENOMEM", 3: "POVAR_ECUDA",
           4: "POVAR_ENUMERIC", 5: "POVAR_ETIMEOUT", 6: "POVAR_ENOTCONVERGED"}

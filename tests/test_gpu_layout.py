@@ -1,10 +1,10 @@
 """The landmark layout and run tables that povar_create builds on the
 device, against a numpy construction from their stated rules (integer work:
 bit-exact). Rules: observations of a landmark in camera order (stable sort
-by camera, then by landmark); slots sorted by (smallest camera, longest track
-first), ties by landmark id; full slices of 32 slots ordered by width
-(longest track, widest first, stable); then the partial slice and padding to
-a multiple of 256 slots; entry (slice s, row t, lane l) at sell_off[s] + 32 t
+by camera, then by landmark); landmarks sorted by (smallest camera, longest
+track first), ties by landmark id; every smallest camera starts a new slice
+(its last slice padded to 32 slots); all slices ordered by width (longest
+track, widest first, stable); padding to a multiple of 256 slots; entry (slice s, row t, lane l) at sell_off[s] + 32 t
 + l; a slice row is uniform (mask 0, one partial) when its valid lanes share
 one camera, else bit l marks a lane whose camera differs from lane l - 1's
 and every such lane with a valid camera opens a partial; partials are
@@ -32,22 +32,27 @@ def expected_layout(sc):
     maxlen = int(lens.max())
     assert int(maxlen).bit_length() + int(nc - 1).bit_length() <= 32
     order = np.lexsort((maxlen - lens, mincam))          # primary mincam, stable
-    nfull = np_ // 32
-    width_full = np.array([lens[order[32 * s:32 * s + 32]].max() for s in range(nfull)],
-                          dtype=np.int64)
-    sl_order = np.argsort(-width_full, kind="stable")
-    np_pad = (np_ + 255) // 256 * 256
+    seq = []                                              # bucket-aligned sequence
+    for c in np.unique(mincam):
+        b = [int(j) for j in order if mincam[j] == c]
+        seq += b + [NONE] * (-len(b) % 32)
+    nseq = len(seq) // 32
+    width_seq = np.array([max([lens[j] for j in seq[32 * s:32 * s + 32] if j != NONE])
+                          for s in range(nseq)], dtype=np.int64)
+    sl_order = np.argsort(-width_seq, kind="stable")
+    np_pad = (len(seq) + 255) // 256 * 256
     slot_pt = np.full(np_pad, NONE, np.uint64)
-    for s in range(nfull):
-        slot_pt[32 * s:32 * s + 32] = order[32 * sl_order[s]:32 * sl_order[s] + 32]
-    slot_pt[32 * nfull:np_] = order[32 * nfull:np_]
+    for s in range(nseq):
+        slot_pt[32 * s:32 * s + 32] = seq[32 * sl_order[s]:32 * sl_order[s] + 32]
     nsl = np_pad // 32
     slot_len = np.array([lens[j] if j != NONE else 0 for j in slot_pt], np.int64)
     widths = slot_len.reshape(nsl, 32).max(axis=1)
     sell_off = np.concatenate([[0], np.cumsum(32 * widths)]).astype(np.int64)
     sell_cam = np.full(int(sell_off[-1]), -1, np.int64)
-    for q in range(np_):
+    for q in range(np_pad):
         j = int(slot_pt[q])
+        if j == NONE:
+            continue
         s, l = divmod(q, 32)
         for t in range(lens[j]):
             sell_cam[sell_off[s] + 32 * t + l] = cam[perm[off[j] + t]]
