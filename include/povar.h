@@ -202,8 +202,8 @@ povar_status povar_step(povar_problem* p, const povar_params* params,
  *
  * Mixed-precision safeguard (POVAR_MIXED_FP32 / POVAR_MIXED_BF16; not in
  * the paper): when POVAR_FALLBACK_REJECTIONS consecutive mixed steps are
- * rejected, or the damping grows 1e10 times above the smallest damping of
- * the solve (or diverges), the remaining steps of this solve run in
+ * rejected, or the damping grows 1e10 times above its value at the start
+ * of the solve (or diverges), the remaining steps of this solve run in
  * POVAR_FP64 (same schedule rule, landmarks re-solved in FP64 first,
  * damping reset to the smallest one of the solve). FP32 series and
  * linearizations cannot resolve the reduced camera system where it is a

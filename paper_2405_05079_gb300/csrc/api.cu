@@ -681,7 +681,7 @@ povar_status povar_create(int32_t n_cams, int32_t n_points, int64_t n_obs, const
     povar_destroy(pp);
     return s;
   }
-  ALLOC(*reinterpret_cast<char**>(&p->part_lin), (size_t)std::max(p->nchunks, 1) * povar::LIN_ACC * sizeof(double));
+  ALLOC(*reinterpret_cast<char**>(&p->part_lin), (size_t)std::max(p->nchunks, 1) * povar::LIN_PART * sizeof(double));
   ALLOC(*reinterpret_cast<char**>(&p->part_ser), (size_t)std::max(p->nchunks, 1) * 12 * sizeof(double));
   // fused schedule when at most half as many run partials as observations
   p->schedule_default = (2 * p->npart <= p->nobs) ? 1 : 0;

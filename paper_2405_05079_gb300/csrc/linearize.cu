@@ -13,6 +13,16 @@
 // numbers with shuffles (no atomics); the per-camera kernel adds the chunk
 // partials in chunk order, so the result is deterministic.
 //
+// Centring (FP32 accumulation only): landmarks far from the origin make U_i
+// a cancellation-prone sum with a huge condition number, and FP32 rounding
+// of its entries then spoils the damped inverse. Each chunk accumulates the
+// moments of x~' = (X - c, 1) about its own centre c (the chunk's mean
+// landmark) and the gradient sums g (x) x~' (the residuals themselves use
+// X); the per-camera kernel maps every chunk's sums back in FP64 exactly
+// (x~ = x~' + (c, 0): S_ab = S'_ab + c_a S'_3b + c_b S'_a3 + c_a c_b S'_33,
+// b_p[r][q] = b'_p[r][q] + c_q b'_p[r][3], with c_3 = 0) before adding them.
+// The FP32 rounding is then relative to a well-conditioned matrix.
+//
 // Tangent space (POVAR_SPHERE): with p^ = P_i / ||P_i|| and Pi = I - p^p^T,
 //   A_i = Pi U_i Pi + lambda Pi + p^ p^T   is SPD and, for any tangent v,
 //   A_i^-1 v = Q (Q^T U_i Q + lambda I)^-1 Q^T v  for every orthonormal basis
@@ -48,8 +58,10 @@ __device__ __forceinline__ void load_x<double>(const float4* __restrict__,
   x0 = __ldg(x); x1 = __ldg(x + 1); x2 = __ldg(x + 2);
 }
 
+// Three blocks per SM in FP32 (at most 85 registers; the centring pass
+// would otherwise raise the count from 80 to about 120).
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 k_linearize(const DeviceState* __restrict__ st, T s1, T s2, int nchunks,
             const int32_t* __restrict__ chunk_cam, const uint32_t* __restrict__ chunk_beg,
             const uint32_t* __restrict__ cm_slot, const typename M2<T>::type* __restrict__ cm_m,
@@ -58,6 +70,7 @@ k_linearize(const DeviceState* __restrict__ st, T s1, T s2, int nchunks,
             const double* __restrict__ X0, const double* __restrict__ X1,
             T* __restrict__ part) {
   if (st->converged || !st->need_lin) return;
+  constexpr bool CENTER = sizeof(T) == 4;
   const int lane = threadIdx.x & 31;
   const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (c >= nchunks) return;
@@ -72,6 +85,23 @@ k_linearize(const DeviceState* __restrict__ st, T s1, T s2, int nchunks,
 #pragma unroll
   for (int e = 0; e < LIN_ACC; ++e) acc[e] = (T)0;
   const uint32_t b = chunk_beg[c], e_ = chunk_beg[c + 1];
+  T ctr[3] = {0, 0, 0};
+  if constexpr (CENTER) {
+    // chunk centre: the mean landmark of the chunk (the pass brings the
+    // chunk's landmark records into the cache for the main loop)
+    for (uint32_t r = b + lane; r < e_; r += 32) {
+      const float4 xa = __ldg(pdA + cm_slot[r]);
+      ctr[0] += xa.x;
+      ctr[1] += xa.y;
+      ctr[2] += xa.z;
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ctr[q] += __shfl_xor_sync(0xffffffffu, ctr[q], o);
+      ctr[q] /= (T)(e_ - b);
+    }
+  }
   for (uint32_t r = b + lane; r < e_; r += 32) {
     const uint32_t slot = cm_slot[r];
     const auto m = cm_m[r];
@@ -84,6 +114,10 @@ k_linearize(const DeviceState* __restrict__ st, T s1, T s2, int nchunks,
     const T r0 = s1 * (y0 - u * y2), r1 = s1 * (y1 - v * y2);
     const T r2 = s2 * (y0 - u), r3 = s2 * (y1 - v);
     const T g[3] = {s1 * r0 + s2 * r2, s1 * r1 + s2 * r3, -s1 * (u * r0 + v * r1)};
+    // moments and gradient about the chunk centre (zero in FP64)
+    x0 -= ctr[0];
+    x1 -= ctr[1];
+    x2 -= ctr[2];
     const T xt[4] = {x0, x1, x2, (T)1};
     const T t10[10] = {x0 * x0, x0 * x1, x0 * x2, x0, x1 * x1, x1 * x2, x1, x2 * x2, x2, (T)1};
 #pragma unroll
@@ -105,10 +139,11 @@ k_linearize(const DeviceState* __restrict__ st, T s1, T s2, int nchunks,
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     acc[e] = v;
   }
-  T* out = part + (size_t)c * LIN_ACC;
+  T* out = part + (size_t)c * LIN_PART;
 #pragma unroll
   for (int e = 0; e < LIN_ACC; ++e)
     if ((e & 31) == lane) out[e] = acc[e];
+  if (lane < 3) out[LIN_ACC + lane] = lane == 0 ? ctr[0] : (lane == 1 ? ctr[1] : ctr[2]);
 }
 
 // index of the unique entry (b, d) of a symmetric 4x4 in the t10 order
@@ -116,6 +151,24 @@ __device__ __forceinline__ int t10_index(int b, int d) {
   const int lo = b < d ? b : d, hi = b < d ? d : b;
   // rows: (0,0..3) -> 0..3, (1,1..3) -> 4..6, (2,2..3) -> 7..8, (3,3) -> 9
   return lo == 0 ? hi : (lo == 1 ? 3 + hi : (lo == 2 ? 5 + hi : 9));
+}
+
+// Entry e of a chunk's sums in the global basis from its centred sums S'
+// (t10 moments of the four weights, then b_p) and its centre c = S'[52..54]
+// (see the centring note above; c_3 = 0).
+__device__ __forceinline__ double uncentre(const double* Sp, int e) {
+  const double* cc = Sp + LIN_ACC;
+  if (e < 40) {
+    const int blk = e / 10 * 10, t = e % 10;
+    // (a, b) of t10 entry t: rows (0,0..3), (1,1..3), (2,2..3), (3,3)
+    const int a = t < 4 ? 0 : t < 7 ? 1 : t < 9 ? 2 : 3;
+    const int bb = t < 4 ? t : t < 7 ? t - 3 : t < 9 ? t - 5 : 3;
+    const double ca = a < 3 ? cc[a] : 0.0, cb = bb < 3 ? cc[bb] : 0.0;
+    return Sp[blk + t] + ca * Sp[blk + t10_index(3, bb)] + cb * Sp[blk + t10_index(a, 3)] +
+           ca * cb * Sp[blk + 9];
+  }
+  const int q = (e - 40) & 3;
+  return Sp[e] + (q < 3 ? cc[q] * Sp[e - q + 3] : 0.0);
 }
 
 template <typename T>
@@ -130,6 +183,7 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
   __shared__ double smA[4][12][13];
   __shared__ double smL[4][12][13];
   __shared__ double smAcc[4][LIN_ACC];
+  __shared__ double smChk[4][LIN_PART];
   __shared__ double smInv[4][12];  // reciprocals of the Cholesky diagonal
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int i = blockIdx.x * 4 + wl;
@@ -151,11 +205,17 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
   double bpl = 0.0;
   if (need_lin) {
     const int n = cam_nchunk[i], c0 = cam_chunk0[i];
-    for (int e = lane; e < LIN_ACC; e += 32) {
-      double s = 0.0;
-      for (int q = 0; q < n; ++q) s += (double)part[(size_t)(c0 + q) * LIN_ACC + e];
-      smAcc[wl][e] = s;
+    double s_lo = 0.0, s_hi = 0.0;   // entries lane and lane + 32
+    for (int q = 0; q < n; ++q) {
+      const T* pc = part + (size_t)(c0 + q) * LIN_PART;
+      for (int e = lane; e < LIN_ACC + 3; e += 32) smChk[wl][e] = (double)pc[e];
+      __syncwarp();
+      s_lo += uncentre(smChk[wl], lane);
+      if (lane + 32 < LIN_ACC) s_hi += uncentre(smChk[wl], lane + 32);
+      __syncwarp();
     }
+    smAcc[wl][lane] = s_lo;
+    if (lane + 32 < LIN_ACC) smAcc[wl][lane + 32] = s_hi;
     __syncwarp();
     if (lane < 12) {
       const int ra = lane >> 2, rb = lane & 3;

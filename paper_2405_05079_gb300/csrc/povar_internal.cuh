@@ -32,6 +32,7 @@ namespace povar {
 constexpr int SLICE = 32;        // landmarks per SELL slice (one warp)
 constexpr int CHUNK = 512;       // observations per camera-major chunk
 constexpr int LIN_ACC = 52;      // linearization accumulators per chunk
+constexpr int LIN_PART = 56;     // per-chunk partial: the accumulators, the chunk's centre (3), pad
 constexpr int BLOCK = 256;       // threads per block for slot kernels
 // Slices per group of the schedule-3 row table (its kernel takes one slice
 // per warp). Groups of two and four slices per warp were measured slower on
@@ -54,7 +55,7 @@ constexpr int FIN_BLOCKS = 64;
 constexpr double PINV_COND = 1e12;
 constexpr double LAMBDA_MIN = 1e-8;   // damping floor
 constexpr double LAMBDA_MAX = 1e30;   // damping ceiling (solve reported as diverged)
-// mixed-precision safeguard: damping growth over the smallest damping of a
+// mixed-precision safeguard: damping growth over its value at the start of a
 // solve after which its FP32 steps are taken to have failed
 constexpr double FALLBACK_LAMBDA_GROWTH = 1e10;
 
@@ -96,6 +97,7 @@ struct DeviceState {
   int x_df[2];        // landmark buffer t holds X as double-float pairs (1) or FP64 (0)
   int rej_run;        // consecutive rejected steps
   double lam_low;     // smallest damping used by a step of the current solve
+  double lam_ref;     // damping at the start of the current solve
   int fallback_after; // mixed-precision safeguard: rejections that trigger it (0: off)
   int fallback;       // set with `converged` when the safeguard triggered
 };

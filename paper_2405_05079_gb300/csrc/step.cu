@@ -8,8 +8,8 @@
 //     kept >= LAMBDA_MIN and a damping above LAMBDA_MAX stops the solve).
 //     Mixed-precision safeguard (not in the paper): when fallback_after > 0
 //     and that many mixed-precision steps in a row were rejected, or the
-//     damping grew FALLBACK_LAMBDA_GROWTH times above the smallest damping of
-//     the solve (or diverged), the controller stops the solve with
+//     damping grew FALLBACK_LAMBDA_GROWTH times above its value at the start
+//     of the solve (or diverged), the controller stops the solve with
 //     `fallback` set, and the host continues
 //     it in FP64 (FP32 cannot resolve the reduced camera system when it is a
 //     strong cancellation of much larger terms, e.g. landmarks drifting
@@ -78,12 +78,12 @@ __global__ void k_controller(DeviceState* __restrict__ st, povar_step_report* __
     st->rej_run += 1;
   }
   // mixed-precision safeguard: rejections in a row, a damping grown far
-  // above the smallest one of this solve, or a diverging damping mean that
+  // above its value at the start of the solve, or a diverging damping mean that
   // the FP32 steps have stopped being useful; the FP64 continuation starts
   // from the smallest damping of the solve
   st->lam_low = fmin(st->lam_low, st->lam_used);
   if (precision != POVAR_FP64 && st->fallback_after > 0 &&
-      (st->rej_run >= st->fallback_after || st->lam > FALLBACK_LAMBDA_GROWTH * st->lam_low ||
+      (st->rej_run >= st->fallback_after || st->lam > FALLBACK_LAMBDA_GROWTH * st->lam_ref ||
        !(st->lam < LAMBDA_MAX))) {
     st->lam = st->lam_low;
     st->nu = 2.0;
@@ -125,6 +125,10 @@ __global__ void k_init_state(DeviceState* __restrict__ st, double lambda0, int r
     st->lam = lambda0;
     st->nu = 2.0;
     st->rej_run = 0;
+    // the damping references of the safeguard follow a reset (it is
+    // enqueued after k_begin when a solve starts from new cameras)
+    st->lam_low = lambda0;
+    st->lam_ref = lambda0;
   }
 }
 
@@ -134,6 +138,7 @@ __global__ void k_begin(DeviceState* __restrict__ st, double ftol, double target
   st->fallback = 0;
   st->fallback_after = fallback_after;
   st->lam_low = st->lam;
+  st->lam_ref = st->lam;
   st->ftol = ftol;
   st->target = target;
   st->max_iters = max_iters > 0 ? st->iteration + max_iters : 0;
