@@ -24,7 +24,12 @@ Initialization-Free Large-Scale Bundle Adjustment", ECCV 2024):
   series x(m) (Sec. 4.2);
 * one damped VarPro step: pose update, closed-form landmark re-solve at the new
   cameras (Sec. 4.2: the landmarks are eliminated in closed form),
-  gain ratio, accept/reject and damping update.
+  gain ratio, accept/reject and damping update;
+* the comparison solvers of Sec. 5.2 on the same problem: PoBA (joint
+  Levenberg-Marquardt whose damped Schur complement is inverted by the
+  power series, landmarks updated by back-substitution; Sec. 2) and the
+  "iterative" VarPro baseline (conjugate gradients on the reduced camera
+  system with the Schur-Jacobi preconditioner).
 
 Readings where the paper is silent or garbled:
 
@@ -332,6 +337,45 @@ def series_step(rs: ReducedSystem, m, eps=0.0):
     return delta, terms
 
 
+def schur_jacobi_blocks(rs: ReducedSystem):
+    """Diagonal blocks S_ii of the explicit Schur complement (the Schur-Jacobi
+    preconditioner of the "iterative" baseline, Sec. 5.2)."""
+    k = rs.Ut.shape[1]
+    n = rs.Ut.shape[0]
+    return np.stack([rs.S[k * i:k * i + k, k * i:k * i + k] for i in range(n)])
+
+
+def pcg_step(rs: ReducedSystem, iters, tol=0.0):
+    """Conjugate gradients on S delta = g from delta = 0, preconditioned by
+    the inverse diagonal blocks of S (Schur-Jacobi): the "iterative" VarPro
+    baseline of Sec. 5.2 (at most 500 inner iterations there). Stops after
+    `iters` iterations, or when ||g - S delta|| <= tol ||g|| (tol > 0).
+    Returns (delta, iterations)."""
+    k = rs.Ut.shape[1]
+    Minv = sla.block_diag(*[np.linalg.inv(b) for b in schur_jacobi_blocks(rs)])
+    g = rs.g
+    delta = np.zeros_like(g)
+    r = g.copy()
+    z = Minv @ r
+    p = z.copy()
+    rz = float(r @ z)
+    gn = float(np.linalg.norm(g))
+    it = 0
+    for it in range(1, iters + 1):
+        Sp = rs.S @ p
+        alpha = rz / float(p @ Sp)
+        delta += alpha * p
+        r -= alpha * Sp
+        if tol > 0 and np.linalg.norm(r) <= tol * gn:
+            break
+        z = Minv @ r
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    assert k > 0
+    return delta, it
+
+
 def series_matrix(rs: ReducedSystem):
     """Dense M = U~^{-1} W~ V^{-1} W~^T (used by the Lemma 1 / 2 pins)."""
     Uinv = sla.block_diag(*[np.linalg.inv(b) for b in rs.Ut])
@@ -349,7 +393,11 @@ class Params:
     m: int = 10                 # number of series terms
     series_eps: float = 0.0     # 0: exactly m terms
     manifold: int = SPHERE
-    solver: str = "series"      # "series" | "exact"
+    solver: str = "series"      # "series" | "exact" | "pcg"
+    method: str = "varpro"      # "varpro" (PoVar) | "poba" (joint LM, Sec. 2 / PoBA)
+    lambda_l: float = 1.0       # PoBA: landmark damping lambda_l * lambda
+    pcg_iters: int = 500        # "pcg": inner iterations (Sec. 5.2)
+    pcg_tol: float = 0.0        # "pcg": stop at ||res|| <= tol ||g|| (0: run pcg_iters)
 
 
 @dataclasses.dataclass
@@ -400,12 +448,17 @@ class Problem:
         return State(P=P, X=X, F=self.cost(P, X, params.eta), lam=params.lambda0)
 
     def step(self, st: State, params: Params):
-        """One damped VarPro iteration at (P, X*(P))."""
+        """One damped VarPro iteration at (P, X*(P)), or one PoBA iteration
+        at (P, X) when params.method == "poba"."""
+        if params.method == "poba":
+            return self.poba_step(st, params)
         ne = self.normal_equations(st.P, st.X, params.eta)
         Q = tangent_bases(st.P, params.manifold)
         rs = reduced_system(ne, Q, st.lam)
         if params.solver == "exact":
             d, terms = exact_step(rs), 0
+        elif params.solver == "pcg":
+            d, terms = pcg_step(rs, params.pcg_iters, params.pcg_tol)
         else:
             d, terms = series_step(rs, params.m, params.series_eps)
         k = Q.shape[2]
@@ -430,6 +483,62 @@ class Problem:
         else:
             new = State(P=st.P, X=st.X, F=st.F, lam=st.lam * st.nu,
                         nu=2.0 * st.nu, iteration=st.iteration + 1)
+        rep.lambda_next = new.lam
+        return new, rep
+
+    def poba_step(self, st: State, params: Params):
+        """One iteration of joint Levenberg-Marquardt on the pOSE cost with
+        the power series on the damped Schur complement (PoBA, Sec. 2): at
+        (P, X) -- X is not re-eliminated -- the joint normal equation
+        [[U + lambda I, W], [W^T, V + lambda_l lambda I]] (dP, dX) =
+        -(b_p, b_l) is reduced to S dP = -(b_p - W V_lambda^-1 b_l) with
+        S = U_lambda - W V_lambda^-1 W^T (tangent-projected on the sphere as
+        in Sec. 4.3), solved by the series (or exactly / by PCG), and the
+        landmarks follow by back-substitution dX = -V_lambda^-1 (b_l + W^T dP).
+        The trial cost is evaluated at (P + dP, X + dX) (retracted cameras);
+        pred is the Gauss-Newton model decrease ||r||^2 - ||r + J (dP, dX)||^2."""
+        eta, lam = params.eta, st.lam
+        ne = self.normal_equations(st.P, st.X, eta)
+        Q = tangent_bases(st.P, params.manifold)
+        n_c, _, k = Q.shape
+        Ut = np.einsum("nai,nab,nbj->nij", Q, ne.U, Q) + lam * np.eye(k)[None]
+        Vd = ne.V + params.lambda_l * lam * np.eye(3)[None]
+        Vinv = blockdiag(np.linalg.inv(Vd))
+        Qbd = blockdiag(Q)
+        Wt = (Qbd.T @ ne.W).tocsr()
+        S = sla.block_diag(*Ut) - (Wt @ Vinv @ Wt.T).toarray()
+        g = -(Qbd.T @ ne.b_p - Wt @ (Vinv @ ne.b_l))
+        rs = ReducedSystem(Ut=Ut, Wt=Wt, Vinv=Vinv, S=S, g=g, Q=Q, lam=lam)
+        if params.solver == "exact":
+            d, terms = exact_step(rs), 0
+        elif params.solver == "pcg":
+            d, terms = pcg_step(rs, params.pcg_iters, params.pcg_tol)
+        else:
+            d, terms = series_step(rs, params.m, params.series_eps)
+        dP = np.einsum("nab,nb->na", Q, d.reshape(n_c, k))
+        dX = -(Vinv @ (ne.b_l + ne.W.T @ dP.ravel())).reshape(-1, 3)
+        P_new = st.P + dP
+        if params.manifold == SPHERE:
+            P_new = P_new / np.linalg.norm(P_new, axis=1, keepdims=True)
+        X_new = st.X + dX
+        F_new = self.cost(P_new, X_new, eta)
+        Jp, Jl = jacobian_blocks(st.P, st.X, self.cam_idx, self.pt_idx, self.meas, eta)
+        J = assemble_jacobian(Jp, Jl, self.cam_idx, self.pt_idx, self.n_cams, self.n_points)
+        r = ne.r.ravel()
+        step = np.concatenate([dP.ravel(), dX.ravel()])
+        pred = float(r @ r - np.sum((r + J @ step) ** 2))
+        rho = (st.F - F_new) / pred if pred > 0 else 0.0
+        accepted = F_new < st.F
+        rep = StepReport(cost_before=st.F, cost_after=F_new, pred=pred, rho=rho,
+                         lambda_used=lam, lambda_next=0.0, accepted=bool(accepted),
+                         terms_used=terms, delta=dP, P_trial=P_new)
+        if accepted:
+            lam_n = max(lam * max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3), LAMBDA_MIN)
+            new = State(P=P_new, X=X_new, F=F_new, lam=lam_n, nu=2.0,
+                        iteration=st.iteration + 1)
+        else:
+            new = State(P=st.P, X=st.X, F=st.F, lam=lam * st.nu, nu=2.0 * st.nu,
+                        iteration=st.iteration + 1)
         rep.lambda_next = new.lam
         return new, rep
 

@@ -447,3 +447,114 @@ def test_matrix_free_step_equals_dense_step(tiny, manifold):
             assert np.allclose(b.delta, a.delta, rtol=1e-9, atol=1e-12 * np.abs(a.delta).max())
             assert abs(a.cost_after - b.cost_after) <= 1e-10 * a.cost_after
             assert abs(a.pred - b.pred) <= 1e-8 * abs(a.pred)
+
+
+# --------------------------------------------------------------- PoBA and PCG (Sec. 2, 5.2)
+
+def _off_optimum(pr, P, X, seed=11, scale=1e-2):
+    rng = np.random.default_rng(seed)
+    return X + scale * rng.normal(size=X.shape)
+
+
+@pytest.mark.parametrize("manifold", [O.EUCLID, O.SPHERE])
+def test_poba_exact_step_is_joint_damped_gauss_newton(micro, manifold):
+    """The PoBA step (Schur reduction with damped V, back-substitution) at a
+    point off the landmark optimum equals the joint damped Gauss-Newton
+    step solved directly from the full Jacobian: with J~ = [J_p Q | J_l] and
+    D = diag(lambda I, lambda_l lambda I), (J~^T J~ + D) (d, dX) = -J~^T r."""
+    pr, P, X, eta = _state(micro)
+    X = _off_optimum(pr, P, X)
+    lam, lam_l = 3e-3, 2.0
+    st = O.State(P=P, X=X, F=pr.cost(P, X, eta), lam=lam)
+    prm = O.Params(eta=eta, manifold=manifold, method="poba", solver="exact", lambda_l=lam_l)
+    _, rep = pr.step(st, prm)
+    Jp, Jl = O.jacobian_blocks(P, X, pr.cam_idx, pr.pt_idx, pr.meas, eta)
+    J = O.assemble_jacobian(Jp, Jl, pr.cam_idx, pr.pt_idx, pr.n_cams, pr.n_points).toarray()
+    Q = O.tangent_bases(P, manifold)
+    k = Q.shape[2]
+    Qbd = sla.block_diag(*Q)
+    nc3 = 12 * pr.n_cams
+    Jt = np.hstack([J[:, :nc3] @ Qbd, J[:, nc3:]])
+    r = O.pose_residuals(P, X, pr.cam_idx, pr.pt_idx, pr.meas, eta).ravel()
+    D = np.diag(np.r_[np.full(k * pr.n_cams, lam), np.full(3 * pr.n_points, lam_l * lam)])
+    sol = np.linalg.solve(Jt.T @ Jt + D, -Jt.T @ r)
+    dP = (Qbd @ sol[:k * pr.n_cams]).reshape(-1, 12)
+    assert np.allclose(rep.delta, dP, rtol=1e-8, atol=1e-10 * np.abs(dP).max())
+    X_trial = X + sol[k * pr.n_cams:].reshape(-1, 3)
+    P_trial = P + dP
+    if manifold == O.SPHERE:
+        P_trial = P_trial / np.linalg.norm(P_trial, axis=1, keepdims=True)
+    assert abs(rep.cost_after - pr.cost(P_trial, X_trial, eta)) <= 1e-9 * rep.cost_after
+    # predicted decrease: ||r||^2 - ||r + J D||^2 = -b^T D + D^T Dmp D at the
+    # exact damped solution (normal-equation identity)
+    b = Jt.T @ r
+    assert abs(rep.pred - (-(b @ sol) + sol @ D @ sol)) <= 1e-8 * abs(rep.pred)
+
+
+def test_poba_series_converges_to_exact_step(micro):
+    """The power series on the damped Schur complement converges to the
+    exact PoBA step as the number of terms grows."""
+    pr, P, X, eta = _state(micro)
+    X = _off_optimum(pr, P, X)
+    st = O.State(P=P, X=X, F=pr.cost(P, X, eta), lam=1e-1)
+    ex = O.Params(eta=eta, manifold=O.SPHERE, method="poba", solver="exact")
+    _, rex = pr.step(st, ex)
+    errs = []
+    for m in (2, 8, 32, 128, 512):
+        prm = O.Params(eta=eta, manifold=O.SPHERE, method="poba", solver="series", m=m)
+        _, rs = pr.step(st, prm)
+        errs.append(np.linalg.norm(rs.delta - rex.delta) / np.linalg.norm(rex.delta))
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] <= 1e-10
+
+
+def test_poba_accepted_steps_never_increase_cost(micro):
+    pr, P, X, eta = _state(micro)
+    prm = O.Params(eta=eta, manifold=O.SPHERE, method="poba", solver="series", m=10)
+    st, reps = pr.solve(P, prm, max_iters=25, ftol=0.0)
+    for rep in reps:
+        if rep.accepted:
+            assert rep.cost_after < rep.cost_before
+
+
+def _reduced(pr, P, X, eta, lam):
+    ne = pr.normal_equations(P, X, eta)
+    return O.reduced_system(ne, O.tangent_bases(P, O.SPHERE), lam)
+
+
+def test_pcg_reaches_the_exact_step_within_the_dimension(micro):
+    """In exact arithmetic conjugate gradients solve the SPD system in at
+    most dim steps; in FP64 (which loses conjugacy on this ill-conditioned
+    system) 2 dim steps reach the Cholesky solution to 1e-10, and the
+    S-energy error never increases."""
+    pr, P, X, eta = _state(micro)
+    rs = _reduced(pr, P, X, eta, 1e-2)
+    exact = O.exact_step(rs)
+    n = len(rs.g)
+    d, it = O.pcg_step(rs, 2 * n)
+    assert it == 2 * n
+    assert np.linalg.norm(d - exact) <= 1e-10 * np.linalg.norm(exact)
+    energy = []
+    for k in range(1, 12):
+        dk, _ = O.pcg_step(rs, k)
+        e = dk - exact
+        energy.append(float(e @ rs.S @ e))
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(energy, energy[1:]))
+
+
+def test_pcg_first_iteration_is_preconditioned_steepest_descent(micro):
+    """One PCG iteration from zero is the exact line minimum along the
+    preconditioned gradient z = M^-1 g: delta = (g^T z / z^T S z) z, with M
+    the block diagonal of S."""
+    pr, P, X, eta = _state(micro)
+    rs = _reduced(pr, P, X, eta, 1e-2)
+    k = rs.Ut.shape[1]
+    M = np.zeros_like(rs.S)
+    for i in range(rs.Ut.shape[0]):
+        sl = slice(k * i, k * i + k)
+        M[sl, sl] = rs.S[sl, sl]
+    z = np.linalg.solve(M, rs.g)
+    expect = (rs.g @ z) / (z @ rs.S @ z) * z
+    d, it = O.pcg_step(rs, 1)
+    assert it == 1
+    assert np.allclose(d, expect, rtol=1e-10, atol=1e-14 * np.abs(expect).max())
