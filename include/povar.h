@@ -60,8 +60,16 @@ enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1, POVAR_MIXED_BF16 = 2 };
  *             povar_init_random (later steps use the adapted damping).
  *  series_eps series threshold: after term k >= 1 the series stops when
  *             ||x_k||_2 <= series_eps * ||delta_k||_2; 0 runs exactly m terms.
- *  lambda_l   reserved landmark damping; must be 0 (VarPro's V_0 is undamped,
- *             Sec. 4.1).
+ *  lambda_l   0: PoVar (Sec. 4: VarPro, landmarks eliminated in closed form,
+ *             V_0 undamped). > 0: PoBA, the comparison solver of Sec. 2 /
+ *             Sec. 5.2 -- joint Levenberg-Marquardt over cameras and
+ *             landmarks with landmark damping lambda_l * lambda (1 = the
+ *             joint damping of PoBA): the same series inverts the damped
+ *             Schur complement U_lambda - W V_lambda^-1 W^T, the landmarks
+ *             follow by back-substitution and are not re-eliminated, pred is
+ *             the Gauss-Newton model decrease. Landmark blocks and
+ *             back-substitution are FP64 in both precisions;
+ *             POVAR_MIXED_BF16 is not available with PoBA (POVAR_EINVAL).
  *  m          number of series terms, >= 1 (delta = sum_{i<m} M^i U^-1 g; the
  *             paper's "order 20" is m = 21).
  *  manifold   POVAR_EUCLID (unconstrained cameras, Eq. ba_first_stage) or

@@ -173,7 +173,10 @@ povar_status check_params(Problem* p, const povar_params* q) {
     return fail(p, POVAR_EINVAL, "lambda0 must be positive");
   if (q->m < 1 || q->m > 10000) return fail(p, POVAR_EINVAL, "m must be in [1, 10000]");
   if (!(q->series_eps >= 0.0)) return fail(p, POVAR_EINVAL, "series_eps must be >= 0");
-  if (q->lambda_l != 0.0) return fail(p, POVAR_EINVAL, "lambda_l must be 0 (undamped V_0)");
+  if (!(q->lambda_l >= 0.0) || !std::isfinite(q->lambda_l))
+    return fail(p, POVAR_EINVAL, "lambda_l must be >= 0 (0: PoVar, > 0: PoBA)");
+  if (q->lambda_l > 0.0 && q->precision == POVAR_MIXED_BF16)
+    return fail(p, POVAR_EINVAL, "PoBA (lambda_l > 0) runs in POVAR_FP64 or POVAR_MIXED_FP32");
   if (q->manifold != POVAR_EUCLID && q->manifold != POVAR_SPHERE)
     return fail(p, POVAR_EINVAL, "unknown manifold");
   if (q->precision != POVAR_FP64 && q->precision != POVAR_MIXED_FP32 &&
@@ -203,6 +206,7 @@ povar_status refresh_landmarks(Problem* p, double eta) {
   if ((s = launch_init_state(p, 0.0, 0, 0)) != POVAR_OK) return s;  // need_lin = 1
   p->eta_cur = eta;
   p->lm_df = false;
+  p->lm_poba = false;
   return POVAR_OK;
 }
 
@@ -249,12 +253,21 @@ povar_status prepare_step(Problem* p, const povar_params* q) {
     p->fresh = false;
   }
   if (q->eta != p->eta_cur && (s = refresh_landmarks(p, q->eta)) != POVAR_OK) return s;
-  // mixed steps solve their trial landmarks in double-float and leave the
-  // FP64 factor unwritten; an FP64 step after them starts from landmarks
-  // re-solved in FP64 at the current cameras
-  if (q->precision == POVAR_FP64 && p->lm_df && (s = refresh_landmarks(p, q->eta)) != POVAR_OK)
+  const bool poba = q->lambda_l > 0.0;
+  // mixed PoVar steps solve their trial landmarks in double-float and leave
+  // the FP64 factor unwritten; an FP64 or PoBA step after them starts from
+  // landmarks re-solved in FP64 at the current cameras; a PoVar step after
+  // PoBA steps starts from the closed-form landmarks of the current cameras
+  if ((q->precision == POVAR_FP64 || poba) && p->lm_df &&
+      (s = refresh_landmarks(p, q->eta)) != POVAR_OK)
     return s;
-  if (q->precision != POVAR_FP64) p->lm_df = true;
+  if (!poba && p->lm_poba && (s = refresh_landmarks(p, q->eta)) != POVAR_OK) return s;
+  if (poba) {
+    if ((s = ensure_poba(p)) != POVAR_OK) return s;
+    p->lm_poba = true;
+  } else if (q->precision != POVAR_FP64) {
+    p->lm_df = true;
+  }
   // stored blocks are allocated here, outside any graph capture
   if (resolve_schedule(p, q) == 4 && (s = ensure_blocks(p, block_kind(q->precision))) != POVAR_OK)
     return s;
@@ -279,21 +292,34 @@ povar_status enqueue_step_kernels(Problem* p, const povar_params* q, std::vector
     }
     return ::povar::mark(pp, m);
   };
+  const bool poba = q->lambda_l > 0.0;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
-  if ((s = launch_linearize(p, prec, q->eta)) != POVAR_OK) return s;
+  // PoBA: damped landmark blocks and b_l at (P, X) first (they change with
+  // the damping, so every PoBA step linearizes)
+  if (poba && (s = launch_poba_prep(p, q->eta, q->lambda_l)) != POVAR_OK) return s;
+  if ((s = launch_linearize(p, prec, q->eta, poba)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
-  if ((s = launch_camera_prepare(p, prec, q->manifold, q->eta)) != POVAR_OK) return s;
+  if ((s = launch_camera_prepare(p, prec, q->manifold, q->eta, poba)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if (sched == 4 && q->m > 1 && (s = launch_build_blocks(p, prec, q->eta)) != POVAR_OK) return s;
   for (int k = 1; k < q->m; ++k)
     if ((s = launch_series_term(p, prec, q->eta, k, q->series_eps, sched)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
-  if ((s = launch_pred(p, prec, q->eta, q->manifold, q->m)) != POVAR_OK) return s;
+  if (poba) {
+    // PoBA's predicted decrease comes with its trial pass below
+    if (q->manifold == POVAR_SPHERE && (s = launch_project_delta(p, prec)) != POVAR_OK) return s;
+  } else if ((s = launch_pred(p, prec, q->eta, q->manifold, q->m)) != POVAR_OK) {
+    return s;
+  }
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_update(p, prec, q->manifold)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
-  if ((s = launch_landmarks(p, 1, q->eta, prec)) != POVAR_OK) return s;
-  if ((s = launch_cost_finish(p, 1)) != POVAR_OK) return s;
+  if (poba) {
+    if ((s = launch_poba_trial(p, prec, q->eta)) != POVAR_OK) return s;
+  } else {
+    if ((s = launch_landmarks(p, 1, q->eta, prec)) != POVAR_OK) return s;
+    if ((s = launch_cost_finish(p, 1)) != POVAR_OK) return s;
+  }
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_controller(p, prec)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
@@ -388,7 +414,8 @@ povar_status autotune_schedule(Problem* p, const povar_params* q) {
 
 bool same_params(const povar_params& a, const povar_params& b) {
   return a.eta == b.eta && a.series_eps == b.series_eps && a.m == b.m &&
-         a.manifold == b.manifold && a.precision == b.precision && a.schedule == b.schedule;
+         a.manifold == b.manifold && a.precision == b.precision && a.schedule == b.schedule &&
+         a.lambda_l == b.lambda_l;
 }
 
 // Graph of one step on p->gstream (captured once per parameter set).
@@ -552,6 +579,8 @@ int64_t povar_estimate_bytes(int32_t n_cams, int32_t n_points, int64_t n_obs) {
   // row), the rest list, per-camera lists and partials (items + run partials)
   b += (nsell / 32) * 16 + (npd / 32 + 1) * 16 + (nc + 1) * 4 +
        (nsell / 32 + no) * (12 * 8 + 4);
+  // PoBA: s_j per slot (allocated at first use)
+  b += npd * (3 * 8 + 16);
   // stored-block schedule: FP64, FP32 and BF16 blocks (each allocated at
   // its first use)
   b += nsell * (72 + 36 + 18);

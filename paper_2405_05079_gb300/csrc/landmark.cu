@@ -582,11 +582,19 @@ static df64 df_host(double x) {
   return {hi, (float)(x - (double)hi)};
 }
 
+// Per-camera landmark tables of the current (0) or trial (1) cameras.
+povar_status launch_ltab(Problem* p, int which_rel, double eta) {
+  k_ltab<<<grid_for((int64_t)p->nc * 64, 256), 256, 0, p->stream>>>(
+      p->state, which_rel, eta, p->P64[0], p->P64[1], p->nc, p->Ltab, p->Ltab_df, p->camP32[0],
+      p->camP32[1]);
+  ++p->launches;
+  return check_launch(p, "ltab");
+}
+
 povar_status launch_landmarks(Problem* p, int which_rel, double eta, int precision) {
-  k_ltab<<<grid_for((int64_t)p->nc * 64, 256), 256, 0, p->stream>>>(p->state, which_rel, eta,
-                                                                      p->P64[0],
-                                                      p->P64[1], p->nc, p->Ltab, p->Ltab_df,
-                                                      p->camP32[0], p->camP32[1]);
+  povar_status s0;
+  if ((s0 = launch_ltab(p, which_rel, eta)) != POVAR_OK) return s0;
+  --p->launches;   // counted with the landmark launch below
   SlotBufs b;
   for (int t = 0; t < 2; ++t) {
     b.X[t] = p->X64[t];

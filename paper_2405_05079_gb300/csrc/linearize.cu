@@ -68,8 +68,13 @@ k_linearize(const DeviceState* __restrict__ st, T s1, T s2, int nchunks,
             const T* __restrict__ P0, const T* __restrict__ P1,
             const float4* __restrict__ pdA0, const float4* __restrict__ pdA1,
             const double* __restrict__ X0, const double* __restrict__ X1,
+            const float4* __restrict__ sbl32, const double* __restrict__ sbl64, int force,
             T* __restrict__ part) {
-  if (st->converged || !st->need_lin) return;
+  // PoBA (sbl given, linearized every step): the residual is evaluated at
+  // the landmark shifted by s_j = V_lambda^-1 b_l, which turns b_p into the
+  // reduced right-hand side b_p - W V_lambda^-1 b_l; U and the outer
+  // products keep X
+  if (st->converged || (!force && !st->need_lin)) return;
   constexpr bool CENTER = sizeof(T) == 4;
   const int lane = threadIdx.x & 31;
   const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -108,9 +113,22 @@ k_linearize(const DeviceState* __restrict__ st, T s1, T s2, int nchunks,
     const T u = m.x, v = m.y, w = u * u + v * v;
     T x0, x1, x2;
     load_x<T>(pdA, X64, slot, x0, x1, x2);
-    const T y0 = P[0] * x0 + P[1] * x1 + P[2] * x2 + P[3];
-    const T y1 = P[4] * x0 + P[5] * x1 + P[6] * x2 + P[7];
-    const T y2 = P[8] * x0 + P[9] * x1 + P[10] * x2 + P[11];
+    T xr0 = x0, xr1 = x1, xr2 = x2;
+    if (sbl32) {
+      if constexpr (sizeof(T) == 4) {
+        const float4 sv = __ldg(sbl32 + slot);
+        xr0 -= sv.x;
+        xr1 -= sv.y;
+        xr2 -= sv.z;
+      } else {
+        xr0 -= sbl64[3 * (size_t)slot];
+        xr1 -= sbl64[3 * (size_t)slot + 1];
+        xr2 -= sbl64[3 * (size_t)slot + 2];
+      }
+    }
+    const T y0 = P[0] * xr0 + P[1] * xr1 + P[2] * xr2 + P[3];
+    const T y1 = P[4] * xr0 + P[5] * xr1 + P[6] * xr2 + P[7];
+    const T y2 = P[8] * xr0 + P[9] * xr1 + P[10] * xr2 + P[11];
     const T r0 = s1 * (y0 - u * y2), r1 = s1 * (y1 - v * y2);
     const T r2 = s2 * (y0 - u), r3 = s2 * (y1 - v);
     const T g[3] = {s1 * r0 + s2 * r2, s1 * r1 + s2 * r3, -s1 * (u * r0 + v * r1)};
@@ -178,7 +196,7 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
                  const T* __restrict__ part, const double* __restrict__ P0,
                  const double* __restrict__ P1, double* __restrict__ U64,
                  double* __restrict__ bp64, double* __restrict__ G64, float* __restrict__ G32, T* __restrict__ Y,
-                 T* __restrict__ D, double* __restrict__ camnorm) {
+                 T* __restrict__ D, double* __restrict__ camnorm, int force) {
   if (st->converged) return;
   __shared__ double smA[4][12][13];
   __shared__ double smL[4][12][13];
@@ -194,7 +212,7 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
   }
   if (i >= nc) return;
   const int cur = st->cur;
-  const int need_lin = st->need_lin;
+  const int need_lin = force || st->need_lin;
   const double lam = st->lam;
   const double a = 1.0 - eta;
   const double* Pc = (cur ? P1 : P0) + 12 * (size_t)i;
@@ -357,36 +375,40 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
 
 }  // namespace
 
-povar_status launch_linearize(Problem* p, int precision, double eta) {
+povar_status launch_linearize(Problem* p, int precision, double eta, bool poba) {
   const unsigned g = grid_for(p->nchunks, 8);
   if (g == 0) return POVAR_OK;
+  const float4* s32 = poba ? p->sbl32 : nullptr;
+  const double* s64 = poba ? p->sbl64 : nullptr;
+  const int force = poba ? 1 : 0;
   if (precision == POVAR_FP64) {
     k_linearize<double><<<g, 256, 0, p->stream>>>(
         p->state, sqrt(1.0 - eta), sqrt(eta), p->nchunks, p->chunk_cam, p->chunk_beg, p->cm_slot,
         p->cm_m64, p->P64[0], p->P64[1], p->pdA[0], p->pdA[1], p->X64[0], p->X64[1],
-        static_cast<double*>(p->part_lin));
+        s64 ? s32 : nullptr, s64, force, static_cast<double*>(p->part_lin));
   } else {
     k_linearize<float><<<g, 256, 0, p->stream>>>(
         p->state, (float)sqrt(1.0 - eta), (float)sqrt(eta), p->nchunks, p->chunk_cam,
         p->chunk_beg, p->cm_slot, p->cm_m32, p->camP32[0], p->camP32[1], p->pdA[0], p->pdA[1],
-        p->X64[0], p->X64[1], static_cast<float*>(p->part_lin));
+        p->X64[0], p->X64[1], s32, s64, force, static_cast<float*>(p->part_lin));
   }
   ++p->launches;
   return check_launch(p, "linearize");
 }
 
-povar_status launch_camera_prepare(Problem* p, int precision, int manifold, double eta) {
+povar_status launch_camera_prepare(Problem* p, int precision, int manifold, double eta,
+                                   bool poba) {
   const unsigned g = grid_for(p->nc, 4);
   if (precision == POVAR_FP64) {
     k_camera_prepare<double><<<g, 128, 0, p->stream>>>(
         p->state, eta, manifold, p->nc, p->cam_nchunk, p->cam_chunk0,
         static_cast<const double*>(p->part_lin), p->P64[0], p->P64[1], p->U64, p->bp64,
-        p->G64, p->G32, p->Y64, p->D64, p->camnorm);
+        p->G64, p->G32, p->Y64, p->D64, p->camnorm, poba ? 1 : 0);
   } else {
     k_camera_prepare<float><<<g, 128, 0, p->stream>>>(
         p->state, eta, manifold, p->nc, p->cam_nchunk, p->cam_chunk0,
         static_cast<const float*>(p->part_lin), p->P64[0], p->P64[1], p->U64, p->bp64,
-        p->G64, p->G32, p->Y32, p->D32, p->camnorm);
+        p->G64, p->G32, p->Y32, p->D32, p->camnorm, poba ? 1 : 0);
   }
   ++p->launches;
   return check_launch(p, "camera_prepare");

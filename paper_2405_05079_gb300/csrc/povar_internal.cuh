@@ -221,6 +221,10 @@ struct Problem {
   float4* pdB[2] = {nullptr, nullptr};  // (F10, F11, F20, F21)
   float* pdC[2] = {nullptr, nullptr};   // F22
   float4* rec32 = nullptr;              // [np_pad*2] (s0 s1 s2 X0)(X1 X2 - -)
+  // PoBA (allocated at first use): s_j = V_lambda^-1 b_l per slot
+  double* sbl64 = nullptr;              // [np_pad*3]
+  float4* sbl32 = nullptr;              // [np_pad] (s0 s1 s2 -)
+  bool lm_poba = false;                 // landmarks are PoBA iterates, not X*(P)
   double2* rec64 = nullptr;             // [np_pad*4] (s0 s1)(s2 X0)(X1 X2)(- -)
   double* cost_part = nullptr;          // [np_pad / 32] one per warp
   double* fin_blk = nullptr;            // [2 * FIN_BLOCKS] block sums of the final reductions
@@ -299,9 +303,14 @@ povar_status launch_landmarks(Problem* p, int which_rel, double eta, int precisi
 povar_status launch_cost_finish(Problem* p, int which_rel);
 
 // ------------------------------------------------- linearize.cu (a4,a5,a6)
-povar_status launch_linearize(Problem* p, int precision, double eta);
+povar_status launch_linearize(Problem* p, int precision, double eta, bool poba = false);
+povar_status launch_ltab(Problem* p, int which_rel, double eta);
+povar_status launch_project_delta(Problem* p, int precision);
+povar_status ensure_poba(Problem* p);
+povar_status launch_poba_prep(Problem* p, double eta, double lambda_l);
+povar_status launch_poba_trial(Problem* p, int precision, double eta);
 povar_status launch_camera_prepare(Problem* p, int precision, int manifold,
-                                   double eta);
+                                   double eta, bool poba = false);
 
 // ---------------------------------------------------- series.cu (a7,a8)
 // schedule 0: point gather + camera-major scatter; 1: fused runs; 2: camera

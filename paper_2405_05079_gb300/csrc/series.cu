@@ -2193,6 +2193,18 @@ povar_status launch_build_blocks(Problem* p, int precision, double eta) {
   return check_launch(p, "build_blocks");
 }
 
+povar_status launch_project_delta(Problem* p, int precision) {
+  const unsigned gc = grid_for(p->nc, 128);
+  if (precision == POVAR_FP64)
+    k_project_delta<double><<<gc, 128, 0, p->stream>>>(p->state, p->nc, p->P64[0], p->P64[1],
+                                                       p->D64);
+  else
+    k_project_delta<float><<<gc, 128, 0, p->stream>>>(p->state, p->nc, p->P64[0], p->P64[1],
+                                                      p->D32);
+  ++p->launches;
+  return check_launch(p, "project_delta");
+}
+
 povar_status launch_pred(Problem* p, int precision, double eta, int manifold, int m) {
   const double a64 = 1.0 - eta;
   const float a32 = (float)a64;

@@ -143,8 +143,10 @@ def _obs_arrays(cam_idx, pt_idx, meas, n_obs=None):
 
 
 def make_params(eta=0.1, lambda0=1e-4, m=10, series_eps=0.0, manifold=SPHERE,
-                precision=MIXED_FP32, schedule=-1) -> Params:
-    return Params(eta=eta, lambda0=lambda0, series_eps=series_eps, lambda_l=0.0, m=m,
+                precision=MIXED_FP32, schedule=-1, lambda_l=0.0) -> Params:
+    """Solver parameters (include/povar.h); lambda_l > 0 selects PoBA (joint
+    LM with landmark damping lambda_l * lambda) instead of PoVar."""
+    return Params(eta=eta, lambda0=lambda0, series_eps=series_eps, lambda_l=lambda_l, m=m,
                   manifold=manifold, precision=precision, schedule=schedule)
 
 
