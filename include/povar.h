@@ -109,6 +109,21 @@ enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1, POVAR_MIXED_BF16 = 2 };
  *             povar_get_tuning). All schedules compute the same series (up
  *             to rounding order). */
 enum { POVAR_NSCHEDULES = 6 };
+/*  solver     POVAR_SOLVER_SERIES (0): the power series above.
+ *             POVAR_SOLVER_PCG (1): the "iterative" baseline of Sec. 5.2 --
+ *             conjugate gradients on the same (damped, tangent-projected)
+ *             reduced camera system from delta = 0, preconditioned by the
+ *             inverse 12x12 diagonal blocks of the Schur complement
+ *             (Schur-Jacobi). Then m is the maximum number of inner
+ *             iterations (500 in Sec. 5.2) and series_eps the relative
+ *             residual tolerance: the iteration stops when
+ *             ||g - S delta||_2 <= series_eps * ||g||_2 (0 runs exactly m
+ *             iterations). One landmark pass of schedule 1 per iteration
+ *             (params->schedule is not used). PCG steps are issued without
+ *             a CUDA graph and read a device flag every 8 iterations; they
+ *             are not available in a batch (POVAR_EINVAL there).
+ *             POVAR_MIXED_BF16 is not available with PCG (POVAR_EINVAL). */
+enum { POVAR_SOLVER_SERIES = 0, POVAR_SOLVER_PCG = 1 };
 typedef struct {
   double eta;
   double lambda0;
@@ -118,6 +133,8 @@ typedef struct {
   int32_t manifold;
   int32_t precision;
   int32_t schedule;
+  int32_t solver;
+  int32_t reserved;    /* must be 0 */
 } povar_params;
 
 /* Report of one damped VarPro iteration. cost_before is F at the iterate the

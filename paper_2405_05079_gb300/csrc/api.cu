@@ -186,6 +186,11 @@ povar_status check_params(Problem* p, const povar_params* q) {
     return fail(p, POVAR_EINVAL, "unknown schedule");
   if (q->precision == POVAR_MIXED_BF16 && q->schedule != -1 && q->schedule != 4)
     return fail(p, POVAR_EINVAL, "POVAR_MIXED_BF16 runs schedule 4 only");
+  if (q->solver != POVAR_SOLVER_SERIES && q->solver != POVAR_SOLVER_PCG)
+    return fail(p, POVAR_EINVAL, "unknown solver");
+  if (q->solver == POVAR_SOLVER_PCG && q->precision == POVAR_MIXED_BF16)
+    return fail(p, POVAR_EINVAL, "PCG runs in POVAR_FP64 or POVAR_MIXED_FP32");
+  if (q->reserved != 0) return fail(p, POVAR_EINVAL, "params->reserved must be 0");
   return POVAR_OK;
 }
 
@@ -269,8 +274,10 @@ povar_status prepare_step(Problem* p, const povar_params* q) {
     p->lm_df = true;
   }
   // stored blocks are allocated here, outside any graph capture
-  if (resolve_schedule(p, q) == 4 && (s = ensure_blocks(p, block_kind(q->precision))) != POVAR_OK)
+  if (q->solver == POVAR_SOLVER_SERIES && resolve_schedule(p, q) == 4 &&
+      (s = ensure_blocks(p, block_kind(q->precision))) != POVAR_OK)
     return s;
+  if (q->solver == POVAR_SOLVER_PCG && (s = ensure_pcg(p)) != POVAR_OK) return s;
   return POVAR_OK;
 }
 
@@ -301,9 +308,16 @@ povar_status enqueue_step_kernels(Problem* p, const povar_params* q, std::vector
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_camera_prepare(p, prec, q->manifold, q->eta, poba)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
-  if (sched == 4 && q->m > 1 && (s = launch_build_blocks(p, prec, q->eta)) != POVAR_OK) return s;
-  for (int k = 1; k < q->m; ++k)
-    if ((s = launch_series_term(p, prec, q->eta, k, q->series_eps, sched)) != POVAR_OK) return s;
+  if (q->solver == POVAR_SOLVER_PCG) {
+    // the reduced system by conjugate gradients (reads device flags: eager only)
+    if ((s = launch_pcg(p, prec, q->manifold, q->eta, q->m, q->series_eps)) != POVAR_OK) return s;
+  } else {
+    if (sched == 4 && q->m > 1 && (s = launch_build_blocks(p, prec, q->eta)) != POVAR_OK)
+      return s;
+    for (int k = 1; k < q->m; ++k)
+      if ((s = launch_series_term(p, prec, q->eta, k, q->series_eps, sched)) != POVAR_OK)
+        return s;
+  }
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if (poba) {
     // PoBA's predicted decrease comes with its trial pass below
@@ -415,7 +429,7 @@ povar_status autotune_schedule(Problem* p, const povar_params* q) {
 bool same_params(const povar_params& a, const povar_params& b) {
   return a.eta == b.eta && a.series_eps == b.series_eps && a.m == b.m &&
          a.manifold == b.manifold && a.precision == b.precision && a.schedule == b.schedule &&
-         a.lambda_l == b.lambda_l;
+         a.lambda_l == b.lambda_l && a.solver == b.solver;
 }
 
 // Graph of one step on p->gstream (captured once per parameter set).
@@ -469,7 +483,7 @@ void fill_report(Problem* p, povar_step_report* r, float ms) {
 povar_status solve_loop(Problem* p, const povar_params* q, int max_iters) {
   povar_status s;
   const int check_every = 4;
-  if (p->use_graphs) {
+  if (p->use_graphs && q->solver == POVAR_SOLVER_SERIES) {
     // one graph launch per step on the library stream, joined to the
     // caller's stream with events before and after
     if ((s = prepare_step(p, q)) != POVAR_OK) return s;
@@ -581,6 +595,9 @@ int64_t povar_estimate_bytes(int32_t n_cams, int32_t n_points, int64_t n_obs) {
        (nsell / 32 + no) * (12 * 8 + 4);
   // PoBA: s_j per slot (allocated at first use)
   b += npd * (3 * 8 + 16);
+  // PCG (allocated at first use): r, z, p, q, the preconditioner blocks in
+  // FP64 and FP32, chunk sums of the diagonal blocks, dot products
+  b += nc * (48 * 8 + 144 * 12 + 16) + chunks * 60 * 8;
   // stored-block schedule: FP64, FP32 and BF16 blocks (each allocated at
   // its first use)
   b += nsell * (72 + 36 + 18);
@@ -1090,6 +1107,8 @@ static povar_status batch_solve(povar_batch* b, const povar_params* params_base,
     Problem* p = &b->probs[k]->impl;
     const povar_params* params = params_base + k * each;
     if ((s = povar::check_params(p, params)) != POVAR_OK) return batch_fail(b, s, p->err);
+    if (params->solver != POVAR_SOLVER_SERIES)
+      return batch_fail(b, POVAR_EINVAL, "a batch runs the series solver only");
     if ((s = povar::sync_state(p)) != POVAR_OK) return batch_fail(b, s, p->err);
     it0[k] = p->h_state->iteration;
     if ((s = povar::launch_begin(p, ftol, target_costs ? target_costs[k] : 0.0, max_iters)) !=

@@ -100,6 +100,11 @@ struct DeviceState {
   double lam_ref;     // damping at the start of the current solve
   int fallback_after; // mixed-precision safeguard: rejections that trigger it (0: off)
   int fallback;       // set with `converged` when the safeguard triggered
+  // conjugate-gradient solver (POVAR_SOLVER_PCG) of the current step
+  double pcg_rz;      // r^T z of the current residual
+  double pcg_gg;      // g^T g (stop test ||r|| <= eps ||g||)
+  double pcg_alpha;   // step length of the current iteration
+  double pcg_beta;    // direction update coefficient
 };
 
 // Host-side handle.
@@ -225,6 +230,13 @@ struct Problem {
   double* sbl64 = nullptr;              // [np_pad*3]
   float4* sbl32 = nullptr;              // [np_pad] (s0 s1 s2 -)
   bool lm_poba = false;                 // landmarks are PoBA iterates, not X*(P)
+  // conjugate-gradient solver (allocated at first use)
+  double* pcg_vec = nullptr;            // [4*nc*12] r, z, p, q (float or double)
+  double* pcg_M64 = nullptr;            // [nc*144] inverse Schur-Jacobi blocks
+  float* pcg_M32 = nullptr;             // [nc*144] their FP32 copies
+  double* pcg_sd = nullptr;             // [nchunks*60] chunk sums of the diagonal blocks
+  double* pcg_vals = nullptr;           // [nc*2] per-camera dot products
+  uint32_t* pcg_ticket = nullptr;       // last-block ticket of the dot products
   double2* rec64 = nullptr;             // [np_pad*4] (s0 s1)(s2 X0)(X1 X2)(- -)
   double* cost_part = nullptr;          // [np_pad / 32] one per warp
   double* fin_blk = nullptr;            // [2 * FIN_BLOCKS] block sums of the final reductions
@@ -318,6 +330,18 @@ povar_status launch_camera_prepare(Problem* p, int precision, int manifold,
 povar_status launch_series_term(Problem* p, int precision, double eta,
                                 int term, double eps, int schedule);
 povar_status launch_pred(Problem* p, int precision, double eta, int manifold, int m);
+// z = W V^-1 W^T vec as run partials (part_run, schedule 1's fused pass) for
+// a camera vector vec of the precision's type.
+povar_status launch_wvw(Problem* p, int precision, double eta, const void* vec);
+
+// ---------------------------------------------------- pcg.cu
+// Conjugate-gradient solve of the reduced camera system into the step buffer
+// (after launch_camera_prepare): at most `iters` iterations, relative
+// residual tolerance eps. Synchronizes the stream every few iterations to
+// stop early; never captured in a graph.
+povar_status ensure_pcg(Problem* p);
+povar_status launch_pcg(Problem* p, int precision, int manifold, double eta, int iters,
+                        double eps);
 // Stored schedule (4) and the BF16 precision: block kind of a precision,
 // allocation (before any capture), plane pointers, and the per-step build of
 // G_k at the current cameras.

@@ -2238,6 +2238,24 @@ povar_status launch_pred(Problem* p, int precision, double eta, int manifold, in
   return check_launch(p, "pred");
 }
 
+povar_status launch_wvw(Problem* p, int precision, double eta, const void* vec) {
+  const double a64 = 1.0 - eta;
+  if (precision == POVAR_FP64) {
+    k_series_fused<double, void><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+        p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1],
+        static_cast<const double*>(vec), point_data<double>(p, 0), point_data<double>(p, 1),
+        p->row_mask, p->row_base, static_cast<double*>(p->part_run), BlockPlanes{});
+  } else {
+    k_series_fused<float, void><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+        p->state, (float)a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
+        p->camP32[1], static_cast<const float*>(vec), point_data<float>(p, 0),
+        point_data<float>(p, 1), p->row_mask, p->row_base, static_cast<float*>(p->part_run),
+        BlockPlanes{});
+  }
+  ++p->launches;
+  return check_launch(p, "wvw");
+}
+
 // The group kernel's dynamic shared memory exceeds the default 48 KB limit in
 // FP64; raise the per-kernel limit once per problem (outside any capture).
 povar_status setup_group_kernels(Problem* p) {

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libpovar.so")
 EUCLID, SPHERE = 0, 1
 FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 NSCHEDULES = 6            # POVAR_NSCHEDULES
+SOLVER_SERIES, SOLVER_PCG = 0, 1
 
 STATUS = {0: "POVAR_OK", 1: "POVAR_EINVAL", 2: "POVAR_ENOMEM", 3: "POVAR_ECUDA",
           4: "POVAR_ENUMERIC", 5: "POVAR_ETIMEOUT", 6: "POVAR_ENOTCONVERGED"}
@@ -33,7 +34,8 @@ class PovarError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("eta", C.c_double), ("lambda0", C.c_double), ("series_eps", C.c_double),
                 ("lambda_l", C.c_double), ("m", C.c_int32), ("manifold", C.c_int32),
-                ("precision", C.c_int32), ("schedule", C.c_int32)]
+                ("precision", C.c_int32), ("schedule", C.c_int32), ("solver", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class StepReport(C.Structure):
@@ -143,11 +145,15 @@ def _obs_arrays(cam_idx, pt_idx, meas, n_obs=None):
 
 
 def make_params(eta=0.1, lambda0=1e-4, m=10, series_eps=0.0, manifold=SPHERE,
-                precision=MIXED_FP32, schedule=-1, lambda_l=0.0) -> Params:
+                precision=MIXED_FP32, schedule=-1, lambda_l=0.0, solver=0) -> Params:
     """Solver parameters (include/povar.h); lambda_l > 0 selects PoBA (joint
-    LM with landmark damping lambda_l * lambda) instead of PoVar."""
+    LM with landmark damping lambda_l * lambda) instead of PoVar; solver
+    SOLVER_PCG replaces the series by Schur-Jacobi preconditioned conjugate
+    gradients (m = maximum inner iterations, series_eps = relative residual
+    tolerance)."""
     return Params(eta=eta, lambda0=lambda0, series_eps=series_eps, lambda_l=lambda_l, m=m,
-                  manifold=manifold, precision=precision, schedule=schedule)
+                  manifold=manifold, precision=precision, schedule=schedule, solver=solver,
+                  reserved=0)
 
 
 def current_stream_handle() -> int | None:

@@ -150,3 +150,31 @@ def test_noalloc_rejects_misaligned_pointers_before_any_cuda_call(libpath):
     for bad in (dict(P=base + 8), dict(meas=base + 0x3008), dict(off=base + 0x1002),
                 dict(cam=base + 0x2001), dict(F=base + 0x5004), dict(X=base + 0x4004)):
         assert call(**bad) == 1, bad
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's Params and StepReport have the header's size and field
+    offsets (compiled with the host C compiler against include/povar.h)."""
+    import shutil
+    import subprocess
+    from paper_2405_05079_gb300 import povar
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"povar_params": povar.Params, "povar_step_report": povar.StepReport}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "povar.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
