@@ -103,18 +103,28 @@ def profiles(traces: dict, taus=TAUS, alphas=ALPHAS) -> dict:
 
 def default_solvers(povar):
     """Solver variants of the family: (name, precision, series terms m (or a
-    function of the scene giving m), camera parametrization)."""
+    function of the scene giving m), camera parametrization[, extra
+    parameters]). Besides PoVar's variants, the two first-stage competitors
+    of Sec. 5.2 on the same kernels: PoBA (joint LM, landmark damping equal
+    to the camera damping, the same series settings) and the "iterative"
+    VarPro baseline (Schur-Jacobi PCG, at most 500 inner iterations, relative
+    residual tolerance 0.01)."""
     return [("mixed m=21", povar.MIXED_FP32, 21, povar.EUCLID),
             ("fp64 m=21", povar.FP64, 21, povar.EUCLID),
             ("mixed m=11", povar.MIXED_FP32, 11, povar.EUCLID),
             ("mixed m=6", povar.MIXED_FP32, 6, povar.EUCLID),
-            ("mixed m=21 sphere", povar.MIXED_FP32, 21, povar.SPHERE)]
+            ("mixed m=21 sphere", povar.MIXED_FP32, 21, povar.SPHERE),
+            ("poba mixed m=21", povar.MIXED_FP32, 21, povar.EUCLID, {"lambda_l": 1.0}),
+            ("iterative mixed pcg500", povar.MIXED_FP32, 500, povar.EUCLID,
+             {"solver": povar.SOLVER_PCG})]
 
 
 def time_to_targets(problems, solvers, eta: float, taus=TAUS, max_iters: int = 50,
                     seed: int = 0):
     """T_tau(p, s) for every tolerance, solver and problem, measured with the
-    GPU solver (povar_solve, one graph launch per LM step).
+    GPU solver (povar_solve: one graph launch per LM step for the series
+    solvers; the PCG solver issues its kernels eagerly, reading a device
+    flag every 8 inner iterations).
 
     Every solver starts problem k from the same cameras (seeded N(0,1)
     entries scaled to unit norm, Sec. 5.2; landmarks from Eq. 8), with
@@ -135,10 +145,11 @@ def time_to_targets(problems, solvers, eta: float, taus=TAUS, max_iters: int = 5
         P0 = scenes.init_cameras(sc.n_cams, seed + k, normalize=True)
         with povar.Problem.from_scene(sc) as pb:
             # m is a number of terms, or a function of the scene (a tuned policy)
-            prms = {name: povar.make_params(eta=eta, lambda0=1e-4,
-                                            m=int(m(sc) if callable(m) else m),
-                                            series_eps=0.01, manifold=man, precision=prec)
-                    for name, prec, m, man in solvers}
+            prms = {name: povar.make_params(**{"eta": eta, "lambda0": 1e-4,
+                                               "m": int(m(sc) if callable(m) else m),
+                                               "series_eps": 0.01, "manifold": man,
+                                               "precision": prec, **(extra[0] if extra else {})})
+                    for name, prec, m, man, *extra in solvers}
             final = {}
             for name in prms:
                 pb.set_cameras(P0, eta)

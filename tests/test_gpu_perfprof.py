@@ -17,8 +17,9 @@ pytestmark = pytest.mark.gpu
 
 def test_time_to_targets_on_small_family():
     fam = scenes.family_scenes("batched", 3, seed=3)
-    solvers = [s for s in pp.default_solvers(povar) if s[0] in ("mixed m=21", "fp64 m=21",
-                                                                 "mixed m=6")]
+    solvers = [s for s in pp.default_solvers(povar) if s[0] in (
+        "mixed m=21", "fp64 m=21", "mixed m=6", "poba mixed m=21", "iterative mixed pcg500")]
+    assert len(solvers) == 5
     eta = 0.2
     T, f0, fstar = pp.time_to_targets(fam, solvers, eta, pp.TAUS, max_iters=20, seed=3)
     names = [s[0] for s in solvers]
