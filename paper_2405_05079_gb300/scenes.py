@@ -255,6 +255,26 @@ def init_cameras(n_cams: int, seed: int, normalize: bool) -> np.ndarray:
     return P
 
 
+def stage2_start(scene: Scene, seed: int, noise: float = 0.01):
+    """A start for the second (projective) stage near the scene's ground
+    truth: the cameras [R | t] and the homogeneous points (X, 1) are moved by
+    one random projective transformation H = I + 0.2 N(0, 1) (P H, H^-1 X
+    keep every projection), then every entry gets relative iid normal noise
+    of size `noise` (of the row's RMS). Returns P [n_cams, 12] (row-major
+    3x4) and X [n_points, 4]; rows are not normalized."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x57A6E2]))
+    while True:
+        H = np.eye(4) + 0.2 * rng.normal(size=(4, 4))
+        if np.linalg.cond(H) < 10.0:
+            break
+    P = np.einsum("nab,bc->nac", scene.gt_cams, H).reshape(scene.n_cams, 12)
+    Xh = np.concatenate([scene.gt_points, np.ones((scene.n_points, 1))], axis=1)
+    X = np.linalg.solve(H, Xh.T).T
+    P = P + noise * np.sqrt(np.mean(P * P, axis=1, keepdims=True)) * rng.normal(size=P.shape)
+    X = X + noise * np.sqrt(np.mean(X * X, axis=1, keepdims=True)) * rng.normal(size=X.shape)
+    return P, X
+
+
 def scene_by_name(name: str, seed: int = 0) -> Scene:
     return {"tiny": tiny_scene, "mid": mid_scene, "large": large_scene}[name](seed)
 
