@@ -207,6 +207,54 @@ povar_status povar_init_random(povar_problem* p, uint64_t seed, int32_t manifold
 povar_status povar_get_cameras(povar_problem* p, double* P_out);
 povar_status povar_get_points(povar_problem* p, double* X_out);
 
+/* ---- Second stage: projective refinement (Eq. second_stage) by Riemannian
+ * PoBA (RiPoBA, Sec. 4.3), on the same observations and handle.
+ * Cameras P_i are 3x4 with vec(P_i) on the unit sphere of R^12 (the same
+ * camera buffers as the first stage, row-major); landmarks are homogeneous
+ * 4-vectors on the unit sphere of R^4. The cost is
+ *   F2 = sum over observations of ||(y1 / y3, y2 / y3) - m_ij||^2,
+ *   y = P_i X_j,
+ * with the normalized measurements given to povar_create. A step is joint
+ * Levenberg-Marquardt on both tangent spaces (projected normal equation of
+ * Sec. 4.3, damping lambda on the cameras and lambda_l * lambda on the
+ * landmarks, D = I): the power series (Lemma 2) inverts the damped
+ * Riemannian Schur complement, the landmarks follow by back-substitution,
+ * cameras and landmarks are retracted by normalization, pred is the
+ * Gauss-Newton model decrease, and accept/reject and the damping rule are
+ * the first stage's.
+ *
+ * povar_s2_set: start the second stage. P (host, n_cams*12) and X (host,
+ * n_points*4, by landmark id), both finite; rows are normalized by the
+ * library. With P == X == NULL the start is the first stage's result:
+ * the current cameras (normalized) and the homogeneous (X_j, 1) of the
+ * first stage's closed-form landmarks at them (re-solved in FP64 when the
+ * last step was mixed); POVAR_EINVAL if there is no first-stage state or
+ * if only P is given. Computes the cost; the next povar_s2_step / solve
+ * starts with damping params->lambda0. Synchronizes the stream.
+ * povar_s2_cost: F2 at the current iterate.
+ * povar_s2_step / povar_s2_solve: as povar_step / povar_solve (same
+ * report, stop rules and mixed-precision safeguard) for the second stage.
+ * params: m, series_eps, lambda0 as for the first stage; lambda_l > 0
+ * (1 = the paper's joint damping); manifold must be POVAR_SPHERE;
+ * precision POVAR_FP64 or POVAR_MIXED_FP32 (FP32 series terms and camera
+ * vectors; landmark blocks, linearization, back-substitution and cost in
+ * FP64); solver POVAR_SOLVER_SERIES; eta and schedule are not used. Steps
+ * are issued without a CUDA graph.
+ * povar_s2_get_points: the current homogeneous landmarks (n_points*4, by
+ * landmark id); the cameras come from povar_get_cameras.
+ * A first-stage call after second-stage steps re-solves the first stage's
+ * landmarks at the current cameras; a second-stage call after first-stage
+ * steps recomputes F2 and restarts the damping. POVAR_EINVAL before the
+ * first povar_s2_set. */
+povar_status povar_s2_set(povar_problem* p, const double* P, const double* X);
+povar_status povar_s2_cost(povar_problem* p, double* cost_out);
+povar_status povar_s2_step(povar_problem* p, const povar_params* params,
+                           povar_step_report* report);
+povar_status povar_s2_solve(povar_problem* p, const povar_params* params, int32_t max_iters,
+                            double ftol, double target_cost, povar_step_report* last,
+                            int32_t* iters_out);
+povar_status povar_s2_get_points(povar_problem* p, double* X_out);
+
 /* pOSE cost F = ||r||^2 (Eq. ba_first_stage) at the current cameras with
  * the landmarks at their closed-form optimum for this eta. */
 povar_status povar_cost(povar_problem* p, double eta, double* cost_out);

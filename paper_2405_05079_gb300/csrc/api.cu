@@ -206,6 +206,7 @@ int resolve_schedule(const Problem* p, const povar_params* q) {
 // Landmarks + cost at the current cameras for eta (no damping reset).
 povar_status refresh_landmarks(Problem* p, double eta) {
   povar_status s;
+  p->s2_current = false;
   if ((s = launch_landmarks(p, 0, eta)) != POVAR_OK) return s;
   if ((s = launch_cost_finish(p, 0)) != POVAR_OK) return s;
   if ((s = launch_init_state(p, 0.0, 0, 0)) != POVAR_OK) return s;  // need_lin = 1
@@ -329,7 +330,7 @@ povar_status enqueue_step_kernels(Problem* p, const povar_params* q, std::vector
   if ((s = launch_update(p, prec, q->manifold)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if (poba) {
-    if ((s = launch_poba_trial(p, prec, q->eta)) != POVAR_OK) return s;
+    if ((s = launch_poba_trial(p, prec, q->eta, q->m)) != POVAR_OK) return s;
   } else {
     if ((s = launch_landmarks(p, 1, q->eta, prec)) != POVAR_OK) return s;
     if ((s = launch_cost_finish(p, 1)) != POVAR_OK) return s;
@@ -538,6 +539,90 @@ povar_status solve_loop(Problem* p, const povar_params* q, int max_iters) {
     if ((s = sync_state(p)) != POVAR_OK) return s;
   }
   return POVAR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Second stage (projective refinement by Riemannian PoBA)
+// ---------------------------------------------------------------------------
+
+povar_status check_s2_params(Problem* p, const povar_params* q) {
+  if (!q) return fail(p, POVAR_EINVAL, "params is NULL");
+  if (!(q->lambda0 > 0.0) || !std::isfinite(q->lambda0))
+    return fail(p, POVAR_EINVAL, "lambda0 must be positive");
+  if (q->m < 1 || q->m > 10000) return fail(p, POVAR_EINVAL, "m must be in [1, 10000]");
+  if (!(q->series_eps >= 0.0)) return fail(p, POVAR_EINVAL, "series_eps must be >= 0");
+  if (!(q->lambda_l > 0.0) || !std::isfinite(q->lambda_l))
+    return fail(p, POVAR_EINVAL, "the second stage needs lambda_l > 0 (1: joint damping)");
+  if (q->manifold != POVAR_SPHERE)
+    return fail(p, POVAR_EINVAL, "the second stage is Riemannian: manifold must be SPHERE");
+  if (q->precision != POVAR_FP64 && q->precision != POVAR_MIXED_FP32)
+    return fail(p, POVAR_EINVAL, "the second stage runs in POVAR_FP64 or POVAR_MIXED_FP32");
+  if (q->solver != POVAR_SOLVER_SERIES)
+    return fail(p, POVAR_EINVAL, "the second stage runs the series solver");
+  if (q->reserved != 0) return fail(p, POVAR_EINVAL, "params->reserved must be 0");
+  if (!p->s2_live) return fail(p, POVAR_EINVAL, "call povar_s2_set first");
+  return POVAR_OK;
+}
+
+// Before a second-stage step: the device state must hold the second stage's
+// cost (a first-stage call in between replaced it), and the damping starts
+// at lambda0 after povar_s2_set.
+povar_status prepare_s2_step(Problem* p, const povar_params* q) {
+  povar_status s;
+  if (!p->s2_current) {
+    if ((s = launch_s2_cost(p)) != POVAR_OK) return s;
+    p->s2_current = true;
+    p->fresh = true;
+  }
+  if (p->fresh) {
+    if ((s = launch_init_state(p, q->lambda0, 1, 0)) != POVAR_OK) return s;
+    p->fresh = false;
+  }
+  // a later first-stage call re-solves its landmarks at the cameras
+  p->eta_cur = -1.0;
+  return POVAR_OK;
+}
+
+povar_status enqueue_s2_step(Problem* p, const povar_params* q) {
+  povar_status s;
+  std::vector<size_t>* mk = nullptr;
+  if (p->profiling) {
+    p->prof_steps.emplace_back();
+    mk = &p->prof_steps.back();
+  }
+  const int prec = q->precision;
+  if ((s = prepare_s2_step(p, q)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
+  if ((s = launch_s2_prep(p, q->lambda_l)) != POVAR_OK) return s;
+  if ((s = launch_s2_linearize(p)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
+  if ((s = launch_s2_camera_prepare(p, prec)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
+  for (int k = 1; k < q->m; ++k)
+    if ((s = launch_s2_series_term(p, prec, k, q->series_eps)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
+  if ((s = launch_project_delta(p, prec)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
+  if ((s = launch_update(p, prec, POVAR_SPHERE)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
+  if ((s = launch_s2_trial(p, prec, q->m)) != POVAR_OK) return s;
+  if ((s = mark(p, mk)) != POVAR_OK) return s;
+  if ((s = launch_controller(p, prec)) != POVAR_OK) return s;
+  p->last_precision = prec;
+  return mark(p, mk);
+}
+
+povar_status s2_solve_loop(Problem* p, const povar_params* q, int max_iters) {
+  povar_status s;
+  const int check_every = 4;
+  for (int it = 0; it < max_iters; ++it) {
+    if ((s = enqueue_s2_step(p, q)) != POVAR_OK) return s;
+    if ((it + 1) % check_every == 0 && it + 1 < max_iters) {
+      if ((s = sync_state(p)) != POVAR_OK) return s;
+      if (p->h_state->converged) break;
+    }
+  }
+  return sync_state(p);
 }
 
 }  // namespace
@@ -802,6 +887,147 @@ povar_status povar_get_points(povar_problem* pp, double* X_out) {
   povar_status s = povar::launch_gather_points(p, d);
   if (s != POVAR_OK) return s;
   POVAR_CUDA(cudaMemcpyAsync(X_out, d, (size_t)p->np * 3 * sizeof(double),
+                             cudaMemcpyDeviceToHost, p->stream));
+  POVAR_CUDA(cudaStreamSynchronize(p->stream));
+  return POVAR_OK;
+}
+
+povar_status povar_s2_set(povar_problem* pp, const double* P, const double* X) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  if (P && !X) return povar::fail(p, POVAR_EINVAL, "X is NULL while P is given");
+  if (P)
+    for (int64_t e = 0; e < (int64_t)p->nc * 12; ++e)
+      if (!std::isfinite(P[e])) return povar::fail(p, POVAR_EINVAL, "non-finite camera");
+  if (X)
+    for (int64_t e = 0; e < (int64_t)p->np * 4; ++e)
+      if (!std::isfinite(X[e])) return povar::fail(p, POVAR_EINVAL, "non-finite landmark");
+  povar_status s;
+  if ((s = povar::ensure_stage2(p)) != POVAR_OK) return s;
+  if (!X) {
+    // from the first stage: its landmarks at the current cameras, in FP64
+    if (p->eta_cur < 0.0)
+      return povar::fail(p, POVAR_EINVAL, "no first-stage landmarks to start from");
+    if (p->lm_df && (s = povar::refresh_landmarks(p, p->eta_cur)) != POVAR_OK) return s;
+    if ((s = povar::launch_init_state(p, 1e-4, 1, 0)) != POVAR_OK) return s;
+  } else {
+    if ((s = povar::launch_init_state(p, 1e-4, 1, 1)) != POVAR_OK) return s;
+  }
+  const double* d_X = nullptr;
+  if (P)
+    POVAR_CUDA(cudaMemcpyAsync(p->P64[0], P, (size_t)p->nc * 12 * sizeof(double),
+                               cudaMemcpyHostToDevice, p->stream));
+  if (X) {
+    // staged in the series record buffer (free between steps)
+    double* d = reinterpret_cast<double*>(p->rec64);
+    POVAR_CUDA(cudaMemcpyAsync(d, X, (size_t)p->np * 4 * sizeof(double), cudaMemcpyHostToDevice,
+                               p->stream));
+    d_X = d;
+  }
+  if ((s = povar::launch_s2_set(p, nullptr, d_X)) != POVAR_OK) return s;
+  if ((s = povar::launch_s2_cost(p)) != POVAR_OK) return s;
+  p->s2_live = true;
+  p->s2_current = true;
+  p->fresh = true;
+  p->eta_cur = -1.0;
+  p->lm_df = false;
+  p->lm_poba = false;
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  if (p->h_state->error) return povar::fail(p, (povar_status)p->h_state->error, "non-finite cost");
+  return POVAR_OK;
+}
+
+povar_status povar_s2_cost(povar_problem* pp, double* cost_out) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  if (!cost_out) return povar::fail(p, POVAR_EINVAL, "cost_out is NULL");
+  if (!p->s2_live) return povar::fail(p, POVAR_EINVAL, "call povar_s2_set first");
+  povar_status s;
+  if (!p->s2_current) {
+    if ((s = povar::launch_s2_cost(p)) != POVAR_OK) return s;
+    p->s2_current = true;
+    p->fresh = true;
+    p->eta_cur = -1.0;
+  }
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  *cost_out = p->h_state->F;
+  return POVAR_OK;
+}
+
+povar_status povar_s2_step(povar_problem* pp, const povar_params* params,
+                           povar_step_report* report) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  povar_status s;
+  if ((s = povar::check_s2_params(p, params)) != POVAR_OK) return s;
+  if ((s = povar::launch_begin(p, 0.0, 0.0, 0)) != POVAR_OK) return s;
+  POVAR_CUDA(cudaEventRecord(p->ev0, p->stream));
+  if ((s = povar::enqueue_s2_step(p, params)) != POVAR_OK) return s;
+  POVAR_CUDA(cudaEventRecord(p->ev1, p->stream));
+  POVAR_CUDA(cudaMemcpyAsync(p->h_report, p->d_report, sizeof(povar_step_report),
+                             cudaMemcpyDeviceToHost, p->stream));
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+  if (report) povar::fill_report(p, report, ms);
+  if (p->h_state->error)
+    return povar::fail(p, (povar_status)p->h_state->error, "device reported a numerical error");
+  return POVAR_OK;
+}
+
+povar_status povar_s2_solve(povar_problem* pp, const povar_params* params, int32_t max_iters,
+                            double ftol, double target_cost, povar_step_report* last,
+                            int32_t* iters_out) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  povar_status s;
+  if ((s = povar::check_s2_params(p, params)) != POVAR_OK) return s;
+  if (max_iters < 1) return povar::fail(p, POVAR_EINVAL, "max_iters must be >= 1");
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  const int it0 = p->h_state->iteration;
+  povar_params q = *params;
+  const bool mixed = q.precision != POVAR_FP64;
+  if ((s = povar::launch_begin(p, ftol, target_cost, max_iters,
+                               mixed ? POVAR_FALLBACK_REJECTIONS : 0)) != POVAR_OK)
+    return s;
+  POVAR_CUDA(cudaEventRecord(p->ev0, p->stream));
+  int fallback_at = 0;
+  for (;;) {
+    const int budget = it0 + max_iters - p->h_state->iteration;
+    if ((s = povar::s2_solve_loop(p, &q, budget)) != POVAR_OK) return s;
+    if (!p->h_state->fallback || q.precision == POVAR_FP64) break;
+    fallback_at = p->h_state->iteration;
+    q.precision = POVAR_FP64;
+    if (it0 + max_iters - fallback_at <= 0) break;
+    if ((s = povar::launch_begin(p, ftol, target_cost, it0 + max_iters - fallback_at, 0)) !=
+        POVAR_OK)
+      return s;
+  }
+  POVAR_CUDA(cudaEventRecord(p->ev1, p->stream));
+  POVAR_CUDA(cudaMemcpyAsync(p->h_report, p->d_report, sizeof(povar_step_report),
+                             cudaMemcpyDeviceToHost, p->stream));
+  if ((s = povar::sync_state(p)) != POVAR_OK) return s;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+  if (last) {
+    povar::fill_report(p, last, ms);
+    last->fp64_fallback_at = fallback_at > 0 ? fallback_at - it0 : 0;
+  }
+  if (iters_out) *iters_out = p->h_state->iteration - it0;
+  if (p->h_state->error)
+    return povar::fail(p, (povar_status)p->h_state->error, "device reported an error");
+  return POVAR_OK;
+}
+
+povar_status povar_s2_get_points(povar_problem* pp, double* X_out) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  if (!X_out) return povar::fail(p, POVAR_EINVAL, "X_out is NULL");
+  if (!p->s2_live) return povar::fail(p, POVAR_EINVAL, "call povar_s2_set first");
+  double* d = reinterpret_cast<double*>(p->rec64);
+  povar_status s;
+  if ((s = povar::launch_s2_gather_points(p, d)) != POVAR_OK) return s;
+  POVAR_CUDA(cudaMemcpyAsync(X_out, d, (size_t)p->np * 4 * sizeof(double),
                              cudaMemcpyDeviceToHost, p->stream));
   POVAR_CUDA(cudaStreamSynchronize(p->stream));
   return POVAR_OK;

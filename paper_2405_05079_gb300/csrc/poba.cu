@@ -211,7 +211,7 @@ k_poba_trial(DeviceState* __restrict__ st, double eta, const uint32_t* __restric
 
 // pred = F - sum of the model partials, one block, fixed order.
 __global__ void __launch_bounds__(256)
-k_poba_pred_finish(DeviceState* __restrict__ st, const double* __restrict__ part, int n) {
+k_poba_pred_finish(DeviceState* __restrict__ st, const double* __restrict__ part, int n, int m) {
   if (st->converged) return;
   __shared__ double red[256];
   double c = 0.0;
@@ -222,10 +222,19 @@ k_poba_pred_finish(DeviceState* __restrict__ st, const double* __restrict__ part
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) st->pred = st->F - red[0];
+  if (threadIdx.x == 0) {
+    st->pred = st->F - red[0];
+    if (!st->stop_series) st->terms_used = m;   // the series ran all m terms
+  }
 }
 
 }  // namespace
+
+povar_status launch_model_pred_finish(Problem* p, int m) {
+  k_poba_pred_finish<<<1, 256, 0, p->stream>>>(p->state, p->pred_part, p->np_pad / 32, m);
+  ++p->launches;
+  return check_launch(p, "model_pred_finish");
+}
 
 povar_status ensure_poba(Problem* p) {
   if (p->sbl64) return POVAR_OK;
@@ -249,7 +258,7 @@ povar_status launch_poba_prep(Problem* p, double eta, double lambda_l) {
   return check_launch(p, "poba_prep");
 }
 
-povar_status launch_poba_trial(Problem* p, int precision, double eta) {
+povar_status launch_poba_trial(Problem* p, int precision, double eta, int m) {
   if (precision == POVAR_FP64)
     k_poba_trial<double><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
         p->state, eta, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1],
@@ -264,7 +273,7 @@ povar_status launch_poba_trial(Problem* p, int precision, double eta) {
   povar_status s;
   if ((s = check_launch(p, "poba_trial")) != POVAR_OK) return s;
   if ((s = launch_cost_finish(p, 1)) != POVAR_OK) return s;
-  k_poba_pred_finish<<<1, 256, 0, p->stream>>>(p->state, p->pred_part, p->np_pad / 32);
+  k_poba_pred_finish<<<1, 256, 0, p->stream>>>(p->state, p->pred_part, p->np_pad / 32, m);
   ++p->launches;
   return check_launch(p, "poba_pred_finish");
 }

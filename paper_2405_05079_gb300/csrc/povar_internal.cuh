@@ -230,6 +230,20 @@ struct Problem {
   double* sbl64 = nullptr;              // [np_pad*3]
   float4* sbl32 = nullptr;              // [np_pad] (s0 s1 s2 -)
   bool lm_poba = false;                 // landmarks are PoBA iterates, not X*(P)
+  // second stage (allocated at first use): homogeneous landmarks per slot
+  double* s2X[2] = {nullptr, nullptr};  // [np_pad*4] unit 4-vectors, double-buffered
+  float4* s2Xf = nullptr;               // [np_pad] FP32 copy of the current ones
+  double* s2Gl64 = nullptr;             // [np_pad*10] projected damped inverse of V
+  float4* s2Gl32 = nullptr;             // [np_pad*3] its FP32 copy (10 of 12 floats)
+  double* s2bl = nullptr;               // [np_pad*4] b_l
+  double* s2s = nullptr;                // [np_pad*4] s = G_l b_l
+  double* s2rec = nullptr;              // [np_pad*4] series record s_j (float or double)
+  double* s2lin = nullptr;              // [nchunks*72] chunk sums of U and the RHS
+  double* s2part = nullptr;             // [nchunks*12] series chunk partials (float or double)
+  uint32_t* s2off = nullptr;            // [nc+1] first chunk of each camera
+  uint32_t* s2idx = nullptr;            // [nchunks] chunk indices 0..nchunks-1
+  bool s2_live = false;                 // second-stage landmarks were set
+  bool s2_current = false;              // the device state's cost is the second stage's
   // conjugate-gradient solver (allocated at first use)
   double* pcg_vec = nullptr;            // [4*nc*12] r, z, p, q (float or double)
   double* pcg_M64 = nullptr;            // [nc*144] inverse Schur-Jacobi blocks
@@ -320,7 +334,7 @@ povar_status launch_ltab(Problem* p, int which_rel, double eta);
 povar_status launch_project_delta(Problem* p, int precision);
 povar_status ensure_poba(Problem* p);
 povar_status launch_poba_prep(Problem* p, double eta, double lambda_l);
-povar_status launch_poba_trial(Problem* p, int precision, double eta);
+povar_status launch_poba_trial(Problem* p, int precision, double eta, int m);
 povar_status launch_camera_prepare(Problem* p, int precision, int manifold,
                                    double eta, bool poba = false);
 
@@ -333,6 +347,25 @@ povar_status launch_pred(Problem* p, int precision, double eta, int manifold, in
 // z = W V^-1 W^T vec as run partials (part_run, schedule 1's fused pass) for
 // a camera vector vec of the precision's type.
 povar_status launch_wvw(Problem* p, int precision, double eta, const void* vec);
+
+// ---------------------------------------------------- stage2.cu
+// Second stage (projective refinement by Riemannian PoBA). P / X are device
+// arrays (n_cams*12 / n_points*4 by landmark id) or null (keep the current
+// cameras; landmarks (X, 1) from the first stage's FP64 landmarks).
+povar_status ensure_stage2(Problem* p);
+povar_status launch_s2_set(Problem* p, const double* d_P, const double* d_X);
+povar_status launch_s2_cost(Problem* p);
+povar_status launch_s2_prep(Problem* p, double lambda_l);
+povar_status launch_s2_linearize(Problem* p);
+povar_status launch_s2_camera_prepare(Problem* p, int precision);
+povar_status launch_s2_series_term(Problem* p, int precision, int term, double eps);
+povar_status launch_s2_trial(Problem* p, int precision, int m);
+povar_status launch_s2_gather_points(Problem* p, double* d_out);
+// the first stage's per-camera series finish over given partial lists
+povar_status launch_series_apply(Problem* p, int precision, int term, double eps,
+                                 const uint32_t* off, const uint32_t* idx, const void* part);
+// pred = F - sum of the model partials in pred_part (PoBA, second stage)
+povar_status launch_model_pred_finish(Problem* p, int m);
 
 // ---------------------------------------------------- pcg.cu
 // Conjugate-gradient solve of the reduced camera system into the step buffer

@@ -2238,6 +2238,21 @@ povar_status launch_pred(Problem* p, int precision, double eta, int manifold, in
   return check_launch(p, "pred");
 }
 
+povar_status launch_series_apply(Problem* p, int precision, int term, double eps,
+                                 const uint32_t* off, const uint32_t* idx, const void* part) {
+  const size_t yoff_out = (term & 1) * (size_t)p->nc * 12;
+  if (precision == POVAR_FP64)
+    k_series_apply<double><<<p->nc, 128, 0, p->stream>>>(
+        p->state, term, eps, p->nc, off, idx, static_cast<const double*>(part), p->G64,
+        p->camnorm, p->done_ticket, p->Y64 + yoff_out, p->D64);
+  else
+    k_series_apply<float><<<p->nc, 128, 0, p->stream>>>(
+        p->state, term, eps, p->nc, off, idx, static_cast<const float*>(part), p->G32,
+        p->camnorm, p->done_ticket, p->Y32 + yoff_out, p->D32);
+  ++p->launches;
+  return check_launch(p, "series_apply");
+}
+
 povar_status launch_wvw(Problem* p, int precision, double eta, const void* vec) {
   const double a64 = 1.0 - eta;
   if (precision == POVAR_FP64) {

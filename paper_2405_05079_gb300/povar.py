@@ -77,6 +77,12 @@ def lib() -> C.CDLL:
     L.povar_step.argtypes = [vp, C.POINTER(Params), C.POINTER(StepReport)]
     L.povar_solve.argtypes = [vp, C.POINTER(Params), i32, C.c_double, C.c_double,
                               C.POINTER(StepReport), C.POINTER(C.c_int32)]
+    L.povar_s2_set.argtypes = [vp, dp, dp]
+    L.povar_s2_cost.argtypes = [vp, dp]
+    L.povar_s2_step.argtypes = [vp, C.POINTER(Params), C.POINTER(StepReport)]
+    L.povar_s2_solve.argtypes = [vp, C.POINTER(Params), i32, C.c_double, C.c_double,
+                                 C.POINTER(StepReport), C.POINTER(C.c_int32)]
+    L.povar_s2_get_points.argtypes = [vp, dp]
     u32p = C.POINTER(C.c_uint32)
     L.povar_get_orders.argtypes = [vp, u32p, u32p, u32p, u32p]
     L.povar_get_layout.argtypes = [vp, C.POINTER(C.c_int64), u32p, u32p,
@@ -154,6 +160,14 @@ def make_params(eta=0.1, lambda0=1e-4, m=10, series_eps=0.0, manifold=SPHERE,
     return Params(eta=eta, lambda0=lambda0, series_eps=series_eps, lambda_l=lambda_l, m=m,
                   manifold=manifold, precision=precision, schedule=schedule, solver=solver,
                   reserved=0)
+
+
+def make_s2_params(lambda0=1e-4, m=21, series_eps=0.01, lambda_l=1.0,
+                   precision=MIXED_FP32) -> Params:
+    """Parameters of the second stage (povar_s2_*): Riemannian PoBA on the
+    unit spheres, landmark damping lambda_l * lambda."""
+    return Params(eta=0.0, lambda0=lambda0, series_eps=series_eps, lambda_l=lambda_l, m=m,
+                  manifold=SPHERE, precision=precision, schedule=-1, solver=0, reserved=0)
 
 
 def current_stream_handle() -> int | None:
@@ -271,6 +285,43 @@ class Problem:
         if not (allow_stall and st == 6):
             self._check(st)
         return rep, it.value
+
+    # ---- second stage: projective refinement by Riemannian PoBA
+    def s2_set(self, P=None, X=None):
+        """povar_s2_set: homogeneous cameras P [n_cams, 12] and landmarks
+        X [n_points, 4] (normalized by the library), or neither (start from
+        the first stage's result)."""
+        if P is None and X is None:
+            self._check(lib().povar_s2_set(self._h, None, None))
+            return
+        Pa = np.ascontiguousarray(np.asarray(P, dtype=np.float64).reshape(self.n_cams, 12))
+        Xa = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(self.n_points, 4))
+        self._check(lib().povar_s2_set(self._h, _ptr(Pa, C.c_double), _ptr(Xa, C.c_double)))
+
+    def s2_cost(self) -> float:
+        out = C.c_double()
+        self._check(lib().povar_s2_cost(self._h, C.byref(out)))
+        return out.value
+
+    def s2_step(self, params: Params) -> StepReport:
+        rep = StepReport()
+        self._check(lib().povar_s2_step(self._h, C.byref(params), C.byref(rep)))
+        return rep
+
+    def s2_solve(self, params: Params, max_iters=50, ftol=1e-6, target_cost=0.0,
+                 allow_stall=False):
+        rep = StepReport()
+        it = C.c_int32()
+        st = lib().povar_s2_solve(self._h, C.byref(params), max_iters, ftol, target_cost,
+                                  C.byref(rep), C.byref(it))
+        if not (allow_stall and st == 6):
+            self._check(st)
+        return rep, it.value
+
+    def s2_points(self):
+        out = np.empty((self.n_points, 4))
+        self._check(lib().povar_s2_get_points(self._h, _ptr(out, C.c_double)))
+        return out
 
     def orders(self):
         no, np_, nc = self.n_obs, self.n_points, self.n_cams
