@@ -236,10 +236,14 @@ povar_status povar_get_points(povar_problem* p, double* X_out);
  * report, stop rules and mixed-precision safeguard) for the second stage.
  * params: m, series_eps, lambda0 as for the first stage; lambda_l > 0
  * (1 = the paper's joint damping); manifold must be POVAR_SPHERE;
- * precision POVAR_FP64 or POVAR_MIXED_FP32 (FP32 series terms and camera
- * vectors; landmark blocks, linearization, back-substitution and cost in
- * FP64); solver POVAR_SOLVER_SERIES; eta and schedule are not used. Steps
- * are issued without a CUDA graph.
+ * precision POVAR_FP64 or POVAR_MIXED_FP32 (FP32 series terms, camera
+ * vectors, sums of the camera linearization and the linearized terms of the
+ * trial (W^T dP, J dP + J dX); landmark blocks and their inverses,
+ * projections, residuals, back-substitution and cost in FP64); solver POVAR_SOLVER_SERIES; schedule 0 = a landmark-major pass
+ * (s_j per landmark) and a camera-major pass over the observation chunks,
+ * 1 or -1 = one landmark-major pass whose camera contributions are summed
+ * over the runs of equal camera in each slice row (the first stage's
+ * schedule 1); eta is not used. Steps are issued without a CUDA graph.
  * povar_s2_get_points: the current homogeneous landmarks (n_points*4, by
  * landmark id); the cameras come from povar_get_cameras.
  * A first-stage call after second-stage steps re-solves the first stage's

@@ -559,6 +559,8 @@ povar_status check_s2_params(Problem* p, const povar_params* q) {
     return fail(p, POVAR_EINVAL, "the second stage runs in POVAR_FP64 or POVAR_MIXED_FP32");
   if (q->solver != POVAR_SOLVER_SERIES)
     return fail(p, POVAR_EINVAL, "the second stage runs the series solver");
+  if (q->schedule < -1 || q->schedule > 1)
+    return fail(p, POVAR_EINVAL, "second-stage series schedules are -1, 0 and 1");
   if (q->reserved != 0) return fail(p, POVAR_EINVAL, "params->reserved must be 0");
   if (!p->s2_live) return fail(p, POVAR_EINVAL, "call povar_s2_set first");
   return POVAR_OK;
@@ -594,12 +596,14 @@ povar_status enqueue_s2_step(Problem* p, const povar_params* q) {
   if ((s = prepare_s2_step(p, q)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_s2_prep(p, q->lambda_l)) != POVAR_OK) return s;
-  if ((s = launch_s2_linearize(p)) != POVAR_OK) return s;
+  if ((s = launch_s2_linearize(p, prec)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_s2_camera_prepare(p, prec)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   for (int k = 1; k < q->m; ++k)
-    if ((s = launch_s2_series_term(p, prec, k, q->series_eps)) != POVAR_OK) return s;
+    if ((s = q->schedule == 0 ? launch_s2_series_term(p, prec, k, q->series_eps)
+                              : launch_s2_fused_term(p, prec, k, q->series_eps)) != POVAR_OK)
+      return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if ((s = launch_project_delta(p, prec)) != POVAR_OK) return s;
   if ((s = mark(p, mk)) != POVAR_OK) return s;

@@ -356,9 +356,11 @@ povar_status ensure_stage2(Problem* p);
 povar_status launch_s2_set(Problem* p, const double* d_P, const double* d_X);
 povar_status launch_s2_cost(Problem* p);
 povar_status launch_s2_prep(Problem* p, double lambda_l);
-povar_status launch_s2_linearize(Problem* p);
+povar_status launch_s2_linearize(Problem* p, int precision);
 povar_status launch_s2_camera_prepare(Problem* p, int precision);
 povar_status launch_s2_series_term(Problem* p, int precision, int term, double eps);
+// the same product in one landmark-major pass with the run tables (series.cu)
+povar_status launch_s2_fused_term(Problem* p, int precision, int term, double eps);
 povar_status launch_s2_trial(Problem* p, int precision, int m);
 povar_status launch_s2_gather_points(Problem* p, double* d_out);
 // the first stage's per-camera series finish over given partial lists

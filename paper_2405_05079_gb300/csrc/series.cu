@@ -16,6 +16,7 @@
 //       = -2 b_p^T d - d^T U d + sum_j ||F_j W^T d||^2   (d tangent, b_l = 0)
 //     with one more gather pass at d and FP64 reductions.
 #include "povar_internal.cuh"
+#include "reproj.cuh"
 
 #include <cuda_bf16.h>
 
@@ -926,6 +927,89 @@ k_series_fused(const DeviceState* __restrict__ st, T a,
       store_runs<T>(v, mask, i >= 0, pbase, lane, part);
     }
     }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Second stage (projective reprojection error): one series product
+// W~ V~^-1 W~^T y in one landmark-major pass over the SELL slices, with the
+// first stage's run tables. Pass 1: lane = landmark j of the warp's slice,
+// t_j = sum_k P_i^T E_k (Y_i X_j) over its observations, s_j = G_l,j t_j
+// (G_l the projected damped inverse of V_j). Pass 2: every slice row's
+// contributions vec((E_k P_i s_j) X_j^T) are summed over the lanes that see
+// the same camera (one warp reduction for a warp-uniform row, a segmented
+// sum over the runs otherwise) into the row's run partials, which
+// k_series_apply adds per camera.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(BLOCK)
+k_s2_fused(const DeviceState* __restrict__ st, const uint32_t* __restrict__ slot_len,
+           const uint32_t* __restrict__ sell_off, const int32_t* __restrict__ sell_cam,
+           const T* __restrict__ camPa, const T* __restrict__ camPb, const T* __restrict__ vec,
+           rp::S2Land<T> land, const uint32_t* __restrict__ row_mask,
+           const uint32_t* __restrict__ row_base, T* __restrict__ part) {
+  if (st->converged || st->stop_series) return;
+  const int lane = threadIdx.x & 31;
+  const int s = blockIdx.x * BLOCK + threadIdx.x;
+  const int cur = st->cur;
+  const T* __restrict__ camP = cur ? camPb : camPa;
+  const uint32_t sbeg = sell_off[s / SLICE];
+  const uint32_t width = (sell_off[s / SLICE + 1] - sbeg) / SLICE;
+  const uint32_t len = slot_len[s];
+  const uint32_t base = sbeg + (uint32_t)lane;
+  T X[4], g[10];
+  land.load(cur, s, X, g);
+  T acc[4] = {0, 0, 0, 0};
+  for (uint32_t k = 0; k < len; ++k) {
+    const int i = ld_stream(sell_cam + base + k * SLICE);
+    T P[12], Y[12];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      load_row<T>(camP, i, r, P + 4 * r);
+      load_row<T>(vec, i, r, Y + 4 * r);
+    }
+    const rp::Proj<T> q = rp::project(P, X);
+    T w[3], ew[3], pt[4];
+    rp::apply_p(Y, X, w);
+    rp::apply_e(q, w, ew);
+    rp::apply_pt(P, ew, pt);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[e] += pt[e];
+  }
+  T sv[4];
+  rp::sym4_mul(g, acc, sv);
+  const uint32_t row0 = sbeg / SLICE;
+  for (uint32_t k = 0; k < width; ++k) {
+    const bool in = k < len;
+    const int i = in ? ld_stream(sell_cam + base + k * SLICE) : -1;
+    const uint32_t mask = __ldg(row_mask + row0 + k), pbase = __ldg(row_base + row0 + k);
+    T v[12];
+#pragma unroll
+    for (int e = 0; e < 12; ++e) v[e] = 0;
+    if (in) {
+      T P[12];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) load_row<T>(camP, i, r, P + 4 * r);
+      const rp::Proj<T> q = rp::project(P, X);
+      T u[3], eu[3];
+      rp::apply_p(P, sv, u);
+      rp::apply_e(q, u, eu);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) v[4 * r + d] = eu[r] * X[d];
+    }
+    if (mask == 0u) {
+      T r3[3];
+      int vb;
+      warp_reduce12<T>(v, lane, r3, vb);
+      if ((lane & 7) == 0) {
+        T* out = part + (size_t)pbase * 12 + vb;
+        out[0] = r3[0]; out[1] = r3[1]; out[2] = r3[2];
+      }
+    } else {
+      store_runs<T>(v, mask, in, pbase, lane, part);
     }
   }
 }
@@ -2251,6 +2335,26 @@ povar_status launch_series_apply(Problem* p, int precision, int term, double eps
         p->camnorm, p->done_ticket, p->Y32 + yoff_out, p->D32);
   ++p->launches;
   return check_launch(p, "series_apply");
+}
+
+povar_status launch_s2_fused_term(Problem* p, int precision, int term, double eps) {
+  const size_t yoff_in = ((term - 1) & 1) * (size_t)p->nc * 12;
+  if (precision == POVAR_FP64) {
+    rp::S2Land<double> land{p->s2X[0], p->s2X[1], p->s2Gl64};
+    k_s2_fused<double><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+        p->state, p->slot_len, p->sell_off, p->sell_cam, p->P64[0], p->P64[1],
+        p->Y64 + yoff_in, land, p->row_mask, p->row_base, static_cast<double*>(p->part_run));
+  } else {
+    rp::S2Land<float> land{p->s2Xf, p->s2Gl32};
+    k_s2_fused<float><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+        p->state, p->slot_len, p->sell_off, p->sell_cam, p->camP32[0], p->camP32[1],
+        p->Y32 + yoff_in, land, p->row_mask, p->row_base, static_cast<float*>(p->part_run));
+  }
+  ++p->launches;
+  povar_status s;
+  if ((s = check_launch(p, "s2_fused")) != POVAR_OK) return s;
+  return launch_series_apply(p, precision, term, eps, p->cam_part_off, p->cam_part_idx,
+                             p->part_run);
 }
 
 povar_status launch_wvw(Problem* p, int precision, double eta, const void* vec) {

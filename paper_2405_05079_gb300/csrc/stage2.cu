@@ -14,9 +14,10 @@
 //   k_s2_prep        per landmark slot (FP64): V = sum (D P)^T (D P),
 //                    b_l = sum (D P)^T r, the projected damped inverse G_l
 //                    (mu = lambda_l lambda), s = G_l b_l; cost partials;
-//   k_s2_linearize   camera-major chunks (FP64): the 60 moments E (x) XX^T of
-//                    U and the reduced right-hand side
-//                    J_p^T (r - J_l s) = b_p - W G_l b_l;
+//   k_s2_linearize   camera-major chunks: the 60 moments E (x) XX^T of U and
+//                    the reduced right-hand side J_p^T (r - J_l s) =
+//                    b_p - W G_l b_l (projection and residual in FP64, sums
+//                    in FP64, or FP32 in mixed precision);
 //   k_s2_camera_prepare  per camera: damped projected 12x12 inverse G, the
 //                    first series term x0 = -G (b_p - W s), FP32 copies;
 //   per series term: k_s2_gather (per slot: s = G_l sum P^T E (Y X)) and
@@ -24,7 +25,9 @@
 //                    first stage's per-camera apply (x = G z, delta += x);
 //   k_s2_trial       per slot: back-substitution dX = -G_l (b_l + W^T dP),
 //                    retraction X' = (X + dX) / |X + dX|, the trial cost at
-//                    (P', X') and the Gauss-Newton model ||r + J dP + J dX||^2.
+//                    (P', X') and the Gauss-Newton model ||r + J dP + J dX||^2
+//                    (projections, residuals and cost in FP64; W^T dP and the
+//                    linearized model terms in FP32 in mixed precision).
 // The per-camera update / retraction and the controller are the first
 // stage's. Sums run in a fixed order (per thread, then fixed shuffles), so
 // results do not depend on scheduling.
@@ -33,85 +36,15 @@
 
 #include "block12.cuh"
 #include "povar_internal.cuh"
+#include "reproj.cuh"
 
 namespace povar {
 namespace {
 
 using namespace b12;
+using namespace rp;
 
 constexpr int S2_LIN = 72;   // 60 moments of U + 12 right-hand-side entries
-
-// y, iz, pi0, pi1 of one observation
-template <typename T>
-struct Proj {
-  T y[3];
-  T iz, p0, p1;
-};
-
-template <typename T>
-__device__ __forceinline__ Proj<T> project(const T P[12], const T X[4]) {
-  Proj<T> o;
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-    o.y[r] = P[4 * r] * X[0] + P[4 * r + 1] * X[1] + P[4 * r + 2] * X[2] + P[4 * r + 3] * X[3];
-  o.iz = (T)1 / o.y[2];
-  o.p0 = o.y[0] * o.iz;
-  o.p1 = o.y[1] * o.iz;
-  return o;
-}
-
-// D w (2-vector)
-template <typename T>
-__device__ __forceinline__ void apply_d(const Proj<T>& q, const T w[3], T out[2]) {
-  out[0] = q.iz * (w[0] - q.p0 * w[2]);
-  out[1] = q.iz * (w[1] - q.p1 * w[2]);
-}
-
-// D^T a (3-vector)
-template <typename T>
-__device__ __forceinline__ void apply_dt(const Proj<T>& q, const T a[2], T out[3]) {
-  out[0] = q.iz * a[0];
-  out[1] = q.iz * a[1];
-  out[2] = -q.iz * (q.p0 * a[0] + q.p1 * a[1]);
-}
-
-// E w = D^T D w
-template <typename T>
-__device__ __forceinline__ void apply_e(const Proj<T>& q, const T w[3], T out[3]) {
-  T d[2];
-  apply_d(q, w, d);
-  apply_dt(q, d, out);
-}
-
-// P^T t (4-vector) for the row-major 3x4 P
-template <typename T>
-__device__ __forceinline__ void apply_pt(const T P[12], const T t[3], T out[4]) {
-#pragma unroll
-  for (int c = 0; c < 4; ++c) out[c] = P[c] * t[0] + P[4 + c] * t[1] + P[8 + c] * t[2];
-}
-
-// P x (3-vector)
-template <typename T>
-__device__ __forceinline__ void apply_p(const T P[12], const T x[4], T out[3]) {
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-    out[r] = P[4 * r] * x[0] + P[4 * r + 1] * x[1] + P[4 * r + 2] * x[2] + P[4 * r + 3] * x[3];
-}
-
-// symmetric 4x4 in 10 entries: 00 01 02 03 11 12 13 22 23 33 (sd_t10 order)
-template <typename T>
-__device__ __forceinline__ void sym4_mul(const T g[10], const T x[4], T out[4]) {
-  out[0] = g[0] * x[0] + g[1] * x[1] + g[2] * x[2] + g[3] * x[3];
-  out[1] = g[1] * x[0] + g[4] * x[1] + g[5] * x[2] + g[6] * x[3];
-  out[2] = g[2] * x[0] + g[5] * x[1] + g[7] * x[2] + g[8] * x[3];
-  out[3] = g[3] * x[0] + g[6] * x[1] + g[8] * x[2] + g[9] * x[3];
-}
-
-template <typename T>
-__device__ __forceinline__ void load12(const T* __restrict__ src, T out[12]) {
-#pragma unroll
-  for (int e = 0; e < 12; ++e) out[e] = src[e];
-}
 
 __device__ __forceinline__ double warp_total(double v) {
 #pragma unroll
@@ -312,8 +245,19 @@ k_s2_prep(DeviceState* __restrict__ st, double lambda_l, const uint32_t* __restr
         bl[a] += g0[a] * r0 + g1[a] * r1;
       }
     }
-    const double mu = lambda_l * st->lam;
-    ok = projected_inverse4(V, X, mu, G);
+    // if rounding leaves the damped block indefinite (a landmark close to a
+    // camera's principal plane makes V huge), its damping is raised as for
+    // the camera blocks: to 1e-12 of the largest diagonal entry, then x100
+    // per attempt, at most 8 attempts, counted in the device state
+    const double vmax = fmax(fmax(V[0], V[4]), fmax(V[7], V[9]));
+    double mu = lambda_l * st->lam;
+    int attempt = 0;
+    for (; attempt < 8; ++attempt) {
+      if (attempt > 0) mu = fmax(mu * 100.0, 1e-12 * vmax);
+      ok = projected_inverse4(V, X, mu, G);
+      if (ok) break;
+    }
+    if (ok && attempt > 0) atomicAdd(&st->n_regularized, 1);
     sym4_mul(G, bl, sv);
   }
   if (!ok) st->error = POVAR_ENUMERIC;
@@ -336,7 +280,11 @@ k_s2_prep(DeviceState* __restrict__ st, double lambda_l, const uint32_t* __restr
 
 // One warp per camera-major chunk: 60 moments E_e X_c X_d (e over the six
 // entries of E, t10 order of the moments) and the right-hand side
-// J_p^T (r - J_l s) = vec((D^T (r - D P s)) X^T) (12), FP64.
+// J_p^T (r - J_l s) = vec((D^T (r - D P s)) X^T) (12). The projection and
+// the residual are FP64; the accumulation runs in TA (FP64, or FP32 in
+// mixed precision: each lane sums at most 16 observations of the chunk, the
+// chunk's lane sums are added by fixed shuffles, chunk totals in FP64).
+template <typename TA>
 __global__ void __launch_bounds__(256)
 k_s2_linearize(const DeviceState* __restrict__ st, int nchunks,
                const int32_t* __restrict__ chunk_cam, const uint32_t* __restrict__ chunk_beg,
@@ -351,45 +299,59 @@ k_s2_linearize(const DeviceState* __restrict__ st, int nchunks,
   const int cur = st->cur;
   double P[12];
   load12((cur ? P1 : P0) + 12 * (size_t)chunk_cam[c], P);
-  const double* Xb = cur ? X4_1 : X4_0;
-  double acc[S2_LIN];
+  TA Pa[12];
 #pragma unroll
-  for (int e = 0; e < S2_LIN; ++e) acc[e] = 0.0;
+  for (int e = 0; e < 12; ++e) Pa[e] = (TA)P[e];
+  const double* Xb = cur ? X4_1 : X4_0;
+  TA acc[S2_LIN];
+#pragma unroll
+  for (int e = 0; e < S2_LIN; ++e) acc[e] = 0;
   const uint32_t b = chunk_beg[c], e_ = chunk_beg[c + 1];
   for (uint32_t r = b + lane; r < e_; r += 32) {
     const uint32_t slot = cm_slot[r];
     const double2 m = cm_m[r];
     const double X[4] = {Xb[4 * (size_t)slot], Xb[4 * (size_t)slot + 1],
                          Xb[4 * (size_t)slot + 2], Xb[4 * (size_t)slot + 3]};
-    const double sv[4] = {s64[4 * (size_t)slot], s64[4 * (size_t)slot + 1],
-                          s64[4 * (size_t)slot + 2], s64[4 * (size_t)slot + 3]};
     const Proj<double> q = project(P, X);
-    const double iz2 = q.iz * q.iz;
-    const double E[6] = {iz2, 0.0, -q.p0 * iz2, iz2, -q.p1 * iz2,
-                         (q.p0 * q.p0 + q.p1 * q.p1) * iz2};
-    const double t10[10] = {X[0] * X[0], X[0] * X[1], X[0] * X[2], X[0] * X[3], X[1] * X[1],
-                            X[1] * X[2], X[1] * X[3], X[2] * X[2], X[2] * X[3], X[3] * X[3]};
+    const TA Xa[4] = {(TA)X[0], (TA)X[1], (TA)X[2], (TA)X[3]};
+    const TA sv[4] = {(TA)s64[4 * (size_t)slot], (TA)s64[4 * (size_t)slot + 1],
+                      (TA)s64[4 * (size_t)slot + 2], (TA)s64[4 * (size_t)slot + 3]};
+    Proj<TA> qa;
+    qa.y[0] = (TA)q.y[0];
+    qa.y[1] = (TA)q.y[1];
+    qa.y[2] = (TA)q.y[2];
+    qa.iz = (TA)q.iz;
+    qa.p0 = (TA)q.p0;
+    qa.p1 = (TA)q.p1;
+    const TA iz2 = qa.iz * qa.iz;
+    const TA E[6] = {iz2, (TA)0, -qa.p0 * iz2, iz2, -qa.p1 * iz2,
+                     (qa.p0 * qa.p0 + qa.p1 * qa.p1) * iz2};
+    const TA t10[10] = {Xa[0] * Xa[0], Xa[0] * Xa[1], Xa[0] * Xa[2], Xa[0] * Xa[3],
+                        Xa[1] * Xa[1], Xa[1] * Xa[2], Xa[1] * Xa[3], Xa[2] * Xa[2],
+                        Xa[2] * Xa[3], Xa[3] * Xa[3]};
 #pragma unroll
     for (int kk = 0; kk < 6; ++kk) {
       if (kk == 1) continue;   // E_01 = 0
 #pragma unroll
       for (int t = 0; t < 10; ++t) acc[10 * kk + t] += E[kk] * t10[t];
     }
-    double ps[3], dps[2], t[3];
-    apply_p(P, sv, ps);
-    apply_d(q, ps, dps);
-    const double a[2] = {q.p0 - m.x - dps[0], q.p1 - m.y - dps[1]};
-    apply_dt(q, a, t);
+    TA ps[3], dps[2], t[3];
+    apply_p(Pa, sv, ps);
+    apply_d(qa, ps, dps);
+    const TA a[2] = {(TA)(q.p0 - m.x) - dps[0], (TA)(q.p1 - m.y) - dps[1]};
+    apply_dt(qa, a, t);
 #pragma unroll
     for (int rr = 0; rr < 3; ++rr)
 #pragma unroll
-      for (int d = 0; d < 4; ++d) acc[60 + 4 * rr + d] += t[rr] * X[d];
+      for (int d = 0; d < 4; ++d) acc[60 + 4 * rr + d] += t[rr] * Xa[d];
   }
   double* out = part + (size_t)c * S2_LIN;
 #pragma unroll
   for (int e = 0; e < S2_LIN; ++e) {
-    const double v = warp_total(acc[e]);
-    if ((e & 31) == lane) out[e] = v;
+    TA v = acc[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((e & 31) == lane) out[e] = (double)v;
   }
 }
 
@@ -497,41 +459,6 @@ k_s2_camera_prepare(DeviceState* __restrict__ st, int nc, const int32_t* __restr
 // Series product W~ V~^-1 W~^T y
 // ---------------------------------------------------------------------------
 
-template <typename T> struct S2Land;
-template <> struct S2Land<double> {
-  const double* X0;
-  const double* X1;
-  const double* G;
-  __device__ void load(int cur, int s, double X[4], double g[10]) const {
-    const double* x = (cur ? X1 : X0) + 4 * (size_t)s;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) X[e] = x[e];
-#pragma unroll
-    for (int e = 0; e < 10; ++e) g[e] = G[10 * (size_t)s + e];
-  }
-  __device__ void load_x(int cur, int s, double X[4]) const {
-    const double* x = (cur ? X1 : X0) + 4 * (size_t)s;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) X[e] = x[e];
-  }
-};
-template <> struct S2Land<float> {
-  const float4* Xf;
-  const float4* G;
-  __device__ void load(int, int s, float X[4], float g[10]) const {
-    load_x(0, s, X);
-    const float4 a = __ldg(G + 3 * (size_t)s), b = __ldg(G + 3 * (size_t)s + 1),
-                 c = __ldg(G + 3 * (size_t)s + 2);
-    g[0] = a.x; g[1] = a.y; g[2] = a.z; g[3] = a.w;
-    g[4] = b.x; g[5] = b.y; g[6] = b.z; g[7] = b.w;
-    g[8] = c.x; g[9] = c.y;
-  }
-  __device__ void load_x(int, int s, float X[4]) const {
-    const float4 x = __ldg(Xf + s);
-    X[0] = x.x; X[1] = x.y; X[2] = x.z; X[3] = x.w;
-  }
-};
-
 // Per slot: s = G_l sum_k P_i^T E_k (Y_i X) (landmark-major pass).
 template <typename T>
 __global__ void __launch_bounds__(BLOCK)
@@ -614,7 +541,12 @@ k_s2_scatter(const DeviceState* __restrict__ st, int nchunks,
 // Back-substitution, retraction, trial cost and model decrease
 // ---------------------------------------------------------------------------
 
-template <typename TD>
+// TD: the type of the camera step; TA: the arithmetic of the linearized
+// parts (W^T dP for the back-substitution, J dP + J dX for the model): FP64,
+// or FP32 in mixed precision. The trial projections and residuals, the
+// residuals at the current point, the back-substitution with G_l and the
+// retraction are FP64 in both.
+template <typename TD, typename TA>
 __global__ void __launch_bounds__(BLOCK)
 k_s2_trial(const DeviceState* __restrict__ st, const uint32_t* __restrict__ slot_len,
            const uint32_t* __restrict__ sell_off, const int32_t* __restrict__ sell_cam,
@@ -631,32 +563,35 @@ k_s2_trial(const DeviceState* __restrict__ st, const uint32_t* __restrict__ slot
   const double* Xs = (cur ? X4_1 : X4_0) + 4 * (size_t)s;
   double* Xo = (cur ? X4_0 : X4_1) + 4 * (size_t)s;
   const double X[4] = {Xs[0], Xs[1], Xs[2], Xs[3]};
+  const TA Xa[4] = {(TA)X[0], (TA)X[1], (TA)X[2], (TA)X[3]};
   const uint32_t len = slot_len[s];
   double cost = 0.0, model = 0.0;
   double Xn[4] = {0, 0, 0, 0};
   if (len > 0) {
     // W^T dP = sum J_l^T J_p dP = sum P^T E (dP X)
-    double a[4] = {0, 0, 0, 0};
+    TA a[4] = {0, 0, 0, 0};
     for (uint32_t k = 0; k < len; ++k) {
       const int i = sell_cam[sell_pos(sell_off, s, k)];
-      double P[12], dP[12];
-      load12(Pc + 12 * (size_t)i, P);
+      TA P[12], dP[12];
 #pragma unroll
-      for (int e = 0; e < 12; ++e) dP[e] = (double)Dp[12 * (size_t)i + e];
-      const Proj<double> q = project(P, X);
-      double w[3], ew[3], pt[4];
-      apply_p(dP, X, w);
+      for (int e = 0; e < 12; ++e) {
+        P[e] = (TA)Pc[12 * (size_t)i + e];
+        dP[e] = (TA)Dp[12 * (size_t)i + e];
+      }
+      const Proj<TA> q = project(P, Xa);
+      TA w[3], ew[3], pt[4];
+      apply_p(dP, Xa, w);
       apply_e(q, w, ew);
       apply_pt(P, ew, pt);
 #pragma unroll
       for (int e = 0; e < 4; ++e) a[e] += pt[e];
     }
-    double g[10], dx[4];
+    double g[10], dx[4], ad[4];
 #pragma unroll
     for (int e = 0; e < 10; ++e) g[e] = Gl64[10 * (size_t)s + e];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) a[e] += bl64[4 * (size_t)s + e];
-    sym4_mul(g, a, dx);
+    for (int e = 0; e < 4; ++e) ad[e] = (double)a[e] + bl64[4 * (size_t)s + e];
+    sym4_mul(g, ad, dx);
     double nn = 0.0;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -667,28 +602,40 @@ k_s2_trial(const DeviceState* __restrict__ st, const uint32_t* __restrict__ slot
     const double f = 1.0 / sqrt(nn);
 #pragma unroll
     for (int e = 0; e < 4; ++e) Xn[e] *= f;
+    const TA dxa[4] = {(TA)dx[0], (TA)dx[1], (TA)dx[2], (TA)dx[3]};
     for (uint32_t k = 0; k < len; ++k) {
       const uint32_t pos = sell_pos(sell_off, s, k);
       const int i = sell_cam[pos];
       const double2 m = sell_m[pos];
-      double P[12], dP[12], Pt[12];
+      double P[12], Pt[12];
       load12(Pc + 12 * (size_t)i, P);
       load12(Pn + 12 * (size_t)i, Pt);
-#pragma unroll
-      for (int e = 0; e < 12; ++e) dP[e] = (double)Dp[12 * (size_t)i + e];
       // trial cost
       const Proj<double> qt = project(Pt, Xn);
       const double t0 = qt.p0 - m.x, t1 = qt.p1 - m.y;
       cost += t0 * t0 + t1 * t1;
       // model: r + D (dP X + P dX) at the current point
       const Proj<double> q = project(P, X);
-      double w[3], pdx[3], dl[2];
-      apply_p(dP, X, w);
-      apply_p(P, dx, pdx);
+      Proj<TA> qa;
+      qa.y[0] = (TA)q.y[0];
+      qa.y[1] = (TA)q.y[1];
+      qa.y[2] = (TA)q.y[2];
+      qa.iz = (TA)q.iz;
+      qa.p0 = (TA)q.p0;
+      qa.p1 = (TA)q.p1;
+      TA Pa[12], dP[12];
+#pragma unroll
+      for (int e = 0; e < 12; ++e) {
+        Pa[e] = (TA)P[e];
+        dP[e] = (TA)Dp[12 * (size_t)i + e];
+      }
+      TA w[3], pdx[3], dl[2];
+      apply_p(dP, Xa, w);
+      apply_p(Pa, dxa, pdx);
 #pragma unroll
       for (int rr = 0; rr < 3; ++rr) w[rr] += pdx[rr];
-      apply_d(q, w, dl);
-      const double l0 = q.p0 - m.x + dl[0], l1 = q.p1 - m.y + dl[1];
+      apply_d(qa, w, dl);
+      const double l0 = q.p0 - m.x + (double)dl[0], l1 = q.p1 - m.y + (double)dl[1];
       model += l0 * l0 + l1 * l1;
     }
   }
@@ -779,12 +726,17 @@ povar_status launch_s2_prep(Problem* p, double lambda_l) {
   return check_launch(p, "s2_prep");
 }
 
-povar_status launch_s2_linearize(Problem* p) {
+povar_status launch_s2_linearize(Problem* p, int precision) {
   const unsigned g = grid_for(p->nchunks, 8);
   if (g == 0) return POVAR_OK;
-  k_s2_linearize<<<g, 256, 0, p->stream>>>(p->state, p->nchunks, p->chunk_cam, p->chunk_beg,
-                                           p->cm_slot, p->cm_m64, p->P64[0], p->P64[1],
-                                           p->s2X[0], p->s2X[1], p->s2s, p->s2lin);
+  if (precision == POVAR_FP64)
+    k_s2_linearize<double><<<g, 256, 0, p->stream>>>(
+        p->state, p->nchunks, p->chunk_cam, p->chunk_beg, p->cm_slot, p->cm_m64, p->P64[0],
+        p->P64[1], p->s2X[0], p->s2X[1], p->s2s, p->s2lin);
+  else
+    k_s2_linearize<float><<<g, 256, 0, p->stream>>>(
+        p->state, p->nchunks, p->chunk_cam, p->chunk_beg, p->cm_slot, p->cm_m64, p->P64[0],
+        p->P64[1], p->s2X[0], p->s2X[1], p->s2s, p->s2lin);
   ++p->launches;
   return check_launch(p, "s2_linearize");
 }
@@ -838,12 +790,12 @@ povar_status launch_s2_series_term(Problem* p, int precision, int term, double e
 
 povar_status launch_s2_trial(Problem* p, int precision, int m) {
   if (precision == POVAR_FP64)
-    k_s2_trial<double><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+    k_s2_trial<double, double><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
         p->state, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1],
         p->D64, p->s2X[0], p->s2X[1], p->s2Gl64, p->s2bl, p->cost_part, p->pred_part,
         p->pinv_part);
   else
-    k_s2_trial<float><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
+    k_s2_trial<float, float><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
         p->state, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0], p->P64[1],
         p->D32, p->s2X[0], p->s2X[1], p->s2Gl64, p->s2bl, p->cost_part, p->pred_part,
         p->pinv_part);

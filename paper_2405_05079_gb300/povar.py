@@ -163,11 +163,11 @@ def make_params(eta=0.1, lambda0=1e-4, m=10, series_eps=0.0, manifold=SPHERE,
 
 
 def make_s2_params(lambda0=1e-4, m=21, series_eps=0.01, lambda_l=1.0,
-                   precision=MIXED_FP32) -> Params:
+                   precision=MIXED_FP32, schedule=-1) -> Params:
     """Parameters of the second stage (povar_s2_*): Riemannian PoBA on the
     unit spheres, landmark damping lambda_l * lambda."""
     return Params(eta=0.0, lambda0=lambda0, series_eps=series_eps, lambda_l=lambda_l, m=m,
-                  manifold=SPHERE, precision=precision, schedule=-1, solver=0, reserved=0)
+                  manifold=SPHERE, precision=precision, schedule=schedule, solver=0, reserved=0)
 
 
 def current_stream_handle() -> int | None:

@@ -71,9 +71,10 @@ def oparams(m, eps=0.0, lambda0=1e-4, lambda_l=1.0):
     return R.Params(lambda0=lambda0, m=m, series_eps=eps, lambda_l=lambda_l)
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("lambda0", [1e-4, 1e-1])
 @pytest.mark.parametrize("name", list(SCENES))
-def test_s2_one_step_fp64_matches_oracle(name, lambda0):
+def test_s2_one_step_fp64_matches_oracle(name, lambda0, schedule):
     sc = SCENES[name]()
     P, X, orc = start(sc)
     op = oparams(10, lambda0=lambda0)
@@ -83,7 +84,7 @@ def test_s2_one_step_fp64_matches_oracle(name, lambda0):
         pb.s2_set(P, X)
         assert abs(pb.s2_cost() - st0.F) <= 1e-12 * st0.F
         rep = pb.s2_step(povar.make_s2_params(lambda0=lambda0, m=10, series_eps=0.0,
-                                              precision=povar.FP64))
+                                              precision=povar.FP64, schedule=schedule))
         U, bp, d = pb.last_step()
         P1, X1 = pb.cameras(), pb.s2_points()
     assert rep.terms_used == 10
@@ -164,7 +165,8 @@ def test_s2_step_on_an_ill_conditioned_scene():
         assert abs(rep.cost_after - orep.cost_after) <= 1e-4 * orep.cost_after
 
 
-def test_s2_mixed_step_close_to_oracle():
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_s2_mixed_step_close_to_oracle(schedule):
     sc = SCENES["ring60"]()
     P, X, orc = start(sc)
     op = oparams(10)
@@ -173,7 +175,8 @@ def test_s2_mixed_step_close_to_oracle():
     with povar.Problem.from_scene(sc) as pb:
         pb.s2_set(P, X)
         X0 = pb.s2_points()
-        rep = pb.s2_step(povar.make_s2_params(m=10, series_eps=0.0, precision=povar.MIXED_FP32))
+        rep = pb.s2_step(povar.make_s2_params(m=10, series_eps=0.0, precision=povar.MIXED_FP32,
+                                              schedule=schedule))
         _, _, d = pb.last_step()
         X1 = pb.s2_points()
     # the landmark update of the GPU step, from the retracted landmarks
@@ -249,6 +252,7 @@ def test_s2_invalid_calls_rejected():
         b = povar.make_s2_params()
         b.solver = povar.SOLVER_PCG
         bad.append(b)
+        bad.append(povar.make_s2_params(schedule=3))
         for prm in bad:
             with pytest.raises(povar.PovarError) as e:
                 pb.s2_step(prm)
