@@ -259,6 +259,28 @@ povar_status povar_s2_solve(povar_problem* p, const povar_params* params, int32_
                             int32_t* iters_out);
 povar_status povar_s2_get_points(povar_problem* p, double* X_out);
 
+/* ---- Metric upgrade (the third stage of the stratified problem;
+ * supplementary section "Metric Upgrade"): finds H = H_0 [[I, 0], [c^T, 1]]
+ * such that K_i^-1 P_i H ~ [R_i t_i] for the handle's current cameras P_i
+ * (after either stage). H_0 puts the calibrated camera 0, K_0^-1 P_0, at
+ * [I | 0]; c (the plane at infinity up to sign) and a scale alpha_i per
+ * camera minimize sum_i ||alpha_i B_i H~ H~^T B_i^T - I||_F^2 with
+ * B_i = K_i^-1 P_i H_0 and H~ = [[I], [c^T]], by Variable Projection: the
+ * alpha_i in closed form, Levenberg-Marquardt on c (lambda0 = 1e-4, the
+ * first stage's damping rule, stop on an accepted step whose relative
+ * decrease is below ftol, or after max_iters iterations) from the linear
+ * estimate of the dual absolute quadric H~ H~^T. All in FP64.
+ * K: n_cams row-major 3x3 intrinsics on the host (invertible), or NULL for
+ * the identity (measurements already normalized). H_out: 16 doubles,
+ * row-major. alpha_out (n_cams, may be NULL): the scales; the metric camera
+ * i is sqrt(|alpha_i|) K_i^-1 P_i H up to sign. cost_out, iters_out may be
+ * NULL. POVAR_EINVAL for fewer than 3 cameras, a singular K_i or reference
+ * camera, non-finite K; the cameras are not changed. Synchronizes the
+ * stream. */
+povar_status povar_metric_upgrade(povar_problem* p, const double* K, int32_t max_iters,
+                                  double ftol, double* H_out, double* alpha_out,
+                                  double* cost_out, int32_t* iters_out);
+
 /* pOSE cost F = ||r||^2 (Eq. ba_first_stage) at the current cameras with
  * the landmarks at their closed-form optimum for this eta. */
 povar_status povar_cost(povar_problem* p, double eta, double* cost_out);

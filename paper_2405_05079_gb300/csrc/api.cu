@@ -1037,6 +1037,34 @@ povar_status povar_s2_get_points(povar_problem* pp, double* X_out) {
   return POVAR_OK;
 }
 
+povar_status povar_metric_upgrade(povar_problem* pp, const double* K, int32_t max_iters,
+                                  double ftol, double* H_out, double* alpha_out,
+                                  double* cost_out, int32_t* iters_out) {
+  if (!pp) return POVAR_EINVAL;
+  Problem* p = &pp->impl;
+  if (!H_out) return povar::fail(p, POVAR_EINVAL, "H_out is NULL");
+  if (p->nc < 3) return povar::fail(p, POVAR_EINVAL, "the metric upgrade needs >= 3 cameras");
+  if (max_iters < 1) return povar::fail(p, POVAR_EINVAL, "max_iters must be >= 1");
+  if (!(ftol >= 0.0)) return povar::fail(p, POVAR_EINVAL, "ftol must be >= 0");
+  povar_status s;
+  const double* d_K = nullptr;
+  if (K) {
+    for (int64_t e = 0; e < (int64_t)p->nc * 9; ++e)
+      if (!std::isfinite(K[e])) return povar::fail(p, POVAR_EINVAL, "non-finite intrinsics");
+    if (!p->mu_K && (s = povar::dev_alloc(p, &p->mu_K, (size_t)p->nc * 9, "mu_K")) != POVAR_OK)
+      return s;
+    POVAR_CUDA(cudaMemcpyAsync(p->mu_K, K, (size_t)p->nc * 9 * sizeof(double),
+                               cudaMemcpyHostToDevice, p->stream));
+    d_K = p->mu_K;
+  }
+  int it = 0;
+  if ((s = povar::launch_metric_upgrade(p, d_K, 1e-4, max_iters, ftol, H_out, alpha_out,
+                                        cost_out, &it)) != POVAR_OK)
+    return s;
+  if (iters_out) *iters_out = it;
+  return POVAR_OK;
+}
+
 povar_status povar_cost(povar_problem* pp, double eta, double* cost_out) {
   if (!pp) return POVAR_EINVAL;
   Problem* p = &pp->impl;

@@ -244,6 +244,11 @@ struct Problem {
   uint32_t* s2idx = nullptr;            // [nchunks] chunk indices 0..nchunks-1
   bool s2_live = false;                 // second-stage landmarks were set
   bool s2_current = false;              // the device state's cost is the second stage's
+  // metric upgrade (allocated at first use)
+  double* mu_B = nullptr;               // [nc*12 + 16] B_i = K_i^-1 P_i H_0, then H_0
+  double* mu_alpha = nullptr;           // [nc] scales
+  void* mu_out = nullptr;               // result record
+  double* mu_K = nullptr;               // [nc*9] intrinsics staged from the host
   // conjugate-gradient solver (allocated at first use)
   double* pcg_vec = nullptr;            // [4*nc*12] r, z, p, q (float or double)
   double* pcg_M64 = nullptr;            // [nc*144] inverse Schur-Jacobi blocks
@@ -368,6 +373,13 @@ povar_status launch_series_apply(Problem* p, int precision, int term, double eps
                                  const uint32_t* off, const uint32_t* idx, const void* part);
 // pred = F - sum of the model partials in pred_part (PoBA, second stage)
 povar_status launch_model_pred_finish(Problem* p, int m);
+
+// ---------------------------------------------------- metric.cu
+// Metric upgrade of the current cameras (d_K: n_cams 3x3 row-major on the
+// device, or null for identity); synchronizes the stream.
+povar_status launch_metric_upgrade(Problem* p, const double* d_K, double lambda0, int max_iters,
+                                   double ftol, double* H_out, double* alpha_out,
+                                   double* cost_out, int* iters_out);
 
 // ---------------------------------------------------- pcg.cu
 // Conjugate-gradient solve of the reduced camera system into the step buffer

@@ -83,6 +83,8 @@ def lib() -> C.CDLL:
     L.povar_s2_solve.argtypes = [vp, C.POINTER(Params), i32, C.c_double, C.c_double,
                                  C.POINTER(StepReport), C.POINTER(C.c_int32)]
     L.povar_s2_get_points.argtypes = [vp, dp]
+    L.povar_metric_upgrade.argtypes = [vp, dp, i32, C.c_double, dp, dp, dp,
+                                       C.POINTER(C.c_int32)]
     u32p = C.POINTER(C.c_uint32)
     L.povar_get_orders.argtypes = [vp, u32p, u32p, u32p, u32p]
     L.povar_get_layout.argtypes = [vp, C.POINTER(C.c_int64), u32p, u32p,
@@ -322,6 +324,22 @@ class Problem:
         out = np.empty((self.n_points, 4))
         self._check(lib().povar_s2_get_points(self._h, _ptr(out, C.c_double)))
         return out
+
+    def metric_upgrade(self, K=None, max_iters=100, ftol=1e-12):
+        """povar_metric_upgrade on the current cameras: returns (H [4, 4],
+        alpha [n_cams], cost, iterations)."""
+        H = np.empty(16)
+        al = np.empty(self.n_cams)
+        cost = C.c_double()
+        it = C.c_int32()
+        Kp = None
+        if K is not None:
+            Ka = np.ascontiguousarray(np.asarray(K, dtype=np.float64).reshape(self.n_cams, 9))
+            Kp = _ptr(Ka, C.c_double)
+        self._check(lib().povar_metric_upgrade(self._h, Kp, max_iters, ftol,
+                                               _ptr(H, C.c_double), _ptr(al, C.c_double),
+                                               C.byref(cost), C.byref(it)))
+        return H.reshape(4, 4), al, cost.value, it.value
 
     def orders(self):
         no, np_, nc = self.n_obs, self.n_points, self.n_cams
