@@ -51,6 +51,7 @@ typedef enum {
 
 enum { POVAR_EUCLID = 0, POVAR_SPHERE = 1 };
 enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1, POVAR_MIXED_BF16 = 2 };
+enum { POVAR_BF16_FP32_TERMS = 6 };  /* POVAR_MIXED_BF16: terms 1..5 in FP32 */
 
 /* Solver parameters (Sec. 5.2 of the paper gives eta = 0.1, lambda0 = 1e-4,
  * series order 20 with threshold 0.01).
@@ -78,13 +79,17 @@ enum { POVAR_FP64 = 0, POVAR_MIXED_FP32 = 1, POVAR_MIXED_BF16 = 2 };
  *  precision  POVAR_FP64: every kernel in FP64.
  *             POVAR_MIXED_FP32: series and linearization in FP32; landmark
  *             elimination, 12x12 inverses, cost and gain ratio in FP64.
- *             POVAR_MIXED_BF16: POVAR_MIXED_FP32 whose series terms read the
- *             stored blocks of schedule 4 in bfloat16 (18 bytes per
- *             observation) and accumulate in FP32: the blocks are rounded,
- *             so its steps differ from the FP32 ones by about the bfloat16
- *             rounding (2^-9 relative per block entry). It always runs
- *             schedule 4; params->schedule must be -1 or 4. The predicted
- *             decrease is computed in FP32 from the unrounded factors.
+ *             POVAR_MIXED_BF16: POVAR_MIXED_FP32 whose series terms from
+ *             term POVAR_BF16_FP32_TERMS on read the stored blocks of
+ *             schedule 4 in bfloat16 (18 bytes per observation) and
+ *             accumulate in FP32; the leading terms x_1 .. x_5 read the
+ *             FP32 factors (the fused pass of schedule 1), where the
+ *             rounding of the blocks would weigh most. The blocks are
+ *             rounded, so its steps differ from the FP32 ones by about the
+ *             bfloat16 rounding (2^-9 relative per block entry) of the
+ *             later terms. params->schedule must be -1 or 4. The
+ *             predicted decrease is computed in FP32 from the unrounded
+ *             factors.
  *  schedule   series schedule: 0 = landmark-major gather pass + camera-major
  *             scatter pass over observation chunks; 1 = one fused
  *             landmark-major pass whose camera contributions are reduced

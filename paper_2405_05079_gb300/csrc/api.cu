@@ -313,11 +313,17 @@ povar_status enqueue_step_kernels(Problem* p, const povar_params* q, std::vector
     // the reduced system by conjugate gradients (reads device flags: eager only)
     if ((s = launch_pcg(p, prec, q->manifold, q->eta, q->m, q->series_eps)) != POVAR_OK) return s;
   } else {
-    if (sched == 4 && q->m > 1 && (s = launch_build_blocks(p, prec, q->eta)) != POVAR_OK)
+    if (sched == 4 && q->m > (prec == POVAR_MIXED_BF16 ? POVAR_BF16_FP32_TERMS : 1) &&
+        (s = launch_build_blocks(p, prec, q->eta)) != POVAR_OK)
       return s;
-    for (int k = 1; k < q->m; ++k)
-      if ((s = launch_series_term(p, prec, q->eta, k, q->series_eps, sched)) != POVAR_OK)
+    for (int k = 1; k < q->m; ++k) {
+      // POVAR_MIXED_BF16: the leading terms read the FP32 factors (the
+      // factored fused pass), the later ones the bfloat16 blocks
+      const bool lead32 = prec == POVAR_MIXED_BF16 && k < POVAR_BF16_FP32_TERMS;
+      if ((s = launch_series_term(p, lead32 ? POVAR_MIXED_FP32 : prec, q->eta, k,
+                                  q->series_eps, lead32 ? 1 : sched)) != POVAR_OK)
         return s;
+    }
   }
   if ((s = mark(p, mk)) != POVAR_OK) return s;
   if (poba) {

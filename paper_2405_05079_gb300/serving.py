@@ -98,7 +98,8 @@ class Server:
                 actual = pb.device_bytes
                 pb.set_cameras(req.P0, self.params.eta)
                 _, iters = pb.solve(self.params_for(sc), max_iters=self.max_iters,
-                                    ftol=self.ftol, target_cost=req.target_cost)
+                                    ftol=self.ftol, target_cost=req.target_cost,
+                                    allow_stall=True)
                 cost = pb.cost(self.params.eta)
                 cams = pb.cameras()
         finally:
