@@ -403,11 +403,16 @@ int64_t povar_launch_count(const povar_problem* p);
  * landmarks and n_obs[k] observations; its observations follow those of
  * problems 0..k-1 in cam_idx / pt_idx / meas (2 doubles each), with indices
  * local to the problem. Cameras of all problems are concatenated likewise
- * (12 doubles per camera). povar_batch_solve runs every iteration of every
- * problem as one CUDA-graph launch whose child graphs are the problems' step
- * graphs (no dependencies between problems, so their kernels overlap); each
- * problem stops on its own device-side convergence flag; the host checks the
- * flags every fourth iteration. With schedule -1 every problem picks its
+ * (12 doubles per camera). povar_batch_solve runs the whole solve as one
+ * CUDA-graph launch: a device-side while loop (a conditional graph node)
+ * whose body holds one step of every problem (the problems' step graphs as
+ * child graphs, without dependencies between problems, so their kernels
+ * overlap) followed by a one-thread kernel that repeats the body while some
+ * problem has not converged and fewer than max_iters steps ran; each problem
+ * stops on its own device-side convergence flag and the host waits once, at
+ * the end. When the problems' phase profiling is on (povar_set_profiling),
+ * or the loop cannot be built, every step is one launch and the host checks
+ * the flags every fourth step. With schedule -1 every problem picks its
  * own series schedule by the autotuner of povar_solve before the first
  * iteration. Results are identical to solving each problem alone with the
  * same parameters and schedule. target_costs,

@@ -1275,6 +1275,9 @@ struct povar_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<povar_params> keys;       // parameters of each problem in the graph
   bool built = false;
+  bool looped = false;                  // the graph is a device-side while loop over steps
+  povar::DeviceState** d_states = nullptr;  // [n] the problems' device states
+  int* d_loops = nullptr;               // [2] steps run, step limit
   std::string err;
 };
 
@@ -1290,6 +1293,8 @@ void povar_batch_destroy(povar_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->d_states) cudaFree(b->d_states);
+  if (b->d_loops) cudaFree(b->d_loops);
   for (povar_problem* q : b->probs) povar_destroy(q);
   delete b;
 }
@@ -1317,6 +1322,21 @@ povar_status povar_batch_create(int32_t n_problems, const int32_t* n_cams, const
     b->cam0.push_back(b->nc_total);
     b->nc_total += n_cams[k];
     o += n_obs[k];
+  }
+  // device state pointers and the step counters of the device-side loop
+  // (without them a solve launches one graph per step)
+  std::vector<povar::DeviceState*> st(b->probs.size());
+  for (size_t k = 0; k < st.size(); ++k) st[k] = b->probs[k]->impl.state;
+  if (cudaMalloc(reinterpret_cast<void**>(&b->d_states), st.size() * sizeof(st[0])) !=
+          cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&b->d_loops), 2 * sizeof(int)) != cudaSuccess ||
+      cudaMemcpy(b->d_states, st.data(), st.size() * sizeof(st[0]), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    if (b->d_states) cudaFree(b->d_states);
+    if (b->d_loops) cudaFree(b->d_loops);
+    b->d_states = nullptr;
+    b->d_loops = nullptr;
   }
   *out = b;
   return POVAR_OK;
@@ -1390,12 +1410,53 @@ static povar_status batch_solve(povar_batch* b, const povar_params* params_base,
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
-    cudaError_t e = cudaGraphCreate(&b->graph, 0);
-    for (size_t k = 0; k < n && e == cudaSuccess; ++k) {
-      cudaGraphNode_t node;
-      e = cudaGraphAddChildGraphNode(&node, b->graph, nullptr, 0, b->probs[k]->impl.graph);
+    b->looped = false;
+    // preferred: the whole solve as one launch, a device-side while node
+    // whose body runs one step of every problem and then decides whether
+    // another step is needed (not with phase profiling: the step graphs
+    // then hold event nodes, which a loop body cannot)
+    bool profiled = false;
+    for (povar_problem* q : b->probs) profiled |= q->impl.profiling;
+    cudaError_t e = cudaSuccess;
+    if (!profiled && b->d_states && b->d_loops) {
+      e = cudaGraphCreate(&b->graph, 0);
+      cudaGraphConditionalHandle h{};
+      if (e == cudaSuccess)
+        e = cudaGraphConditionalHandleCreate(&h, b->graph, 1, cudaGraphCondAssignDefault);
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t cnode;
+      if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, b->graph, nullptr, nullptr, 0, &cp);
+      std::vector<cudaGraphNode_t> kids(n);
+      for (size_t k = 0; k < n && e == cudaSuccess; ++k)
+        e = cudaGraphAddChildGraphNode(&kids[k], cp.conditional.phGraph_out[0], nullptr, 0,
+                                       b->probs[k]->impl.graph);
+      if (e == cudaSuccess)
+        e = povar::add_batch_continue(cp.conditional.phGraph_out[0], kids.data(), n, h,
+                                      b->d_states, (int)n, b->d_loops);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      if (e == cudaSuccess) {
+        b->looped = true;
+      } else {
+        cudaGetLastError();
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+      }
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    // otherwise one launch per step of a graph holding every problem's step
+    if (!b->looped) {
+      e = cudaGraphCreate(&b->graph, 0);
+      for (size_t k = 0; k < n && e == cudaSuccess; ++k) {
+        cudaGraphNode_t node;
+        e = cudaGraphAddChildGraphNode(&node, b->graph, nullptr, 0, b->probs[k]->impl.graph);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       b->built = false;
@@ -1405,8 +1466,24 @@ static povar_status batch_solve(povar_batch* b, const povar_params* params_base,
     for (size_t k = 0; k < n; ++k) b->keys[k] = params_base[k * each];
     b->built = true;
   }
+  if (b->looped) {
+    // one launch for the whole solve; the loop stops on the device
+    const int h_loops[2] = {0, max_iters};
+    int done[2] = {0, 0};
+    if (cudaMemcpyAsync(b->d_loops, h_loops, sizeof(h_loops), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess ||
+        cudaGraphLaunch(b->exec, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(done, b->d_loops, sizeof(done), cudaMemcpyDeviceToHost, b->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return batch_fail(b, POVAR_ECUDA, "batch loop launch");
+    }
+    for (povar_problem* q : b->probs) q->impl.launches += (int64_t)done[0] * q->impl.g_launches;
+    b->probs[0]->impl.launches += done[0];   // the loop's condition kernel
+  }
   const int check_every = 4;
-  for (int it = 0; it < max_iters; ++it) {
+  for (int it = 0; it < (b->looped ? 0 : max_iters); ++it) {
     const cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
     if (e != cudaSuccess)
       return batch_fail(b, POVAR_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));

@@ -405,6 +405,12 @@ povar_status launch_init_state(Problem* p, double lambda0, int reset_lm, int res
 povar_status launch_begin(Problem* p, double ftol, double target, int max_iters,
                           int fallback_after = 0);
 povar_status launch_random_cameras(Problem* p, uint64_t seed, int normalize);
+// Kernel node of a batch's device-side loop: sets the while node's condition
+// (some problem not converged and fewer than d_loops[1] steps; d_loops[0]
+// counts the steps).
+cudaError_t add_batch_continue(cudaGraph_t body, const cudaGraphNode_t* deps, size_t ndeps,
+                               cudaGraphConditionalHandle h, DeviceState** d_states, int n,
+                               int* d_loops);
 povar_status launch_gather_points(Problem* p, double* d_out);
 
 }  // namespace povar

@@ -229,6 +229,39 @@ povar_status launch_init_state(Problem* p, double lambda0, int reset_lm, int res
   return check_launch(p, "init_state");
 }
 
+namespace {
+
+// Loop condition of a batch solve's device-side while node: one more batch
+// step while some problem has not converged and fewer than loops[1] steps
+// ran (loops[0] counts them).
+__global__ void k_batch_continue(cudaGraphConditionalHandle h,
+                                 DeviceState* const* __restrict__ states, int n,
+                                 int* __restrict__ loops) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int l = loops[0] + 1;
+  loops[0] = l;
+  int any = 0;
+  for (int k = 0; k < n; ++k) any |= states[k]->converged ? 0 : 1;
+  cudaGraphSetConditional(h, (any && l < loops[1]) ? 1u : 0u);
+}
+
+}  // namespace
+
+cudaError_t add_batch_continue(cudaGraph_t body, const cudaGraphNode_t* deps, size_t ndeps,
+                               cudaGraphConditionalHandle h, DeviceState** d_states, int n,
+                               int* d_loops) {
+  cudaKernelNodeParams kp = {};
+  void* args[] = {&h, &d_states, &n, &d_loops};
+  kp.func = reinterpret_cast<void*>(k_batch_continue);
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(32);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  cudaGraphNode_t node;
+  return cudaGraphAddKernelNode(&node, body, deps, ndeps, &kp);
+}
+
 povar_status launch_begin(Problem* p, double ftol, double target, int max_iters,
                           int fallback_after) {
   k_begin<<<1, 1, 0, p->stream>>>(p->state, ftol, target, max_iters, fallback_after);

@@ -539,8 +539,10 @@ def test_autotuner_picks_a_schedule_without_changing_the_solve():
 
 
 def test_batch_solve_equals_each_problem_alone():
-    """Problems of uneven sizes solved as one batch (one graph launch per
-    iteration) give bit-identical results to solving each alone."""
+    """Problems of uneven sizes solved as one batch (one graph launch for the
+    whole solve: a device-side loop over the batch step) give bit-identical
+    results to solving each alone, with the per-problem stop rules applied
+    on the device."""
     scs = [SCENES["tiny"](), SCENES["traj"](), SCENES["ragged"](),
            scenes.ring_scene(7, 300, 9, eta=0.1)]
     P0s = [scenes.init_cameras(s.n_cams, 10 + k, normalize=True) for k, s in enumerate(scs)]
