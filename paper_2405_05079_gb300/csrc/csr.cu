@@ -932,22 +932,30 @@ povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
   }
   // flat tables; items: for row k the slices that reach it (a prefix of the
   // group, widest first) in ranges of at most G5_ITEM
-  std::vector<uint32_t> goff(1, 0), gsl, roff(1, 0), ioff(1, 0), items;
-  std::vector<int32_t> rowcam;
+  std::vector<uint32_t> goff(1, 0), gsl, roff(1, 0), ioff(1, 0), items, sinfo;
+  std::vector<int32_t> rowcam, ghdr;
   std::vector<int32_t> item_cam;
   std::vector<char> grouped_part((size_t)p->npart, 0);
   int64_t g_obs_rows = 0;
   for (const Grp& g : groups) {
     std::vector<uint32_t> width;
+    uint32_t mrow = 0;
     for (uint32_t sidx : g.sl) {
       gsl.push_back(sidx);
       const uint32_t w = (off[sidx + 1] - off[sidx]) / SLICE;
       width.push_back(w);
+      sinfo.insert(sinfo.end(), {sidx, off[sidx], w, mrow});
+      mrow += w;
       const uint32_t r0 = off[sidx] / SLICE;
       for (uint32_t k = 0; k < w; ++k) grouped_part[rbase[r0 + k]] = 1;   // uniform: one partial
       g_obs_rows += w;
     }
     goff.push_back((uint32_t)gsl.size());
+    bool consecutive = !g.cam.empty();
+    for (size_t k = 1; consecutive && k < g.cam.size(); ++k)
+      consecutive = g.cam[k] == g.cam[0] + (int32_t)k;
+    ghdr.push_back((int32_t)mrow);
+    ghdr.push_back(consecutive ? g.cam[0] : -1);
     for (int32_t c : g.cam) rowcam.push_back(c);
     roff.push_back((uint32_t)rowcam.size());
     for (uint32_t k = 0; k < (uint32_t)g.cam.size(); ++k) {
@@ -988,8 +996,11 @@ povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
   if ((s = up32(&p->g5_off, goff, "g5_off")) || (s = up32(&p->g5_slices, gsl, "g5_slices")) ||
       (s = up32(&p->g5_roff, roff, "g5_roff")) || (s = up32(&p->g5_ioff, ioff, "g5_ioff")) ||
       (s = up32(&p->g5_items, items, "g5_items")) || (s = up32(&p->g5_rest, rest, "g5_rest")) ||
-      (s = up32(&p->cam5_off, c5off, "cam5_off")) || (s = up32(&p->cam5_idx, c5idx, "cam5_idx")))
+      (s = up32(&p->cam5_off, c5off, "cam5_off")) || (s = up32(&p->cam5_idx, c5idx, "cam5_idx")) ||
+      (s = up32(&p->g5_sinfo, sinfo, "g5_sinfo")))
     return s;
+  if ((s = dev_alloc(p, &p->g5_ghdr, std::max<size_t>(ghdr.size(), 2), "g5_ghdr"))) return s;
+  if (!ghdr.empty()) POVAR_COPY(p->g5_ghdr, ghdr.data(), ghdr.size(), cudaMemcpyHostToDevice);
   if ((s = dev_alloc(p, &p->g5_rowcam, std::max<size_t>(rowcam.size(), 1), "g5_rowcam")))
     return s;
   if (!rowcam.empty())

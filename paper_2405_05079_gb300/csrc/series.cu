@@ -1180,6 +1180,10 @@ struct G5Tables {
   const uint32_t* ioff;    // [ngroups + 1] items of group g
   const uint32_t* items;   // (row << 16) | (first slice << 8) | end slice
   const uint32_t* rest;    // slices outside groups
+  const uint4* sinfo;      // per grouped slice: slice, first SELL entry, width, first
+                           // staged measurement row (slices order)
+  const int2* ghdr;        // per group: staged measurement rows, first row camera if the
+                           // rows' cameras are consecutive (else -1)
   int ngroups;
 };
 
@@ -1206,46 +1210,51 @@ __device__ __forceinline__ void g5_group_block(
   const int g = blockIdx.x, lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const uint32_t sb = tb.off[g], ns = tb.off[g + 1] - sb;
   const uint32_t rb = tb.roff[g], nr = tb.roff[g + 1] - rb;
+  const int2 hdr = __ldg(tb.ghdr + g);   // staged measurement rows, first row camera
 
-  if (threadIdx.x < ns) {
-    const uint32_t sl = __ldg(tb.slices + sb + threadIdx.x);
-    const uint32_t o = sell_off[sl];
-    s_idx[threadIdx.x] = sl;
-    s_off[threadIdx.x] = o;
-    s_w[threadIdx.x] = (sell_off[sl + 1] - o) / SLICE;
-  }
-  __syncthreads();
   if (wl == 0) {
-    // staged measurement rows of each slice (the host keeps the sum of the
-    // widths within G5_MROWS), the expected byte count, then the bulk copies
-    // of slice j issued by lane j
+    // lane j < ns: slice j's table entry (slice, first SELL entry, width,
+    // first staged measurement row; the host keeps the rows within
+    // G5_MROWS); lane 0 sets the expected byte count, then lane j issues the
+    // bulk copies of slice j, and lane 0 those of the group's camera rows
+    // when their cameras are consecutive
+    const uint4 info = (uint32_t)lane < ns ? __ldg(tb.sinfo + sb + lane) : make_uint4(0, 0, 0, 0);
+    if ((uint32_t)lane < ns) {
+      s_idx[lane] = info.x;
+      s_off[lane] = info.y;
+      s_w[lane] = info.z;
+      s_mrow[lane] = info.w;
+    }
     if (lane == 0) {
-      uint32_t r = 0;
-      for (uint32_t j = 0; j < ns; ++j) {
-        s_mrow[j] = r;
-        r += s_w[j];
-      }
       mbar_init(bar, 1);
-      mbar_arrive_expect_tx(bar, r * SLICE * (uint32_t)sizeof(M2) +
-                                     ns * (G5Pd<T>::SLICE_BYTES + SLICE * 4u));
+      mbar_arrive_expect_tx(bar, (uint32_t)hdr.x * SLICE * (uint32_t)sizeof(M2) +
+                                     ns * (G5Pd<T>::SLICE_BYTES + SLICE * 4u) +
+                                     (hdr.y >= 0 ? 2u * nr * 12u * (uint32_t)sizeof(T) : 0u));
     }
     __syncwarp();
     if ((uint32_t)lane < ns) {
-      const uint32_t j = (uint32_t)lane, slot0 = s_idx[j] * SLICE;
-      bulk_g2s(sm + L::MEAS + (size_t)s_mrow[j] * SLICE * sizeof(M2), sell_m + s_off[j],
-               s_w[j] * SLICE * (uint32_t)sizeof(M2), bar);
+      const uint32_t j = (uint32_t)lane, slot0 = info.x * SLICE;
+      bulk_g2s(sm + L::MEAS + (size_t)info.w * SLICE * sizeof(M2), sell_m + info.y,
+               info.z * SLICE * (uint32_t)sizeof(M2), bar);
       bulk_g2s(sm + L::LEN + (size_t)j * SLICE * 4, slot_len + slot0, SLICE * 4, bar);
       G5Pd<T>::copy(sm_pd, (int)j, pd, slot0, bar);
     }
+    if (lane == 0 && hdr.y >= 0) {
+      bulk_g2s(cP, camP + 12 * (size_t)hdr.y, nr * 12u * (uint32_t)sizeof(T), bar);
+      bulk_g2s(cY, vec + 12 * (size_t)hdr.y, nr * 12u * (uint32_t)sizeof(T), bar);
+    }
   }
-  // camera rows of the group rows while the copies are in flight
-  for (uint32_t q = threadIdx.x; q < nr * 24; q += G5_THREADS) {
-    const uint32_t r = q / 24, e = q % 24;
-    const size_t c = (size_t)__ldg(tb.rowcam + rb + r);
-    if (e < 12)
-      cP[12 * r + e] = camP[12 * c + e];
-    else
-      cY[12 * r + e - 12] = vec[12 * c + e - 12];
+  if (hdr.y < 0) {
+    // camera rows of the group rows (not consecutive cameras) while the
+    // copies are in flight
+    for (uint32_t q = threadIdx.x; q < nr * 24; q += G5_THREADS) {
+      const uint32_t r = q / 24, e = q % 24;
+      const size_t c = (size_t)__ldg(tb.rowcam + rb + r);
+      if (e < 12)
+        cP[12 * r + e] = camP[12 * c + e];
+      else
+        cY[12 * r + e - 12] = vec[12 * c + e - 12];
+    }
   }
   __syncthreads();
   const bool arrived = mbar_wait_bounded(bar, 0);
@@ -2095,7 +2104,9 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
     const unsigned gb = (unsigned)(p->g5_ngroups + p->g5_nrest);
     const int64_t nit = p->g5_nitems;
     const G5Tables tb{p->g5_off,  p->g5_slices, p->g5_roff, p->g5_rowcam,
-                      p->g5_ioff, p->g5_items,  p->g5_rest, p->g5_ngroups};
+                      p->g5_ioff, p->g5_items,  p->g5_rest,
+                      reinterpret_cast<const uint4*>(p->g5_sinfo),
+                      reinterpret_cast<const int2*>(p->g5_ghdr), p->g5_ngroups};
     if (precision == POVAR_FP64) {
       double* part = static_cast<double*>(p->part5);
       if (gb > 0)
