@@ -508,12 +508,12 @@ def run_ours(args, rank: int, world: int) -> dict | None:
 
 # ----------------------------------------------------------------- batched / serving
 
-def family_params(povar, precision: int):
+def family_params(povar, precision: int, schedule: int = -1):
     """Solver settings of the batched and serving workloads: Sec. 5.2 values
-    (eta 0.1, lambda0 1e-4, order 20 with threshold 0.01), autotuned series
-    schedule per problem."""
+    (eta 0.1, lambda0 1e-4, order 20 with threshold 0.01), the series
+    schedule autotuned per problem (-1) or the one given."""
     return povar.make_params(eta=0.1, lambda0=1e-4, m=21, series_eps=0.01,
-                             manifold=povar.EUCLID, precision=precision, schedule=-1)
+                             manifold=povar.EUCLID, precision=precision, schedule=schedule)
 
 
 def run_batched(args) -> dict:
@@ -539,7 +539,7 @@ def run_batched(args) -> dict:
             m_table = json.load(f)
     with povar.Batch(scs, stream=stream.cuda_stream) as b:
         for name, prec in (("mixed", povar.MIXED_FP32), ("fp64", povar.FP64)):
-            prm = family_params(povar, prec)
+            prm = family_params(povar, prec, args.schedule)
             if m_table is not None and prec == povar.MIXED_FP32:
                 from paper_2405_05079_gb300.autotune import params_with_m
                 prm = [params_with_m(m_table, prm, int(n)) for n in b.n_obs]
@@ -557,7 +557,7 @@ def run_batched(args) -> dict:
                          "costs": b.costs(0.1).tolist()}
     # the same problems, one handle each, solved one after another
     probs = [povar.Problem.from_scene(s, stream=stream.cuda_stream) for s in scs]
-    prm = family_params(povar, povar.MIXED_FP32)
+    prm = family_params(povar, povar.MIXED_FP32, args.schedule)
     times = []
     for k in range(args.warmup + args.steps):
         for q, P0 in zip(probs, P0s):
@@ -792,8 +792,8 @@ def run_serving(args) -> dict:
     reqs = [serving.Request(rid=k, arrival=float(arr[k]), scene=s,
                             P0=scenes.init_cameras(s.n_cams, 200 + k, normalize=True))
             for k, s in enumerate(scs)]
-    mixed = family_params(povar, povar.MIXED_FP32)
-    fp64 = family_params(povar, povar.FP64)
+    mixed = family_params(povar, povar.MIXED_FP32, args.schedule)
+    fp64 = family_params(povar, povar.FP64, args.schedule)
     m_table = None
     if args.m_table:
         with open(args.m_table) as f:
