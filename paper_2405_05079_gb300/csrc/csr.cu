@@ -940,6 +940,7 @@ povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
   for (const Grp& g : groups) {
     std::vector<uint32_t> width;
     uint32_t mrow = 0;
+    const size_t sbase = sinfo.size();
     for (uint32_t sidx : g.sl) {
       gsl.push_back(sidx);
       const uint32_t w = (off[sidx + 1] - off[sidx]) / SLICE;
@@ -950,6 +951,7 @@ povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
       for (uint32_t k = 0; k < w; ++k) grouped_part[rbase[r0 + k]] = 1;   // uniform: one partial
       g_obs_rows += w;
     }
+    sinfo.resize(sbase + 4 * (size_t)G5_SLICES, 0u);   // G5_SLICES entries per group
     goff.push_back((uint32_t)gsl.size());
     bool consecutive = !g.cam.empty();
     for (size_t k = 1; consecutive && k < g.cam.size(); ++k)

@@ -193,8 +193,9 @@ struct Problem {
   uint32_t* g5_ioff = nullptr;       // [ngroups + 1] items of group g
   uint32_t* g5_items = nullptr;      // (row << 16) | (first slice << 8) | end slice
   uint32_t* g5_rest = nullptr;       // [nrest] slices outside groups
-  uint32_t* g5_sinfo = nullptr;      // [4 * grouped slices] slice, first SELL entry, width,
-                                     // first staged measurement row (g5_slices order)
+  uint32_t* g5_sinfo = nullptr;      // [4 * G5_SLICES * ngroups] per group and slice: slice,
+                                     // first SELL entry, width, first staged measurement
+                                     // row (zero past the group's slices)
   int32_t* g5_ghdr = nullptr;        // [2 * ngroups] staged measurement rows, first row
                                      // camera when the rows' cameras are consecutive (else -1)
   uint32_t* cam5_off = nullptr;      // [nc + 1]

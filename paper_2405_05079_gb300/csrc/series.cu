@@ -1153,7 +1153,7 @@ __device__ __forceinline__ void srow<double>(const double* tab, uint32_t k, int 
 // mbarrier; camera rows P and Y per group row; staged measurements
 // (G5_MROWS rows of 32); staged landmark records; s_j (3 planes); staged
 // track lengths; per slice its index, first SELL entry, width and first
-// staged measurement row.
+// staged measurement row; the group's work items.
 template <typename T> struct G5Layout {
   using M2 = typename Vt<T>::m2;
   static constexpr size_t BAR = 0;
@@ -1164,8 +1164,11 @@ template <typename T> struct G5Layout {
   static constexpr size_t S = PD + G5Pd<T>::BYTES;
   static constexpr size_t LEN = S + 3 * (size_t)G5_SLICES * SLICE * sizeof(T);
   static constexpr size_t INFO = LEN + (size_t)G5_SLICES * SLICE * sizeof(uint32_t);
-  static constexpr size_t BYTES = INFO + 4 * (size_t)G5_SLICES * sizeof(uint32_t);
+  static constexpr size_t ITEMS = INFO + 4 * (size_t)G5_SLICES * sizeof(uint32_t);
+  static constexpr size_t BYTES = ITEMS + (size_t)G5_ROWS * sizeof(uint32_t);
 };
+// one item per group row: a row's slices (at most G5_SLICES) fit one item
+static_assert(G5_SLICES <= G5_ITEM, "at most G5_ROWS items per group");
 template <typename T>
 constexpr size_t g5_smem_bytes() {
   return G5Layout<T>::BYTES;
@@ -1180,8 +1183,8 @@ struct G5Tables {
   const uint32_t* ioff;    // [ngroups + 1] items of group g
   const uint32_t* items;   // (row << 16) | (first slice << 8) | end slice
   const uint32_t* rest;    // slices outside groups
-  const uint4* sinfo;      // per grouped slice: slice, first SELL entry, width, first
-                           // staged measurement row (slices order)
+  const uint4* sinfo;      // per group G5_SLICES entries (zero past its slices): slice,
+                           // first SELL entry, width, first staged measurement row
   const int2* ghdr;        // per group: staged measurement rows, first row camera if the
                            // rows' cameras are consecutive (else -1)
   int ngroups;
@@ -1207,9 +1210,13 @@ __device__ __forceinline__ void g5_group_block(
   uint32_t* s_off = s_idx + G5_SLICES;
   uint32_t* s_w = s_off + G5_SLICES;
   uint32_t* s_mrow = s_w + G5_SLICES;
+  uint32_t* s_items = reinterpret_cast<uint32_t*>(sm + L::ITEMS);
   const int g = blockIdx.x, lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const uint32_t sb = tb.off[g], ns = tb.off[g + 1] - sb;
-  const uint32_t rb = tb.roff[g], nr = tb.roff[g + 1] - rb;
+  // the group's table entries are at fixed offsets from g: one round of
+  // independent loads before the copies are issued
+  const uint32_t ns = __ldg(tb.off + g + 1) - __ldg(tb.off + g);
+  const uint32_t rb = __ldg(tb.roff + g), nr = __ldg(tb.roff + g + 1) - rb;
+  const uint32_t ib = __ldg(tb.ioff + g), ni = __ldg(tb.ioff + g + 1) - ib;
   const int2 hdr = __ldg(tb.ghdr + g);   // staged measurement rows, first row camera
 
   if (wl == 0) {
@@ -1218,7 +1225,8 @@ __device__ __forceinline__ void g5_group_block(
     // G5_MROWS); lane 0 sets the expected byte count, then lane j issues the
     // bulk copies of slice j, and lane 0 those of the group's camera rows
     // when their cameras are consecutive
-    const uint4 info = (uint32_t)lane < ns ? __ldg(tb.sinfo + sb + lane) : make_uint4(0, 0, 0, 0);
+    const uint4 info = lane < G5_SLICES ? __ldg(tb.sinfo + (size_t)g * G5_SLICES + lane)
+                                        : make_uint4(0, 0, 0, 0);
     if ((uint32_t)lane < ns) {
       s_idx[lane] = info.x;
       s_off[lane] = info.y;
@@ -1244,6 +1252,8 @@ __device__ __forceinline__ void g5_group_block(
       bulk_g2s(cY, vec + 12 * (size_t)hdr.y, nr * 12u * (uint32_t)sizeof(T), bar);
     }
   }
+  // the group's work items while the copies are in flight
+  for (uint32_t q = threadIdx.x; q < ni; q += G5_THREADS) s_items[q] = __ldg(tb.items + ib + q);
   if (hdr.y < 0) {
     // camera rows of the group rows (not consecutive cameras) while the
     // copies are in flight
@@ -1304,9 +1314,8 @@ __device__ __forceinline__ void g5_group_block(
   __syncthreads();
 
   // phase 2: one partial per work item
-  const uint32_t ib = tb.ioff[g], ni = tb.ioff[g + 1] - ib;
   for (uint32_t it = wl; it < ni; it += NW) {
-    const uint32_t item = __ldg(tb.items + ib + it);
+    const uint32_t item = s_items[it];
     const uint32_t k = item >> 16, j0 = (item >> 8) & 0xffu, j1 = item & 0xffu;
     T P0[4], P1[4], P2[4];
     srow<T>(cP, k, 0, P0);
