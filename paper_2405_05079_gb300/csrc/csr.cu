@@ -972,21 +972,33 @@ povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
     ioff.push_back((uint32_t)items.size());
   }
   const int64_t nitems = (int64_t)items.size();
-  // per camera: its items in item order, then its remaining run partials
-  std::vector<uint32_t> c5off((size_t)p->nc + 1, 0), c5idx;
+  // per camera: its items in item order, then its remaining run partials.
+  // An item's partial is written at its list position (idest), so a list
+  // entry of an item indexes itself; run partials follow all lists.
+  std::vector<uint32_t> c5off((size_t)p->nc + 1, 0), c5idx, c5nd((size_t)p->nc, 0),
+      idest((size_t)nitems);
+  int64_t nlist = nitems;
+  for (int64_t e = 0; e < p->npart; ++e) nlist += grouped_part[(size_t)e] ? 0 : 1;
   {
     std::vector<std::vector<uint32_t>> per((size_t)p->nc);
     for (int64_t q = 0; q < nitems; ++q) per[(size_t)item_cam[(size_t)q]].push_back((uint32_t)q);
     for (int c = 0; c < p->nc; ++c) {
-      for (uint32_t q : per[(size_t)c]) c5idx.push_back(q);
+      for (uint32_t q : per[(size_t)c]) {
+        idest[q] = (uint32_t)c5idx.size();
+        c5idx.push_back(idest[q]);
+      }
+      c5nd[(size_t)c] = (uint32_t)per[(size_t)c].size();
       for (uint32_t e = poff[c]; e < poff[c + 1]; ++e)
-        if (!grouped_part[pidx[e]]) c5idx.push_back((uint32_t)nitems + pidx[e]);
+        if (!grouped_part[pidx[e]]) c5idx.push_back((uint32_t)nlist + pidx[e]);
       c5off[(size_t)c + 1] = (uint32_t)c5idx.size();
     }
   }
+  if ((int64_t)c5idx.size() != nlist || nlist + p->npart >= ((int64_t)1 << 32))
+    return fail(p, POVAR_EINVAL, "group schedule: partial list size");
   p->g5_ngroups = (int32_t)groups.size();
   p->g5_nrest = (int32_t)rest.size();
   p->g5_nitems = nitems;
+  p->g5_nlist = nlist;
   p->g5_nslices = (int64_t)gsl.size();
   p->g5_obs = g_obs_rows;
   povar_status s;
@@ -999,7 +1011,9 @@ povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
       (s = up32(&p->g5_roff, roff, "g5_roff")) || (s = up32(&p->g5_ioff, ioff, "g5_ioff")) ||
       (s = up32(&p->g5_items, items, "g5_items")) || (s = up32(&p->g5_rest, rest, "g5_rest")) ||
       (s = up32(&p->cam5_off, c5off, "cam5_off")) || (s = up32(&p->cam5_idx, c5idx, "cam5_idx")) ||
-      (s = up32(&p->g5_sinfo, sinfo, "g5_sinfo")))
+      (s = up32(&p->g5_sinfo, sinfo, "g5_sinfo")) ||
+      (s = up32(&p->g5_idest, idest, "g5_idest")) ||
+      (s = up32(&p->cam5_ndirect, c5nd, "cam5_ndirect")))
     return s;
   if ((s = dev_alloc(p, &p->g5_ghdr, std::max<size_t>(ghdr.size(), 2), "g5_ghdr"))) return s;
   if (!ghdr.empty()) POVAR_COPY(p->g5_ghdr, ghdr.data(), ghdr.size(), cudaMemcpyHostToDevice);
@@ -1008,7 +1022,7 @@ povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
   if (!rowcam.empty())
     POVAR_COPY(p->g5_rowcam, rowcam.data(), rowcam.size(), cudaMemcpyHostToDevice);
   if ((s = dev_alloc_bytes(p, &p->part5,
-                           (size_t)(nitems + (int64_t)p->npart) * 12 * sizeof(double), "part5")))
+                           (size_t)(nlist + (int64_t)p->npart) * 12 * sizeof(double), "part5")))
     return s;
   return setup_group_kernels(p);
 }

@@ -183,15 +183,18 @@ struct Problem {
   // that see the same camera at every row index; work items (row, slice
   // range) of each group; slices outside groups (g5_rest) run the fused pass;
   // per camera the item partials, then the run partials of its rows outside
-  // groups (offset by g5_nitems), in a fixed order
+  // groups, in a fixed order; an item's partial is stored at its position
+  // in these lists (g5_idest), the run partials after all lists (offset by
+  // g5_nlist)
   int32_t g5_ngroups = 0, g5_nrest = 0;
-  int64_t g5_nitems = 0, g5_nslices = 0, g5_obs = 0;
+  int64_t g5_nitems = 0, g5_nslices = 0, g5_obs = 0, g5_nlist = 0;
   uint32_t* g5_off = nullptr;        // [ngroups + 1] slices of group g in g5_slices
   uint32_t* g5_slices = nullptr;     // [grouped slices] slice indices, widest first
   uint32_t* g5_roff = nullptr;       // [ngroups + 1] rows of group g in g5_rowcam
   int32_t* g5_rowcam = nullptr;      // camera of each group row
   uint32_t* g5_ioff = nullptr;       // [ngroups + 1] items of group g
   uint32_t* g5_items = nullptr;      // (row << 16) | (first slice << 8) | end slice
+  uint32_t* g5_idest = nullptr;      // [nitems] list position of each item's partial
   uint32_t* g5_rest = nullptr;       // [nrest] slices outside groups
   uint32_t* g5_sinfo = nullptr;      // [4 * G5_SLICES * ngroups] per group and slice: slice,
                                      // first SELL entry, width, first staged measurement
@@ -199,8 +202,10 @@ struct Problem {
   int32_t* g5_ghdr = nullptr;        // [2 * ngroups] staged measurement rows, first row
                                      // camera when the rows' cameras are consecutive (else -1)
   uint32_t* cam5_off = nullptr;      // [nc + 1]
-  uint32_t* cam5_idx = nullptr;
-  void* part5 = nullptr;             // [(nitems + npart) * 12] float or double
+  uint32_t* cam5_idx = nullptr;      // [nlist] partial of each list entry (an item's own
+                                     // position, or nlist + run partial index)
+  uint32_t* cam5_ndirect = nullptr;  // [nc] item partials at the head of camera i's list
+  void* part5 = nullptr;             // [(nlist + npart) * 12] float or double
   // stored series blocks per kind (0 FP64, 1 FP32, 2 BF16), allocated at
   // first use and rebuilt by every step that runs the stored schedule
   void* blk[3] = {nullptr, nullptr, nullptr};

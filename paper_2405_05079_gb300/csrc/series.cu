@@ -1153,7 +1153,8 @@ __device__ __forceinline__ void srow<double>(const double* tab, uint32_t k, int 
 // mbarrier; camera rows P and Y per group row; staged measurements
 // (G5_MROWS rows of 32); staged landmark records; s_j (3 planes); staged
 // track lengths; per slice its index, first SELL entry, width and first
-// staged measurement row; the group's work items.
+// staged measurement row; the group's work items and their partials'
+// positions.
 template <typename T> struct G5Layout {
   using M2 = typename Vt<T>::m2;
   static constexpr size_t BAR = 0;
@@ -1165,7 +1166,8 @@ template <typename T> struct G5Layout {
   static constexpr size_t LEN = S + 3 * (size_t)G5_SLICES * SLICE * sizeof(T);
   static constexpr size_t INFO = LEN + (size_t)G5_SLICES * SLICE * sizeof(uint32_t);
   static constexpr size_t ITEMS = INFO + 4 * (size_t)G5_SLICES * sizeof(uint32_t);
-  static constexpr size_t BYTES = ITEMS + (size_t)G5_ROWS * sizeof(uint32_t);
+  static constexpr size_t IDEST = ITEMS + (size_t)G5_ROWS * sizeof(uint32_t);
+  static constexpr size_t BYTES = IDEST + (size_t)G5_ROWS * sizeof(uint32_t);
 };
 // one item per group row: a row's slices (at most G5_SLICES) fit one item
 static_assert(G5_SLICES <= G5_ITEM, "at most G5_ROWS items per group");
@@ -1182,6 +1184,7 @@ struct G5Tables {
   const int32_t* rowcam;   // camera of each group row
   const uint32_t* ioff;    // [ngroups + 1] items of group g
   const uint32_t* items;   // (row << 16) | (first slice << 8) | end slice
+  const uint32_t* idest;   // per item: position of its partial (camera order)
   const uint32_t* rest;    // slices outside groups
   const uint4* sinfo;      // per group G5_SLICES entries (zero past its slices): slice,
                            // first SELL entry, width, first staged measurement row
@@ -1194,8 +1197,9 @@ template <typename T>
 __device__ __forceinline__ void g5_group_block(
     DeviceState* __restrict__ st, T a, const uint32_t* __restrict__ slot_len,
     const uint32_t* __restrict__ sell_off, const typename Vt<T>::m2* __restrict__ sell_m,
-    const T* __restrict__ camP, const T* __restrict__ vec, const PointData<T>& pd,
-    const G5Tables& tb, T* __restrict__ part, unsigned char* sm) {
+    const T* __restrict__ camPa, const T* __restrict__ camPb, const T* __restrict__ vec,
+    const PointData<T>& pd0, const PointData<T>& pd1, const G5Tables& tb, T* __restrict__ part,
+    unsigned char* sm) {
   using L = G5Layout<T>;
   using M2 = typename Vt<T>::m2;
   constexpr int NW = G5_THREADS / 32;
@@ -1211,13 +1215,21 @@ __device__ __forceinline__ void g5_group_block(
   uint32_t* s_w = s_off + G5_SLICES;
   uint32_t* s_mrow = s_w + G5_SLICES;
   uint32_t* s_items = reinterpret_cast<uint32_t*>(sm + L::ITEMS);
+  uint32_t* s_dest = reinterpret_cast<uint32_t*>(sm + L::IDEST);
   const int g = blockIdx.x, lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  // the group's table entries are at fixed offsets from g: one round of
-  // independent loads before the copies are issued
+  // the group's table entries are at fixed offsets from g, so they load in
+  // one round together with the state flags, before the copies are issued
   const uint32_t ns = __ldg(tb.off + g + 1) - __ldg(tb.off + g);
   const uint32_t rb = __ldg(tb.roff + g), nr = __ldg(tb.roff + g + 1) - rb;
   const uint32_t ib = __ldg(tb.ioff + g), ni = __ldg(tb.ioff + g + 1) - ib;
   const int2 hdr = __ldg(tb.ghdr + g);   // staged measurement rows, first row camera
+  const uint4 info = wl == 0 && lane < G5_SLICES
+                         ? __ldg(tb.sinfo + (size_t)g * G5_SLICES + lane)
+                         : make_uint4(0, 0, 0, 0);
+  if (st->converged || st->stop_series) return;
+  const bool cur = st->cur != 0;
+  const T* __restrict__ camP = cur ? camPb : camPa;
+  const PointData<T>& pd = cur ? pd1 : pd0;
 
   if (wl == 0) {
     // lane j < ns: slice j's table entry (slice, first SELL entry, width,
@@ -1225,8 +1237,6 @@ __device__ __forceinline__ void g5_group_block(
     // G5_MROWS); lane 0 sets the expected byte count, then lane j issues the
     // bulk copies of slice j, and lane 0 those of the group's camera rows
     // when their cameras are consecutive
-    const uint4 info = lane < G5_SLICES ? __ldg(tb.sinfo + (size_t)g * G5_SLICES + lane)
-                                        : make_uint4(0, 0, 0, 0);
     if ((uint32_t)lane < ns) {
       s_idx[lane] = info.x;
       s_off[lane] = info.y;
@@ -1253,7 +1263,10 @@ __device__ __forceinline__ void g5_group_block(
     }
   }
   // the group's work items while the copies are in flight
-  for (uint32_t q = threadIdx.x; q < ni; q += G5_THREADS) s_items[q] = __ldg(tb.items + ib + q);
+  for (uint32_t q = threadIdx.x; q < ni; q += G5_THREADS) {
+    s_items[q] = __ldg(tb.items + ib + q);
+    s_dest[q] = __ldg(tb.idest + ib + q);
+  }
   if (hdr.y < 0) {
     // camera rows of the group rows (not consecutive cameras) while the
     // copies are in flight
@@ -1340,7 +1353,7 @@ __device__ __forceinline__ void g5_group_block(
     int vb;
     warp_reduce12<T>(v, lane, r, vb);
     if ((lane & 7) == 0) {
-      T* out = part + (size_t)(ib + it) * 12 + vb;
+      T* out = part + (size_t)s_dest[it] * 12 + vb;
       out[0] = r[0];
       out[1] = r[1];
       out[2] = r[2];
@@ -1436,8 +1449,8 @@ __device__ __forceinline__ void g5_rest_block(
 }
 
 // Blocks [0, ngroups) run the groups, the next ones the slices outside
-// groups. part holds the item partials, followed by the run partials
-// (part_run).
+// groups. part holds the item partials at their positions in the per-camera
+// lists; the run partials of the slices outside groups go to part_run.
 template <typename T>
 __global__ void __launch_bounds__(G5_THREADS, sizeof(T) == 4 ? 1024 / G5_THREADS : 1)
 k_series_group(DeviceState* __restrict__ st, T a, const uint32_t* __restrict__ slot_len,
@@ -1447,15 +1460,17 @@ k_series_group(DeviceState* __restrict__ st, T a, const uint32_t* __restrict__ s
                PointData<T> pd1, G5Tables tb, const uint32_t* __restrict__ row_mask,
                const uint32_t* __restrict__ row_base, T* __restrict__ part,
                T* __restrict__ part_run) {
-  if (st->converged || st->stop_series) return;
   extern __shared__ __align__(16) unsigned char g5_smem[];
-  const T* __restrict__ camP = st->cur ? camPb : camPa;
-  const PointData<T>& pd = st->cur ? pd1 : pd0;
-  if ((int)blockIdx.x < tb.ngroups)
-    g5_group_block<T>(st, a, slot_len, sell_off, sell_m, camP, vec, pd, tb, part, g5_smem);
-  else
+  if ((int)blockIdx.x < tb.ngroups) {
+    g5_group_block<T>(st, a, slot_len, sell_off, sell_m, camPa, camPb, vec, pd0, pd1, tb, part,
+                      g5_smem);
+  } else {
+    if (st->converged || st->stop_series) return;
+    const T* __restrict__ camP = st->cur ? camPb : camPa;
+    const PointData<T>& pd = st->cur ? pd1 : pd0;
     g5_rest_block<T>(a, slot_len, sell_off, sell_cam, sell_m, camP, vec, pd, row_mask, row_base,
                      __ldg(tb.rest + (blockIdx.x - tb.ngroups)), part_run, g5_smem);
+  }
 }
 
 // Per camera (one warp): z_i = sum of its partials in index order, then the
@@ -1549,21 +1564,29 @@ __device__ __forceinline__ void stop_check(DeviceState* __restrict__ st, int ter
 // Blocks per SM: twelve in FP32 (40 registers, a few spilled), so that a
 // camera count up to 12 x the SM count (1,824 on 152 SMs) runs in one wave
 // instead of 1.3; six in FP64 (80 registers, as without a bound).
+//
+// With cam_ndirect (group schedule), the first cam_ndirect[i] entries of
+// camera i's list are partials stored at their own list position (entry q
+// reads part[q], the index table holds q there), so they are read without
+// the index load; the others through the index table.
 template <typename T>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 6)
 k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
                const uint32_t* __restrict__ cam_part_off, const uint32_t* __restrict__ cam_part_idx,
-               const T* __restrict__ part, const T* __restrict__ G, double* __restrict__ camnorm,
+               const uint32_t* __restrict__ cam_ndirect, const T* __restrict__ part,
+               const T* __restrict__ G, double* __restrict__ camnorm,
                uint32_t* __restrict__ done_ticket, T* __restrict__ Y, T* __restrict__ D) {
   // one block of 4 warps per camera: each warp adds a strided quarter of the
   // camera's partials, the four warp sums are combined in a fixed order;
   // warp 0 loads the camera's row of G and of delta before the partials
   // arrive, so the update waits on no further load
-  if (st->converged || st->stop_series) return;
   __shared__ T sh[4][12];
   __shared__ int sh_last;
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int i = blockIdx.x;
+  const uint32_t b = __ldg(cam_part_off + i), e_ = __ldg(cam_part_off + i + 1);
+  const uint32_t bd = cam_ndirect ? b + __ldg(cam_ndirect + i) : b;
+  if (st->converged || st->stop_series) return;
   T g[12], dprev = 0;
   if (wl == 0) {
     Row12<T>::load(G + 144 * (size_t)i + 12 * (lane < 12 ? lane : 0), g);
@@ -1572,14 +1595,14 @@ k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
   T acc[12];
 #pragma unroll
   for (int e = 0; e < 12; ++e) acc[e] = 0;
-  const uint32_t b = cam_part_off[i], e_ = cam_part_off[i + 1];
   uint32_t q = b + threadIdx.x;
   for (; q + 128 < e_; q += 256) {
-    const uint32_t i0 = __ldg(cam_part_idx + q), i1 = __ldg(cam_part_idx + q + 128);
+    const uint32_t i0 = q < bd ? q : __ldg(cam_part_idx + q);
+    const uint32_t i1 = q + 128 < bd ? q + 128 : __ldg(cam_part_idx + q + 128);
     Rec12<T>::add(part + (size_t)i0 * 12, acc);
     Rec12<T>::add(part + (size_t)i1 * 12, acc);
   }
-  if (q < e_) Rec12<T>::add(part + (size_t)__ldg(cam_part_idx + q) * 12, acc);
+  if (q < e_) Rec12<T>::add(part + (size_t)(q < bd ? q : __ldg(cam_part_idx + q)) * 12, acc);
   {
     T r[3];
     int vb;
@@ -2085,7 +2108,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
           p->P64[1], p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1),
           p->row_mask, p->row_base, static_cast<double*>(p->part_run), bp);
       k_series_apply<double><<<ga, 128, 0, p->stream>>>(
-          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
+          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx, nullptr,
           static_cast<const double*>(p->part_run), p->G64, p->camnorm, p->done_ticket,
           p->Y64 + yoff_out, p->D64);
     } else {
@@ -2100,7 +2123,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
             p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1),
             p->row_mask, p->row_base, static_cast<float*>(p->part_run), bp);
       k_series_apply<float><<<ga, 128, 0, p->stream>>>(
-          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
+          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx, nullptr,
           static_cast<const float*>(p->part_run), p->G32, p->camnorm, p->done_ticket,
           p->Y32 + yoff_out, p->D32);
     }
@@ -2111,9 +2134,9 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
     // one launch for the groups and the slices outside groups (run partials
     // after the item partials), then the per-camera sums
     const unsigned gb = (unsigned)(p->g5_ngroups + p->g5_nrest);
-    const int64_t nit = p->g5_nitems;
+    const int64_t nit = p->g5_nlist;
     const G5Tables tb{p->g5_off,  p->g5_slices, p->g5_roff, p->g5_rowcam,
-                      p->g5_ioff, p->g5_items,  p->g5_rest,
+                      p->g5_ioff, p->g5_items,  p->g5_idest, p->g5_rest,
                       reinterpret_cast<const uint4*>(p->g5_sinfo),
                       reinterpret_cast<const int2*>(p->g5_ghdr), p->g5_ngroups};
     if (precision == POVAR_FP64) {
@@ -2124,7 +2147,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
             p->P64[1], p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1), tb,
             p->row_mask, p->row_base, part, part + nit * 12);
       k_series_apply<double><<<p->nc, 128, 0, p->stream>>>(
-          p->state, term, eps, p->nc, p->cam5_off, p->cam5_idx, part, p->G64, p->camnorm,
+          p->state, term, eps, p->nc, p->cam5_off, p->cam5_idx, p->cam5_ndirect, part, p->G64, p->camnorm,
           p->done_ticket, p->Y64 + yoff_out, p->D64);
     } else {
       float* part = static_cast<float*>(p->part5);
@@ -2134,7 +2157,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
             p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1), tb,
             p->row_mask, p->row_base, part, part + nit * 12);
       k_series_apply<float><<<p->nc, 128, 0, p->stream>>>(
-          p->state, term, eps, p->nc, p->cam5_off, p->cam5_idx, part, p->G32, p->camnorm,
+          p->state, term, eps, p->nc, p->cam5_off, p->cam5_idx, p->cam5_ndirect, part, p->G32, p->camnorm,
           p->done_ticket, p->Y32 + yoff_out, p->D32);
     }
     p->launches += 1 + (gb > 0);
@@ -2173,7 +2196,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
             p->grp_slice0, p->grp_row0, p->ngroups, p->grow_cam, p->grow_base, p->srow_mask,
             p->srow_base, static_cast<double*>(p->part3));
       k_series_apply<double><<<p->nc, 128, 0, p->stream>>>(
-          p->state, term, eps, p->nc, p->cam_part3_off, p->cam_part3_idx,
+          p->state, term, eps, p->nc, p->cam_part3_off, p->cam_part3_idx, nullptr,
           static_cast<const double*>(p->part3), p->G64, p->camnorm, p->done_ticket,
           p->Y64 + yoff_out, p->D64);
     } else {
@@ -2184,7 +2207,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
             p->grp_slice0, p->grp_row0, p->ngroups, p->grow_cam, p->grow_base, p->srow_mask,
             p->srow_base, static_cast<float*>(p->part3));
       k_series_apply<float><<<p->nc, 128, 0, p->stream>>>(
-          p->state, term, eps, p->nc, p->cam_part3_off, p->cam_part3_idx,
+          p->state, term, eps, p->nc, p->cam_part3_off, p->cam_part3_idx, nullptr,
           static_cast<const float*>(p->part3), p->G32, p->camnorm, p->done_ticket,
           p->Y32 + yoff_out, p->D32);
     }
@@ -2199,7 +2222,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
           p->P64[1], p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1), p->row_mask,
           p->row_base, static_cast<double*>(p->part_run), BlockPlanes{});
       k_series_apply<double><<<ga, 128, 0, p->stream>>>(
-          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
+          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx, nullptr,
           static_cast<const double*>(p->part_run), p->G64, p->camnorm, p->done_ticket, p->Y64 + yoff_out,
           p->D64);
     } else {
@@ -2208,7 +2231,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
           p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1), p->row_mask,
           p->row_base, static_cast<float*>(p->part_run), BlockPlanes{});
       k_series_apply<float><<<ga, 128, 0, p->stream>>>(
-          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx,
+          p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx, nullptr,
           static_cast<const float*>(p->part_run), p->G32, p->camnorm, p->done_ticket, p->Y32 + yoff_out,
           p->D32);
     }
@@ -2347,11 +2370,11 @@ povar_status launch_series_apply(Problem* p, int precision, int term, double eps
   const size_t yoff_out = (term & 1) * (size_t)p->nc * 12;
   if (precision == POVAR_FP64)
     k_series_apply<double><<<p->nc, 128, 0, p->stream>>>(
-        p->state, term, eps, p->nc, off, idx, static_cast<const double*>(part), p->G64,
+        p->state, term, eps, p->nc, off, idx, nullptr, static_cast<const double*>(part), p->G64,
         p->camnorm, p->done_ticket, p->Y64 + yoff_out, p->D64);
   else
     k_series_apply<float><<<p->nc, 128, 0, p->stream>>>(
-        p->state, term, eps, p->nc, off, idx, static_cast<const float*>(part), p->G32,
+        p->state, term, eps, p->nc, off, idx, nullptr, static_cast<const float*>(part), p->G32,
         p->camnorm, p->done_ticket, p->Y32 + yoff_out, p->D32);
   ++p->launches;
   return check_launch(p, "series_apply");
