@@ -105,6 +105,10 @@ struct DeviceState {
   double pcg_gg;      // g^T g (stop test ||r|| <= eps ||g||)
   double pcg_alpha;   // step length of the current iteration
   double pcg_beta;    // direction update coefficient
+  // series threshold rule checked one term late (group schedule): set by
+  // the term-t group launch when the rule held after term t - 1, so that
+  // term t's camera finish ends the series instead of updating
+  int series_halt;
 };
 
 // Host-side handle.

@@ -1041,6 +1041,54 @@ k_s2_fused(const DeviceState* __restrict__ st, const uint32_t* __restrict__ slot
 // both kinds of partials per camera in a fixed order.
 // ---------------------------------------------------------------------------
 
+// All cameras' squared norms summed by threads [0, 32 NW) of the block in a
+// fixed order (thread t takes cameras t, t + 32 NW, ...; the warps are
+// combined in index order); the sums are valid in thread 0. Every thread of
+// the block calls it (it holds a block barrier).
+template <int NW>
+__device__ __forceinline__ void camera_norm_sums(const double* __restrict__ camnorm, int nc,
+                                                 double (*shn)[2], double& sy_out,
+                                                 double& sd_out) {
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  double sy = 0.0, sd = 0.0;
+  if (wl < NW) {
+    for (int c0 = (int)threadIdx.x; c0 < nc; c0 += 4 * NW * 32) {
+      double vy[4], vd[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u * NW * 32;
+        vy[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c) : 0.0;
+        vd[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c + 1) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        sy += vy[u];
+        sd += vd[u];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    }
+    if (lane == 0) {
+      shn[wl][0] = sy;
+      shn[wl][1] = sd;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sy = 0.0;
+    sd = 0.0;
+    for (int w = 0; w < NW; ++w) {
+      sy += shn[w][0];
+      sd += shn[w][1];
+    }
+  }
+  sy_out = sy;
+  sd_out = sd;
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -1448,6 +1496,21 @@ __device__ __forceinline__ void g5_rest_block(
   }
 }
 
+// The threshold rule of the series for the previous term (term - 1 >= 1),
+// checked by block 0 of the term's group launch: the same sums in the same
+// order as the last camera block of a per-camera finish would take them
+// (camera_norm_sums over 4 warps); sets series_halt, which the term's
+// camera finish reads. The finish kernels then need no ticket.
+__device__ __forceinline__ void series_halt_check(DeviceState* __restrict__ st, int term,
+                                                  double eps,
+                                                  const double* __restrict__ camnorm, int nc) {
+  __shared__ double shn[4][2];
+  const bool check = term >= 2 && eps > 0.0 && !(st->converged || st->stop_series);
+  double sy = 0.0, sd = 0.0;
+  if (check) camera_norm_sums<4>(camnorm, nc, shn, sy, sd);
+  if (threadIdx.x == 0) st->series_halt = check && sy <= eps * eps * sd ? 1 : 0;
+}
+
 // Blocks [0, ngroups) run the groups, the next ones the slices outside
 // groups. part holds the item partials at their positions in the per-camera
 // lists; the run partials of the slices outside groups go to part_run.
@@ -1459,8 +1522,10 @@ k_series_group(DeviceState* __restrict__ st, T a, const uint32_t* __restrict__ s
                const T* __restrict__ camPb, const T* __restrict__ vec, PointData<T> pd0,
                PointData<T> pd1, G5Tables tb, const uint32_t* __restrict__ row_mask,
                const uint32_t* __restrict__ row_base, T* __restrict__ part,
-               T* __restrict__ part_run) {
+               T* __restrict__ part_run, int term, double eps,
+               const double* __restrict__ camnorm, int nc) {
   extern __shared__ __align__(16) unsigned char g5_smem[];
+  if (blockIdx.x == 0) series_halt_check(st, term, eps, camnorm, nc);
   if ((int)blockIdx.x < tb.ngroups) {
     g5_group_block<T>(st, a, slot_len, sell_off, sell_m, camPa, camPb, vec, pd0, pd1, tb, part,
                       g5_smem);
@@ -1502,16 +1567,14 @@ template <> struct Rec12<double> {
 // Threshold rule of the series (stop after term k when ||x_k|| <= eps
 // ||delta_k||): every camera block stores the two squared norms of its
 // camera; the block that arrives last on the ticket adds all cameras'
-// norms with all of its NW warps in a fixed order (thread t takes cameras
-// t, t + 32 NW, ...; the warps are combined in index order) and sets the
-// stop flag. Thread 0 of the block holds the camera's norms on entry.
+// norms (camera_norm_sums) and sets the stop flag. Thread 0 of the block
+// holds the camera's norms on entry.
 template <int NW>
 __device__ __forceinline__ void stop_check(DeviceState* __restrict__ st, int term, double eps,
                                            int nc, int i, double yy, double dd,
                                            double* __restrict__ camnorm,
                                            uint32_t* __restrict__ done_ticket, int* sh_last,
                                            double (*shn)[2]) {
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     camnorm[2 * (size_t)i] = yy;
     camnorm[2 * (size_t)i + 1] = dd;
@@ -1521,38 +1584,9 @@ __device__ __forceinline__ void stop_check(DeviceState* __restrict__ st, int ter
   __syncthreads();
   if (!*sh_last) return;
   __threadfence();
-  double sy = 0.0, sd = 0.0;
-  for (int c0 = (int)threadIdx.x; c0 < nc; c0 += 4 * NW * 32) {
-    double vy[4], vd[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = c0 + u * NW * 32;
-      vy[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c) : 0.0;
-      vd[u] = c < nc ? __ldcg(camnorm + 2 * (size_t)c + 1) : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      sy += vy[u];
-      sd += vd[u];
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sy += __shfl_xor_sync(0xffffffffu, sy, o);
-    sd += __shfl_xor_sync(0xffffffffu, sd, o);
-  }
-  if (lane == 0) {
-    shn[wl][0] = sy;
-    shn[wl][1] = sd;
-  }
-  __syncthreads();
+  double sy, sd;
+  camera_norm_sums<NW>(camnorm, nc, shn, sy, sd);
   if (threadIdx.x == 0) {
-    sy = 0.0;
-    sd = 0.0;
-    for (int w = 0; w < NW; ++w) {
-      sy += shn[w][0];
-      sd += shn[w][1];
-    }
     *done_ticket = 0;
     if (sy <= eps * eps * sd) {
       st->stop_series = 1;
@@ -1575,7 +1609,8 @@ k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
                const uint32_t* __restrict__ cam_part_off, const uint32_t* __restrict__ cam_part_idx,
                const uint32_t* __restrict__ cam_ndirect, const T* __restrict__ part,
                const T* __restrict__ G, double* __restrict__ camnorm,
-               uint32_t* __restrict__ done_ticket, T* __restrict__ Y, T* __restrict__ D) {
+               uint32_t* __restrict__ done_ticket, T* __restrict__ Y, T* __restrict__ D,
+               int late_check) {
   // one block of 4 warps per camera: each warp adds a strided quarter of the
   // camera's partials, the four warp sums are combined in a fixed order;
   // warp 0 loads the camera's row of G and of delta before the partials
@@ -1587,6 +1622,15 @@ k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
   const uint32_t b = __ldg(cam_part_off + i), e_ = __ldg(cam_part_off + i + 1);
   const uint32_t bd = cam_ndirect ? b + __ldg(cam_ndirect + i) : b;
   if (st->converged || st->stop_series) return;
+  if (late_check && st->series_halt) {
+    // the threshold rule held after the previous term (checked by this
+    // term's group launch): the series ends with that term
+    if (i == 0 && threadIdx.x == 0) {
+      st->stop_series = 1;
+      st->terms_used = term;
+    }
+    return;
+  }
   T g[12], dprev = 0;
   if (wl == 0) {
     Row12<T>::load(G + 144 * (size_t)i + 12 * (lane < 12 ? lane : 0), g);
@@ -1641,6 +1685,14 @@ k_series_apply(DeviceState* __restrict__ st, int term, double eps, int nc,
     dd = (double)d2;
   }
   if (eps <= 0.0) return;
+  if (late_check) {
+    // the next term's group launch adds the norms (camera_norm_sums)
+    if (threadIdx.x == 0) {
+      camnorm[2 * (size_t)i] = yy;
+      camnorm[2 * (size_t)i + 1] = dd;
+    }
+    return;
+  }
   stop_check<NWARPS>(st, term, eps, nc, i, yy, dd, camnorm, done_ticket, &sh_last, shn);
 }
 
@@ -2110,7 +2162,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
       k_series_apply<double><<<ga, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx, nullptr,
           static_cast<const double*>(p->part_run), p->G64, p->camnorm, p->done_ticket,
-          p->Y64 + yoff_out, p->D64);
+          p->Y64 + yoff_out, p->D64, 0);
     } else {
       if (precision == POVAR_MIXED_BF16)
         k_series_fused<float, Bf16><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
@@ -2125,7 +2177,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
       k_series_apply<float><<<ga, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx, nullptr,
           static_cast<const float*>(p->part_run), p->G32, p->camnorm, p->done_ticket,
-          p->Y32 + yoff_out, p->D32);
+          p->Y32 + yoff_out, p->D32, 0);
     }
     p->launches += 2;
     return check_launch(p, "series_term (stored blocks)");
@@ -2145,20 +2197,20 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
         k_series_group<double><<<gb, G5_THREADS, g5_smem_bytes<double>(), p->stream>>>(
             p->state, a64, p->slot_len, p->sell_off, p->sell_cam, p->sell_m64, p->P64[0],
             p->P64[1], p->Y64 + yoff_in, point_data<double>(p, 0), point_data<double>(p, 1), tb,
-            p->row_mask, p->row_base, part, part + nit * 12);
+            p->row_mask, p->row_base, part, part + nit * 12, term, eps, p->camnorm, p->nc);
       k_series_apply<double><<<p->nc, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam5_off, p->cam5_idx, p->cam5_ndirect, part, p->G64, p->camnorm,
-          p->done_ticket, p->Y64 + yoff_out, p->D64);
+          p->done_ticket, p->Y64 + yoff_out, p->D64, gb > 0 ? 1 : 0);
     } else {
       float* part = static_cast<float*>(p->part5);
       if (gb > 0)
         k_series_group<float><<<gb, G5_THREADS, g5_smem_bytes<float>(), p->stream>>>(
             p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
             p->camP32[1], p->Y32 + yoff_in, point_data<float>(p, 0), point_data<float>(p, 1), tb,
-            p->row_mask, p->row_base, part, part + nit * 12);
+            p->row_mask, p->row_base, part, part + nit * 12, term, eps, p->camnorm, p->nc);
       k_series_apply<float><<<p->nc, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam5_off, p->cam5_idx, p->cam5_ndirect, part, p->G32, p->camnorm,
-          p->done_ticket, p->Y32 + yoff_out, p->D32);
+          p->done_ticket, p->Y32 + yoff_out, p->D32, gb > 0 ? 1 : 0);
     }
     p->launches += 1 + (gb > 0);
     return check_launch(p, "series_term (groups)");
@@ -2198,7 +2250,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
       k_series_apply<double><<<p->nc, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam_part3_off, p->cam_part3_idx, nullptr,
           static_cast<const double*>(p->part3), p->G64, p->camnorm, p->done_ticket,
-          p->Y64 + yoff_out, p->D64);
+          p->Y64 + yoff_out, p->D64, 0);
     } else {
       if (gg > 0)
         k_series_rows<float><<<gg, BLOCK, 0, p->stream>>>(
@@ -2209,7 +2261,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
       k_series_apply<float><<<p->nc, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam_part3_off, p->cam_part3_idx, nullptr,
           static_cast<const float*>(p->part3), p->G32, p->camnorm, p->done_ticket,
-          p->Y32 + yoff_out, p->D32);
+          p->Y32 + yoff_out, p->D32, 0);
     }
     p->launches += gg > 0 ? 2 : 1;
     return check_launch(p, "series_term (grouped)");
@@ -2224,7 +2276,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
       k_series_apply<double><<<ga, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx, nullptr,
           static_cast<const double*>(p->part_run), p->G64, p->camnorm, p->done_ticket, p->Y64 + yoff_out,
-          p->D64);
+          p->D64, 0);
     } else {
       k_series_fused<float, void><<<p->n_slot_blocks, BLOCK, 0, p->stream>>>(
           p->state, a32, p->slot_len, p->sell_off, p->sell_cam, p->sell_m32, p->camP32[0],
@@ -2233,7 +2285,7 @@ povar_status launch_series_term(Problem* p, int precision, double eta, int term,
       k_series_apply<float><<<ga, 128, 0, p->stream>>>(
           p->state, term, eps, p->nc, p->cam_part_off, p->cam_part_idx, nullptr,
           static_cast<const float*>(p->part_run), p->G32, p->camnorm, p->done_ticket, p->Y32 + yoff_out,
-          p->D32);
+          p->D32, 0);
     }
     p->launches += 2;
     return check_launch(p, "series_term (fused)");
@@ -2371,11 +2423,11 @@ povar_status launch_series_apply(Problem* p, int precision, int term, double eps
   if (precision == POVAR_FP64)
     k_series_apply<double><<<p->nc, 128, 0, p->stream>>>(
         p->state, term, eps, p->nc, off, idx, nullptr, static_cast<const double*>(part), p->G64,
-        p->camnorm, p->done_ticket, p->Y64 + yoff_out, p->D64);
+        p->camnorm, p->done_ticket, p->Y64 + yoff_out, p->D64, 0);
   else
     k_series_apply<float><<<p->nc, 128, 0, p->stream>>>(
         p->state, term, eps, p->nc, off, idx, nullptr, static_cast<const float*>(part), p->G32,
-        p->camnorm, p->done_ticket, p->Y32 + yoff_out, p->D32);
+        p->camnorm, p->done_ticket, p->Y32 + yoff_out, p->D32, 0);
   ++p->launches;
   return check_launch(p, "series_apply");
 }
