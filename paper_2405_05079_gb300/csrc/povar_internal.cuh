@@ -42,13 +42,14 @@ constexpr int BLOCK = 256;       // threads per block for slot kernels
 // the slot kernels.
 constexpr int GROUP = 1;
 // Group schedule (5): at most G5_SLICES slices, G5_ROWS rows and G5_MROWS
-// slice rows (staged measurement rows) per group (one block each, four
-// blocks per SM in FP32), work items of at most G5_ITEM slices of one row.
+// slice rows (staged measurement rows) per group (one block each, three
+// blocks per SM in FP32: 71 KB of shared memory each), work items of at
+// most G5_ITEM slices of one row.
 constexpr int G5_THREADS = 256;
-constexpr int G5_SLICES = 16;
+constexpr int G5_SLICES = 20;
 constexpr int G5_ROWS = 64;
-constexpr int G5_MROWS = 88;
-constexpr int G5_ITEM = 16;
+constexpr int G5_MROWS = 128;
+constexpr int G5_ITEM = 20;
 // Blocks of the final cost and predicted-decrease sums (each block adds a
 // fixed range, the last block to finish adds the block sums in order).
 constexpr int FIN_BLOCKS = 64;

@@ -1515,7 +1515,7 @@ __device__ __forceinline__ void series_halt_check(DeviceState* __restrict__ st, 
 // groups. part holds the item partials at their positions in the per-camera
 // lists; the run partials of the slices outside groups go to part_run.
 template <typename T>
-__global__ void __launch_bounds__(G5_THREADS, sizeof(T) == 4 ? 1024 / G5_THREADS : 1)
+__global__ void __launch_bounds__(G5_THREADS, sizeof(T) == 4 ? 3 : 1)
 k_series_group(DeviceState* __restrict__ st, T a, const uint32_t* __restrict__ slot_len,
                const uint32_t* __restrict__ sell_off, const int32_t* __restrict__ sell_cam,
                const typename Vt<T>::m2* __restrict__ sell_m, const T* __restrict__ camPa,
