@@ -258,6 +258,21 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
     bpl = bp64[(size_t)i * 12 + lane];
   }
   __syncwarp();
+  // The 78 entries (r, j), j <= r, of a 12 x 12 lower triangle ordered by
+  // column j descending (rows ascending within a column): the entries right
+  // of column k are the first (11 - k)(12 - k) / 2. Lane l owns entries l,
+  // l + 32 and l + 64 (< 78), so the triangular loops below run on all 32
+  // lanes; every entry keeps its own operations in their original order.
+  int tr[3], tj[3];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    const int e = lane + 32 * u;
+    int m = 0;
+    while ((m + 1) * (m + 2) / 2 <= e) ++m;   // e in column 11 - m
+    tj[u] = 11 - m;
+    tr[u] = tj[u] + (e - m * (m + 1) / 2);
+    if (e >= 78) tj[u] = -1;                  // no entry
+  }
   // Damped block and its Cholesky factor. If rounding leaves the block not
   // numerically positive definite (an FP32-accumulated U with a huge
   // condition number), the damping of this camera is raised -- to at least
@@ -319,8 +334,10 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
       __syncwarp();
       if (lane > k && lane < 12) A[lane][k] *= inv[k];
       __syncwarp();
-      if (lane > k && lane < 12)
-        for (int j = k + 1; j <= lane; ++j) A[lane][j] -= A[lane][k] * A[j][k];
+      // trailing update A[r][j] -= A[r][k] A[j][k] for k < j <= r
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        if (tj[u] > k) A[tr[u]][tj[u]] -= A[tr[u]][k] * A[tj[u]][k];
       __syncwarp();
     }
     bad = __any_sync(0xffffffffu, lbad);
@@ -343,15 +360,17 @@ k_camera_prepare(DeviceState* __restrict__ st, double eta, int manifold, int nc,
     }
   }
   __syncwarp();
-  // A^-1 = L^-T L^-1, minus p^p^T on the sphere; x0 = -G b_p
+  // A^-1 = L^-T L^-1 (entry (r, j), j <= r: the sum over k >= r of
+  // L^-1[k][r] L^-1[k][j], mirrored), minus p^p^T on the sphere; x0 = -G b_p
   double x0 = 0.0;
-  if (lane < 12) {
-    for (int q = 0; q < 12; ++q) {
-      const int k0 = lane > q ? lane : q;
-      double s = 0.0;
-      for (int k = k0; k < 12; ++k) s += L[k][lane] * L[k][q];
-      A[lane][q] = s;  // row `lane` is only read back by this lane below
-    }
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    if (tj[u] < 0) continue;
+    const int r = tr[u], j = tj[u];
+    double s = 0.0;
+    for (int k = r; k < 12; ++k) s += L[k][r] * L[k][j];
+    A[r][j] = s;
+    A[j][r] = s;
   }
   __syncwarp();
   for (int q = 0; q < 12; ++q) {
