@@ -229,14 +229,26 @@ def landmark_flops_per_launch(n_obs: int, n_points: int) -> int:
     return 98 * n_obs + 60 * n_points
 
 
+def code_hash(path: str) -> str:
+    """sha256 prefix of a C++/CUDA source with its comments and blank lines
+    removed and each line stripped, so that an edit of comments alone keeps
+    the hash of the code that a capture measured."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    lines = [ln.strip() for ln in text.splitlines()]
+    code = "\n".join(ln for ln in lines if ln)
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
+
+
 def ncu_traffic(kernel_file: str, key: str):
     """Per-launch DRAM bytes recorded in profiles/ncu_traffic.txt for a kernel
-    source (one ncu capture), or None when the source changed since."""
+    source (one ncu capture), or None when its code changed since."""
     prof = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     src = os.path.join(ROOT, "paper_2405_05079_gb300", "csrc", kernel_file)
     try:
         text = open(prof).read()
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = code_hash(src)
     except OSError:
         return None
     m = re.search(rf"^{key}\s+sha={h}\s+bytes_per_launch=(\d+)", text, re.M)

@@ -109,7 +109,8 @@ enum { POVAR_BF16_FP32_TERMS = 6 };  /* POVAR_MIXED_BF16: terms 1..5 in FP32 */
  *             rows are all warp-uniform and see the same camera at each row
  *             index (tracks over the same consecutive cameras): one block
  *             per group stages the rows' cameras and the landmarks' s_j in
- *             shared memory and reduces once per (row, up to 8 slices);
+ *             shared memory and reduces once per row (at most 20 slices
+ *             and 128 slice rows per group);
  *             other slices run the fused pass of 1; -1 = autotuned (see
  *             povar_get_tuning). All schedules compute the same series (up
  *             to rounding order). */

@@ -1538,10 +1538,12 @@ k_series_group(DeviceState* __restrict__ st, T a, const uint32_t* __restrict__ s
   }
 }
 
-// Per camera (one warp): z_i = sum of its partials in index order, then the
-// camera update. With the threshold rule, each block writes the sum of its
-// eight cameras' norms and the last block (atomic ticket) adds the block sums
-// in block order and sets the stop flag.
+// Per camera (k_series_apply, one block of 4 warps): z_i = sum of its
+// partials in list order, then the camera update. With the threshold rule,
+// the block that finishes last (atomic ticket) adds all cameras' norms and
+// sets the stop flag (stop_check); in the group schedule the next term's
+// group launch adds them instead (series_halt_check) and the block only
+// stores its camera's norms.
 template <typename T> struct Rec12;
 template <> struct Rec12<float> {
   static __device__ __forceinline__ void add(const float* src, float acc[12]) {

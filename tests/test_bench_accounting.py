@@ -30,3 +30,14 @@ def test_landmark_work_per_launch():
 def test_traffic_lookup_refuses_unknown_keys_and_sources():
     assert bench.ncu_traffic("series.cu", "no_such_kernel") is None
     assert bench.ncu_traffic("no_such_file.cu", "series_product_s1") is None
+
+
+def test_code_hash_ignores_comments_but_not_code(tmp_path):
+    base = "int f(int a) {\n  return a + 1;  // one more\n}\n"
+    p = tmp_path / "k.cu"
+    p.write_text(base)
+    h = bench.code_hash(str(p))
+    p.write_text("/* a kernel\n   note */\nint f(int a) {\n\n    return a + 1;   // another note\n}\n")
+    assert bench.code_hash(str(p)) == h          # comments, blank lines, indentation
+    p.write_text(base.replace("a + 1", "a + 2"))
+    assert bench.code_hash(str(p)) != h          # a change of code
