@@ -374,7 +374,8 @@ povar_status povar_get_profile(povar_problem* p, double* ms_out, int64_t* steps_
 
 /* Series-schedule autotuner. The first povar_solve with params->schedule
  * = -1 times every schedule (0 .. POVAR_NSCHEDULES-1) on the live state
- * with CUDA events (one warm-up term, then three timed terms, two rounds)
+ * with CUDA events (one warm-up term, then three timed terms; a second
+ * round re-times the schedules within 15% of the first round's fastest)
  * and keeps the fastest for that precision; the per-step build of the
  * stored blocks of schedule 4 is timed too and charged to that schedule
  * spread over the m - 1 terms of a step. Later solves and povar_step with

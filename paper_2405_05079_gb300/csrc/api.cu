@@ -377,8 +377,9 @@ void sample_graph_profile(Problem* p, bool last_step_worked) {
 
 // Series-schedule autotuner: on the live state of the first step, run every
 // schedule for one untimed term (caches and instruction caches warm) and then
-// three timed terms, in two rounds over the schedules, and keep the schedule
-// with the smallest time per term for this precision. The stored schedule
+// three timed terms; a second round re-times the schedules within 15% of the
+// first round's fastest; keep the schedule with the smallest time per term
+// for this precision. The stored schedule
 // (4) also pays its per-step block build, timed before its terms and spread
 // over the m - 1 terms of a step. The damped blocks are re-prepared
 // afterwards, so the solve continues from exactly the state it would have
@@ -397,7 +398,12 @@ povar_status autotune_schedule(Problem* p, const povar_params* q) {
   float best_ms = 1e30f;
   for (int sched = 0; sched < POVAR_NSCHEDULES; ++sched) p->tune_ms[prec][sched] = 1e30f;
   for (int round = 0; round < 2 && s == POVAR_OK; ++round) {
+    float lead_ms = 1e30f;
+    for (int sched = 0; sched < POVAR_NSCHEDULES; ++sched)
+      lead_ms = std::min(lead_ms, p->tune_ms[prec][sched]);
     for (int sched = 0; sched < POVAR_NSCHEDULES; ++sched) {
+      // second round: only the schedules that can still win
+      if (round > 0 && !(p->tune_ms[prec][sched] <= 1.15f * lead_ms)) continue;
       float build_ms = 0.f;
       if (sched == 4) {
         if ((s = ensure_blocks(p, block_kind(q->precision))) != POVAR_OK) break;
