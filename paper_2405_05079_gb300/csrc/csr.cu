@@ -7,7 +7,6 @@
 // match/ballot and a per-digit running count, which keeps it stable.
 #include "povar_internal.cuh"
 
-#include <unordered_map>
 
 #include <algorithm>
 
@@ -894,14 +893,17 @@ povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
   POVAR_COPY(rbase.data(), p->row_base, rbase.size(), cudaMemcpyDeviceToHost);
   POVAR_COPY(poff.data(), p->cam_part_off, poff.size(), cudaMemcpyDeviceToHost);
   POVAR_COPY(pidx.data(), p->cam_part_idx, pidx.size(), cudaMemcpyDeviceToHost);
+  // groups as fixed-capacity records (no allocation per group); open[c] is
+  // the group last opened for first-row camera c
   struct Grp {
-    std::vector<uint32_t> sl;
-    std::vector<int32_t> cam;
-    uint32_t rows = 0;   // sum of the slices' widths (staged measurement rows)
+    uint32_t ns = 0, nr = 0, rows = 0;   // slices, rows, staged measurement rows
+    uint32_t sl[G5_SLICES];
+    int32_t cam[G5_ROWS];
   };
   std::vector<Grp> groups;
+  groups.reserve((size_t)nsl / 4 + 16);
   std::vector<uint32_t> rest;
-  std::unordered_map<int32_t, int> open;   // first-row camera -> open group
+  std::vector<int> open((size_t)p->nc, -1);
   for (int sidx = 0; sidx < nsl; ++sidx) {
     const uint32_t r0 = off[sidx] / SLICE, w = (off[sidx + 1] - off[sidx]) / SLICE;
     bool uni = w > 0 && w <= (uint32_t)G5_ROWS && w <= (uint32_t)G5_MROWS;
@@ -911,40 +913,57 @@ povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
       continue;
     }
     const int32_t key = rcam[r0];
-    auto it = open.find(key);
-    int gi = -1;
-    if (it != open.end()) {
-      Grp& g = groups[(size_t)it->second];
-      bool ok = g.sl.size() < (size_t)G5_SLICES && g.rows + w <= (uint32_t)G5_MROWS;
-      const uint32_t kk = std::min<uint32_t>(w, (uint32_t)g.cam.size());
+    int gi = open[(size_t)key];
+    if (gi >= 0) {
+      const Grp& g = groups[(size_t)gi];
+      bool ok = g.ns < (uint32_t)G5_SLICES && g.rows + w <= (uint32_t)G5_MROWS;
+      const uint32_t kk = std::min<uint32_t>(w, g.nr);
       for (uint32_t k = 0; ok && k < kk; ++k) ok = g.cam[k] == rcam[r0 + k];
-      if (ok) gi = it->second;
+      if (!ok) gi = -1;
     }
     if (gi < 0) {
       gi = (int)groups.size();
       groups.emplace_back();
-      open[key] = gi;
+      open[(size_t)key] = gi;
     }
     Grp& g = groups[(size_t)gi];
-    g.sl.push_back((uint32_t)sidx);
+    g.sl[g.ns++] = (uint32_t)sidx;
     g.rows += w;
-    for (uint32_t k = (uint32_t)g.cam.size(); k < w; ++k) g.cam.push_back(rcam[r0 + k]);
+    for (uint32_t k = g.nr; k < w; ++k) g.cam[g.nr++] = rcam[r0 + k];
   }
   // flat tables; items: for row k the slices that reach it (a prefix of the
-  // group, widest first) in ranges of at most G5_ITEM
-  std::vector<uint32_t> goff(1, 0), gsl, roff(1, 0), ioff(1, 0), items, sinfo;
-  std::vector<int32_t> rowcam, ghdr;
-  std::vector<int32_t> item_cam;
+  // group, widest first) in ranges of at most G5_ITEM slices
+  const size_t ngr = groups.size();
+  size_t nrow_tot = 0, nitem_tot = 0;
+  for (const Grp& g : groups) {
+    nrow_tot += g.nr;
+    nitem_tot += (size_t)g.nr * ((g.ns + G5_ITEM - 1) / G5_ITEM);
+  }
+  std::vector<uint32_t> goff, gsl, roff, ioff, items, sinfo;
+  std::vector<int32_t> rowcam, ghdr, item_cam;
+  goff.reserve(ngr + 1);
+  roff.reserve(ngr + 1);
+  ioff.reserve(ngr + 1);
+  ghdr.reserve(2 * ngr);
+  gsl.reserve((size_t)nsl);
+  sinfo.reserve(4 * (size_t)G5_SLICES * ngr);
+  rowcam.reserve(nrow_tot);
+  items.reserve(nitem_tot);
+  item_cam.reserve(nitem_tot);
+  goff.push_back(0);
+  roff.push_back(0);
+  ioff.push_back(0);
   std::vector<char> grouped_part((size_t)p->npart, 0);
   int64_t g_obs_rows = 0;
   for (const Grp& g : groups) {
-    std::vector<uint32_t> width;
+    uint32_t width[G5_SLICES];
     uint32_t mrow = 0;
     const size_t sbase = sinfo.size();
-    for (uint32_t sidx : g.sl) {
+    for (uint32_t j = 0; j < g.ns; ++j) {
+      const uint32_t sidx = g.sl[j];
       gsl.push_back(sidx);
       const uint32_t w = (off[sidx + 1] - off[sidx]) / SLICE;
-      width.push_back(w);
+      width[j] = w;
       sinfo.insert(sinfo.end(), {sidx, off[sidx], w, mrow});
       mrow += w;
       const uint32_t r0 = off[sidx] / SLICE;
@@ -953,16 +972,18 @@ povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
     }
     sinfo.resize(sbase + 4 * (size_t)G5_SLICES, 0u);   // G5_SLICES entries per group
     goff.push_back((uint32_t)gsl.size());
-    bool consecutive = !g.cam.empty();
-    for (size_t k = 1; consecutive && k < g.cam.size(); ++k)
+    bool consecutive = g.nr > 0;
+    for (uint32_t k = 1; consecutive && k < g.nr; ++k)
       consecutive = g.cam[k] == g.cam[0] + (int32_t)k;
     ghdr.push_back((int32_t)mrow);
     ghdr.push_back(consecutive ? g.cam[0] : -1);
-    for (int32_t c : g.cam) rowcam.push_back(c);
+    rowcam.insert(rowcam.end(), g.cam, g.cam + g.nr);
     roff.push_back((uint32_t)rowcam.size());
-    for (uint32_t k = 0; k < (uint32_t)g.cam.size(); ++k) {
-      uint32_t n = 0;
-      while (n < width.size() && width[n] > k) ++n;
+    // row k is reached by the slices of width > k: a prefix, as the widths
+    // do not increase within a group
+    uint32_t n = g.ns;
+    for (uint32_t k = 0; k < g.nr; ++k) {
+      while (n > 0 && width[n - 1] <= k) --n;
       for (uint32_t j0 = 0; j0 < n; j0 += G5_ITEM) {
         const uint32_t j1 = std::min<uint32_t>(n, j0 + G5_ITEM);
         items.push_back((k << 16) | (j0 << 8) | j1);
@@ -972,29 +993,33 @@ povar_status build_groups5(Problem* p, const int32_t* d_rcam) {
     ioff.push_back((uint32_t)items.size());
   }
   const int64_t nitems = (int64_t)items.size();
-  // per camera: its items in item order, then its remaining run partials.
-  // An item's partial is written at its list position (idest), so a list
-  // entry of an item indexes itself; run partials follow all lists.
-  std::vector<uint32_t> c5off((size_t)p->nc + 1, 0), c5idx, c5nd((size_t)p->nc, 0),
+  // per camera: its items in item order, then its remaining run partials
+  // (a counting sort by camera). An item's partial is written at its list
+  // position (idest), so a list entry of an item indexes itself; run
+  // partials follow all lists.
+  std::vector<uint32_t> c5off((size_t)p->nc + 1, 0), c5nd((size_t)p->nc, 0),
       idest((size_t)nitems);
+  for (int64_t q = 0; q < nitems; ++q) ++c5nd[(size_t)item_cam[(size_t)q]];
   int64_t nlist = nitems;
-  for (int64_t e = 0; e < p->npart; ++e) nlist += grouped_part[(size_t)e] ? 0 : 1;
-  {
-    std::vector<std::vector<uint32_t>> per((size_t)p->nc);
-    for (int64_t q = 0; q < nitems; ++q) per[(size_t)item_cam[(size_t)q]].push_back((uint32_t)q);
-    for (int c = 0; c < p->nc; ++c) {
-      for (uint32_t q : per[(size_t)c]) {
-        idest[q] = (uint32_t)c5idx.size();
-        c5idx.push_back(idest[q]);
-      }
-      c5nd[(size_t)c] = (uint32_t)per[(size_t)c].size();
-      for (uint32_t e = poff[c]; e < poff[c + 1]; ++e)
-        if (!grouped_part[pidx[e]]) c5idx.push_back((uint32_t)nlist + pidx[e]);
-      c5off[(size_t)c + 1] = (uint32_t)c5idx.size();
-    }
+  for (int c = 0; c < p->nc; ++c) {
+    uint32_t nrun = 0;
+    for (uint32_t e = poff[c]; e < poff[c + 1]; ++e) nrun += grouped_part[pidx[e]] ? 0 : 1;
+    nlist += nrun;
+    c5off[(size_t)c + 1] = c5off[(size_t)c] + c5nd[(size_t)c] + nrun;
   }
-  if ((int64_t)c5idx.size() != nlist || nlist + p->npart >= ((int64_t)1 << 32))
+  if (nlist + p->npart >= ((int64_t)1 << 32))
     return fail(p, POVAR_EINVAL, "group schedule: partial list size");
+  std::vector<uint32_t> c5idx((size_t)nlist), cursor(c5off.begin(), c5off.end() - 1);
+  for (int64_t q = 0; q < nitems; ++q) {
+    const uint32_t d = cursor[(size_t)item_cam[(size_t)q]]++;
+    idest[(size_t)q] = d;
+    c5idx[d] = d;
+  }
+  for (int c = 0; c < p->nc; ++c) {
+    uint32_t d = cursor[(size_t)c];
+    for (uint32_t e = poff[c]; e < poff[c + 1]; ++e)
+      if (!grouped_part[pidx[e]]) c5idx[d++] = (uint32_t)nlist + pidx[e];
+  }
   p->g5_ngroups = (int32_t)groups.size();
   p->g5_nrest = (int32_t)rest.size();
   p->g5_nitems = nitems;
